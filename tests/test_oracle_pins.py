@@ -1,0 +1,278 @@
+"""Pins of the CPU oracle against facts fixed by the mathematics and the paper.
+
+None of these re-types the oracle's own formulas: each checks the oracle
+against a closed form, an exact rational computation, a library routine, an
+invariant or the paper's own statements (Section 3, eq. (cholesky), eq.
+(iterref), Algorithms 1 and 2, Fig. 3b, Section 4).
+"""
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+U64 = 2.0 ** -53
+
+
+# --------------------------------------------------------------------------
+# Cholesky factor (Section 3.1, eq. (cholesky)): closed forms
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 2, 5, 17, 64])
+def test_potrf_min_matrix_closed_form(n):
+    # A_ij = min(i, j) (1-based) has R_ij = 1 for all i <= j.
+    i = np.arange(1, n + 1)
+    A = np.minimum(i[:, None], i[None, :]).astype(float)
+    R = oracle.potrf(A)
+    assert np.array_equal(R, np.triu(np.ones((n, n))))
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 50])
+def test_potrf_laplacian_closed_form(n):
+    # tridiag(-1, 2, -1): R_kk = sqrt((k+1)/k), R_{k,k+1} = -sqrt(k/(k+1)), k 1-based.
+    A = 2 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    R = oracle.potrf(A)
+    k = np.arange(1, n + 1)
+    np.testing.assert_allclose(np.diag(R), np.sqrt((k + 1) / k), rtol=4 * n * U64)
+    np.testing.assert_allclose(np.diag(R, 1), -np.sqrt(k[:-1] / (k[:-1] + 1)), rtol=4 * n * U64)
+    assert np.all(np.triu(R, 2) == 0) and np.all(np.tril(R, -1) == 0)
+
+
+def test_potrf_identity_and_diagonal():
+    assert np.array_equal(oracle.potrf(np.eye(7)), np.eye(7))
+    d = np.array([4.0, 9.0, 0.25, 2.0])
+    np.testing.assert_allclose(oracle.potrf(np.diag(d)), np.diag(np.sqrt(d)), rtol=0, atol=0)
+
+
+def test_potrf_reads_only_lower_triangle():
+    A = W.gram_shifted(40, seed=3)
+    B = A.copy()
+    B[np.triu_indices(40, 1)] = 1e300  # garbage above the diagonal
+    assert np.array_equal(oracle.potrf(A), oracle.potrf(B))
+
+
+@pytest.mark.parametrize("n", [33, 200])
+def test_potrf_backward_invariant(n):
+    A = W.gram_shifted(n, seed=1)
+    R = oracle.potrf(A)
+    rel = np.linalg.norm(R.T @ R - A) / np.linalg.norm(A)
+    assert rel <= 2 * n * U64
+    # agrees with LAPACK's factor (numpy: L lower with A = L L^T, so R = L^T)
+    L = np.linalg.cholesky(A)
+    np.testing.assert_allclose(R, L.T, rtol=0, atol=50 * n * U64 * np.abs(L).max())
+
+
+def test_potrf_not_spd_reports_column():
+    A = np.eye(5)
+    A[3, 3] = -1.0
+    with pytest.raises(ValueError) as e:
+        oracle.potrf(A)
+    assert e.value.args[1] == 4  # 1-based, LAPACK convention
+
+
+# --------------------------------------------------------------------------
+# Solve X = R^{-1} R^{-T} B: exact rationals and a planted solution
+# --------------------------------------------------------------------------
+def _exact_solve(A_int, b_int):
+    n = len(b_int)
+    M = [[Fraction(int(A_int[i][j])) for j in range(n)] + [Fraction(int(b_int[i]))] for i in range(n)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [a - f * b for a, b in zip(M[r], M[c])]
+    return [M[i][n] / M[i][i] for i in range(n)]
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (3, 1), (5, 2), (8, 3), (8, 4)])
+def test_solve_matches_exact_rational_elimination(n, seed):
+    g = np.random.default_rng(seed)
+    G = g.integers(-3, 4, size=(n, n))
+    A = G @ G.T + np.eye(n, dtype=np.int64)
+    b = g.integers(-5, 6, size=n)
+    x_exact = np.array([float(v) for v in _exact_solve(A.tolist(), b.tolist())])
+    x = oracle.solve(A.astype(float), b.astype(float)[:, None])[:, 0]
+    kappa = np.linalg.cond(A.astype(float))
+    assert np.max(np.abs(x - x_exact)) <= 8 * n * kappa * U64 * np.max(np.abs(x_exact))
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_solve_planted_solution_known_eigendecomposition(kappa):
+    n = 120
+    A, lam, V = W.householder_spectrum(n, kappa, k=8, seed=5)
+    # Q from its reflectors, built independently of the oracle
+    Q = np.eye(n)
+    for j in range(V.shape[1]):
+        v = V[:, j:j + 1]
+        Q = Q @ (np.eye(n) - 2 * v @ v.T)
+    x_true = W.gaussian_rhs(n, 3, 11)
+    b = Q @ (lam[:, None] * (Q.T @ x_true))
+    x = oracle.solve(A, b)
+    fwd = np.max(np.abs(x - x_true)) / np.max(np.abs(x_true))
+    assert fwd <= 10 * kappa * 1e-16 * n ** 0.5
+
+
+def test_berr_and_residual_hand_example():
+    A = np.array([[4.0, 1.0], [1.0, 3.0]])
+    x = np.array([[1.0], [2.0]])
+    b = np.array([[6.0], [7.5]])  # A x = [6, 7]
+    r = oracle.residual(A, b, x)
+    np.testing.assert_array_equal(r, [[0.0], [0.5]])
+    # ||r||_inf / (||A||_inf ||x||_inf) = 0.5 / (5 * 2)
+    assert oracle.berr(A, b, x) == pytest.approx(0.05, rel=0, abs=1e-17)
+    assert oracle.norm_inf(A) == 5.0
+
+
+# --------------------------------------------------------------------------
+# Conjugate gradients
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n", [2, 5, 8])
+def test_cg_terminates_in_n_steps(n):
+    g = np.random.default_rng(n)
+    Q, _ = np.linalg.qr(g.standard_normal((n, n)))
+    lam = np.linspace(1.0, 9.0, n)  # kappa <= 10
+    A = (Q * lam) @ Q.T
+    A = 0.5 * (A + A.T)
+    b = g.standard_normal((n, 1))
+    X, it, rr, ok = oracle.cg(A, b, tol_rel=1e-13, maxit=n)
+    assert ok and it[0] <= n
+    np.testing.assert_allclose(X, np.linalg.solve(A, b), rtol=1e-10, atol=1e-12)
+
+
+def test_cg_distinct_eigenvalues():
+    # a diagonal matrix with 3 distinct eigenvalues: exact in 3 steps
+    d = np.array([1.0, 1.0, 2.0, 2.0, 2.0, 5.0, 5.0, 1.0])
+    A = np.diag(d)
+    b = np.arange(1, 9, dtype=float)[:, None]
+    X, it, rr, ok = oracle.cg(A, b, tol_rel=1e-14, maxit=8)
+    assert ok and it[0] == 3
+    np.testing.assert_allclose(X[:, 0], b[:, 0] / d, rtol=1e-13)
+
+
+def test_cg_agrees_with_cholesky():
+    A = W.gram_shifted(300, seed=0, shift=0.1)
+    B = W.gaussian_rhs(300, 2, 4)
+    X, it, rr, ok = oracle.cg(A, B, tol_rel=1e-14)
+    assert ok
+    Xc = oracle.solve(A, B)
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(X - Xc)) <= 10 * kappa * 1e-14 * np.max(np.abs(Xc))
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 and eq. (iterref)
+# --------------------------------------------------------------------------
+def test_chol_ir_single_factor_reaches_double_accuracy():
+    n = 256
+    A = W.gram_shifted(n, seed=0, shift=0.1)
+    x_true = W.gaussian_rhs(n, 1, 7)
+    b = A @ x_true
+    Rt = oracle.potrf_f32(A)
+    X, it, err, ok = oracle.chol_ir(A, Rt, b, tol=1e-14)
+    assert ok and err[0] <= 1e-14
+    assert 1 <= it[0] <= 6
+    # the float64 factor needs no sweep at all
+    _, it0, _, ok0 = oracle.chol_ir_f64(A, oracle.potrf(A), b, tol=1e-14)
+    assert ok0 and it0[0] == 0
+
+
+def test_iterref_condition_planted_perturbation():
+    """eq. (iterref): the inner solve is (A + dA) z = r.  The error obeys
+    e' = (A + dA)^{-1} dA e, so refinement converges whenever
+    ||A^{-1} dA|| < 1/2 for any sign of dA, and for every ||A^{-1} dA|| < 1
+    when dA is positive semidefinite.  A negative dA with
+    1/2 < ||A^{-1} dA|| < 1 can diverge: the printed bound is read as
+    "less than one half" for indefinite perturbations."""
+    n = 80
+    A = W.gram_shifted(n, seed=2, shift=0.5)
+    b = W.gaussian_rhs(n, 1, 3)
+    Ainv = np.linalg.inv(A)
+    g = np.random.default_rng(9)
+    S = g.standard_normal((n, n))
+    S = 0.5 * (S + S.T)                      # indefinite
+    G = g.standard_normal((n, n))
+    P = G @ G.T / n                          # positive semidefinite
+    for E, target in [(S, 0.3), (S, 0.45), (P, 0.9)]:
+        dA = E * (target / np.linalg.norm(Ainv @ E, np.inf))
+        assert np.linalg.norm(Ainv @ dA, np.inf) == pytest.approx(target)
+        X, it, err, ok = oracle.chol_ir_f64(A, oracle.potrf(A + dA), b, tol=1e-14, maxit=2000)
+        assert ok, target
+    # sufficient, not necessary: dA = 3A gives e' = (3/4) e
+    X, it, err, ok = oracle.chol_ir_f64(A, oracle.potrf(4.0 * A), b, tol=1e-14, maxit=400)
+    assert ok
+    # dA = -0.6 A: ||A^{-1} dA|| = 0.6 < 1 yet e' = -1.5 e diverges
+    X, it, err, ok = oracle.chol_ir_f64(A, oracle.potrf(0.4 * A), b, tol=1e-14, maxit=60)
+    assert not ok
+
+
+def test_perturbed_factor_sweep_fig3b():
+    """Fig. 3b: a float64 factor perturbed by an upper-triangular E with
+    ||E||_2 / ||R||_2 = 10^gamma still converges for every gamma in
+    {-1, -3.25, -5.5, -7.75, -10}; the iteration count grows with gamma."""
+    n = 150
+    A = W.gram_shifted(n, seed=4, shift=1.0)
+    b = W.uniform_rhs(n, 1, 0)
+    R = oracle.potrf(A)
+    g = np.random.default_rng(12)
+    E0 = np.triu(g.standard_normal((n, n)))
+    E0 /= np.linalg.norm(E0, 2)
+    its = []
+    for gamma in [-10, -7.75, -5.5, -3.25, -1]:
+        Rp = R + (10.0 ** gamma) * np.linalg.norm(R, 2) * E0
+        X, it, err, ok = oracle.chol_ir_f64(A, Rp, b, tol=1e-14, maxit=500)
+        assert ok, gamma
+        its.append(int(it[0]))
+    assert its == sorted(its)
+    assert its[-1] > its[0]
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2 (nested reading) and Section 4's model covariance
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_model_covariance_is_spd(d):
+    A = W.model_covariance(300, d)
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A).min() > 0.0
+    oracle.potrf(A)  # no breakdown
+
+
+def test_cg_ir_paper_tolerance_and_decay_ordering():
+    """Section 4: tolerance 1e-5 on U[0,1] right-hand sides; stronger decay
+    (larger d) is easier for CG; the result is a solution of A x = b."""
+    n = 1500
+    lows = {}
+    for d in (1, 4):
+        A = W.model_covariance(n, d)
+        b = W.uniform_rhs(n, 1, 0)
+        X, lo, hi, fe, ok = oracle.cg_ir(A, b, tol=1e-5, crit="abs2", eta=0.0)
+        assert ok and fe[0] < 1e-5
+        assert np.linalg.norm(oracle.residual(A, b, X)) < 1e-5
+        lows[d] = int(lo[0])
+    assert lows[1] >= lows[4]
+
+
+def test_banded_cg_ir_equals_dense_counts_at_strong_decay():
+    """Section 4.1: at d = 4 the banded (bandwidth 33) inner solver needs the
+    same low/high iteration counts as the dense one (at n = 70000).  At this
+    small n the entries dropped from the band are relatively larger, so the
+    pin is a band: low counts within 15 %, high counts within one."""
+    n = 2000
+    A = W.model_covariance(n, 4)
+    b = W.uniform_rhs(n, 1, 0)
+    _, lo_d, hi_d, _, ok1 = oracle.cg_ir(A, b, tol=1e-5, crit="abs2", eta=0.0)
+    _, lo_b, hi_b, fe, ok2 = oracle.cg_ir(A, b, band=16, tol=1e-5, crit="abs2", eta=0.0)
+    assert ok1 and ok2
+    assert abs(int(lo_b[0]) - int(lo_d[0])) <= 0.15 * lo_d[0] and abs(int(hi_b[0]) - int(hi_d[0])) <= 1
+
+
+def test_cg_ir_relative_target_reaches_double_accuracy():
+    A = W.gram_shifted(400, seed=0, shift=0.1)
+    b = W.gaussian_rhs(400, 1, 1)
+    X, lo, hi, fe, ok = oracle.cg_ir(A, b, tol=1e-14, crit="rel", eta=1e-4)
+    assert ok
+    assert np.linalg.norm(oracle.residual(A, b, X)) <= 1e-14 * np.linalg.norm(b)
+    assert hi[0] >= 2  # single-precision inner matvecs cannot get there in one sweep
