@@ -1,0 +1,240 @@
+/*
+ * spd.h -- C ABI of libspd, a GB300 (sm_103a) solver for dense symmetric
+ * positive-definite systems  A X = B  (Section 3, eqs. (problemSingleRHS)
+ * and (problemMultipleRHS) of Klavik, Malossi, Bekas, Curioni, "Changing
+ * Computing Paradigms Towards Power Efficiency", arXiv:1405.4644).
+ *
+ * The library implements the two mixed-precision refinement schemes of
+ * Section 3: Cholesky with iterative refinement (Algorithm 1) and conjugate
+ * gradients with iterative refinement (Algorithm 2), plus batched and
+ * preconditioned variants.  Low-precision work (factorisation, triangular
+ * solves, CG matrix-vector products) runs in the precision the caller picks;
+ * residuals, solution updates, norms and convergence tests run in float64.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Memory   All matrix and vector arguments are DEVICE pointers unless the
+ *          name ends in _host.  They are float64, column-major, with a
+ *          leading dimension >= the row count.  A is symmetric and both
+ *          triangles must hold it: the factorisation reads only the lower
+ *          triangle (i >= j) and the float64 residual streams the whole
+ *          matrix.  Buffers belong to the caller; the library never frees
+ *          them.  The library owns its handle, factor objects and workspace,
+ *          released by the matching *_destroy call.
+ * Streams  Every call is ordered on the stream given to spd_create and
+ *          returns after that stream has drained (the report is filled on
+ *          the host), unless stated otherwise.
+ * Errors   Every call returns an spd_status; no exception or signal crosses
+ *          the ABI.  spd_last_error_string(h) describes the last failure on
+ *          a handle.  On SPD_ERR_NOT_SPD, report.info holds the 1-based
+ *          column of the first non-positive pivot (LAPACK potrf
+ *          convention).  On SPD_ERR_NO_CONVERGENCE, X holds the best iterate.
+ *          On SPD_ERR_TIMEOUT a bounded device wait gave up and the context
+ *          is still usable.  NaN or Inf in A gives SPD_ERR_ARG.
+ * Sizes    n, m >= 0 (n = 0 or m = 0 is a no-op returning SPD_OK).
+ *          int is 32-bit; n * lda must fit in 63 bits.
+ */
+#ifndef SPD_H
+#define SPD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spd_status {
+    SPD_OK = 0,
+    SPD_ERR_ARG = 1,            /* invalid argument or non-finite input        */
+    SPD_ERR_NOT_SPD = 2,        /* factorisation broke down (report.info)      */
+    SPD_ERR_NO_CONVERGENCE = 3, /* refinement / CG did not reach the tolerance */
+    SPD_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired          */
+    SPD_ERR_CUDA = 5,           /* a CUDA runtime call failed                  */
+    SPD_ERR_OOM = 6,            /* device allocation failed                    */
+    SPD_ERR_UNSUPPORTED = 7     /* precision / mode not available              */
+} spd_status;
+
+/* Precision of the low-precision work (Section 3.1, "~" quantities).
+ * FP64 is the plain baseline: the whole factorisation in float64.
+ * FP32 keeps the factor and its updates in float32 (SIMT).
+ * TF32/BF16/FP16/FP8 keep the factor in float32 but feed the trailing
+ * updates to the tensor cores with operands rounded (RNE) to that type and
+ * float32 accumulation; FP8 is OCP E4M3 with one power-of-two scale per
+ * 128-row tile.  AUTO picks per matrix (see spd_factor). */
+typedef enum spd_prec {
+    SPD_PREC_FP64 = 0,
+    SPD_PREC_FP32 = 1,
+    SPD_PREC_TF32 = 2,
+    SPD_PREC_BF16 = 3,
+    SPD_PREC_FP16 = 4,
+    SPD_PREC_FP8 = 5,
+    SPD_PREC_AUTO = 6
+} spd_prec;
+
+/* Stopping rules (Alg. 1 and Alg. 2 print ||r||_2 >= tolerance; the
+ * normwise backward error is the accuracy target of this library). */
+typedef enum spd_crit {
+    SPD_CRIT_BERR = 0, /* ||b - A x||_inf / (||A||_inf ||x||_inf) <= tol */
+    SPD_CRIT_REL2 = 1, /* ||b - A x||_2 <= tol * ||b||_2               */
+    SPD_CRIT_ABS2 = 2  /* ||b - A x||_2 <  tol   (as printed, Alg. 1/2)  */
+} spd_crit;
+
+/* Preconditioners for spd_cg. */
+typedef enum spd_precond {
+    SPD_PC_NONE = 0,   /* Algorithm 2 as printed                           */
+    SPD_PC_JACOBI = 1, /* M = diag(A)^{-1}                                  */
+    SPD_PC_FACTOR = 2  /* M = (R~^T R~)^{-1} from an spd_factor object      */
+} spd_precond;
+
+/* Arithmetic of the float64-accurate residual r = b - A x. */
+typedef enum spd_resid {
+    SPD_RESID_FP64 = 0 /* float64 fused multiply-adds */
+} spd_resid;
+
+/* Flags of spd_factor. */
+#define SPD_SCALE_DIAG 1u /* factor D^{-1/2} A D^{-1/2} (D = diag A); default */
+
+typedef struct spd_opts {
+    double tol;      /* stopping threshold (default 1e-14)                    */
+    int crit;        /* spd_crit (default SPD_CRIT_BERR)                      */
+    int maxit;       /* max refinement sweeps / outer CG steps (default 50)   */
+    int maxit_inner; /* spd_cg: max inner steps per outer step (default 2000) */
+    double eta;      /* spd_cg: inner stop at ||r_in|| <= eta ||r|| (1e-4)    */
+    int band;        /* spd_cg: half bandwidth of the inner matrix, -1 dense  */
+    int fallback;    /* spd_solve_ir: on stagnation switch to factor-
+                        preconditioned CG in float64 (default 1)              */
+    int resid;       /* spd_resid (default SPD_RESID_FP64)                    */
+    int polish;      /* spd_solve_ir: extra sweeps after a column first meets
+                        the rule, to bring its forward error to the float64
+                        floor (default 1)                                     */
+} spd_opts;
+
+typedef struct spd_report {
+    int status;      /* spd_status of the call                               */
+    int info;        /* SPD_ERR_NOT_SPD: 1-based failing column              */
+    int iters_low;   /* low-precision iterations (solves or inner CG steps)  */
+    int iters_high;  /* float64 residual evaluations after the first         */
+    int prec_used;   /* spd_prec actually used                               */
+    int fell_back;   /* 1 if the stagnation fallback ran                     */
+    double berr;     /* final max-over-columns normwise backward error       */
+    double rel_resid;/* final max-over-columns ||r||_2 / ||b||_2             */
+    double time_ms;  /* device time of the call (CUDA events)                */
+    double cond_est; /* spd_factor with AUTO: estimated 1-norm condition
+                        number of the scaled matrix (Hager's estimator), or 0 */
+} spd_report;
+
+typedef struct spd_handle spd_handle;
+typedef struct spd_factor_t spd_factor_t;
+
+/* ---- handle ------------------------------------------------------------ */
+/* Create a handle bound to the current CUDA device and `stream`
+ * (a cudaStream_t; NULL = the legacy default stream). */
+spd_status spd_create(spd_handle **h, void *stream);
+spd_status spd_destroy(spd_handle *h);
+/* Text of the last failure on h (static storage owned by h; never NULL). */
+const char *spd_last_error_string(const spd_handle *h);
+/* Fill *o with the defaults listed in spd_opts. */
+void spd_opts_default(spd_opts *o);
+
+/* ---- Algorithm 1, step 1: low-precision Cholesky --------------------------
+ * Factor A ~= R~^T R~ (Section 3.1, eq. (cholesky), Alg. 1 line 1) in
+ * precision `prec`, after the symmetric diagonal scaling D^{-1/2} A D^{-1/2}
+ * when flags has SPD_SCALE_DIAG.  Blocked right-looking Cholesky with
+ * recursive blocking: 128x128 diagonal-block factorisations, panel
+ * triangular solves, and trailing updates A22 -= L21 L21^T.
+ * A: n x n, lda >= n, read-only, lower triangle read.  On success *F owns
+ * the factor (release with spd_factor_destroy).  AUTO keeps the cheapest
+ * factor whose estimated ||A^{-1} dA|| keeps refinement convergent
+ * (eq. (iterref)): FP16 first;
+ * if its factor breaks down, or kappa_1 / sqrt(n) * 2^-11 > 1/4 with
+ * kappa_1 the 1-norm condition number of the scaled matrix estimated by
+ * Hager's method through the FP16 factor, FP32; if that breaks down, FP64.
+ * rep may be NULL. */
+spd_status spd_factor(spd_handle *h, int n, const double *A, int lda, int prec,
+                      unsigned flags, spd_factor_t **F, spd_report *rep);
+spd_status spd_factor_destroy(spd_factor_t *F);
+
+/* Order and precision of a factor (either output may be NULL). */
+spd_status spd_factor_info(const spd_factor_t *F, int *n, int *prec);
+
+/* Copy a factor out for inspection: L receives n rows of the working
+ * matrix, row-major with leading dimension ldl >= n (float32, or float64
+ * for SPD_PREC_FP64 factors); its lower triangle is R~^T of the scaled
+ * matrix diag(d) A diag(d), the upper triangle is scratch.  d receives the
+ * n scaling factors.  L and d may be host or device pointers (either may
+ * be NULL).  Synchronous. */
+spd_status spd_factor_copy(const spd_factor_t *F, void *L, int ldl, double *d);
+
+/* ---- Algorithm 1, lines 2-7: refinement --------------------------------
+ * Solve A X = B with the factor F: X = R~^{-1} R~^{-T} B (line 2), then
+ * repeat r = B - A X in float64 (lines 3, 7), Z = R~^{-1} R~^{-T} r in
+ * low precision (line 5), X += Z in float64 (line 6) until every column
+ * meets opts->crit/tol.  Converged columns are frozen.  When the error
+ * stagnates (two sweeps each shrinking it by less than half) and
+ * opts->fallback is set, the remaining columns continue with conjugate
+ * gradients on A in float64 preconditioned by F.
+ * B: n x m (ldb); X: n x m (ldx) output.  opts may be NULL (defaults). */
+spd_status spd_solve_ir(spd_handle *h, const spd_factor_t *F, int n, int m,
+                        const double *A, int lda, const double *B, int ldb,
+                        double *X, int ldx, const spd_opts *opts, spd_report *rep);
+
+/* Factor and refine in one call on HOST buffers: copies A and B to the
+ * device, runs spd_factor + spd_solve_ir, copies X back (column-major,
+ * lda/ldb/ldx >= n).  The device buffers are the library's. */
+spd_status spd_solve_ir_host(spd_handle *h, int n, int m, const double *A_host, int lda,
+                             const double *B_host, int ldb, double *X_host, int ldx,
+                             int prec, const spd_opts *opts, spd_report *rep);
+
+/* Z = R~^{-1} R~^{-T} R (Alg. 1 line 5): the two low-precision triangular
+ * solves with F, including the diagonal scaling.  R, Z: n x m. */
+spd_status spd_factor_solve(spd_handle *h, const spd_factor_t *F, int n, int m,
+                            const double *R, int ldr, double *Z, int ldz);
+
+/* R = B - A X in float64 (Alg. 1 lines 3/7, Alg. 2 line 2), plus per-column
+ * norms written to colnorms (device, 3*m float64, may be NULL):
+ * [||r_c||_inf, ||r_c||_2, ||x_c||_inf] for column c at 3c..3c+2. */
+spd_status spd_residual(spd_handle *h, int n, int m, const double *A, int lda,
+                        const double *B, int ldb, const double *X, int ldx,
+                        double *R, int ldr, double *colnorms);
+
+/* ---- Algorithm 2: CG with iterative refinement ---------------------------
+ * Outer ("high") steps: r = B - A X in float64, stop when opts->crit/tol
+ * holds.  Inner ("low") steps: Algorithm 2's loop on A e = r with the
+ * matrix-vector product z = A~ p taken with A~ = A stored in `matvec_prec`
+ * (SPD_PREC_FP32, SPD_PREC_BF16 or SPD_PREC_FP64) -- banded to
+ * |i - j| <= opts->band when band >= 0 (Section 4.1) -- and rho, alpha,
+ * beta and the vector updates in float64; then X += e.  beta is the
+ * Fletcher-Reeves quotient r'^T r' / rho.  pc selects the preconditioner;
+ * pc_data is the spd_factor_t* for SPD_PC_FACTOR, else NULL.  X starts
+ * from zero.  The m columns are independent CG runs sharing each pass
+ * over A~. */
+spd_status spd_cg(spd_handle *h, int n, int m, const double *A, int lda, int matvec_prec,
+                  int pc, const void *pc_data, const double *B, int ldb, double *X, int ldx,
+                  const spd_opts *opts, spd_report *rep);
+
+/* ---- phase timing ---------------------------------------------------------
+ * Code-phase markers in the spirit of the paper's instrumentation library
+ * (Section 2): when enabled, every launch of a hot-path kernel on h's
+ * stream is bracketed by CUDA events and tagged with its phase and its
+ * algorithmic work (flops and minimum HBM bytes).  Enabling clears the
+ * statistics; reading synchronises the stream and sums the event times. */
+typedef enum spd_phase {
+    SPD_PHASE_CONVERT = 0,  /* A0: scaling + conversion                  */
+    SPD_PHASE_LEAF = 1,     /* A1/A2: diagonal-block factor, panel solve */
+    SPD_PHASE_TRAILING = 2, /* A3: trailing updates (GEMM/SYRK)          */
+    SPD_PHASE_SOLVE = 3,    /* A4: low-precision triangular solves       */
+    SPD_PHASE_RESID = 4,    /* A5/C3: float64 residual / products        */
+    SPD_PHASE_MATVEC = 5,   /* C1: low-precision CG products             */
+    SPD_PHASE_VECTOR = 6,   /* A6/C2: float64 vector updates and dots    */
+    SPD_PHASE_COUNT = 7
+} spd_phase;
+
+spd_status spd_profile_enable(spd_handle *h, int on);
+/* launches, summed device milliseconds, flops and bytes of one phase. */
+spd_status spd_profile_read(spd_handle *h, int phase, int *launches, double *ms, double *flops,
+                            double *bytes);
+/* Total kernels launched through h since it was created (every phase). */
+spd_status spd_launch_count(const spd_handle *h, long long *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPD_H */

@@ -1,0 +1,299 @@
+"""paper_1405_4644_gb300 -- Python binding of libspd (include/spd.h).
+
+A thin ctypes layer: every function here marshals torch tensors (device
+memory) or numpy arrays (host memory) into the C ABI of the same name and
+returns what it returns.  All arithmetic runs in libspd's CUDA kernels; if
+the library is missing or cannot load, importing ``lib()`` raises -- there is
+no fallback.
+
+Layout convention: matrices are column-major, as in the C ABI.  A symmetric
+C-contiguous (n, n) tensor is already its own column-major form.  An (n, m)
+right-hand-side block must have stride(0) == 1 (build it as
+``torch.empty(m, n).t()`` or use ``colmajor``); its leading dimension is
+stride(1).  One-dimensional vectors are taken as (n, 1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from .build import LIB as _LIB_PATH
+
+__all__ = [
+    "SPD_OK", "SPD_ERR_ARG", "SPD_ERR_NOT_SPD", "SPD_ERR_NO_CONVERGENCE", "SPD_ERR_TIMEOUT", "SPD_ERR_CUDA",
+    "SPD_ERR_OOM", "SPD_ERR_UNSUPPORTED", "PREC", "SPD_SCALE_DIAG", "SpdOpts", "SpdReport", "SpdError",
+    "lib", "colmajor", "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor",
+    "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
+    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count",
+]
+
+SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
+SPD_ERR_TIMEOUT, SPD_ERR_CUDA, SPD_ERR_OOM, SPD_ERR_UNSUPPORTED = 4, 5, 6, 7
+PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto": 6}
+PREC_NAME = {v: k for k, v in PREC.items()}
+CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
+PC = {"none": 0, "jacobi": 1, "factor": 2}
+SPD_SCALE_DIAG = 1
+
+# every symbol include/spd.h declares
+EXPORTED = [
+    "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
+    "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read",
+    "spd_launch_count",
+]
+
+
+class SpdOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("crit", C.c_int), ("maxit", C.c_int), ("maxit_inner", C.c_int),
+                ("eta", C.c_double), ("band", C.c_int), ("fallback", C.c_int), ("resid", C.c_int),
+                ("polish", C.c_int)]
+
+
+class SpdReport(C.Structure):
+    _fields_ = [("status", C.c_int), ("info", C.c_int), ("iters_low", C.c_int), ("iters_high", C.c_int),
+                ("prec_used", C.c_int), ("fell_back", C.c_int), ("berr", C.c_double), ("rel_resid", C.c_double),
+                ("time_ms", C.c_double), ("cond_est", C.c_double)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["prec_used"] = PREC_NAME.get(d["prec_used"], d["prec_used"])
+        return d
+
+
+class SpdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libspd status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libspd.so (built in-tree by ``build.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise SpdError(SPD_ERR_CUDA, f"libspd.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(_LIB_PATH)
+    P, I, D, U = C.c_void_p, C.c_int, C.c_double, C.c_uint
+    PP = C.POINTER(C.c_void_p)
+    R = C.POINTER(SpdReport)
+    O = C.POINTER(SpdOpts)
+    sig = {
+        "spd_create": (I, [PP, P]),
+        "spd_destroy": (I, [P]),
+        "spd_last_error_string": (C.c_char_p, [P]),
+        "spd_opts_default": (None, [O]),
+        "spd_factor": (I, [P, I, P, I, I, U, PP, R]),
+        "spd_factor_destroy": (I, [P]),
+        "spd_factor_info": (I, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "spd_factor_copy": (I, [P, P, I, P]),
+        "spd_solve_ir": (I, [P, P, I, I, P, I, P, I, P, I, O, R]),
+        "spd_solve_ir_host": (I, [P, I, I, P, I, P, I, P, I, I, O, R]),
+        "spd_factor_solve": (I, [P, P, I, I, P, I, P, I]),
+        "spd_residual": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
+        "spd_cg": (I, [P, I, I, P, I, I, I, P, P, I, P, I, O, R]),
+        "spd_profile_enable": (I, [P, I]),
+        "spd_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
+        "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def colmajor(t):
+    """(pointer, leading dimension, rows, cols) of a column-major matrix view."""
+    import torch
+    if t.dim() == 1:
+        return t.data_ptr(), max(t.shape[0], 1), t.shape[0], 1
+    n, m = t.shape
+    if m == 1 or n == 0:
+        return t.data_ptr(), max(t.stride(1) if m > 1 else n, 1), n, m
+    if t.stride(0) != 1:
+        raise ValueError("matrix must be column-major (stride(0) == 1)")
+    return t.data_ptr(), t.stride(1), n, m
+
+
+def _sym(A):
+    """Pointer and lda of a symmetric matrix given as a C- or F-contiguous tensor."""
+    n = A.shape[0]
+    if A.shape != (n, n):
+        raise ValueError("A must be square")
+    if A.is_contiguous():
+        return A.data_ptr(), max(A.stride(0), 1) if n > 1 else 1, n
+    if A.stride(0) == 1:
+        return A.data_ptr(), A.stride(1), n
+    raise ValueError("A must be contiguous (row- or column-major)")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, SpdOpts):
+        return C.byref(opts)
+    o = spd_opts_default()
+    for k, v in dict(opts).items():
+        if k == "crit" and isinstance(v, str):
+            v = CRIT[v]
+        setattr(o, k, v)
+    return C.byref(o)
+
+
+def _prec(p):
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, one function each
+# ---------------------------------------------------------------------------
+def spd_create(stream=None):
+    h = C.c_void_p()
+    st = lib().spd_create(C.byref(h), _stream_ptr(stream))
+    if st != SPD_OK:
+        raise SpdError(st, "spd_create failed")
+    return h
+
+
+def spd_destroy(h):
+    return lib().spd_destroy(h)
+
+
+def spd_last_error_string(h):
+    s = lib().spd_last_error_string(h)
+    return s.decode() if s else ""
+
+
+def spd_opts_default():
+    o = SpdOpts()
+    lib().spd_opts_default(C.byref(o))
+    return o
+
+
+def spd_factor(h, A, prec="fp32", flags=SPD_SCALE_DIAG):
+    """Returns (status, factor handle or None, SpdReport)."""
+    pA, lda, n = _sym(A)
+    F = C.c_void_p()
+    rep = SpdReport()
+    st = lib().spd_factor(h, n, pA, lda, _prec(prec), flags, C.byref(F), C.byref(rep))
+    return st, (F if st == SPD_OK else None), rep
+
+
+def spd_factor_destroy(F):
+    return lib().spd_factor_destroy(F)
+
+
+def spd_factor_info(F):
+    """(n, precision code) of a factor."""
+    n, prec = C.c_int(), C.c_int()
+    st = lib().spd_factor_info(F, C.byref(n), C.byref(prec))
+    if st != SPD_OK:
+        raise SpdError(st, "spd_factor_info failed")
+    return n.value, prec.value
+
+
+def spd_factor_copy(F, L=None, d=None):
+    """Copy the factor's rows (row-major, ld = L.shape[1]) and scaling into
+    numpy arrays or torch tensors (host or device)."""
+    def ptr(a):
+        if a is None:
+            return None
+        return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+    ldl = L.shape[1] if L is not None else 0
+    return lib().spd_factor_copy(F, ptr(L), ldl, ptr(d))
+
+
+def spd_solve_ir(h, F, A, B, X, opts=None):
+    pA, lda, n = _sym(A)
+    pB, ldb, nb, m = colmajor(B)
+    pX, ldx, nx, mx = colmajor(X)
+    rep = SpdReport()
+    st = lib().spd_solve_ir(h, F, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), C.byref(rep))
+    return st, rep
+
+
+def spd_solve_ir_host(h, A, B, X, prec="fp32", opts=None):
+    """Host numpy buffers: A (n, n) symmetric, B and X (n, m) Fortran-ordered."""
+    import numpy as np
+    n = A.shape[0]
+    B2 = B if B.ndim == 2 else B[:, None]
+    X2 = X if X.ndim == 2 else X[:, None]
+    if A.dtype != np.float64 or not (A.flags.c_contiguous or A.flags.f_contiguous):
+        raise ValueError("A must be a contiguous float64 array")
+    for t in (B2, X2):
+        if t.dtype != np.float64 or not (t.flags.f_contiguous or (t.flags.c_contiguous and t.shape[1] == 1)):
+            raise ValueError("host buffers must be float64 and column-major")
+    m = B2.shape[1]
+    rep = SpdReport()
+    st = lib().spd_solve_ir_host(h, n, m, A.ctypes.data, n, B2.ctypes.data, B2.shape[0], X2.ctypes.data,
+                                 X2.shape[0], _prec(prec), _opts(opts), C.byref(rep))
+    return st, rep
+
+
+def spd_factor_solve(h, F, R, Z):
+    pR, ldr, n, m = colmajor(R)
+    pZ, ldz, _, _ = colmajor(Z)
+    return lib().spd_factor_solve(h, F, n, m, pR, ldr, pZ, ldz)
+
+
+def spd_residual(h, A, B, X, R, colnorms=None):
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = colmajor(B)
+    pX, ldx, _, _ = colmajor(X)
+    pR, ldr, _, _ = colmajor(R)
+    pc = colnorms.data_ptr() if colnorms is not None else None
+    return lib().spd_residual(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
+
+
+def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = colmajor(B)
+    pX, ldx, _, _ = colmajor(X)
+    rep = SpdReport()
+    pcv = PC[pc] if isinstance(pc, str) else int(pc)
+    st = lib().spd_cg(h, n, m, pA, lda, _prec(matvec_prec), pcv, pc_data, pB, ldb, pX, ldx, _opts(opts),
+                      C.byref(rep))
+    return st, rep
+
+
+PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector"]
+
+
+def spd_profile_enable(h, on=True):
+    return lib().spd_profile_enable(h, 1 if on else 0)
+
+
+def spd_profile_read(h, phase):
+    """dict(launches, ms, flops, bytes) of one phase (name or spd_phase code)."""
+    ph = PHASES.index(phase) if isinstance(phase, str) else int(phase)
+    n = C.c_int()
+    ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+    st = lib().spd_profile_read(h, ph, C.byref(n), C.byref(ms), C.byref(fl), C.byref(by))
+    if st != SPD_OK:
+        raise SpdError(st, "spd_profile_read failed")
+    return {"launches": n.value, "ms": ms.value, "flops": fl.value, "bytes": by.value}
+
+
+def spd_launch_count(h):
+    c = C.c_longlong()
+    st = lib().spd_launch_count(h, C.byref(c))
+    if st != SPD_OK:
+        raise SpdError(st, "spd_launch_count failed")
+    return c.value

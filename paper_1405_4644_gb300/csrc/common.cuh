@@ -1,0 +1,104 @@
+// common.cuh -- shared device helpers for libspd (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#define SPD_LEAF 128   // order of the diagonal blocks factored by one CTA
+#define SPD_SUB 32     // order of the warp-level sub-blocks inside a leaf
+#define SPD_MAXM 4096  // largest right-hand-side count per call
+
+// Device-side error word: bit flags raised by kernels, read by the host.
+enum : int {
+    SPD_DEV_NONFINITE = 1,   // NaN/Inf met in an input
+    SPD_DEV_BREAKDOWN = 2,   // non-positive pivot
+    SPD_DEV_TIMEOUT = 4,     // a bounded wait gave up
+    SPD_DEV_BADDIAG = 8      // non-positive diagonal entry (scaling impossible)
+};
+
+struct DevStatus {
+    int flags;      // OR of SPD_DEV_*
+    int info;       // smallest 1-based failing column (INT32_MAX = none)
+    int pad[2];
+};
+
+__device__ __forceinline__ void dev_raise(DevStatus* st, int flag) { atomicOr(&st->flags, flag); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Round-to-nearest-even conversions of a float32 value into the tensor-core
+// operand types.  tf32 is kept in a 32-bit container with the low 13
+// fraction bits cleared.
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) == 0x7f800000u) return x;  // Inf/NaN unchanged
+    uint32_t lsb = (u >> 13) & 1u;
+    u = (u + 0x0fffu + lsb) & 0xffffe000u;
+    return __uint_as_float(u);
+}
+
+template <typename OpT> struct OpConv;
+template <> struct OpConv<float> {  // tf32 operands
+    static __device__ __forceinline__ float cvt(float x) { return round_tf32(x); }
+};
+template <> struct OpConv<__nv_bfloat16> {
+    static __device__ __forceinline__ __nv_bfloat16 cvt(float x) { return __float2bfloat16_rn(x); }
+};
+template <> struct OpConv<__half> {
+    static __device__ __forceinline__ __half cvt(float x) { return __float2half_rn(x); }
+};
+template <> struct OpConv<__nv_fp8_e4m3> {
+    static __device__ __forceinline__ __nv_fp8_e4m3 cvt(float x) { return __nv_fp8_e4m3(x); }
+};
+
+// Description of the tensor-core operand mirror of the factor: the
+// finalised entries of L are also written here, rounded to the operand type,
+// so that trailing updates read them without a conversion pass.
+struct Mirror {
+    void* ptr;     // n x ld elements of the operand type (nullptr = no mirror)
+    long ld;       // leading dimension in elements (row-major)
+    int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3
+    const float* rowscale;  // fp8 only: per-128-row-tile power-of-two scale
+};
+
+__device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, float v) {
+    switch (m.kind) {
+        case 1: ((float*)m.ptr)[r * m.ld + c] = round_tf32(v); break;
+        case 2: ((__nv_bfloat16*)m.ptr)[r * m.ld + c] = __float2bfloat16_rn(v); break;
+        case 3: ((__half*)m.ptr)[r * m.ld + c] = __float2half_rn(v); break;
+        case 4: {
+            float s = m.rowscale ? m.rowscale[r / SPD_LEAF] : 1.0f;
+            ((__nv_fp8_e4m3*)m.ptr)[r * m.ld + c] = __nv_fp8_e4m3(v * s);
+            break;
+        }
+        default: break;
+    }
+}
+__device__ __forceinline__ void mirror_store(const Mirror&, long, long, double) {}
+
+template <typename T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+// Bounded spin-wait on a device flag (volatile load).  Returns false after
+// `limit` polls without seeing `want`.
+__device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int want, long limit) {
+    for (long it = 0; it < limit; ++it) {
+        if (*flag >= want) return true;
+        __nanosleep(64);
+    }
+    return false;
+}

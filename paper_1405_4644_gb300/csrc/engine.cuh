@@ -1,0 +1,168 @@
+// engine.cuh -- host-side engine of libspd: handle, workspace, launch helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cmath>
+#include <climits>
+#include <vector>
+#include <algorithm>
+#include "spd.h"
+#include "common.cuh"
+
+struct ProfRec {
+    cudaEvent_t a, b;
+    int phase;
+    double flops, bytes;
+};
+
+struct spd_handle {
+    cudaStream_t stream = nullptr;
+    bool prof_on = false;
+    long long launches = 0;             // kernels launched through this handle
+    std::vector<ProfRec> prof;          // recorded launches
+    std::vector<cudaEvent_t> ev_pool;   // free events
+    int device = 0;
+    int sms = 0;
+    char err[512] = {0};
+    DevStatus* dst = nullptr;   // device status word
+    void* pinned = nullptr;     // 4 KB pinned host scratch
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    void* ws = nullptr;         // grow-only device workspace
+    size_t ws_bytes = 0;
+};
+
+struct spd_factor_t {
+    spd_handle* h = nullptr;
+    int n = 0;
+    long ldw = 0;
+    int prec = SPD_PREC_FP32;
+    float* W = nullptr;        // float32 factor (row-major lower)
+    double* W64 = nullptr;     // float64 factor (SPD_PREC_FP64)
+    void* Wh = nullptr;        // tensor-core operand mirror
+    long ldh = 0;
+    double* d = nullptr;       // scaling
+    float* Dinv = nullptr;     // 32x32 diagonal sub-block inverses
+    double* Dinv64 = nullptr;
+    int nblk128 = 0;
+};
+
+static spd_status set_err(spd_handle* h, spd_status s, const char* fmt, ...) {
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+#define CUDA_TRY(h, call)                                                                        \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            if (e_ == cudaErrorMemoryAllocation) {                                               \
+                cudaGetLastError();                                                              \
+                return set_err(h, SPD_ERR_OOM, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                               __FILE__, __LINE__);                                              \
+            }                                                                                    \
+            return set_err(h, SPD_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
+                           __FILE__, __LINE__);                                                  \
+        }                                                                                        \
+    } while (0)
+
+#define LAUNCH_CHECK(h) CUDA_TRY(h, cudaGetLastError())
+
+static inline long round_up(long x, long a) { return (x + a - 1) / a * a; }
+static inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// Bump allocator over the handle's workspace.  size() first, then take().
+struct WsPlan {
+    size_t bytes = 0;
+    template <typename T> size_t add(size_t count) {
+        size_t off = bytes;
+        bytes += round_up((long)(count * sizeof(T)), 256);
+        return off;
+    }
+};
+
+static spd_status ws_reserve(spd_handle* h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return SPD_OK;
+    if (h->ws) {
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        CUDA_TRY(h, cudaFree(h->ws));
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = (size_t)round_up((long)bytes, 1 << 20);
+    CUDA_TRY(h, cudaMalloc(&h->ws, want));
+    h->ws_bytes = want;
+    return SPD_OK;
+}
+
+template <typename T> static inline T* ws_at(spd_handle* h, size_t off) {
+    return reinterpret_cast<T*>(static_cast<char*>(h->ws) + off);
+}
+
+static inline int grid_for(long work, int threads, int cap) {
+    long g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// Read and clear the device status word; map to spd_status.
+static spd_status check_dev_status(spd_handle* h, spd_report* rep, const char* what) {
+    DevStatus* hs = static_cast<DevStatus*>(h->pinned);
+    CUDA_TRY(h, cudaMemcpyAsync(hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    DevStatus s = *hs;
+    if (s.flags == 0) return SPD_OK;
+    DevStatus clear{0, INT_MAX, {0, 0}};
+    CUDA_TRY(h, cudaMemcpyAsync(h->dst, &clear, sizeof(DevStatus), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (rep) rep->info = (s.info == INT_MAX) ? 0 : s.info;
+    if (s.flags & SPD_DEV_NONFINITE) return set_err(h, SPD_ERR_ARG, "%s: non-finite entry in the input", what);
+    if (s.flags & SPD_DEV_BADDIAG)
+        return set_err(h, SPD_ERR_NOT_SPD, "%s: non-positive diagonal entry at %d", what, s.info);
+    if (s.flags & SPD_DEV_BREAKDOWN)
+        return set_err(h, SPD_ERR_NOT_SPD, "%s: non-positive pivot at column %d", what, s.info);
+    if (s.flags & SPD_DEV_TIMEOUT) return set_err(h, SPD_ERR_TIMEOUT, "%s: bounded device wait expired", what);
+    return set_err(h, SPD_ERR_CUDA, "%s: device status 0x%x", what, s.flags);
+}
+
+// RAII phase marker: records an event pair around the launches in scope.
+struct ProfScope {
+    spd_handle* h;
+    ProfRec r;
+    bool on;
+    static cudaEvent_t get_event(spd_handle* h) {
+        if (!h->ev_pool.empty()) {
+            cudaEvent_t e = h->ev_pool.back();
+            h->ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ProfScope(spd_handle* hh, int phase, double flops, double bytes) : h(hh), on(hh->prof_on) {
+        if (!on) return;
+        r.a = get_event(h);
+        r.b = get_event(h);
+        r.phase = phase;
+        r.flops = flops;
+        r.bytes = bytes;
+        cudaEventRecord(r.a, h->stream);
+    }
+    ~ProfScope() {
+        if (!on) return;
+        cudaEventRecord(r.b, h->stream);
+        h->prof.push_back(r);
+    }
+};
+
+// y <- (L L^T)^{-1} y for one float32 vector of the scaled system (no d
+// scaling); defined with the triangular-solve kernels.
+spd_status factor_apply_scaled_f32(spd_handle* h, const spd_factor_t* F, float* y);

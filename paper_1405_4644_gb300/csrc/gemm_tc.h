@@ -1,0 +1,17 @@
+// gemm_tc.h -- tensor-core (tcgen05) trailing update of the factorisation:
+//     W[r0+r][c0+c] -= sum_k Wh[r0+r][k0+k] * Wh[c0+c][k0+k]
+// with W float32 (row-major, ldw) and Wh the operand mirror (tf32 / bf16 /
+// fp16 / fp8 e4m3, row-major, ldh), float32 accumulation in tensor memory.
+#pragma once
+#include <cuda_runtime.h>
+#include "spd.h"
+#include "common.cuh"
+
+struct TcGemm;
+
+// Plan for one factor: tensor maps over Wh for the operand tiles.
+// Returns SPD_ERR_UNSUPPORTED when the operand kind has no tensor-core path.
+spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n);
+spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
+                       DevStatus* st);
+void tc_gemm_destroy(TcGemm* g);

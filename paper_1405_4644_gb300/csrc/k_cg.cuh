@@ -1,0 +1,299 @@
+// k_cg.cuh -- steps C1/C2 of Algorithm 2 (CG with iterative refinement):
+// the low-precision product z = A~ p (C1) and the float64 scalar/vector
+// work rho, alpha, x += alpha p, r -= alpha z, beta, p = r + beta p (C2).
+// m right-hand sides are m independent CG runs that share each pass over
+// A~.  Dots are reduced in a fixed order (per-CTA partials, then every
+// consumer CTA sums them in the same order), so runs are reproducible.
+#pragma once
+#include "common.cuh"
+
+#define MV_ROWS_PER_WARP 4
+#define MV_ROWS (8 * MV_ROWS_PER_WARP)
+#define MV_JCH 512
+
+__device__ __forceinline__ float4 ld4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+    uint2 u = *reinterpret_cast<const uint2*>(p);
+    __nv_bfloat162 a = *reinterpret_cast<__nv_bfloat162*>(&u.x);
+    __nv_bfloat162 b = *reinterpret_cast<__nv_bfloat162*>(&u.y);
+    float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// Q[:, c0:c0+mc] = A~ Pf (float32 products and sums), A~ row-major n x ldt
+// (ldt a multiple of 4, padding columns zero), Pf float32 n x m (ld n).
+// One warp per row group; lanes stride the row 4 elements at a time.
+template <typename T, int MC>
+static __global__ void __launch_bounds__(256) k_matvec_lp(const T* __restrict__ At, long ldt, int n,
+                                                   const float* __restrict__ Pf, int c0, int mc,
+                                                   double* __restrict__ Q, const int* __restrict__ done) {
+    __shared__ __align__(16) float ps[MC][MV_JCH];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int rbase = blockIdx.x * MV_ROWS + warp * MV_ROWS_PER_WARP;
+    float acc[MV_ROWS_PER_WARP][MC];
+#pragma unroll
+    for (int r = 0; r < MV_ROWS_PER_WARP; ++r)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) acc[r][c] = 0.f;
+    for (int jb = 0; jb < n; jb += MV_JCH) {
+        const int jn = min(MV_JCH, n - jb);
+        __syncthreads();
+        for (int e = tid; e < MC * MV_JCH; e += 256) {
+            int c = e / MV_JCH, jj = e % MV_JCH;
+            ps[c][jj] = (c < mc && jj < jn) ? Pf[(long)(c0 + c) * n + jb + jj] : 0.f;
+        }
+        __syncthreads();
+        const int jlim = (jn + 3) & ~3;  // padding columns of A~ are zero
+#pragma unroll
+        for (int r = 0; r < MV_ROWS_PER_WARP; ++r) {
+            const int row = rbase + r;
+            if (row >= n) break;
+            const T* arow = At + (long)row * ldt + jb;
+            for (int jj = lane * 4; jj < jlim; jj += 128) {
+                float4 a = ld4(arow + jj);
+#pragma unroll
+                for (int c = 0; c < MC; ++c) {
+                    float4 p = *reinterpret_cast<const float4*>(&ps[c][jj]);
+                    acc[r][c] = fmaf(a.x, p.x, fmaf(a.y, p.y, fmaf(a.z, p.z, fmaf(a.w, p.w, acc[r][c]))));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < MV_ROWS_PER_WARP; ++r) {
+        const int row = rbase + r;
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+            float v = warp_sum(acc[r][c]);
+            if (lane == 0 && row < n && c < mc) Q[(long)(c0 + c) * n + row] = (double)v;
+        }
+    }
+}
+
+// Banded product with the diagonal-major band Ab[(o+band)*n + i] = A~(i, i+o).
+static __global__ void k_matvec_band(const float* __restrict__ Ab, int n, int band, const float* __restrict__ Pf,
+                              int m, double* __restrict__ Q) {
+    long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        int c = (int)(e / n), i = (int)(e % n);
+        const float* p = Pf + (long)c * n;
+        float acc = 0.f;
+        for (int o = -band; o <= band; ++o) {
+            int j = i + o;
+            if (j >= 0 && j < n) acc = fmaf(Ab[(long)(o + band) * n + i], p[j], acc);
+        }
+        Q[(long)c * n + i] = (double)acc;
+    }
+}
+
+// Per-CTA partial dots: part[(blk*m + c)*2 + {0,1}] = sum a1.b1, sum a2.b2
+// over the CTA's rows (a2/b2 may be NULL).
+static __global__ void __launch_bounds__(256) k_dot2(const double* __restrict__ a1, const double* __restrict__ b1,
+                                              const double* __restrict__ a2, const double* __restrict__ b2,
+                                              int n, int m, double* __restrict__ part) {
+    __shared__ double red[2][8];
+    const int rows_per = (n + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * rows_per, i1 = min(n, i0 + rows_per);
+    for (int c = 0; c < m; ++c) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int i = i0 + threadIdx.x; i < i1; i += 256) {
+            long k = (long)c * n + i;
+            s1 += a1[k] * b1[k];
+            if (a2) s2 += a2[k] * b2[k];
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        if ((threadIdx.x & 31) == 0) {
+            red[0][threadIdx.x >> 5] = s1;
+            red[1][threadIdx.x >> 5] = s2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t1 = 0.0, t2 = 0.0;
+            for (int k = 0; k < 8; ++k) {
+                t1 += red[0][k];
+                t2 += red[1][k];
+            }
+            part[((long)blockIdx.x * m + c) * 2 + 0] = t1;
+            part[((long)blockIdx.x * m + c) * 2 + 1] = t2;
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ double sum_parts(const double* part, int G, int m, int c, int which) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += part[((long)g * m + c) * 2 + which];
+    return s;
+}
+
+// Per-column CG state (inner loop of Algorithm 2).
+struct CgCol {
+    double rho[2];    // r^T z, double-buffered by iteration parity
+    double alpha;
+    double stop;      // stop when ||r_in||_2 <= stop
+    double rr;        // latest r^T r
+    int done;         // 1 once the column stopped
+    int iters;        // inner steps taken in the current outer step
+    int total;        // inner steps over all outer steps
+    int pad;
+};
+
+// alpha_c = rho_c / (p^T q)_c (every CTA computes it identically from the
+// partials); e += alpha p; r -= alpha q; with Jacobi z = dinv .* r.
+static __global__ void __launch_bounds__(256) k_cg_update(const double* __restrict__ part, int G, int n, int m,
+                                                   CgCol* __restrict__ cols, int parity,
+                                                   double* __restrict__ E, double* __restrict__ Rr,
+                                                   const double* __restrict__ P, const double* __restrict__ Qv,
+                                                   const double* __restrict__ dinv, double* __restrict__ Z) {
+    __shared__ double s_alpha[64];
+    for (int cb = 0; cb < m; cb += 64) {
+        const int cn = min(64, m - cb);
+        __syncthreads();
+        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
+            const CgCol& st = cols[cb + c];
+            double pq = sum_parts(part, G, m, cb + c, 0);
+            s_alpha[c] = st.done ? 0.0 : st.rho[parity] / pq;
+        }
+        __syncthreads();
+        long total = (long)n * cn;
+        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+            int cl = (int)(e / n), i = (int)(e % n);
+            int c = cb + cl;
+            double a = s_alpha[cl];
+            long k = (long)c * n + i;
+            if (a != 0.0) {
+                E[k] = fma(a, P[k], E[k]);
+                Rr[k] = fma(-a, Qv[k], Rr[k]);
+            }
+            if (dinv) Z[k] = dinv[i] * Rr[k];
+        }
+        if (blockIdx.x == 0 && threadIdx.x < cn) cols[cb + threadIdx.x].alpha = s_alpha[threadIdx.x];
+    }
+}
+
+// rho'_c = (r^T z)_c, rr_c = (r^T r)_c from partials; beta = rho'/rho;
+// p = z + beta p, pf = fl32(p); CTA 0 records rho' and the stop test.
+static __global__ void __launch_bounds__(256) k_cg_pupdate(const double* __restrict__ part, int G, int n, int m,
+                                                    CgCol* __restrict__ cols, int parity, int* __restrict__ active,
+                                                    double* __restrict__ P, float* __restrict__ Pf,
+                                                    const double* __restrict__ Z) {
+    __shared__ double s_beta[64];
+    __shared__ int s_done[64];
+    __shared__ int s_active;
+    if (threadIdx.x == 0) s_active = 0;
+    for (int cb = 0; cb < m; cb += 64) {
+        const int cn = min(64, m - cb);
+        __syncthreads();
+        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
+            CgCol st = cols[cb + c];
+            double rz = sum_parts(part, G, m, cb + c, 0);
+            double rr = sum_parts(part, G, m, cb + c, 1);
+            bool was_done = st.done;
+            bool stop = was_done || (sqrt(rr) <= st.stop);
+            s_beta[c] = stop ? 0.0 : rz / st.rho[parity];
+            s_done[c] = stop;
+            if (blockIdx.x == 0) {
+                if (!was_done) {
+                    st.iters += 1;
+                    st.total += 1;
+                    st.rho[parity ^ 1] = rz;
+                    st.rr = rr;
+                }
+                st.done = stop;
+                cols[cb + c] = st;
+                if (!stop) atomicAdd(&s_active, 1);
+            }
+        }
+        __syncthreads();
+        long total = (long)n * cn;
+        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+            int cl = (int)(e / n), i = (int)(e % n);
+            if (s_done[cl]) continue;
+            long k = (long)(cb + cl) * n + i;
+            double p = fma(s_beta[cl], P[k], Z[k]);
+            P[k] = p;
+            Pf[k] = (float)p;
+        }
+    }
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *active = s_active;
+}
+
+// Start of an inner loop: e = 0, r_in = r, z = M r (Jacobi or identity),
+// p = z, pf = fl32(p).
+static __global__ void k_cg_start(int n, int m, const double* __restrict__ R, long ldr, double* __restrict__ E,
+                           double* __restrict__ Rr, double* __restrict__ Z, double* __restrict__ P,
+                           float* __restrict__ Pf, const double* __restrict__ dinv, int set_pz) {
+    long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        int c = (int)(e / n), i = (int)(e % n);
+        double r = R[(long)c * ldr + i];
+        E[e] = 0.0;
+        Rr[e] = r;
+        double z = dinv ? dinv[i] * r : r;
+        if (dinv) Z[e] = z;
+        if (set_pz) {
+            P[e] = z;
+            Pf[e] = (float)z;
+        }
+    }
+}
+
+// p = z, pf = fl32(z) (after a preconditioner applied outside).
+static __global__ void k_copy_p(int n, int m, const double* __restrict__ Z, double* __restrict__ P, float* __restrict__ Pf) {
+    long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        P[e] = Z[e];
+        Pf[e] = (float)Z[e];
+    }
+}
+
+// Initialise the per-column CG state for one inner loop:
+// rho[0] = (r^T z), rr = r^T r, stop = max(eta * ||r||_2, target_c).
+static __global__ void k_cg_init_cols(const double* __restrict__ part, int G, int m, CgCol* __restrict__ cols,
+                               const int* __restrict__ frozen, double eta, const double* __restrict__ target) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        CgCol st = cols[c];
+        double rz = sum_parts(part, G, m, c, 0);
+        double rr = sum_parts(part, G, m, c, 1);
+        st.rho[0] = rz;
+        st.rho[1] = rz;
+        st.rr = rr;
+        st.stop = fmax(eta * sqrt(rr), target[c]);
+        st.iters = 0;
+        st.done = (frozen && frozen[c]) || !(sqrt(rr) > st.stop);
+        cols[c] = st;
+    }
+}
+
+// X += E on columns not frozen.
+static __global__ void k_add_cols(double* __restrict__ X, long ldx, const double* __restrict__ E, int n, int m,
+                           const int* __restrict__ frozen) {
+    long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        int c = (int)(e / n), i = (int)(e % n);
+        if (frozen && frozen[c]) continue;
+        X[(long)c * ldx + i] += E[e];
+    }
+}
+
+// target_c for the inner stop: crit ABS2 -> tol, REL2 -> tol * ||b_c||,
+// BERR -> tol * ||A||_inf * ||x_c||_inf (a 2-norm proxy of the rule).
+static __global__ void k_inner_target(const double* __restrict__ b2, const double* __restrict__ colnorms,
+                               const double* __restrict__ anorm, int m, int crit, double tol, int n,
+                               double* __restrict__ target) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+        double t;
+        if (crit == 2) t = tol;
+        else if (crit == 1) t = tol * b2[c];
+        else t = tol * (*anorm) * fmax(colnorms[3 * c + 2], 1e-300);
+        target[c] = t;
+    }
+}
+
+// dinv_i = 1 / A_ii
+static __global__ void k_jacobi_dinv(const double* __restrict__ A, long lda, int n, double* __restrict__ dinv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dinv[i] = 1.0 / A[(long)i * lda + i];
+}

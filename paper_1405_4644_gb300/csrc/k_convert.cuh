@@ -1,0 +1,103 @@
+// k_convert.cuh -- step A0: symmetric diagonal scaling and conversion of the
+// float64 input into the working matrix of the factorisation.
+#pragma once
+#include "common.cuh"
+
+// d_i = 1/sqrt(A_ii) (or 1 when scaling is off).  A non-positive or
+// non-finite diagonal entry raises SPD_DEV_BADDIAG / SPD_DEV_NONFINITE and
+// records the 1-based index in st->info.
+static __global__ void k_diag_scale(const double* __restrict__ A, long lda, int n, int scale,
+                             double* __restrict__ d, DevStatus* st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double a = A[(long)i * lda + i];
+    if (!isfinite(a)) {
+        dev_raise(st, SPD_DEV_NONFINITE);
+        atomicMin(&st->info, i + 1);
+        d[i] = 1.0;
+        return;
+    }
+    if (!(a > 0.0)) {
+        dev_raise(st, SPD_DEV_BADDIAG);
+        atomicMin(&st->info, i + 1);
+        d[i] = 1.0;
+        return;
+    }
+    d[i] = scale ? 1.0 / sqrt(a) : 1.0;
+}
+
+// W (row-major, ldw) lower triangle <- d_i A_ij d_j for i >= j, rounded to
+// T.  A is column-major (lda); element (i, j) lives at A[i + j*lda].  A
+// 32x32 tile is read along i (coalesced in A) and written along j
+// (coalesced in W) through shared memory.  Tiles strictly above the
+// diagonal are skipped.  Non-finite entries raise SPD_DEV_NONFINITE.
+template <typename T>
+static __global__ void k_scale_convert(const double* __restrict__ A, long lda, int n,
+                                const double* __restrict__ d, T* __restrict__ W, long ldw,
+                                DevStatus* st) {
+    __shared__ double tile[32][33];
+    int bi = blockIdx.y, bj = blockIdx.x;  // tile row (i) and column (j)
+    if (bj > bi) return;
+    int i0 = bi * 32, j0 = bj * 32;
+    int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    bool bad = false;
+    // read: columns j0+jj, rows i0+tx (contiguous in A)
+    for (int jj = ty; jj < 32; jj += 8) {
+        int i = i0 + tx, j = j0 + jj;
+        double v = 0.0;
+        if (i < n && j < n && j <= i) {
+            v = A[(long)j * lda + i];
+            if (!isfinite(v)) bad = true;
+            v = d[i] * v * d[j];
+        }
+        tile[tx][jj] = v;  // tile[i_local][j_local]
+    }
+    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+    __syncthreads();
+    // write: rows i0+ii, columns j0+tx (contiguous in W)
+    for (int ii = ty; ii < 32; ii += 8) {
+        int i = i0 + ii, j = j0 + tx;
+        if (i < n && j < n && j <= i) W[(long)i * ldw + j] = (T)tile[ii][tx];
+    }
+}
+
+// Full low-precision copy A~ = fl(A) for the CG matrix-vector product:
+// row-major n x lda_out (A is symmetric, so this is also its column-major
+// copy).  T is float or __nv_bfloat16.
+template <typename T>
+static __global__ void k_convert_full(const double* __restrict__ A, long lda, int n,
+                               T* __restrict__ At, long ldt, DevStatus* st) {
+    long total = (long)n * n;
+    bool bad = false;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        long j = e / n, i = e - j * n;  // column-major walk: coalesced reads
+        double v = A[j * lda + i];
+        if (!isfinite(v)) bad = true;
+        // symmetric: A(i, j) = A(j, i); write row j, column i of the copy
+        At[j * ldt + i] = (T)(float)v;
+    }
+    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+}
+
+// Banded low-precision copy in diagonal-major layout:
+// Ab[(o + band) * n + i] = fl(A(i, i + o)) for |o| <= band (0 outside).
+static __global__ void k_convert_band(const double* __restrict__ A, long lda, int n, int band,
+                               float* __restrict__ Ab, DevStatus* st) {
+    long total = (long)(2 * band + 1) * n;
+    bool bad = false;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+         e += (long)gridDim.x * blockDim.x) {
+        int o = (int)(e / n) - band;
+        int i = (int)(e % n);
+        int j = i + o;
+        float v = 0.0f;
+        if (j >= 0 && j < n) {
+            double a = A[(long)j * lda + i];
+            if (!isfinite(a)) bad = true;
+            v = (float)a;
+        }
+        Ab[e] = v;
+    }
+    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+}

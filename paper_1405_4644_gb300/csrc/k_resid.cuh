@@ -1,0 +1,261 @@
+// k_resid.cuh -- step A5: the float64 residual R = B - A X of Algorithm 1
+// (lines 3, 7) and Algorithm 2 (line 2), and float64 products Q = A P for
+// the float64 CG fallback; plus per-column norms and the convergence test
+// (A7).  All reductions run in a fixed order, so results are bitwise
+// reproducible run to run.
+//
+// Pass 1 (k_resid_partial): grid (row blocks of 256) x (S column splits);
+//   thread i accumulates sum_{j in split} A[i + j lda] X[j, c] for MT
+//   columns in float64 registers; X rows are staged through shared memory.
+//   A is read once per launch (coalesced along i), optionally with the
+//   float32 row sums of |A| for ||A||_inf.
+// Pass 2 (k_resid_final): R = B - sum_s P_s (or Q = sum_s P_s), per-block
+//   partial norms.  Pass 3 (k_colnorms): per-column norms.
+#pragma once
+#include "common.cuh"
+
+#define RESID_ROWS 256
+#define RESID_JT 64
+
+template <int MT>
+static __global__ void __launch_bounds__(RESID_ROWS) k_resid_partial(const double* __restrict__ A, long lda, int n,
+                                                              const double* __restrict__ X, long ldx, int c0,
+                                                              int mc, int jchunk, int mtot,
+                                                              double* __restrict__ P, float* __restrict__ rowabs) {
+    __shared__ __align__(16) double xs[RESID_JT][MT];
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * RESID_ROWS + tid;
+    const int s = blockIdx.y;
+    const int j0 = s * jchunk;
+    const int j1 = min(n, j0 + jchunk);
+    double acc[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[c] = 0.0;
+    float asum = 0.f;
+    const double* Ai = A + (i < n ? i : 0);
+    for (int jb = j0; jb < j1; jb += RESID_JT) {
+        const int jn = min(RESID_JT, j1 - jb);
+        __syncthreads();
+        for (int e = tid; e < RESID_JT * MT; e += RESID_ROWS) {
+            int jj = e % RESID_JT, c = e / RESID_JT;
+            xs[jj][c] = (jj < jn && c < mc) ? X[(long)(c0 + c) * ldx + jb + jj] : 0.0;
+        }
+        __syncthreads();
+        if (i < n) {
+            const double* ap = Ai + (long)jb * lda;
+            if (jn == RESID_JT) {
+#pragma unroll 4
+                for (int jj = 0; jj < RESID_JT; ++jj) {
+                    double a = __ldg(ap + (long)jj * lda);
+                    if (rowabs) asum += fabsf((float)a);
+#pragma unroll
+                    for (int c = 0; c < MT; ++c) acc[c] = fma(a, xs[jj][c], acc[c]);
+                }
+            } else {
+                for (int jj = 0; jj < jn; ++jj) {
+                    double a = __ldg(ap + (long)jj * lda);
+                    if (rowabs) asum += fabsf((float)a);
+#pragma unroll
+                    for (int c = 0; c < MT; ++c) acc[c] = fma(a, xs[jj][c], acc[c]);
+                }
+            }
+        }
+    }
+    if (i < n) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c)
+            if (c < mc) P[((long)s * mtot + c0 + c) * n + i] = acc[c];
+        if (rowabs) rowabs[(long)s * n + i] = asum;
+    }
+}
+
+// mode 0: R = B - sum_s P_s ; mode 1: R = sum_s P_s.  Block partial norms
+// NP[(blk * m + c) * 3 + {0,1,2}] = max|r|, sum r^2, max|x| (x from X; if X
+// is NULL the third entry is 0).
+static __global__ void __launch_bounds__(256) k_resid_final(const double* __restrict__ B, long ldb, int n, int m,
+                                                     const double* __restrict__ P, int S,
+                                                     double* __restrict__ R, long ldr,
+                                                     const double* __restrict__ X, long ldx,
+                                                     double* __restrict__ NP, int mode) {
+    __shared__ double red[3][8];
+    const int c = blockIdx.y;
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    double rmax = 0.0, r2 = 0.0, xmax = 0.0;
+    if (i < n) {
+        double s = 0.0;
+        for (int k = 0; k < S; ++k) s += P[((long)k * m + c) * n + i];
+        double r = (mode == 0) ? B[(long)c * ldb + i] - s : s;
+        R[(long)c * ldr + i] = r;
+        rmax = fabs(r);
+        r2 = r * r;
+        if (X) xmax = fabs(X[(long)c * ldx + i]);
+    }
+    rmax = warp_max(rmax);
+    r2 = warp_sum(r2);
+    xmax = warp_max(xmax);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = rmax;
+        red[1][w] = r2;
+        red[2][w] = xmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0, x = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            a = fmax(a, red[0][k]);
+            b += red[1][k];
+            x = fmax(x, red[2][k]);
+        }
+        double* o = NP + ((long)blockIdx.x * m + c) * 3;
+        o[0] = a;
+        o[1] = b;
+        o[2] = x;
+    }
+}
+
+// colnorms[3c..3c+2] = ||r_c||_inf, ||r_c||_2, ||x_c||_inf from G block partials.
+static __global__ void __launch_bounds__(256) k_colnorms(const double* __restrict__ NP, int G, int m,
+                                                  double* __restrict__ colnorms) {
+    __shared__ double red[3][8];
+    const int c = blockIdx.x;
+    double a = 0.0, b = 0.0, x = 0.0;
+    for (int g = threadIdx.x; g < G; g += 256) {
+        const double* o = NP + ((long)g * m + c) * 3;
+        a = fmax(a, o[0]);
+        b += o[1];
+        x = fmax(x, o[2]);
+    }
+    a = warp_max(a);
+    b = warp_sum(b);
+    x = warp_max(x);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        red[0][w] = a;
+        red[1][w] = b;
+        red[2][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A_ = 0.0, B_ = 0.0, X_ = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            A_ = fmax(A_, red[0][k]);
+            B_ += red[1][k];
+            X_ = fmax(X_, red[2][k]);
+        }
+        colnorms[3 * c + 0] = A_;
+        colnorms[3 * c + 1] = sqrt(B_);
+        colnorms[3 * c + 2] = X_;
+    }
+}
+
+// ||A||_inf = max_i sum_s rowabs[s][i]  (single CTA, fixed order)
+static __global__ void __launch_bounds__(1024) k_anorm(const float* __restrict__ rowabs, int S, int n,
+                                                double* __restrict__ anorm) {
+    __shared__ double red[32];
+    double best = 0.0;
+    for (int i = threadIdx.x; i < n; i += 1024) {
+        double s = 0.0;
+        for (int k = 0; k < S; ++k) s += (double)rowabs[(long)k * n + i];
+        best = fmax(best, s);
+    }
+    best = warp_max(best);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int k = 0; k < 32; ++k) b = fmax(b, red[k]);
+        *anorm = b;
+    }
+}
+
+// ||b_c||_2 for m columns (one CTA per column, fixed order)
+static __global__ void __launch_bounds__(256) k_col_nrm2(const double* __restrict__ B, long ldb, int n,
+                                                  double* __restrict__ out) {
+    __shared__ double red[8];
+    const int c = blockIdx.x;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        double v = B[(long)c * ldb + i];
+        s += v * v;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k];
+        out[c] = sqrt(t);
+    }
+}
+
+// Convergence bookkeeping for the refinement loops (A7).
+struct IrCol {
+    double err;       // current value of the stopping quantity
+    double prev;      // previous value
+    int conv;         // 1 once the column met the rule (frozen)
+    int stall;        // consecutive sweeps that shrank err by less than half
+    int iters;        // sweeps applied to this column
+    int extra;        // polish sweeps still owed once the rule holds
+};
+struct IrSummary {
+    int active;       // columns not yet converged
+    int stagnated;    // columns whose stall count reached 2
+    double max_berr;  // max over columns of the backward error
+    double max_rel;   // max over columns of ||r||_2 / ||b||_2
+};
+
+// One CTA: update per-column state from colnorms; crit as spd_crit.
+static __global__ void k_ir_check(const double* __restrict__ colnorms, const double* __restrict__ anorm,
+                           const double* __restrict__ b2, int m, int crit, double tol,
+                           IrCol* __restrict__ cols, IrSummary* __restrict__ sum, int count_sweep, int polish) {
+    __shared__ int s_active, s_stag;
+    __shared__ double s_berr, s_rel;
+    if (threadIdx.x == 0) {
+        s_active = 0;
+        s_stag = 0;
+        s_berr = 0.0;
+        s_rel = 0.0;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) {
+        IrCol st = cols[c];
+        double rinf = colnorms[3 * c], r2 = colnorms[3 * c + 1], xinf = colnorms[3 * c + 2];
+        double an = *anorm;
+        double berr = (an > 0.0 && xinf > 0.0) ? rinf / (an * xinf) : rinf;
+        double rel = (b2[c] > 0.0) ? r2 / b2[c] : r2;
+        double err = (crit == 0) ? berr : (crit == 1 ? rel : r2);
+        if (!st.conv) {
+            if (count_sweep) st.iters += 1;
+            bool ok = (crit == 2) ? (err < tol) : (err <= tol);
+            if (ok) {
+                if (st.extra > 0) st.extra -= 1;  // meets the rule: polish once more
+                else st.conv = 1;
+                st.stall = 0;
+            } else {
+                st.extra = polish;
+                if (count_sweep) st.stall = (err > 0.5 * st.prev) ? st.stall + 1 : 0;
+            }
+            st.prev = err;
+            st.err = err;
+        }
+        cols[c] = st;
+        if (!st.conv) atomicAdd(&s_active, 1);
+        if (!st.conv && st.stall >= 2) atomicAdd(&s_stag, 1);
+        // max of non-negative doubles through their bit patterns (order-independent)
+        atomicMax((unsigned long long*)&s_berr, (unsigned long long)__double_as_longlong(berr));
+        atomicMax((unsigned long long*)&s_rel, (unsigned long long)__double_as_longlong(rel));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sum->active = s_active;
+        sum->stagnated = s_stag;
+        sum->max_berr = s_berr;
+        sum->max_rel = s_rel;
+    }
+}
+
+// frozen[c] = cols[c].conv
+static __global__ void k_frozen_from_cols(const IrCol* __restrict__ cols, int m, int* __restrict__ frozen) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) frozen[c] = cols[c].conv;
+}

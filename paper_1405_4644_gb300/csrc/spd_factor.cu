@@ -1,0 +1,385 @@
+// spd_factor.cu -- Algorithm 1 line 1: the low-precision Cholesky
+// factorisation A ~= R~^T R~ (Section 3.1, eq. (cholesky)), blocked
+// right-looking with recursive blocking:
+//
+//   chol(A)   : chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; chol(A22)
+//   trsm(B,L) : trsm(B1, L11); B2 -= X1 L21^T; trsm(B2, L22)
+//
+// with 128x128 leaves (k_potrf_leaf / k_trsm_leaf) and every off-leaf
+// update a GEMM on the working matrix (tensor cores for TF32/BF16/FP16/FP8,
+// CUDA cores for FP32/FP64).  Split points are multiples of 128, so only the
+// very last leaf can be ragged.
+#include "engine.cuh"
+#include "k_convert.cuh"
+#include "k_leaf.cuh"
+#include "k_gemm_simt.cuh"
+#include "gemm_tc.h"
+
+namespace {
+
+struct FCtx {
+    spd_handle* h;
+    spd_factor_t* F;
+    Mirror mir;
+    TcGemm* tc;   // tensor-core GEMM plan (nullptr: CUDA cores)
+};
+
+template <typename T> T* wptr(spd_factor_t* F);
+template <> float* wptr<float>(spd_factor_t* F) { return F->W; }
+template <> double* wptr<double>(spd_factor_t* F) { return F->W64; }
+template <typename T> T* dinvptr(spd_factor_t* F);
+template <> float* dinvptr<float>(spd_factor_t* F) { return F->Dinv; }
+template <> double* dinvptr<double>(spd_factor_t* F) { return F->Dinv64; }
+
+template <typename T> constexpr int rb_of() { return sizeof(T) == 4 ? 64 : 32; }
+
+template <typename T>
+spd_status leaf_potrf(FCtx& c, int k, int nb) {
+    spd_factor_t* F = c.F;
+    ProfScope ps(c.h, SPD_PHASE_LEAF, (double)nb * nb * nb / 3.0, (double)nb * nb * sizeof(T));
+    size_t smem = potrf_leaf_smem<T>();
+    ++(c.h)->launches, k_potrf_leaf<T><<<1, 256, smem, c.h->stream>>>(wptr<T>(F), F->ldw, k, nb, dinvptr<T>(F), c.mir, c.h->dst);
+    LAUNCH_CHECK(c.h);
+    return SPD_OK;
+}
+
+template <typename T>
+spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
+    spd_factor_t* F = c.F;
+    ProfScope ps(c.h, SPD_PHASE_LEAF, (double)m * kb * kb, 2.0 * m * kb * sizeof(T));
+    constexpr int RB = rb_of<T>();
+    size_t smem = trsm_leaf_smem<T, RB>();
+    ++(c.h)->launches, k_trsm_leaf<T, RB><<<ceil_div(m, RB), 256, smem, c.h->stream>>>(wptr<T>(F), F->ldw, r0, m, c0, kb,
+                                                                    dinvptr<T>(F), c.mir, c.h->dst);
+    LAUNCH_CHECK(c.h);
+    return SPD_OK;
+}
+
+template <typename T>
+spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower) {
+    if (M <= 0 || N <= 0 || K <= 0) return SPD_OK;
+    spd_factor_t* F = c.F;
+    cudaStream_t s = c.h->stream;
+    // algorithmic work: lower-triangle SYRK or full GEMM; C read+written once
+    // in T, each operand row read once in the operand type
+    const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+    const double opsz = sizeof(T) == 8 ? 8.0 : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
+    ProfScope ps(c.h, SPD_PHASE_TRAILING, 2.0 * celems * K,
+                 2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N));
+    if constexpr (sizeof(T) == 8) {
+        dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
+        ++(c.h)->launches, k_gemm_nt_simt<double, double, 4, 4, 8><<<grid, 256, 0, s>>>(F->W64, F->ldw, F->W64, F->ldw, r0, M, c0, N,
+                                                                     k0, K, lower, c.h->dst);
+    } else {
+        if (c.tc) {
+            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst);
+            if (st != SPD_OK) return set_err(c.h, st, "tensor-core trailing update failed");
+            return SPD_OK;
+        }
+        dim3 grid(ceil_div(N, 128), ceil_div(M, 128));
+        switch (c.mir.kind) {
+            case 0:
+            ++(c.h)->launches, k_gemm_nt_simt<float, float, 8, 8, 8><<<grid, 256, 0, s>>>(F->W, F->ldw, F->W, F->ldw, r0, M, c0,
+                                                                           N, k0, K, lower, c.h->dst);
+                break;
+            case 1:
+            ++(c.h)->launches, k_gemm_nt_simt<float, float, 8, 8, 8><<<grid, 256, 0, s>>>(
+                    F->W, F->ldw, (const float*)F->Wh, F->ldh, r0, M, c0, N, k0, K, lower, c.h->dst);
+                break;
+            case 2:
+            ++(c.h)->launches, k_gemm_nt_simt<float, __nv_bfloat16, 8, 8, 8><<<grid, 256, 0, s>>>(
+                    F->W, F->ldw, (const __nv_bfloat16*)F->Wh, F->ldh, r0, M, c0, N, k0, K, lower, c.h->dst);
+                break;
+            case 3:
+            ++(c.h)->launches, k_gemm_nt_simt<float, __half, 8, 8, 8><<<grid, 256, 0, s>>>(
+                    F->W, F->ldw, (const __half*)F->Wh, F->ldh, r0, M, c0, N, k0, K, lower, c.h->dst);
+                break;
+            default:
+                return set_err(c.h, SPD_ERR_UNSUPPORTED, "no CUDA-core path for this operand type");
+        }
+    }
+    LAUNCH_CHECK(c.h);
+    return SPD_OK;
+}
+
+inline int split_point(int nn) {
+    int n1 = ((nn / 2 + SPD_LEAF - 1) / SPD_LEAF) * SPD_LEAF;
+    if (n1 >= nn) n1 = nn - SPD_LEAF;
+    return n1;
+}
+
+#define TRY(x)                            \
+    do {                                  \
+        spd_status s_ = (x);              \
+        if (s_ != SPD_OK) return s_;      \
+    } while (0)
+
+template <typename T>
+spd_status trsm_rec(FCtx& c, int r0, int m, int c0, int k) {
+    if (m <= 0) return SPD_OK;
+    if (k <= SPD_LEAF) return leaf_trsm<T>(c, r0, m, c0, k);
+    int k1 = split_point(k);
+    TRY(trsm_rec<T>(c, r0, m, c0, k1));
+    TRY(gemm<T>(c, r0, m, c0 + k1, k - k1, c0, k1, 0));
+    return trsm_rec<T>(c, r0, m, c0 + k1, k - k1);
+}
+
+template <typename T>
+spd_status potrf_rec(FCtx& c, int n0, int nn) {
+    if (nn <= SPD_LEAF) return leaf_potrf<T>(c, n0, nn);
+    int n1 = split_point(nn);
+    TRY(potrf_rec<T>(c, n0, n1));
+    TRY(trsm_rec<T>(c, n0 + n1, nn - n1, n0, n1));
+    TRY(gemm<T>(c, n0 + n1, nn - n1, n0 + n1, nn - n1, n0, n1, 1));
+    return potrf_rec<T>(c, n0 + n1, nn - n1);
+}
+
+void free_factor(spd_factor_t* F) {
+    if (!F) return;
+    cudaFree(F->W);
+    cudaFree(F->W64);
+    cudaFree(F->Wh);
+    cudaFree(F->d);
+    cudaFree(F->Dinv);
+    cudaFree(F->Dinv64);
+    delete F;
+}
+
+int mirror_kind(int prec) {
+    switch (prec) {
+        case SPD_PREC_TF32: return 1;
+        case SPD_PREC_BF16: return 2;
+        case SPD_PREC_FP16: return 3;
+        case SPD_PREC_FP8: return 4;
+        default: return 0;
+    }
+}
+size_t mirror_elem(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
+
+// One factorisation attempt in a fixed precision.
+spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
+                       spd_factor_t** out, spd_report* rep) {
+    spd_factor_t* F = new spd_factor_t();
+    F->h = h;
+    F->n = n;
+    F->prec = prec;
+    F->ldw = round_up(std::max(n, 1), 64);
+    F->nblk128 = ceil_div(n, SPD_LEAF);
+    const size_t nW = (size_t)n * F->ldw;
+    const int kind = mirror_kind(prec);
+    auto fail = [&](spd_status s) {
+        free_factor(F);
+        return s;
+    };
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&F->d, sizeof(double) * std::max(n, 1));
+    if (e == cudaSuccess && prec == SPD_PREC_FP64) {
+        e = cudaMalloc(&F->W64, sizeof(double) * std::max<size_t>(nW, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv64, sizeof(double) * 4096 * std::max(F->nblk128, 1));
+    } else if (e == cudaSuccess) {
+        e = cudaMalloc(&F->W, sizeof(float) * std::max<size_t>(nW, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv, sizeof(float) * 4096 * std::max(F->nblk128, 1));
+        if (e == cudaSuccess && kind) {
+            F->ldh = F->ldw;
+            e = cudaMalloc(&F->Wh, mirror_elem(kind) * std::max<size_t>(nW, 1));
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(set_err(h, e == cudaErrorMemoryAllocation ? SPD_ERR_OOM : SPD_ERR_CUDA,
+                            "factor allocation (n=%d): %s", n, cudaGetErrorString(e)));
+    }
+    cudaStream_t s = h->stream;
+    if (n > 0) {
+        ProfScope* pconv = new ProfScope(h, SPD_PHASE_CONVERT, 3.0 * n * (double)n / 2.0,
+                                         8.0 * n * (double)n / 2.0 + (prec == SPD_PREC_FP64 ? 8.0 : 4.0) * n * (double)n / 2.0);
+                                         ++(h)->launches, k_diag_scale<<<ceil_div(n, 256), 256, 0, s>>>(A, lda, n, (flags & SPD_SCALE_DIAG) ? 1 : 0, F->d, h->dst);
+        dim3 cg(ceil_div(n, 32), ceil_div(n, 32)), cb(32, 8);
+        if (prec == SPD_PREC_FP64)
+            ++(h)->launches, k_scale_convert<double><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W64, F->ldw, h->dst);
+        else
+            ++(h)->launches, k_scale_convert<float><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W, F->ldw, h->dst);
+        delete pconv;
+        if (cudaGetLastError() != cudaSuccess) return fail(set_err(h, SPD_ERR_CUDA, "convert launch failed"));
+        spd_status st = check_dev_status(h, rep, "spd_factor");
+        if (st != SPD_OK) return fail(st);
+
+        FCtx c{h, F, Mirror{F->Wh, F->ldh, kind, nullptr}, nullptr};
+        TcGemm* tc = nullptr;
+        if (kind) {
+            st = tc_gemm_create(&tc, F->W, F->ldw, F->Wh, F->ldh, kind, n);
+            if (st == SPD_OK) c.tc = tc;
+            else if (st != SPD_ERR_UNSUPPORTED) return fail(set_err(h, st, "tensor-core plan failed"));
+        }
+        if (prec == SPD_PREC_FP64) st = potrf_rec<double>(c, 0, n);
+        else st = potrf_rec<float>(c, 0, n);
+        if (st == SPD_OK) st = check_dev_status(h, rep, "spd_factor");
+        if (tc) tc_gemm_destroy(tc);
+        if (st != SPD_OK) return fail(st);
+    }
+    *out = F;
+    return SPD_OK;
+}
+
+// colsum[j] = d_j sum_i |A_ij| d_i  (one warp per column; A column-major)
+__global__ void k_scaled_colsum(const double* __restrict__ A, long lda, int n, const double* __restrict__ d,
+                                double* __restrict__ colsum) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += fabs(A[(long)j * lda + i]) * d[i];
+    s = warp_sum(s);
+    if (lane == 0) colsum[j] = s * d[j];
+}
+
+// Hager's 1-norm estimator of ||As^{-1}||_1 (As = D A D), applied through
+// the factor F (the inverse is symmetric, so its transpose is itself).
+spd_status hager_inv_norm1(spd_handle* h, const spd_factor_t* F, double* out) {
+    const int n = F->n;
+    float* dv = nullptr;
+    CUDA_TRY(h, cudaMallocAsync(&dv, sizeof(float) * n, h->stream));
+    std::vector<float> x(n, 1.0f / n), y(n), z(n), xi(n);
+    double est = 0.0;
+    spd_status st = SPD_OK;
+    auto solve = [&](std::vector<float>& in, std::vector<float>& outv) -> spd_status {
+        CUDA_TRY(h, cudaMemcpyAsync(dv, in.data(), sizeof(float) * n, cudaMemcpyHostToDevice, h->stream));
+        spd_status s2 = factor_apply_scaled_f32(h, F, dv);
+        if (s2 != SPD_OK) return s2;
+        CUDA_TRY(h, cudaMemcpyAsync(outv.data(), dv, sizeof(float) * n, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+        return SPD_OK;
+    };
+    for (int k = 0; k < 5; ++k) {
+        if ((st = solve(x, y)) != SPD_OK) break;
+        double e1 = 0.0;
+        for (int i = 0; i < n; ++i) e1 += fabs((double)y[i]);
+        if (k > 0 && e1 <= est) break;
+        est = e1;
+        for (int i = 0; i < n; ++i) xi[i] = (y[i] >= 0.f) ? 1.f : -1.f;
+        if ((st = solve(xi, z)) != SPD_OK) break;
+        int jmax = 0;
+        double zx = 0.0;
+        for (int i = 0; i < n; ++i) {
+            if (fabs(z[i]) > fabs(z[jmax])) jmax = i;
+            zx += (double)z[i] * x[i];
+        }
+        if (k > 0 && fabs((double)z[jmax]) <= zx) break;
+        std::fill(x.begin(), x.end(), 0.f);
+        x[jmax] = 1.f;
+    }
+    cudaFreeAsync(dv, h->stream);
+    *out = est;
+    return st;
+}
+
+spd_status cond_estimate(spd_handle* h, const spd_factor_t* F, const double* A, int lda, double* kappa) {
+    const int n = F->n;
+    double* cs = nullptr;
+    CUDA_TRY(h, cudaMallocAsync(&cs, sizeof(double) * n, h->stream));
+    ++h->launches, k_scaled_colsum<<<ceil_div(n, 8), 256, 0, h->stream>>>(A, lda, n, F->d, cs);
+    std::vector<double> hc(n);
+    CUDA_TRY(h, cudaMemcpyAsync(hc.data(), cs, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    cudaFreeAsync(cs, h->stream);
+    double anorm1 = 0.0;
+    for (double v : hc) anorm1 = std::max(anorm1, v);
+    double inv1 = 0.0;
+    spd_status st = hager_inv_norm1(h, F, &inv1);
+    *kappa = anorm1 * inv1;
+    return st;
+}
+
+}  // namespace
+
+static void setup_leaf_attrs() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_potrf_leaf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<float>());
+    cudaFuncSetAttribute(k_potrf_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<double>());
+    cudaFuncSetAttribute(k_trsm_leaf<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)trsm_leaf_smem<float, 64>());
+    cudaFuncSetAttribute(k_trsm_leaf<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)trsm_leaf_smem<double, 32>());
+}
+
+extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
+                                 spd_factor_t** F, spd_report* rep) {
+    if (!h) return SPD_ERR_ARG;
+    if (!F || n < 0 || (n > 0 && (!A || lda < n)))
+        return set_err(h, SPD_ERR_ARG, "spd_factor: bad arguments (n=%d lda=%d)", n, lda);
+    if (prec < SPD_PREC_FP64 || prec > SPD_PREC_AUTO)
+        return set_err(h, SPD_ERR_ARG, "spd_factor: unknown precision %d", prec);
+    *F = nullptr;
+    if (rep) memset(rep, 0, sizeof(*rep));
+    setup_leaf_attrs();
+    CUDA_TRY(h, cudaEventRecord(h->e0, h->stream));
+    spd_status st;
+    int used = prec;
+    double kappa = 0.0;
+    if (prec == SPD_PREC_AUTO) {
+        // FP16 tensor-core factor first; keep it when the estimated
+        // kappa u_fp16 <= 1/4 (eq. (iterref) with margin), else FP32, and
+        // FP64 if FP32 breaks down too.  kappa_1 / sqrt(n) stands in for the
+        // 2-norm condition number (kappa_1 / n <= kappa_2 <= kappa_1 for a
+        // symmetric matrix).
+        used = SPD_PREC_FP16;
+        st = factor_once(h, n, A, lda, SPD_PREC_FP16, flags, F, rep);
+        if (st == SPD_OK && n > 0) {
+            st = cond_estimate(h, *F, A, lda, &kappa);
+            if (st == SPD_OK && !(kappa / sqrt((double)n) * 0x1p-11 <= 0.25)) {
+                spd_factor_destroy(*F);
+                *F = nullptr;
+                st = SPD_ERR_NOT_SPD;
+            }
+        }
+        if (st == SPD_ERR_NOT_SPD) {
+            used = SPD_PREC_FP32;
+            st = factor_once(h, n, A, lda, SPD_PREC_FP32, flags, F, rep);
+        }
+        if (st == SPD_ERR_NOT_SPD) {
+            used = SPD_PREC_FP64;
+            st = factor_once(h, n, A, lda, SPD_PREC_FP64, flags, F, rep);
+        }
+    } else {
+        st = factor_once(h, n, A, lda, prec, flags, F, rep);
+    }
+    CUDA_TRY(h, cudaEventRecord(h->e1, h->stream));
+    CUDA_TRY(h, cudaEventSynchronize(h->e1));
+    if (rep) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->e0, h->e1);
+        rep->time_ms = ms;
+        rep->status = st;
+        rep->prec_used = used;
+        rep->cond_est = kappa;
+    }
+    return st;
+}
+
+extern "C" spd_status spd_factor_destroy(spd_factor_t* F) {
+    free_factor(F);
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_factor_info(const spd_factor_t* F, int* n, int* prec) {
+    if (!F) return SPD_ERR_ARG;
+    if (n) *n = F->n;
+    if (prec) *prec = F->prec;
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_factor_copy(const spd_factor_t* F, void* L, int ldl, double* d) {
+    if (!F || (L && ldl < F->n)) return SPD_ERR_ARG;
+    spd_handle* h = F->h;
+    const int n = F->n;
+    if (n == 0) return SPD_OK;
+    const size_t es = F->W64 ? sizeof(double) : sizeof(float);
+    const void* src = F->W64 ? (const void*)F->W64 : (const void*)F->W;
+    if (L)
+        CUDA_TRY(h, cudaMemcpy2DAsync(L, es * ldl, src, es * F->ldw, es * n, n, cudaMemcpyDefault, h->stream));
+    if (d) CUDA_TRY(h, cudaMemcpyAsync(d, F->d, sizeof(double) * n, cudaMemcpyDefault, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SPD_OK;
+}

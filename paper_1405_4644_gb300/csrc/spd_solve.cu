@@ -1,0 +1,773 @@
+// spd_solve.cu -- handle management, the float64 residual, the
+// low-precision triangular solves, Algorithm 1's refinement loop and
+// Algorithm 2's CG with iterative refinement.
+#include "engine.cuh"
+#include "k_convert.cuh"
+#include "k_solve.cuh"
+#include "k_resid.cuh"
+#include "k_cg.cuh"
+
+// ---------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------
+extern "C" void spd_opts_default(spd_opts* o) {
+    if (!o) return;
+    o->tol = 1e-14;
+    o->crit = SPD_CRIT_BERR;
+    o->maxit = 50;
+    o->maxit_inner = 2000;
+    o->eta = 1e-4;
+    o->band = -1;
+    o->fallback = 1;
+    o->resid = SPD_RESID_FP64;
+    o->polish = 1;
+}
+
+extern "C" spd_status spd_create(spd_handle** out, void* stream) {
+    if (!out) return SPD_ERR_ARG;
+    *out = nullptr;
+    spd_handle* h = new spd_handle();
+    h->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaMalloc(&h->dst, sizeof(DevStatus));
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 4096);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
+    if (e == cudaSuccess) {
+        DevStatus clear{0, INT_MAX, {0, 0}};
+        e = cudaMemcpy(h->dst, &clear, sizeof(clear), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->dst) cudaFree(h->dst);
+        if (h->pinned) cudaFreeHost(h->pinned);
+        if (h->e0) cudaEventDestroy(h->e0);
+        if (h->e1) cudaEventDestroy(h->e1);
+        delete h;
+        return e == cudaErrorMemoryAllocation ? SPD_ERR_OOM : SPD_ERR_CUDA;
+    }
+    *out = h;
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_destroy(spd_handle* h) {
+    if (!h) return SPD_OK;
+    cudaStreamSynchronize(h->stream);
+    cudaFree(h->ws);
+    cudaFree(h->dst);
+    cudaFreeHost(h->pinned);
+    cudaEventDestroy(h->e0);
+    cudaEventDestroy(h->e1);
+    for (auto& r : h->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+    return SPD_OK;
+}
+
+extern "C" const char* spd_last_error_string(const spd_handle* h) { return h ? h->err : "null handle"; }
+
+// ---------------------------------------------------------------------------
+// internal building blocks
+// ---------------------------------------------------------------------------
+namespace {
+
+struct ResidWs {
+    double* P;      // S x m x n partial sums
+    float* rowabs;  // S x n
+    double* NP;     // G x m x 3
+    int S;
+};
+
+int resid_splits(spd_handle* h, int n) {
+    int rowblk = ceil_div(n, RESID_ROWS);
+    int want = std::max(1, (4 * h->sms + rowblk - 1) / rowblk);
+    int maxs = std::max(1, n / (4 * RESID_JT));
+    return std::min(want, maxs);
+}
+
+size_t resid_plan(WsPlan& p, spd_handle* h, int n, int m, size_t* offs) {
+    int S = resid_splits(h, n);
+    int G = ceil_div(n, 256);
+    offs[0] = p.add<double>((size_t)S * m * n);
+    offs[1] = p.add<float>((size_t)S * n);
+    offs[2] = p.add<double>((size_t)G * m * 3);
+    return S;
+}
+
+// R = B - A X (mode 0) or R = A X (mode 1), float64; colnorms[3m]; if anorm
+// is non-null also ||A||_inf.
+spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda, const double* B,
+                     long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
+                     int mode) {
+    cudaStream_t s = h->stream;
+    ProfScope ps(h, SPD_PHASE_RESID, 2.0 * n * (double)n * m, 8.0 * n * (double)n + 24.0 * n * (double)m);
+    const int S = w.S;
+    const int jchunk = (int)round_up(ceil_div(n, S), RESID_JT);
+    dim3 grid(ceil_div(n, RESID_ROWS), S);
+    for (int c0 = 0; c0 < m; c0 += 16) {
+        int mc = std::min(16, m - c0);
+        float* ra = (anorm && c0 == 0) ? w.rowabs : nullptr;
+        if (mc == 1)
+            ++(h)->launches, k_resid_partial<1><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+        else if (mc == 2)
+            ++(h)->launches, k_resid_partial<2><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+        else if (mc <= 4)
+            ++(h)->launches, k_resid_partial<4><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+        else if (mc <= 8)
+            ++(h)->launches, k_resid_partial<8><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+        else
+            ++(h)->launches, k_resid_partial<16><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+        LAUNCH_CHECK(h);
+    }
+    const int G = ceil_div(n, 256);
+    ++(h)->launches, k_resid_final<<<dim3(G, m), 256, 0, s>>>(B, ldb, n, m, w.P, S, R, ldr, X, ldx, w.NP, mode);
+    LAUNCH_CHECK(h);
+    if (colnorms) {
+        ++(h)->launches, k_colnorms<<<m, 256, 0, s>>>(w.NP, G, m, colnorms);
+        LAUNCH_CHECK(h);
+    }
+    if (anorm) {
+        ++(h)->launches, k_anorm<<<1, 1024, 0, s>>>(w.rowabs, S, n, anorm);
+        LAUNCH_CHECK(h);
+    }
+    return SPD_OK;
+}
+
+template <typename T>
+void setup_solve_attrs() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    constexpr int MC = solve_mc<T>();
+    cudaFuncSetAttribute(k_trsv_fwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)solve_smem_bytes<T>());
+    cudaFuncSetAttribute(k_trsv_bwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)solve_smem_bytes<T>());
+}
+
+// Y <- L^{-T} L^{-1} Y in place (n x m, ld n) with the factor's L and the
+// inverses of its 32x32 diagonal sub-blocks.
+template <typename T>
+spd_status lp_sweeps(spd_handle* h, const T* W, long ldw, const T* Dinv, int n, int m, T* Y) {
+    setup_solve_attrs<T>();
+    ProfScope ps(h, SPD_PHASE_SOLVE, 2.0 * n * (double)n * m, (double)sizeof(T) * n * (double)n);
+    constexpr int MC = solve_mc<T>();
+    cudaStream_t s = h->stream;
+    const int NB = ceil_div(n, 128);
+    const size_t smem = solve_smem_bytes<T>();
+    for (int c0 = 0; c0 < m; c0 += MC) {
+        int mc = std::min(MC, m - c0);
+        for (int J = -1; J <= NB - 2; ++J) {
+            int grid = NB - 1 - J;
+            ++(h)->launches, k_trsv_fwd_step<T, MC><<<grid, 256, smem, s>>>(W, ldw, n, Dinv, Y, c0, mc, J);
+        }
+        LAUNCH_CHECK(h);
+        for (int J = NB; J >= 1; --J) {
+            int grid = (J == NB) ? 1 : J;
+            ++(h)->launches, k_trsv_bwd_step<T, MC><<<grid, 256, smem, s>>>(W, ldw, n, NB, Dinv, Y, c0, mc, J);
+        }
+        LAUNCH_CHECK(h);
+    }
+    return SPD_OK;
+}
+
+// X = d .* (L^{-T} L^{-1} (d .* R))  (mode 0)  or  X += ... on unfrozen
+// columns (mode 1).  Y is scratch of n*m elements of the factor's type.
+spd_status lp_apply(spd_handle* h, const spd_factor_t* F, int n, int m, const double* R, long ldr, void* Y,
+                    double* X, long ldx, const int* frozen, int mode) {
+    cudaStream_t s = h->stream;
+    int g = grid_for((long)n * m, 256, 8 * h->sms);
+    spd_status st;
+    if (F->prec == SPD_PREC_FP64) {
+        double* y = static_cast<double*>(Y);
+        ++(h)->launches, k_scale_to<double><<<g, 256, 0, s>>>(R, ldr, F->d, n, m, y);
+        LAUNCH_CHECK(h);
+        st = lp_sweeps<double>(h, F->W64, F->ldw, F->Dinv64, n, m, y);
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_apply_correction<double><<<g, 256, 0, s>>>(X, ldx, F->d, y, n, m, frozen, mode);
+    } else {
+        float* y = static_cast<float*>(Y);
+        ++(h)->launches, k_scale_to<float><<<g, 256, 0, s>>>(R, ldr, F->d, n, m, y);
+        LAUNCH_CHECK(h);
+        st = lp_sweeps<float>(h, F->W, F->ldw, F->Dinv, n, m, y);
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_apply_correction<float><<<g, 256, 0, s>>>(X, ldx, F->d, y, n, m, frozen, mode);
+    }
+    LAUNCH_CHECK(h);
+    return SPD_OK;
+}
+
+}  // namespace
+
+spd_status factor_apply_scaled_f32(spd_handle* h, const spd_factor_t* F, float* y) {
+    return lp_sweeps<float>(h, F->W, F->ldw, F->Dinv, F->n, 1, y);
+}
+
+namespace {
+
+__global__ void k_ircols_init(IrCol* cols, int m, int polish) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < m) {
+        IrCol z;
+        z.err = 0.0;
+        z.prev = INFINITY;
+        z.conv = 0;
+        z.stall = 0;
+        z.iters = 0;
+        z.extra = polish;
+        cols[c] = z;
+    }
+}
+
+bool bad_args(int n, int m, const void* A, int lda, const void* B, int ldb, const void* X, int ldx) {
+    if (n < 0 || m < 0) return true;
+    if (n == 0 || m == 0) return false;
+    if (!A || !B || !X) return true;
+    if (lda < n || ldb < n || ldx < n) return true;
+    if (m > SPD_MAXM) return true;
+    return false;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public building blocks
+// ---------------------------------------------------------------------------
+extern "C" spd_status spd_residual(spd_handle* h, int n, int m, const double* A, int lda, const double* B, int ldb,
+                                   const double* X, int ldx, double* R, int ldr, double* colnorms) {
+    if (!h) return SPD_ERR_ARG;
+    if (bad_args(n, m, A, lda, B, ldb, X, ldx) || (n > 0 && m > 0 && (!R || ldr < n)))
+        return set_err(h, SPD_ERR_ARG, "spd_residual: bad arguments");
+    if (n == 0 || m == 0) return SPD_OK;
+    WsPlan p;
+    size_t off[3];
+    int S = (int)resid_plan(p, h, n, m, off);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    ResidWs w{ws_at<double>(h, off[0]), ws_at<float>(h, off[1]), ws_at<double>(h, off[2]), S};
+    st = resid_run(h, w, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms, nullptr, 0);
+    if (st != SPD_OK) return st;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_factor_solve(spd_handle* h, const spd_factor_t* F, int n, int m, const double* R, int ldr,
+                                       double* Z, int ldz) {
+    if (!h) return SPD_ERR_ARG;
+    if (!F || F->n != n || bad_args(n, m, F, n, R, ldr, Z, ldz))
+        return set_err(h, SPD_ERR_ARG, "spd_factor_solve: bad arguments");
+    if (n == 0 || m == 0) return SPD_OK;
+    WsPlan p;
+    size_t oy = p.add<double>((size_t)n * m);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    st = lp_apply(h, F, n, m, R, ldr, ws_at<double>(h, oy), Z, ldz, nullptr, 0);
+    if (st != SPD_OK) return st;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return SPD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CG with iterative refinement (Algorithm 2, nested low/high reading); also
+// the float64 factor-preconditioned CG used as the refinement fallback.
+// ---------------------------------------------------------------------------
+namespace {
+
+enum MatvecKind { MV_FP64 = 0, MV_FP32 = 1, MV_BF16 = 2, MV_BAND = 3 };
+
+struct CgSetup {
+    int matvec = MV_FP64;
+    const void* At = nullptr;  // low-precision copy (dense row-major n x ldt, or band)
+    long ldt = 0;
+    int band = -1;
+    int pc = SPD_PC_NONE;
+    const spd_factor_t* F = nullptr;
+    const double* dinv = nullptr;
+};
+
+template <typename T, int MC>
+void mv_launch(spd_handle* h, const CgSetup& cs, int n, int m, const float* Pf, double* Q) {
+    ProfScope ps(h, SPD_PHASE_MATVEC, 2.0 * n * (double)n * m, (double)sizeof(T) * n * (double)n);
+    int grid = ceil_div(n, MV_ROWS);
+    for (int c0 = 0; c0 < m; c0 += MC) {
+        int mc = std::min(MC, m - c0);
+        ++(h)->launches, k_matvec_lp<T, MC><<<grid, 256, 0, h->stream>>>(static_cast<const T*>(cs.At), cs.ldt, n, Pf, c0, mc, Q,
+                                                        nullptr);
+    }
+}
+
+template <typename T>
+void mv_dispatch(spd_handle* h, const CgSetup& cs, int n, int m, const float* Pf, double* Q) {
+    if (m == 1) mv_launch<T, 1>(h, cs, n, m, Pf, Q);
+    else if (m <= 4) mv_launch<T, 4>(h, cs, n, m, Pf, Q);
+    else if (m <= 8) mv_launch<T, 8>(h, cs, n, m, Pf, Q);
+    else mv_launch<T, 16>(h, cs, n, m, Pf, Q);
+}
+
+struct CgWs {
+    ResidWs rw;
+    double *R, *colnorms, *anorm, *b2, *target, *E, *Rr, *Z, *P, *Q, *part, *Yz;
+    float* Pf;
+    IrCol* cols;
+    IrSummary* sum;
+    CgCol* cg;
+    int *frozen, *active;
+    int G2;
+};
+
+size_t cg_plan(WsPlan& p, spd_handle* h, int n, int m, size_t* o, int* S, int* G2) {
+    *S = (int)resid_plan(p, h, n, m, o);
+    *G2 = std::max(1, std::min(2 * h->sms, ceil_div(n, 256)));
+    size_t nm = (size_t)n * m;
+    o[3] = p.add<double>(nm);       // R
+    o[4] = p.add<double>(3 * m);    // colnorms
+    o[5] = p.add<double>(1);        // anorm
+    o[6] = p.add<double>(m);        // b2
+    o[7] = p.add<double>(m);        // target
+    o[8] = p.add<double>(nm);       // E
+    o[9] = p.add<double>(nm);       // Rr
+    o[10] = p.add<double>(nm);      // Z
+    o[11] = p.add<double>(nm);      // P
+    o[12] = p.add<double>(nm);      // Q
+    o[13] = p.add<double>((size_t)(*G2) * m * 2);  // part
+    o[14] = p.add<double>(nm);      // Yz (factor preconditioner scratch)
+    o[15] = p.add<float>(nm);       // Pf
+    o[16] = p.add<IrCol>(m);
+    o[17] = p.add<IrSummary>(1);
+    o[18] = p.add<CgCol>(m);
+    o[19] = p.add<int>(m);          // frozen
+    o[20] = p.add<int>(1);          // active
+    return p.bytes;
+}
+
+CgWs cg_bind(spd_handle* h, const size_t* o, int S, int G2) {
+    CgWs w;
+    w.rw = ResidWs{ws_at<double>(h, o[0]), ws_at<float>(h, o[1]), ws_at<double>(h, o[2]), S};
+    w.R = ws_at<double>(h, o[3]);
+    w.colnorms = ws_at<double>(h, o[4]);
+    w.anorm = ws_at<double>(h, o[5]);
+    w.b2 = ws_at<double>(h, o[6]);
+    w.target = ws_at<double>(h, o[7]);
+    w.E = ws_at<double>(h, o[8]);
+    w.Rr = ws_at<double>(h, o[9]);
+    w.Z = ws_at<double>(h, o[10]);
+    w.P = ws_at<double>(h, o[11]);
+    w.Q = ws_at<double>(h, o[12]);
+    w.part = ws_at<double>(h, o[13]);
+    w.Yz = ws_at<double>(h, o[14]);
+    w.Pf = ws_at<float>(h, o[15]);
+    w.cols = ws_at<IrCol>(h, o[16]);
+    w.sum = ws_at<IrSummary>(h, o[17]);
+    w.cg = ws_at<CgCol>(h, o[18]);
+    w.frozen = ws_at<int>(h, o[19]);
+    w.active = ws_at<int>(h, o[20]);
+    w.G2 = G2;
+    return w;
+}
+
+spd_status read_summary(spd_handle* h, const IrSummary* d, IrSummary* out) {
+    IrSummary* hs = reinterpret_cast<IrSummary*>(static_cast<char*>(h->pinned) + 64);
+    CUDA_TRY(h, cudaMemcpyAsync(hs, d, sizeof(IrSummary), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *out = *hs;
+    return SPD_OK;
+}
+
+spd_status read_int(spd_handle* h, const int* d, int* out) {
+    int* hs = reinterpret_cast<int*>(static_cast<char*>(h->pinned) + 128);
+    CUDA_TRY(h, cudaMemcpyAsync(hs, d, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    *out = *hs;
+    return SPD_OK;
+}
+
+// The nested CG-IR loop.  If reuse_state, the outer state (cols, R,
+// colnorms, anorm, b2) already describes the current X.
+spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, long lda, const double* B, long ldb,
+                      double* X, long ldx, const spd_opts& o, const CgSetup& cs, bool reuse_state, int* low,
+                      int* high, IrSummary* last) {
+    cudaStream_t s = h->stream;
+    const int gv = grid_for((long)n * m, 256, 8 * h->sms);
+    spd_status st;
+    if (!reuse_state) {
+        CUDA_TRY(h, cudaMemset2DAsync(X, sizeof(double) * ldx, 0, sizeof(double) * n, m, s));
+        ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, 0);
+        ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0);
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0, 0);
+        LAUNCH_CHECK(h);
+    }
+    CUDA_TRY(h, cudaMemsetAsync(w.cg, 0, sizeof(CgCol) * m, s));
+    const double* Zr = (cs.pc == SPD_PC_NONE) ? w.Rr : w.Z;
+    int outer = 0;
+    IrSummary sm{};
+    for (;;) {
+        st = read_summary(h, w.sum, &sm);
+        if (st != SPD_OK) return st;
+        if (sm.active == 0) break;
+        if (outer >= o.maxit) {
+            *last = sm;
+            return set_err(h, SPD_ERR_NO_CONVERGENCE, "CG refinement: %d columns above tolerance after %d outer steps",
+                           sm.active, outer);
+        }
+        ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
+        ++(h)->launches, k_inner_target<<<ceil_div(m, 128), 128, 0, s>>>(w.b2, w.colnorms, w.anorm, m, o.crit, o.tol, n, w.target);
+        const bool fac = (cs.pc == SPD_PC_FACTOR);
+        ++(h)->launches, k_cg_start<<<gv, 256, 0, s>>>(n, m, w.R, n, w.E, w.Rr, w.Z, w.P, w.Pf,
+                                      cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, fac ? 0 : 1);
+        LAUNCH_CHECK(h);
+        if (fac) {
+            st = lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0);
+            if (st != SPD_OK) return st;
+            ++(h)->launches, k_copy_p<<<gv, 256, 0, s>>>(n, m, w.Z, w.P, w.Pf);
+        }
+        ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
+        ++(h)->launches, k_cg_init_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.part, w.G2, m, w.cg, w.frozen, o.eta, w.target);
+        LAUNCH_CHECK(h);
+        for (int t = 0; t < o.maxit_inner; ++t) {
+            const int par = t & 1;
+            switch (cs.matvec) {
+                case MV_FP32: mv_dispatch<float>(h, cs, n, m, w.Pf, w.Q); break;
+                case MV_BF16: mv_dispatch<__nv_bfloat16>(h, cs, n, m, w.Pf, w.Q); break;
+                case MV_BAND:
+                ++(h)->launches, k_matvec_band<<<gv, 256, 0, s>>>(static_cast<const float*>(cs.At), n, cs.band, w.Pf, m, w.Q);
+                    break;
+                default:
+                    st = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1);
+                    if (st != SPD_OK) return st;
+            }
+            LAUNCH_CHECK(h);
+            ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.P, w.Q, nullptr, nullptr, n, m, w.part);
+            ++(h)->launches, k_cg_update<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.E, w.Rr, w.P, w.Q,
+                                           cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, w.Z);
+            LAUNCH_CHECK(h);
+            if (fac) {
+                st = lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0);
+                if (st != SPD_OK) return st;
+            }
+            ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
+            ++(h)->launches, k_cg_pupdate<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.active, w.P, w.Pf, Zr);
+            LAUNCH_CHECK(h);
+            if ((t + 1) % 8 == 0 || t + 1 == o.maxit_inner) {
+                int act = 0;
+                st = read_int(h, w.active, &act);
+                if (st != SPD_OK) return st;
+                if (act == 0) break;
+            }
+        }
+        ++(h)->launches, k_add_cols<<<gv, 256, 0, s>>>(X, ldx, w.E, n, m, w.frozen);
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0);
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1, 0);
+        LAUNCH_CHECK(h);
+        ++outer;
+    }
+    *last = sm;
+    // inner-step totals (max over columns)
+    std::vector<CgCol> hc(m);
+    CUDA_TRY(h, cudaMemcpy(hc.data(), w.cg, sizeof(CgCol) * m, cudaMemcpyDeviceToHost));
+    int mx = 0;
+    for (auto& c : hc) mx = std::max(mx, c.total);
+    *low += mx;
+    *high += outer;
+    return SPD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Algorithm 1: refinement with a low-precision factor
+// ---------------------------------------------------------------------------
+extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, int m, const double* A, int lda,
+                                   const double* B, int ldb, double* X, int ldx, const spd_opts* opts_in,
+                                   spd_report* rep) {
+    if (!h) return SPD_ERR_ARG;
+    spd_opts o;
+    spd_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (rep) memset(rep, 0, sizeof(*rep));
+    if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || !(o.tol >= 0.0) ||
+        o.crit < 0 || o.crit > 2)
+        return set_err(h, SPD_ERR_ARG, "spd_solve_ir: bad arguments");
+    if (n == 0 || m == 0) return SPD_OK;
+    cudaStream_t s = h->stream;
+    WsPlan p;
+    size_t o_[21];
+    int S, G2;
+    cg_plan(p, h, n, m, o_, &S, &G2);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    CgWs w = cg_bind(h, o_, S, G2);
+    CUDA_TRY(h, cudaEventRecord(h->e0, s));
+
+    ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, std::max(0, o.polish));
+    ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
+    LAUNCH_CHECK(h);
+    st = lp_apply(h, F, n, m, B, ldb, w.Yz, X, ldx, nullptr, 0);  // line 2
+    if (st != SPD_OK) return st;
+    st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0);  // line 3
+    if (st != SPD_OK) return st;
+    ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0,
+                                                  std::max(0, o.polish));
+    LAUNCH_CHECK(h);
+
+    int sweeps = 0, low = 1, high = 1, fell = 0;
+    IrSummary sm{};
+    spd_status result = SPD_OK;
+    for (;;) {
+        st = read_summary(h, w.sum, &sm);
+        if (st != SPD_OK) return st;
+        if (sm.active == 0) break;
+        if (sweeps >= o.maxit) {
+            result = set_err(h, SPD_ERR_NO_CONVERGENCE, "refinement: %d columns above tolerance after %d sweeps",
+                             sm.active, sweeps);
+            break;
+        }
+        if (sm.stagnated && o.fallback) {
+            // eq. (iterref) no longer holds in practice: continue with CG on A
+            // in float64 preconditioned by the low-precision factor
+            CgSetup cs;
+            cs.matvec = MV_FP64;
+            cs.pc = SPD_PC_FACTOR;
+            cs.F = F;
+            spd_opts fo = o;
+            fo.maxit = std::max(1, o.maxit - sweeps);
+            fo.eta = std::min(o.eta, 1e-6);
+            int lo2 = 0, hi2 = 0;
+            result = cg_ir_core(h, w, n, m, A, lda, B, ldb, X, ldx, fo, cs, true, &lo2, &hi2, &sm);
+            low += lo2;
+            high += hi2;
+            fell = 1;
+            break;
+        }
+        ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
+        st = lp_apply(h, F, n, m, w.R, n, w.Yz, X, ldx, w.frozen, 1);  // lines 5-6
+        if (st != SPD_OK) return st;
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0);  // line 7
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1,
+                                                      std::max(0, o.polish));
+        LAUNCH_CHECK(h);
+        ++sweeps;
+        ++low;
+        ++high;
+    }
+    CUDA_TRY(h, cudaEventRecord(h->e1, s));
+    CUDA_TRY(h, cudaEventSynchronize(h->e1));
+    if (result != SPD_ERR_NO_CONVERGENCE && result != SPD_OK) return result;
+    if (rep) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->e0, h->e1);
+        rep->status = result;
+        rep->iters_low = low;
+        rep->iters_high = high;
+        rep->prec_used = F->prec;
+        rep->fell_back = fell;
+        rep->berr = sm.max_berr;
+        rep->rel_resid = sm.max_rel;
+        rep->time_ms = ms;
+    }
+    return result;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 2
+// ---------------------------------------------------------------------------
+extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int lda, int matvec_prec, int pc,
+                             const void* pc_data, const double* B, int ldb, double* X, int ldx,
+                             const spd_opts* opts_in, spd_report* rep) {
+    if (!h) return SPD_ERR_ARG;
+    spd_opts o;
+    spd_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (rep) memset(rep, 0, sizeof(*rep));
+    if (bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || o.maxit_inner < 1 || !(o.tol >= 0.0) ||
+        o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_FACTOR || (pc == SPD_PC_FACTOR && !pc_data))
+        return set_err(h, SPD_ERR_ARG, "spd_cg: bad arguments");
+    if (matvec_prec != SPD_PREC_FP64 && matvec_prec != SPD_PREC_FP32 && matvec_prec != SPD_PREC_BF16)
+        return set_err(h, SPD_ERR_UNSUPPORTED, "spd_cg: matrix-vector precision must be FP64, FP32 or BF16");
+    if (o.band >= 0 && matvec_prec != SPD_PREC_FP32)
+        return set_err(h, SPD_ERR_UNSUPPORTED, "spd_cg: the banded inner matrix is stored in FP32");
+    if (pc == SPD_PC_FACTOR && static_cast<const spd_factor_t*>(pc_data)->n != n)
+        return set_err(h, SPD_ERR_ARG, "spd_cg: factor order differs from n");
+    if (n == 0 || m == 0) return SPD_OK;
+    cudaStream_t s = h->stream;
+    WsPlan p;
+    size_t o_[21];
+    int S, G2;
+    cg_plan(p, h, n, m, o_, &S, &G2);
+    CgSetup cs;
+    cs.pc = pc;
+    cs.F = static_cast<const spd_factor_t*>(pc_data);
+    size_t o_at = 0, o_dinv = 0;
+    long ldt = round_up(n, 64);
+    if (o.band >= 0) {
+        cs.matvec = MV_BAND;
+        cs.band = o.band;
+        o_at = p.add<float>((size_t)(2 * o.band + 1) * n);
+    } else if (matvec_prec == SPD_PREC_FP32) {
+        cs.matvec = MV_FP32;
+        o_at = p.add<float>((size_t)n * ldt);
+    } else if (matvec_prec == SPD_PREC_BF16) {
+        cs.matvec = MV_BF16;
+        o_at = p.add<__nv_bfloat16>((size_t)n * ldt);
+    }
+    if (pc == SPD_PC_JACOBI) o_dinv = p.add<double>(n);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    CgWs w = cg_bind(h, o_, S, G2);
+    CUDA_TRY(h, cudaEventRecord(h->e0, s));
+    const int gbig = grid_for((long)n * n, 256, 16 * h->sms);
+    if (cs.matvec == MV_BAND) {
+        float* Ab = ws_at<float>(h, o_at);
+        ++(h)->launches, k_convert_band<<<grid_for((long)(2 * o.band + 1) * n, 256, 16 * h->sms), 256, 0, s>>>(A, lda, n, o.band, Ab,
+                                                                                            h->dst);
+        cs.At = Ab;
+    } else if (cs.matvec == MV_FP32) {
+        float* At = ws_at<float>(h, o_at);
+        CUDA_TRY(h, cudaMemsetAsync(At, 0, sizeof(float) * n * ldt, s));
+        ++(h)->launches, k_convert_full<float><<<gbig, 256, 0, s>>>(A, lda, n, At, ldt, h->dst);
+        cs.At = At;
+        cs.ldt = ldt;
+    } else if (cs.matvec == MV_BF16) {
+        __nv_bfloat16* At = ws_at<__nv_bfloat16>(h, o_at);
+        CUDA_TRY(h, cudaMemsetAsync(At, 0, sizeof(__nv_bfloat16) * n * ldt, s));
+        ++(h)->launches, k_convert_full<__nv_bfloat16><<<gbig, 256, 0, s>>>(A, lda, n, At, ldt, h->dst);
+        cs.At = At;
+        cs.ldt = ldt;
+    }
+    if (pc == SPD_PC_JACOBI) {
+        double* dinv = ws_at<double>(h, o_dinv);
+        ++(h)->launches, k_jacobi_dinv<<<ceil_div(n, 256), 256, 0, s>>>(A, lda, n, dinv);
+        cs.dinv = dinv;
+    }
+    LAUNCH_CHECK(h);
+    st = check_dev_status(h, rep, "spd_cg");
+    if (st != SPD_OK) return st;
+    int low = 0, high = 0;
+    IrSummary sm{};
+    spd_status result = cg_ir_core(h, w, n, m, A, lda, B, ldb, X, ldx, o, cs, false, &low, &high, &sm);
+    CUDA_TRY(h, cudaEventRecord(h->e1, s));
+    CUDA_TRY(h, cudaEventSynchronize(h->e1));
+    if (result != SPD_ERR_NO_CONVERGENCE && result != SPD_OK) return result;
+    if (rep) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->e0, h->e1);
+        rep->status = result;
+        rep->iters_low = low;
+        rep->iters_high = high;
+        rep->prec_used = matvec_prec;
+        rep->berr = sm.max_berr;
+        rep->rel_resid = sm.max_rel;
+        rep->time_ms = ms;
+    }
+    return result;
+}
+
+// ---------------------------------------------------------------------------
+// host-buffer convenience entry point
+// ---------------------------------------------------------------------------
+extern "C" spd_status spd_solve_ir_host(spd_handle* h, int n, int m, const double* A_host, int lda,
+                                        const double* B_host, int ldb, double* X_host, int ldx, int prec,
+                                        const spd_opts* opts, spd_report* rep) {
+    if (!h) return SPD_ERR_ARG;
+    if (bad_args(n, m, A_host, lda, B_host, ldb, X_host, ldx))
+        return set_err(h, SPD_ERR_ARG, "spd_solve_ir_host: bad arguments");
+    if (rep) memset(rep, 0, sizeof(*rep));
+    if (n == 0 || m == 0) return SPD_OK;
+    cudaStream_t s = h->stream;
+    double *dA = nullptr, *dB = nullptr, *dX = nullptr;
+    size_t bytesA = sizeof(double) * (size_t)n * n, bytesB = sizeof(double) * (size_t)n * m;
+    CUDA_TRY(h, cudaMallocAsync(&dA, bytesA, s));
+    CUDA_TRY(h, cudaMallocAsync(&dB, bytesB, s));
+    CUDA_TRY(h, cudaMallocAsync(&dX, bytesB, s));
+    auto release = [&]() {
+        cudaFreeAsync(dA, s);
+        cudaFreeAsync(dB, s);
+        cudaFreeAsync(dX, s);
+        cudaStreamSynchronize(s);
+    };
+    cudaError_t e = cudaMemcpy2DAsync(dA, sizeof(double) * n, A_host, sizeof(double) * lda, sizeof(double) * n, n,
+                                      cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(dB, sizeof(double) * n, B_host, sizeof(double) * ldb, sizeof(double) * n, m,
+                              cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        release();
+        return set_err(h, SPD_ERR_CUDA, "spd_solve_ir_host: copy to device: %s", cudaGetErrorString(e));
+    }
+    spd_factor_t* F = nullptr;
+    spd_report fr{};
+    spd_status st = spd_factor(h, n, dA, n, prec, SPD_SCALE_DIAG, &F, &fr);
+    if (st != SPD_OK) {
+        if (rep) *rep = fr;
+        release();
+        return st;
+    }
+    st = spd_solve_ir(h, F, n, m, dA, n, dB, n, dX, n, opts, rep);
+    if (st == SPD_OK || st == SPD_ERR_NO_CONVERGENCE) {
+        e = cudaMemcpy2DAsync(X_host, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, m,
+                              cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "spd_solve_ir_host: copy back: %s", cudaGetErrorString(e));
+    }
+    if (rep) {
+        rep->time_ms += fr.time_ms;
+        rep->prec_used = fr.prec_used;
+    }
+    spd_factor_destroy(F);
+    release();
+    return st;
+}
+
+// ---------------------------------------------------------------------------
+// phase timing
+// ---------------------------------------------------------------------------
+static void prof_clear(spd_handle* h) {
+    for (auto& r : h->prof) {
+        h->ev_pool.push_back(r.a);
+        h->ev_pool.push_back(r.b);
+    }
+    h->prof.clear();
+}
+
+extern "C" spd_status spd_profile_enable(spd_handle* h, int on) {
+    if (!h) return SPD_ERR_ARG;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    prof_clear(h);
+    h->prof_on = on != 0;
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_profile_read(spd_handle* h, int phase, int* launches, double* ms, double* flops,
+                                       double* bytes) {
+    if (!h || phase < 0 || phase >= SPD_PHASE_COUNT) return SPD_ERR_ARG;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    int cnt = 0;
+    double t = 0.0, f = 0.0, b = 0.0;
+    for (auto& r : h->prof) {
+        if (r.phase != phase) continue;
+        float e = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&e, r.a, r.b));
+        ++cnt;
+        t += e;
+        f += r.flops;
+        b += r.bytes;
+    }
+    if (launches) *launches = cnt;
+    if (ms) *ms = t;
+    if (flops) *flops = f;
+    if (bytes) *bytes = b;
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_launch_count(const spd_handle* h, long long* count) {
+    if (!h || !count) return SPD_ERR_ARG;
+    *count = h->launches;
+    return SPD_OK;
+}

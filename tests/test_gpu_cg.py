@@ -1,0 +1,143 @@
+"""GPU parity: Algorithm 2 (CG with iterative refinement) through the C ABI
+against the float64 CPU oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1405_4644_gb300 as spd
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import check, dev_cols, dev_sym, dev_zeros, host  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "table1_n70000.json")
+
+
+def resid_noise(A, X):
+    """Rounding error of evaluating b - A x in float64, per column: the GPU and
+    the oracle sum in different orders, so at a 1e-14 target their residual
+    norms may differ by up to about 2 sqrt(n) u || |A| |x| ||_2."""
+    n = A.shape[0]
+    return 2.0 * np.sqrt(n) * 2.0 ** -53 * np.linalg.norm(np.abs(A) @ np.abs(X), axis=0)
+
+
+@pytest.fixture(scope="module")
+def h():
+    import torch
+    hh = spd.spd_create(torch.cuda.current_stream())
+    yield hh
+    spd.spd_destroy(hh)
+
+
+@pytest.mark.parametrize("mv", ["fp32", "bf16", "fp64"])
+@pytest.mark.parametrize("n,m", [(1, 1), (10, 2), (1024, 1), (700, 5), (513, 20)])
+def test_cg_ir_relative_target(h, mv, n, m):
+    """Relative residual <= 1e-14 (the plain-method configuration) and the
+    oracle's float64 solution within 10 kappa 1e-14."""
+    A = W.gram_shifted(n, seed=0, shift=0.1)
+    x_true = W.gaussian_rhs(n, m, 1)
+    B = A @ x_true
+    X = dev_zeros(n, m)
+    st, rep = spd.spd_cg(h, dev_sym(A), dev_cols(B), X, mv, opts={"tol": 1e-14, "crit": "rel2"})
+    check(h, st)
+    Xg = host(X)
+    r = oracle.residual(A, B, Xg)
+    assert np.all(np.linalg.norm(r, axis=0) <= 1e-14 * np.linalg.norm(B, axis=0) + resid_noise(A, Xg))
+    Xo = oracle.solve(A, B)
+    kappa = np.linalg.cond(A)
+    assert np.max(np.abs(Xg - Xo)) <= 10 * kappa * 1e-14 * np.max(np.abs(Xo))
+    if n > 10 and mv != "fp64":
+        assert rep.iters_high >= 2  # a low-precision inner solve needs a refinement step
+
+
+def test_cg_backward_error_target(h):
+    n, m = 800, 3
+    A = W.gram_shifted(n, seed=4, shift=0.1)
+    B = W.gaussian_rhs(n, m, 2)
+    X = dev_zeros(n, m)
+    st, rep = spd.spd_cg(h, dev_sym(A), dev_cols(B), X, "fp32", opts={"tol": 1e-14, "crit": "berr"})
+    check(h, st)
+    assert oracle.berr(A, B, host(X)) <= 1e-14
+
+
+@pytest.mark.parametrize("d", [1, 2, 4])
+def test_cg_ir_paper_rule_iteration_counts(h, d):
+    """Section 4 rule (absolute ||r||_2 < 1e-5, U[0,1] right-hand sides) on
+    the model covariance: the GPU's low/high counts match the oracle's
+    Algorithm 2 (both with float32 products; summation orders differ)."""
+    n = 3000
+    A = W.model_covariance(n, d)
+    B = W.uniform_rhs(n, 1, 0)
+    X = dev_zeros(n, 1)
+    st, rep = spd.spd_cg(h, dev_sym(A), dev_cols(B), X, "fp32",
+                         opts={"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000})
+    check(h, st)
+    _, lo, hi, fe, ok = oracle.cg_ir(A, B, tol=1e-5, crit="abs2", eta=0.0)
+    assert ok
+    assert np.linalg.norm(oracle.residual(A, B, host(X))) < 1e-5
+    assert abs(rep.iters_low - int(lo[0])) <= max(3, 0.1 * lo[0])
+    assert abs(rep.iters_high - int(hi[0])) <= 1
+
+
+def test_banded_cg_matches_oracle_band(h):
+    n = 3000
+    A = W.model_covariance(n, 4)
+    B = W.uniform_rhs(n, 2, 0)
+    X = dev_zeros(n, 2)
+    st, rep = spd.spd_cg(h, dev_sym(A), dev_cols(B), X, "fp32",
+                         opts={"tol": 1e-5, "crit": "abs2", "eta": 0.0, "band": 16, "maxit_inner": 5000})
+    check(h, st)
+    _, lo, hi, fe, ok = oracle.cg_ir(A, B, band=16, tol=1e-5, crit="abs2", eta=0.0)
+    assert ok
+    assert np.all(np.linalg.norm(oracle.residual(A, B, host(X)), axis=0) < 1e-5)
+    assert abs(rep.iters_low - int(lo.max())) <= max(3, 0.1 * lo.max())
+
+
+def test_jacobi_and_factor_preconditioners(h):
+    n, m = 600, 2
+    A = W.model_covariance(n, 1)
+    B = W.uniform_rhs(n, m, 3)
+    Ad = dev_sym(A)
+    X0 = dev_zeros(n, m)
+    st, rep0 = spd.spd_cg(h, Ad, dev_cols(B), X0, "fp64", opts={"tol": 1e-14, "crit": "rel2"})
+    check(h, st)
+    X1 = dev_zeros(n, m)
+    st, rep1 = spd.spd_cg(h, Ad, dev_cols(B), X1, "fp64", "jacobi", opts={"tol": 1e-14, "crit": "rel2"})
+    check(h, st)
+    st, F, _ = spd.spd_factor(h, Ad, "bf16")
+    check(h, st)
+    X2 = dev_zeros(n, m)
+    st, rep2 = spd.spd_cg(h, Ad, dev_cols(B), X2, "fp64", "factor", F, opts={"tol": 1e-14, "crit": "rel2"})
+    spd.spd_factor_destroy(F)
+    check(h, st)
+    for X in (X0, X1, X2):
+        r = oracle.residual(A, B, host(X))
+        assert np.all(np.linalg.norm(r, axis=0) <= 1e-14 * np.linalg.norm(B, axis=0) + resid_noise(A, host(X)))
+    assert rep2.iters_low < rep1.iters_low <= rep0.iters_low
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("d", [4])
+def test_table1_iteration_band_full_size(h, d):
+    """Table 1 (n = 70000, d = 4, 1 RHS, tolerance 1e-5): the paper's printed
+    low/high counts, within a 25 % band (RNG and summation order differ)."""
+    import torch
+    g = json.load(open(GOLDEN))
+    row = next(r for r in g["rows"] if r[0] == "cg" and r[1] == d and r[2] == 1)
+    n = g["n"]
+    i = torch.arange(n, dtype=torch.float64, device="cuda")
+    k = (i[:, None] - i[None, :]).abs_()
+    A = torch.where(k > 0, 1.0 / k.clamp_min(1.0).pow(d), torch.zeros((), dtype=torch.float64, device="cuda"))
+    del k
+    A.diagonal().copy_(1.0 + torch.sqrt(i + 1.0))
+    B = dev_cols(W.uniform_rhs(n, 1, 0))
+    X = dev_zeros(n, 1)
+    st, rep = spd.spd_cg(h, A, B, X, "fp32", opts={"tol": g["tolerance"], "crit": "abs2", "eta": 0.0,
+                                                   "maxit_inner": 5000})
+    check(h, st)
+    assert abs(rep.iters_low - row[3]) <= 0.25 * row[3]
+    assert abs(rep.iters_high - row[4]) <= 1
