@@ -91,6 +91,10 @@ typedef enum spd_resid {
 
 /* Flags of spd_factor. */
 #define SPD_SCALE_DIAG 1u /* factor D^{-1/2} A D^{-1/2} (D = diag A); default */
+#define SPD_FACTOR_CUDA_CORES 2u /* run the trailing updates of a TF32/BF16/FP16
+                                    factor on the CUDA cores (same rounded
+                                    operands, float32 accumulation): a
+                                    reference engine for validation       */
 
 typedef struct spd_opts {
     double tol;      /* stopping threshold (default 1e-14)                    */
@@ -209,6 +213,17 @@ spd_status spd_residual(spd_handle *h, int n, int m, const double *A, int lda,
 spd_status spd_cg(spd_handle *h, int n, int m, const double *A, int lda, int matvec_prec,
                   int pc, const void *pc_data, const double *B, int ldb, double *X, int ldx,
                   const spd_opts *opts, spd_report *rep);
+
+/* ---- the trailing update as a standalone operation -------------------------
+ * C -= A B^T (step A3 of the factorisation, eq. (cholesky)'s O(n^3) part) on
+ * the tensor cores: A (M x K) and B (N x K) float32 row-major are rounded
+ * (RNE) to `prec` (SPD_PREC_TF32, BF16, FP16 or FP8 -- FP8 multiplies the
+ * operands by 2^8 before rounding, so |entries| <= 1.75 stay in range)
+ * and multiplied with float32 accumulation; C is float32 row-major
+ * (ldc >= N).  lower != 0 (requires A == B, M == N, lda == ldb) updates
+ * only entries with row >= column.  Device pointers; synchronous. */
+spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,
+                           const float *B, int ldb, float *C, int ldc, int lower);
 
 /* ---- phase timing ---------------------------------------------------------
  * Code-phase markers in the spirit of the paper's instrumentation library

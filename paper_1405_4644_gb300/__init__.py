@@ -24,7 +24,7 @@ __all__ = [
     "SPD_ERR_OOM", "SPD_ERR_UNSUPPORTED", "PREC", "SPD_SCALE_DIAG", "SpdOpts", "SpdReport", "SpdError",
     "lib", "colmajor", "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor",
     "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
-    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count",
+    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
@@ -34,12 +34,13 @@ PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
 PC = {"none": 0, "jacobi": 1, "factor": 2}
 SPD_SCALE_DIAG = 1
+SPD_FACTOR_CUDA_CORES = 2
 
 # every symbol include/spd.h declares
 EXPORTED = [
     "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
     "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read",
-    "spd_launch_count",
+    "spd_launch_count", "spd_gemm_update",
 ]
 
 
@@ -97,6 +98,7 @@ def lib():
         "spd_cg": (I, [P, I, I, P, I, I, I, P, P, I, P, I, O, R]),
         "spd_profile_enable": (I, [P, I]),
         "spd_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
+        "spd_gemm_update": (I, [P, I, I, I, I, P, I, P, I, P, I, I]),
         "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     }
@@ -297,3 +299,12 @@ def spd_launch_count(h):
     if st != SPD_OK:
         raise SpdError(st, "spd_launch_count failed")
     return c.value
+
+
+def spd_gemm_update(h, prec, A, B, C, lower=False):
+    """C -= round(A) round(B)^T on the tensor cores; float32 row-major device
+    tensors A (M, K), B (N, K), C (M, N)."""
+    M, K = A.shape
+    N = B.shape[0]
+    return lib().spd_gemm_update(h, _prec(prec), M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
+                                 C.data_ptr(), C.stride(0), 1 if lower else 0)

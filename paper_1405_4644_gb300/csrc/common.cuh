@@ -9,6 +9,7 @@
 #define SPD_LEAF 128   // order of the diagonal blocks factored by one CTA
 #define SPD_SUB 32     // order of the warp-level sub-blocks inside a leaf
 #define SPD_MAXM 4096  // largest right-hand-side count per call
+#define SPD_FP8_SCALE 256.0f  // operand scale of the e4m3 mirror (products carry 2^16)
 
 // Device-side error word: bit flags raised by kernels, read by the host.
 enum : int {
@@ -70,8 +71,8 @@ template <> struct OpConv<__nv_fp8_e4m3> {
 struct Mirror {
     void* ptr;     // n x ld elements of the operand type (nullptr = no mirror)
     long ld;       // leading dimension in elements (row-major)
-    int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3
-    const float* rowscale;  // fp8 only: per-128-row-tile power-of-two scale
+    int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3 (x SPD_FP8_SCALE)
+    const float* unused;
 };
 
 __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, float v) {
@@ -79,11 +80,9 @@ __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, fl
         case 1: ((float*)m.ptr)[r * m.ld + c] = round_tf32(v); break;
         case 2: ((__nv_bfloat16*)m.ptr)[r * m.ld + c] = __float2bfloat16_rn(v); break;
         case 3: ((__half*)m.ptr)[r * m.ld + c] = __float2half_rn(v); break;
-        case 4: {
-            float s = m.rowscale ? m.rowscale[r / SPD_LEAF] : 1.0f;
-            ((__nv_fp8_e4m3*)m.ptr)[r * m.ld + c] = __nv_fp8_e4m3(v * s);
+        case 4:  // fixed power-of-two scale: |entries| <= 1 after diagonal scaling
+            ((__nv_fp8_e4m3*)m.ptr)[r * m.ld + c] = __nv_fp8_e4m3(v * SPD_FP8_SCALE);
             break;
-        }
         default: break;
     }
 }

@@ -1,17 +1,274 @@
-// gemm_tc.cu -- placeholder until the tcgen05 kernel lands: no tensor-core
-// plan, so the factorisation takes the CUDA-core path with the same
-// rounded operands.
+// gemm_tc.cu -- step A3 on the 5th-generation tensor cores: the trailing
+// update C -= A B^T of the blocked Cholesky factorisation (Section 3.1,
+// eq. (cholesky); the O(n^3) part that "stresses the components to their
+// limits").
+//
+// One CTA computes a 128 x 256 tile of C.  Operand tiles (128 rows of A,
+// 256 rows of B, 128 bytes of K each) are fetched by TMA into shared memory
+// in the 128-byte swizzled K-major layout, through a 4-stage mbarrier
+// pipeline: warp 0 (one thread) issues the loads, warp 1 (one thread) issues
+// tcgen05.mma into a 128 x 256 float32 accumulator in tensor memory and
+// frees each stage with tcgen05.commit.  The four warps then read the
+// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows
+// of the tile) and apply C -= scale * acc to float32 C in global memory.
+// Every wait is bounded; a wait that gives up raises SPD_DEV_TIMEOUT.
+#include <cudaTypedefs.h>
+#include <cstring>
 #include "gemm_tc.h"
+#include "tc_ptx.cuh"
 
-struct TcGemm {
-    int unused;
+namespace {
+
+constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int A_STAGE = BM * 128;               // bytes: 128 rows x 128 B
+constexpr int B_STAGE = BN * 128;               // bytes: 256 rows x 128 B
+constexpr int STAGE_BYTES = A_STAGE + B_STAGE;  // 48 KB
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
+constexpr uint32_t TMEM_COLS = 256;
+constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
+
+template <int KIND> struct KindTraits;
+template <> struct KindTraits<0> {  // fp16 / bf16
+    static constexpr int BK = 64, KMMA = 16;
+};
+template <> struct KindTraits<1> {  // tf32
+    static constexpr int BK = 32, KMMA = 8;
+};
+template <> struct KindTraits<2> {  // fp8 e4m3
+    static constexpr int BK = 128, KMMA = 32;
 };
 
-spd_status tc_gemm_create(TcGemm** out, float*, long, void*, long, int, int) {
+template <int KIND>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
+              uint32_t idesc, float scale, DevStatus* st) {
+    constexpr int BK = KindTraits<KIND>::BK;
+    constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    unsigned char* sA = base;
+    unsigned char* sB = base + STAGES * A_STAGE;
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bm = blockIdx.y, bn = blockIdx.x;
+    if (lower && (bm * BM + BM - 1 < bn * BN)) return;  // whole tile above the diagonal
+    if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            tc::mbar_init(&full[s], 1);
+            tc::mbar_init(&empty[s], 1);
+        }
+        tc::mbar_init(accf, 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+        tc::prefetch_tmap(&mapA);
+        tc::prefetch_tmap(&mapB);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, TMEM_COLS);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const int nk = K / BK;
+
+    if (warp == 0) {
+        if (lane == 0) {  // TMA producer
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                const uint32_t ph = (kt / STAGES) & 1u;
+                if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) break;
+                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                tc::tma_load_2d(sA + s * A_STAGE, &mapA, k0 + kt * BK, a_row0 + bm * BM, &full[s]);
+                tc::tma_load_2d(sB + s * B_STAGE, &mapB, k0 + kt * BK, b_row0 + bn * BN, &full[s]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            for (int kt = 0; kt < nk; ++kt) {
+                const int s = kt % STAGES;
+                const uint32_t ph = (kt / STAGES) & 1u;
+                if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) break;
+                tc::fence_after_sync();
+                const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_STAGE));
+                const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_STAGE));
+#pragma unroll
+                for (int k = 0; k < MMA_PER_STAGE; ++k)  // +32 bytes of K = +2 in the address field
+                    tc::mma<KIND>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                tc::mma_commit(&empty[s]);
+            }
+            tc::mma_commit(accf);
+        }
+        __syncwarp();
+    }
+
+    // epilogue: TMEM -> registers -> C -= scale * acc
+    bool ok = tc::mbar_wait(accf, 0, abort_flag, WAIT_NS) && !*abort_flag;
+    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+    tc::fence_after_sync();
+    if (ok) {
+        const int rloc = warp * 32 + lane;
+        const int row = bm * BM + rloc;
+        const int rowmax_warp = bm * BM + warp * 32 + 31;
+        for (int ch = 0; ch < BN / 32; ++ch) {
+            const int col0 = bn * BN + ch * 32;
+            if (col0 >= N) break;                         // warp-uniform
+            if (lower && rowmax_warp < col0) continue;    // warp-uniform: chunk above the diagonal
+            float v[32];
+            tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32, v);
+            if (row < M) {
+                float* crow = C + (long)row * ldc + col0;
+                const bool full_chunk = (col0 + 32 <= N) && !(lower && row < col0 + 31) &&
+                                        ((reinterpret_cast<uintptr_t>(crow) & 15) == 0);
+                if (full_chunk) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 c = reinterpret_cast<float4*>(crow)[q];
+                        c.x -= scale * v[4 * q + 0];
+                        c.y -= scale * v[4 * q + 1];
+                        c.z -= scale * v[4 * q + 2];
+                        c.w -= scale * v[4 * q + 3];
+                        reinterpret_cast<float4*>(crow)[q] = c;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int col = col0 + j;
+                        if (col < N && !(lower && row < col)) crow[j] -= scale * v[j];
+                    }
+                }
+            }
+        }
+    }
+    if (!ok && threadIdx.x == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+int elem_bytes(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
+
+// 2-D map over a row-major (rows x cols, ld elements) operand array with a
+// box of (128 bytes of K) x box_rows, 128-byte swizzle, zero fill.
+bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols, long ld, int box_rows) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    CUtensorMapDataType dt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                             : kind == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                         : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    const int es = elem_bytes(kind);
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+uint32_t idesc_for(int kind) {
+    switch (kind) {
+        case 1: return tc::idesc_f32acc(2, BM, BN);  // tf32
+        case 2: return tc::idesc_f32acc(1, BM, BN);  // bf16
+        case 3: return tc::idesc_f32acc(0, BM, BN);  // fp16
+        default: return tc::idesc_f32acc(0, BM, BN); // e4m3 (kind::f8f6f4)
+    }
+}
+
+void set_attrs() {
+    static bool done = false;
+    if (done) return;
+    done = true;
+    cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+}
+
+}  // namespace
+
+struct TcGemm {
+    CUtensorMap mapA, mapB;  // box heights 128 (A) and 256 (B)
+    float* C;
+    long ldc;
+    int kind;
+};
+
+float tc_fp8_scale() { return SPD_FP8_SCALE; }
+
+spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
+                               long b_ld, long cols, float* C, long ldc, int kind) {
     *out = nullptr;
-    return SPD_ERR_UNSUPPORTED;
+    if (kind < 1 || kind > 4) return SPD_ERR_UNSUPPORTED;
+    TcGemm* g = new TcGemm();
+    memset(g, 0, sizeof(*g));
+    if (!make_map(&g->mapA, Ah, kind, a_rows, cols, a_ld, BM) || !make_map(&g->mapB, Bh, kind, b_rows, cols, b_ld, BN)) {
+        delete g;
+        return SPD_ERR_UNSUPPORTED;
+    }
+    g->C = C;
+    g->ldc = ldc;
+    g->kind = kind;
+    set_attrs();
+    *out = g;
+    return SPD_OK;
 }
-spd_status tc_gemm_run(TcGemm*, cudaStream_t, int, int, int, int, int, int, int, DevStatus*) {
-    return SPD_ERR_UNSUPPORTED;
+
+spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n) {
+    return tc_gemm_create_maps(out, Wh, n, ldh, Wh, n, ldh, n, W, ldw, kind);
 }
-void tc_gemm_destroy(TcGemm*) {}
+
+spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
+                          int k0, int lower, DevStatus* st) {
+    const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
+    if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
+    const uint32_t idesc = idesc_for(g->kind);
+    switch (g->kind) {
+        case 1:
+            k_gemm_tc<1><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
+                                                       idesc, scale, st);
+            break;
+        case 4:
+            k_gemm_tc<2><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
+                                                       idesc, scale, st);
+            break;
+        default:
+            k_gemm_tc<0><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
+                                                       idesc, scale, st);
+    }
+    return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;
+}
+
+spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
+                       DevStatus* st) {
+    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st);
+}
+
+void tc_gemm_destroy(TcGemm* g) { delete g; }

@@ -15,3 +15,8 @@ spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, 
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
                        DevStatus* st);
 void tc_gemm_destroy(TcGemm* g);
+// General form: separate operand arrays (rows x cols, ld elements each).
+spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
+                               long b_ld, long cols, float* C, long ldc, int kind);
+spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
+                          int k0, int lower, DevStatus* st);

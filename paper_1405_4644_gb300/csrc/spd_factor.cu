@@ -206,7 +206,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
 
         FCtx c{h, F, Mirror{F->Wh, F->ldh, kind, nullptr}, nullptr};
         TcGemm* tc = nullptr;
-        if (kind) {
+        if (kind && !(flags & SPD_FACTOR_CUDA_CORES)) {
             st = tc_gemm_create(&tc, F->W, F->ldw, F->Wh, F->ldh, kind, n);
             if (st == SPD_OK) c.tc = tc;
             else if (st != SPD_ERR_UNSUPPORTED) return fail(set_err(h, st, "tensor-core plan failed"));

@@ -1,0 +1,68 @@
+// spd_gemm.cu -- the tensor-core trailing update exposed as a standalone
+// C-ABI operation (operands rounded into tensor-core mirrors first).
+#include "engine.cuh"
+#include "gemm_tc.h"
+
+namespace {
+
+// out[r][k] = round(A[r][k]) for k < K, 0 for K <= k < Kp  (row-major, ldo)
+__global__ void k_to_mirror(const float* __restrict__ A, long lda, int rows, int K, int Kp, void* out, long ldo,
+                            int kind) {
+    long total = (long)rows * Kp;
+    Mirror m{out, ldo, kind, nullptr};
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        long r = e / Kp, k = e - r * Kp;
+        float v = (k < K) ? A[r * lda + k] : 0.f;
+        mirror_store(m, r, k, v);
+    }
+}
+
+int kind_of(int prec) {
+    switch (prec) {
+        case SPD_PREC_TF32: return 1;
+        case SPD_PREC_BF16: return 2;
+        case SPD_PREC_FP16: return 3;
+        case SPD_PREC_FP8: return 4;
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int K, const float* A, int lda,
+                                      const float* B, int ldb, float* C, int ldc, int lower) {
+    if (!h) return SPD_ERR_ARG;
+    const int kind = kind_of(prec);
+    if (!kind) return set_err(h, SPD_ERR_UNSUPPORTED, "spd_gemm_update: precision must be TF32, BF16, FP16 or FP8");
+    if (M < 0 || N < 0 || K < 0 || (M > 0 && K > 0 && (!A || lda < K)) || (N > 0 && K > 0 && (!B || ldb < K)) ||
+        (M > 0 && N > 0 && (!C || ldc < N)) || (lower && (M != N || A != B || lda != ldb)))
+        return set_err(h, SPD_ERR_ARG, "spd_gemm_update: bad arguments");
+    if (M == 0 || N == 0 || K == 0) return SPD_OK;
+    const int es = kind == 1 ? 4 : kind == 4 ? 1 : 2;
+    const long Kp = round_up(K, 128);
+    const long ldo = round_up(Kp, 64);
+    WsPlan p;
+    size_t oa = p.add<unsigned char>((size_t)M * ldo * es);
+    size_t ob = lower ? oa : p.add<unsigned char>((size_t)N * ldo * es);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    void* Ah = ws_at<unsigned char>(h, oa);
+    void* Bh = ws_at<unsigned char>(h, ob);
+    ProfScope ps(h, SPD_PHASE_TRAILING, 2.0 * M * (double)N * K,
+                 8.0 * M * (double)N + (double)es * K * (lower ? M : (double)M + N));
+    cudaStream_t s = h->stream;
+    ++h->launches, k_to_mirror<<<grid_for((long)M * Kp, 256, 8 * h->sms), 256, 0, s>>>(A, lda, M, K, (int)Kp, Ah, ldo,
+                                                                                        kind);
+    if (!lower)
+        ++h->launches, k_to_mirror<<<grid_for((long)N * Kp, 256, 8 * h->sms), 256, 0, s>>>(B, ldb, N, K, (int)Kp, Bh,
+                                                                                            ldo, kind);
+    LAUNCH_CHECK(h);
+    TcGemm* g = nullptr;
+    st = tc_gemm_create_maps(&g, Ah, M, ldo, Bh, N, ldo, Kp, C, ldc, kind);
+    if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: tensor map creation failed");
+    ++h->launches;
+    st = tc_gemm_launch(g, s, C, ldc, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
+    tc_gemm_destroy(g);
+    if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: launch failed");
+    return check_dev_status(h, nullptr, "spd_gemm_update");
+}

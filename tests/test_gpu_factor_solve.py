@@ -240,3 +240,25 @@ def test_iterref_planted_perturbation_on_gpu(h):
     check(h, st)
     assert rep.fell_back == 1
     assert oracle.berr(A, B, host(X)) <= 1e-14
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("n", [257, 1000, 2049])
+def test_tensor_core_and_cuda_core_factors_agree(h, prec, n):
+    """The tcgen05 trailing update and the CUDA-core reference engine use the
+    same rounded operands; their factors differ only by float32 summation
+    order."""
+    A = W.gram_shifted(n, seed=n + 1, shift=0.5)
+    Ad = dev_sym(A)
+    st, F1, _ = spd.spd_factor(h, Ad, prec)
+    check(h, st)
+    st, F2, _ = spd.spd_factor(h, Ad, prec, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_CUDA_CORES)
+    check(h, st)
+    try:
+        L1, _, _ = factor_L(F1)
+        L2, _, _ = factor_L(F2)
+    finally:
+        spd.spd_factor_destroy(F1)
+        spd.spd_factor_destroy(F2)
+    kappa = np.linalg.cond(L2) ** 2
+    assert np.max(np.abs(L1 - L2)) <= 64 * kappa * n * 2.0 ** -24

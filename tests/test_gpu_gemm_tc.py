@@ -1,0 +1,82 @@
+"""GPU parity of the tensor-core trailing update (step A3, tcgen05 + TMA)
+against the oracle's float64 product of the same rounded operands."""
+import numpy as np
+import pytest
+
+import paper_1405_4644_gb300 as spd
+from oracle.precision import ROUND
+
+pytestmark = pytest.mark.gpu
+
+from tests.gpu_util import DEV, check  # noqa: E402
+
+FP8_SCALE = 256.0
+
+
+@pytest.fixture(scope="module")
+def h():
+    import torch
+    hh = spd.spd_create(torch.cuda.current_stream())
+    yield hh
+    spd.spd_destroy(hh)
+
+
+def rounded(x, prec):
+    if prec == "fp8":  # operands carry a 2^8 scale into e4m3
+        return ROUND["fp8"](x * FP8_SCALE) / FP8_SCALE
+    return ROUND[prec](ROUND["fp32"](x))
+
+
+def run(h, prec, A, B, C0, lower=False):
+    import torch
+    At = torch.from_numpy(A.astype(np.float32)).to(DEV)
+    Bt = At if lower else torch.from_numpy(B.astype(np.float32)).to(DEV)
+    Ct = torch.from_numpy(C0.astype(np.float32)).to(DEV)
+    check(h, spd.spd_gemm_update(h, prec, At, Bt, Ct, lower))
+    return Ct.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "fp8"])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (128, 256, 128), (300, 500, 200), (1000, 1000, 1024),
+                                   (37, 290, 1), (513, 129, 640)])
+def test_gemm_update_matches_rounded_product(h, prec, M, N, K):
+    g = np.random.default_rng(M * 7 + N * 3 + K)
+    scale = 1.0 if prec == "fp8" else 2.0
+    A = g.uniform(-1, 1, (M, K)) * scale
+    B = g.uniform(-1, 1, (N, K)) * scale
+    C0 = g.standard_normal((M, N)).astype(np.float32).astype(np.float64)
+    Ar, Br = rounded(A, prec), rounded(B, prec)
+    ref = C0 - Ar @ Br.T
+    got = run(h, prec, A, B, C0)
+    bound = 4 * K * 2.0 ** -23 * (np.abs(Ar) @ np.abs(Br).T) + 2.0 ** -22 * np.abs(C0) + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+    if K >= 64:  # the operands really were rounded to the low-precision type
+        A32, B32 = rounded(A, "fp32"), rounded(B, "fp32")
+        unrounded = C0 - A32 @ B32.T
+        if prec != "tf32" or K >= 128:
+            assert np.max(np.abs(got - unrounded)) > 8 * np.max(err)
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16"])
+@pytest.mark.parametrize("M,K", [(256, 128), (700, 384)])
+def test_gemm_update_lower_triangle(h, prec, M, K):
+    g = np.random.default_rng(M + K)
+    A = g.uniform(-1, 1, (M, K))
+    C0 = g.standard_normal((M, M)).astype(np.float32).astype(np.float64)
+    Ar = rounded(A, prec)
+    ref = C0 - Ar @ Ar.T
+    got = run(h, prec, A, None, C0, lower=True)
+    iu = np.triu_indices(M, 1)
+    assert np.array_equal(got[iu], C0[iu])  # strictly upper part untouched
+    il = np.tril_indices(M)
+    bound = 4 * K * 2.0 ** -23 * (np.abs(Ar) @ np.abs(Ar).T) + 2.0 ** -22 * np.abs(C0)
+    assert np.all(np.abs(got[il] - ref[il]) <= bound[il])
+
+
+def test_gemm_update_rejects_bad_arguments(h):
+    import torch
+    A = torch.zeros(8, 8, dtype=torch.float32, device=DEV)
+    assert spd.spd_gemm_update(h, "fp32", A, A, A) == spd.SPD_ERR_UNSUPPORTED
+    assert spd.lib().spd_gemm_update(h, spd.PREC["bf16"], 8, 8, 8, A.data_ptr(), 4, A.data_ptr(), 8,
+                                     A.data_ptr(), 8, 0) == spd.SPD_ERR_ARG
