@@ -233,13 +233,14 @@ spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const f
  * statistics; reading synchronises the stream and sums the event times. */
 typedef enum spd_phase {
     SPD_PHASE_CONVERT = 0,  /* A0: scaling + conversion                  */
-    SPD_PHASE_LEAF = 1,     /* A1/A2: diagonal-block factor, panel solve */
+    SPD_PHASE_LEAF = 1,     /* A1: diagonal-block factorisations         */
     SPD_PHASE_TRAILING = 2, /* A3: trailing updates (GEMM/SYRK)          */
     SPD_PHASE_SOLVE = 3,    /* A4: low-precision triangular solves       */
     SPD_PHASE_RESID = 4,    /* A5/C3: float64 residual / products        */
     SPD_PHASE_MATVEC = 5,   /* C1: low-precision CG products             */
     SPD_PHASE_VECTOR = 6,   /* A6/C2: float64 vector updates and dots    */
-    SPD_PHASE_COUNT = 7
+    SPD_PHASE_PANEL = 7,    /* A2: panel triangular solves (leaf TRSM)   */
+    SPD_PHASE_COUNT = 8
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

@@ -275,7 +275,7 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
     return st, rep
 
 
-PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector"]
+PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel"]
 
 
 def spd_profile_enable(h, on=True):

@@ -31,6 +31,9 @@ struct spd_handle {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     void* ws = nullptr;         // grow-only device workspace
     size_t ws_bytes = 0;
+    int* ready = nullptr;       // block flags of the persistent triangular sweeps
+    int ready_n = 0;
+    int epoch = 0;              // last flag value handed out
 };
 
 struct spd_factor_t {
@@ -43,8 +46,8 @@ struct spd_factor_t {
     void* Wh = nullptr;        // tensor-core operand mirror
     long ldh = 0;
     double* d = nullptr;       // scaling
-    float* Dinv = nullptr;     // 32x32 diagonal sub-block inverses
-    double* Dinv64 = nullptr;
+    double* Dinv64 = nullptr;  // float64 factor: 32x32 diagonal sub-block inverses
+    float* LinvT = nullptr;    // float32 factor: (L_JJ^{-1})^T of every 128x128 block
     int nblk128 = 0;
 };
 

@@ -32,7 +32,7 @@ constexpr size_t potrf_leaf_smem() {
 // also written to the operand mirror.  A non-positive pivot raises
 // SPD_DEV_BREAKDOWN with the 1-based global column in st->info.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potrf_leaf(T* __restrict__ W, long ldw, int k, int nb,
+__global__ void __launch_bounds__(256, 1) k_potrf_leaf(T* __restrict__ W, long ldw, int k, int nb,
                                                     T* __restrict__ Dinv, Mirror mir, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);  // [128][129]
@@ -65,12 +65,13 @@ __global__ void __launch_bounds__(256) k_potrf_leaf(T* __restrict__ W, long ldw,
                 }
                 T dj = dsqrt(piv);
                 T inv = T(1) / dj;
-                if (lane == j) a[j] = dj;
-                else if (lane > j) a[j] *= inv;
+                a[j] = (lane == j) ? dj : (lane > j ? a[j] * inv : a[j]);
 #pragma unroll
-                for (int l = j + 1; l < 32; ++l) {
-                    T t = __shfl_sync(0xffffffffu, a[j], l);
-                    if (lane >= l) a[l] -= a[j] * t;
+                for (int l = 0; l < 32; ++l) {  // constant bounds keep a[] in registers
+                    if (l > j) {
+                        T t = __shfl_sync(0xffffffffu, a[j], l);
+                        a[l] = (lane >= l) ? a[l] - a[j] * t : a[l];
+                    }
                 }
             }
 #pragma unroll
@@ -85,10 +86,12 @@ __global__ void __launch_bounds__(256) k_potrf_leaf(T* __restrict__ W, long ldw,
             T x[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
+                const T* li = S + (o + i) * LDS_LEAF + o;
                 T s = (i == lane) ? T(1) : T(0);
 #pragma unroll
-                for (int l = 0; l < i; ++l) s -= S[(o + i) * LDS_LEAF + o + l] * x[l];
-                x[i] = s / S[(o + i) * LDS_LEAF + o + i];
+                for (int l = 0; l < 32; ++l)
+                    if (l < i) s -= li[l] * x[l];
+                x[i] = s / li[i];
             }
             T* Dg = Dinv + (long)((k + o) / 32) * 1024;
 #pragma unroll

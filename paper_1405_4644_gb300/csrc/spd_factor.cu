@@ -12,6 +12,7 @@
 #include "engine.cuh"
 #include "k_convert.cuh"
 #include "k_leaf.cuh"
+#include "k_leaf32.cuh"
 #include "k_gemm_simt.cuh"
 #include "gemm_tc.h"
 
@@ -24,21 +25,19 @@ struct FCtx {
     TcGemm* tc;   // tensor-core GEMM plan (nullptr: CUDA cores)
 };
 
-template <typename T> T* wptr(spd_factor_t* F);
-template <> float* wptr<float>(spd_factor_t* F) { return F->W; }
-template <> double* wptr<double>(spd_factor_t* F) { return F->W64; }
-template <typename T> T* dinvptr(spd_factor_t* F);
-template <> float* dinvptr<float>(spd_factor_t* F) { return F->Dinv; }
-template <> double* dinvptr<double>(spd_factor_t* F) { return F->Dinv64; }
 
-template <typename T> constexpr int rb_of() { return sizeof(T) == 4 ? 64 : 32; }
 
 template <typename T>
 spd_status leaf_potrf(FCtx& c, int k, int nb) {
     spd_factor_t* F = c.F;
     ProfScope ps(c.h, SPD_PHASE_LEAF, (double)nb * nb * nb / 3.0, (double)nb * nb * sizeof(T));
-    size_t smem = potrf_leaf_smem<T>();
-    ++(c.h)->launches, k_potrf_leaf<T><<<1, 256, smem, c.h->stream>>>(wptr<T>(F), F->ldw, k, nb, dinvptr<T>(F), c.mir, c.h->dst);
+    if constexpr (sizeof(T) == 8) {
+        ++(c.h)->launches, k_potrf_leaf<double><<<1, 256, potrf_leaf_smem<double>(), c.h->stream>>>(
+            F->W64, F->ldw, k, nb, F->Dinv64, c.mir, c.h->dst);
+    } else {
+        ++(c.h)->launches, k_potrf_leaf32<<<1, 256, potrf_leaf32_smem(), c.h->stream>>>(F->W, F->ldw, k, nb,
+                                                                                          F->LinvT, c.mir, c.h->dst);
+    }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
 }
@@ -46,11 +45,14 @@ spd_status leaf_potrf(FCtx& c, int k, int nb) {
 template <typename T>
 spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
     spd_factor_t* F = c.F;
-    ProfScope ps(c.h, SPD_PHASE_LEAF, (double)m * kb * kb, 2.0 * m * kb * sizeof(T));
-    constexpr int RB = rb_of<T>();
-    size_t smem = trsm_leaf_smem<T, RB>();
-    ++(c.h)->launches, k_trsm_leaf<T, RB><<<ceil_div(m, RB), 256, smem, c.h->stream>>>(wptr<T>(F), F->ldw, r0, m, c0, kb,
-                                                                    dinvptr<T>(F), c.mir, c.h->dst);
+    ProfScope ps(c.h, SPD_PHASE_PANEL, (double)m * kb * kb, 2.0 * m * kb * sizeof(T));
+    if constexpr (sizeof(T) == 8) {
+        ++(c.h)->launches, k_trsm_leaf<double, 32><<<ceil_div(m, 32), 256, trsm_leaf_smem<double, 32>(), c.h->stream>>>(
+            F->W64, F->ldw, r0, m, c0, kb, F->Dinv64, c.mir, c.h->dst);
+    } else {
+        ++(c.h)->launches, k_trsm_leaf32<<<ceil_div(m, 64), 256, trsm_leaf32_smem(), c.h->stream>>>(
+            F->W, F->ldw, r0, m, c0, F->LinvT, c.mir, c.h->dst);
+    }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
 }
@@ -140,7 +142,7 @@ void free_factor(spd_factor_t* F) {
     cudaFree(F->W64);
     cudaFree(F->Wh);
     cudaFree(F->d);
-    cudaFree(F->Dinv);
+    cudaFree(F->LinvT);
     cudaFree(F->Dinv64);
     delete F;
 }
@@ -178,7 +180,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (e == cudaSuccess) e = cudaMalloc(&F->Dinv64, sizeof(double) * 4096 * std::max(F->nblk128, 1));
     } else if (e == cudaSuccess) {
         e = cudaMalloc(&F->W, sizeof(float) * std::max<size_t>(nW, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv, sizeof(float) * 4096 * std::max(F->nblk128, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&F->LinvT, sizeof(float) * 128 * 128 * std::max(F->nblk128, 1));
         if (e == cudaSuccess && kind) {
             F->ldh = F->ldw;
             e = cudaMalloc(&F->Wh, mirror_elem(kind) * std::max<size_t>(nW, 1));
@@ -296,10 +298,9 @@ static void setup_leaf_attrs() {
     static bool done = false;
     if (done) return;
     done = true;
-    cudaFuncSetAttribute(k_potrf_leaf<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<float>());
+    cudaFuncSetAttribute(k_potrf_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf32_smem());
     cudaFuncSetAttribute(k_potrf_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<double>());
-    cudaFuncSetAttribute(k_trsm_leaf<float, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)trsm_leaf_smem<float, 64>());
+    cudaFuncSetAttribute(k_trsm_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_leaf32_smem());
     cudaFuncSetAttribute(k_trsm_leaf<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)trsm_leaf_smem<double, 32>());
 }

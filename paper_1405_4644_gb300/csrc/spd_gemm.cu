@@ -48,8 +48,6 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
     if (st != SPD_OK) return st;
     void* Ah = ws_at<unsigned char>(h, oa);
     void* Bh = ws_at<unsigned char>(h, ob);
-    ProfScope ps(h, SPD_PHASE_TRAILING, 2.0 * M * (double)N * K,
-                 8.0 * M * (double)N + (double)es * K * (lower ? M : (double)M + N));
     cudaStream_t s = h->stream;
     ++h->launches, k_to_mirror<<<grid_for((long)M * Kp, 256, 8 * h->sms), 256, 0, s>>>(A, lda, M, K, (int)Kp, Ah, ldo,
                                                                                         kind);
@@ -61,7 +59,12 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
     st = tc_gemm_create_maps(&g, Ah, M, ldo, Bh, N, ldo, Kp, C, ldc, kind);
     if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: tensor map creation failed");
     ++h->launches;
-    st = tc_gemm_launch(g, s, C, ldc, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
+    {
+        const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+        ProfScope ps(h, SPD_PHASE_TRAILING, 2.0 * celems * K,
+                     8.0 * celems + (double)es * Kp * (lower ? M : (double)M + N));
+        st = tc_gemm_launch(g, s, C, ldc, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
+    }
     tc_gemm_destroy(g);
     if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: launch failed");
     return check_dev_status(h, nullptr, "spd_gemm_update");

@@ -4,6 +4,7 @@
 #include "engine.cuh"
 #include "k_convert.cuh"
 #include "k_solve.cuh"
+#include "k_trsv32.cuh"
 #include "k_resid.cuh"
 #include "k_cg.cuh"
 
@@ -59,6 +60,7 @@ extern "C" spd_status spd_destroy(spd_handle* h) {
     cudaFreeHost(h->pinned);
     cudaEventDestroy(h->e0);
     cudaEventDestroy(h->e1);
+    cudaFree(h->ready);
     for (auto& r : h->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
@@ -175,6 +177,59 @@ spd_status lp_sweeps(spd_handle* h, const T* W, long ldw, const T* Dinv, int n, 
     return SPD_OK;
 }
 
+template <int MC>
+spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, int c0, int mc) {
+    static int max_ctas[2] = {0, 0};
+    const size_t smem = trsv32_smem<MC>();
+    auto fwd = k_trsv32<MC, true>;
+    auto bwd = k_trsv32<MC, false>;
+    static bool attrs = false;
+    if (!attrs) {
+        attrs = true;
+        cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd, 256, smem);
+        max_ctas[0] = std::max(1, per_sm) * h->sms;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd, 256, smem);
+        max_ctas[1] = std::max(1, per_sm) * h->sms;
+    }
+    const int NB = ceil_div(n, 128);
+    if (h->ready_n < NB) {
+        if (h->ready) CUDA_TRY(h, cudaFree(h->ready));
+        h->ready = nullptr;
+        CUDA_TRY(h, cudaMalloc(&h->ready, sizeof(int) * NB));
+        CUDA_TRY(h, cudaMemsetAsync(h->ready, 0, sizeof(int) * NB, h->stream));
+        h->ready_n = NB;
+        h->epoch = 0;
+    }
+    for (int dir = 0; dir < 2; ++dir) {
+        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, Y, c0, mc, h->ready, ++h->epoch, h->dst};
+        void* args[] = {&a};
+        const int grid = std::min(NB, max_ctas[dir]);
+        ++h->launches;
+        CUDA_TRY(h, cudaLaunchCooperativeKernel(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(grid),
+                                                dim3(256), args, smem, h->stream));
+    }
+    return SPD_OK;
+}
+
+// Y <- (L L^T)^{-1} Y for a float32 factor (n x m, ld n).
+spd_status lp_sweeps32(spd_handle* h, const spd_factor_t* F, int n, int m, float* Y) {
+    ProfScope ps(h, SPD_PHASE_SOLVE, 2.0 * n * (double)n * m, 4.0 * n * (double)n);
+    for (int c0 = 0; c0 < m; c0 += 16) {
+        const int mc = std::min(16, m - c0);
+        spd_status st;
+        if (mc == 1) st = trsv32_pass<1>(h, F, Y, n, c0, mc);
+        else if (mc <= 2) st = trsv32_pass<2>(h, F, Y, n, c0, mc);
+        else if (mc <= 4) st = trsv32_pass<4>(h, F, Y, n, c0, mc);
+        else if (mc <= 8) st = trsv32_pass<8>(h, F, Y, n, c0, mc);
+        else st = trsv32_pass<16>(h, F, Y, n, c0, mc);
+        if (st != SPD_OK) return st;
+    }
+    return SPD_OK;
+}
+
 // X = d .* (L^{-T} L^{-1} (d .* R))  (mode 0)  or  X += ... on unfrozen
 // columns (mode 1).  Y is scratch of n*m elements of the factor's type.
 spd_status lp_apply(spd_handle* h, const spd_factor_t* F, int n, int m, const double* R, long ldr, void* Y,
@@ -193,7 +248,7 @@ spd_status lp_apply(spd_handle* h, const spd_factor_t* F, int n, int m, const do
         float* y = static_cast<float*>(Y);
         ++(h)->launches, k_scale_to<float><<<g, 256, 0, s>>>(R, ldr, F->d, n, m, y);
         LAUNCH_CHECK(h);
-        st = lp_sweeps<float>(h, F->W, F->ldw, F->Dinv, n, m, y);
+        st = lp_sweeps32(h, F, n, m, y);
         if (st != SPD_OK) return st;
         ++(h)->launches, k_apply_correction<float><<<g, 256, 0, s>>>(X, ldx, F->d, y, n, m, frozen, mode);
     }
@@ -204,7 +259,7 @@ spd_status lp_apply(spd_handle* h, const spd_factor_t* F, int n, int m, const do
 }  // namespace
 
 spd_status factor_apply_scaled_f32(spd_handle* h, const spd_factor_t* F, float* y) {
-    return lp_sweeps<float>(h, F->W, F->ldw, F->Dinv, F->n, 1, y);
+    return lp_sweeps32(h, F, F->n, 1, y);
 }
 
 namespace {
