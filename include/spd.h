@@ -49,7 +49,9 @@ typedef enum spd_status {
     SPD_ERR_TIMEOUT = 4,        /* a bounded device-side wait expired          */
     SPD_ERR_CUDA = 5,           /* a CUDA runtime call failed                  */
     SPD_ERR_OOM = 6,            /* device allocation failed                    */
-    SPD_ERR_UNSUPPORTED = 7     /* precision / mode not available              */
+    SPD_ERR_UNSUPPORTED = 7,    /* precision / mode not available              */
+    SPD_ERR_SCRATCH = 8         /* problem too large for spd_residual_static's
+                                   fixed scratch array                         */
 } spd_status;
 
 /* Precision of the low-precision work (Section 3.1, "~" quantities).
@@ -198,6 +200,24 @@ spd_status spd_factor_solve(spd_handle *h, const spd_factor_t *F, int n, int m,
 spd_status spd_residual(spd_handle *h, int n, int m, const double *A, int lda,
                         const double *B, int ldb, const double *X, int ldx,
                         double *R, int ldr, double *colnorms);
+
+/* The same float64 residual and norms as spd_residual, for callers that may
+ * not allocate device memory at all (host callbacks, allocator hooks,
+ * processes with a fixed memory budget, real-time loops).  It takes no
+ * handle and calls no allocator: its partial sums live in a fixed 16 MiB
+ * scratch array compiled into the library, which every GPU that loads the
+ * library keeps until exit.  Limit: n*m + 3*m*ceil(n/256) float64 values
+ * must fit in that array (n*m up to about 2.09 million); larger problems
+ * return SPD_ERR_SCRATCH.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make it
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (no part of it has to start at zero); calls that
+ * overlap on the GPU race on it and must be serialised by the caller.
+ * Ordered on `stream` (a cudaStream_t, NULL = legacy default stream);
+ * synchronous.  This entry point has no counterpart in the paper. */
+spd_status spd_residual_static(void *stream, int n, int m, const double *A, int lda,
+                               const double *B, int ldb, const double *X, int ldx, double *R,
+                               int ldr, double *colnorms);
 
 /* ---- Algorithm 2: CG with iterative refinement ---------------------------
  * Outer ("high") steps: r = B - A X in float64, stop when opts->crit/tol

@@ -24,11 +24,12 @@ __all__ = [
     "SPD_ERR_OOM", "SPD_ERR_UNSUPPORTED", "PREC", "SPD_SCALE_DIAG", "SpdOpts", "SpdReport", "SpdError",
     "lib", "colmajor", "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor",
     "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
-    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update",
+    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
 SPD_ERR_TIMEOUT, SPD_ERR_CUDA, SPD_ERR_OOM, SPD_ERR_UNSUPPORTED = 4, 5, 6, 7
+SPD_ERR_SCRATCH = 8
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto": 6}
 PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
@@ -40,7 +41,7 @@ SPD_FACTOR_CUDA_CORES = 2
 EXPORTED = [
     "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
     "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read",
-    "spd_launch_count", "spd_gemm_update",
+    "spd_launch_count", "spd_gemm_update", "spd_residual_static",
 ]
 
 
@@ -99,6 +100,7 @@ def lib():
         "spd_profile_enable": (I, [P, I]),
         "spd_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "spd_gemm_update": (I, [P, I, I, I, I, P, I, P, I, P, I, I]),
+        "spd_residual_static": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
         "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     }
@@ -308,3 +310,13 @@ def spd_gemm_update(h, prec, A, B, C, lower=False):
     N = B.shape[0]
     return lib().spd_gemm_update(h, _prec(prec), M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                  C.data_ptr(), C.stride(0), 1 if lower else 0)
+
+
+def spd_residual_static(stream, A, B, X, R, colnorms=None):
+    """R = B - A X through the allocation-free entry point (fixed scratch)."""
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = colmajor(B)
+    pX, ldx, _, _ = colmajor(X)
+    pR, ldr, _, _ = colmajor(R)
+    pc = colnorms.data_ptr() if colnorms is not None else None
+    return lib().spd_residual_static(_stream_ptr(stream), n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
