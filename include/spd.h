@@ -234,6 +234,42 @@ spd_status spd_cg(spd_handle *h, int n, int m, const double *A, int lda, int mat
                   int pc, const void *pc_data, const double *B, int ldb, double *X, int ldx,
                   const spd_opts *opts, spd_report *rep);
 
+/* ---- batched solves ----------------------------------------------------------
+ * Many independent systems A_i x_i = b_i (1 <= n_i <= 512, one right-hand
+ * side each) solved in ONE persistent launch, replayed from a CUDA graph.
+ * Each CTA takes whole systems from a shared counter over the systems
+ * sorted by decreasing n, so results do not depend on the schedule.
+ *   SPD_BATCH_CHOL_IR     Algorithm 1 per system: scaled Cholesky in float32
+ *                         (with the trailing-update operands rounded to
+ *                         `prec`: FP32, BF16 or FP16), float32 triangular
+ *                         solves, float64 residual and update; stops at
+ *                         opts->tol on the normwise backward error (plus
+ *                         opts->polish sweeps), at most opts->maxit sweeps.
+ *   SPD_BATCH_PCG_JACOBI  conjugate gradients in float64 with M = diag(A)^-1,
+ *                         x0 = 0, at most opts->maxit_inner steps.
+ * spd_batch_create copies the descriptors (host arrays of DEVICE pointers:
+ * A_i column-major with lda_i, b_i, x_i) into a plan; the plan may be
+ * solved any number of times (the buffers' contents may change between
+ * solves, the pointers may not).  The first solve of a method times the
+ * CTA-size candidates (256, 512 threads) and keeps the fastest.  Per-system
+ * results go to the optional host arrays status/berr/iters (count each);
+ * summary gets the worst backward error and the device time of the launch.
+ * Returns SPD_ERR_NOT_SPD if any system broke down, SPD_ERR_NO_CONVERGENCE
+ * if any missed the tolerance (per-system status tells which). */
+#define SPD_BATCH_CHOL_IR 0
+#define SPD_BATCH_PCG_JACOBI 1
+typedef struct spd_batch spd_batch;
+spd_status spd_batch_create(spd_handle *h, int count, const int *n, const double *const *A,
+                            const int *lda, const double *const *B, double *const *X,
+                            spd_batch **plan);
+spd_status spd_batch_solve(spd_batch *plan, int method, int prec, const spd_opts *opts,
+                           spd_report *summary, int *status, double *berr, int *iters);
+/* Tuned CTA size (0 before the first solve), CTA count and the timed
+ * candidates (ms for 256 and 512 threads; tune_ms may be NULL). */
+spd_status spd_batch_info(const spd_batch *plan, int method, int *threads_per_cta, int *ctas,
+                          float *tune_ms);
+spd_status spd_batch_destroy(spd_batch *plan);
+
 /* ---- the trailing update as a standalone operation -------------------------
  * C -= A B^T (step A3 of the factorisation, eq. (cholesky)'s O(n^3) part) on
  * the tensor cores: A (M x K) and B (N x K) float32 row-major are rounded
@@ -260,7 +296,8 @@ typedef enum spd_phase {
     SPD_PHASE_MATVEC = 5,   /* C1: low-precision CG products             */
     SPD_PHASE_VECTOR = 6,   /* A6/C2: float64 vector updates and dots    */
     SPD_PHASE_PANEL = 7,    /* A2: panel triangular solves (leaf TRSM)   */
-    SPD_PHASE_COUNT = 8
+    SPD_PHASE_BATCH = 8,    /* B1: persistent batched solves             */
+    SPD_PHASE_COUNT = 9
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

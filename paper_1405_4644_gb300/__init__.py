@@ -24,7 +24,8 @@ __all__ = [
     "SPD_ERR_OOM", "SPD_ERR_UNSUPPORTED", "PREC", "SPD_SCALE_DIAG", "SpdOpts", "SpdReport", "SpdError",
     "lib", "colmajor", "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor",
     "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
-    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static",
+    "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "BATCH",
+    "spd_batch_create", "spd_batch_solve", "spd_batch_info", "spd_batch_destroy",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
@@ -34,6 +35,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto":
 PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
 PC = {"none": 0, "jacobi": 1, "factor": 2}
+BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
 
@@ -41,7 +43,8 @@ SPD_FACTOR_CUDA_CORES = 2
 EXPORTED = [
     "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
     "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read",
-    "spd_launch_count", "spd_gemm_update", "spd_residual_static",
+    "spd_launch_count", "spd_gemm_update", "spd_residual_static", "spd_batch_create", "spd_batch_solve",
+    "spd_batch_info", "spd_batch_destroy",
 ]
 
 
@@ -101,6 +104,10 @@ def lib():
         "spd_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
         "spd_gemm_update": (I, [P, I, I, I, I, P, I, P, I, P, I, I]),
         "spd_residual_static": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
+        "spd_batch_create": (I, [P, I, P, P, P, P, P, PP]),
+        "spd_batch_solve": (I, [P, I, I, O, R, P, P, P]),
+        "spd_batch_info": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+        "spd_batch_destroy": (I, [P]),
         "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     }
@@ -277,7 +284,7 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
     return st, rep
 
 
-PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel"]
+PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch"]
 
 
 def spd_profile_enable(h, on=True):
@@ -320,3 +327,48 @@ def spd_residual_static(stream, A, B, X, R, colnorms=None):
     pR, ldr, _, _ = colmajor(R)
     pc = colnorms.data_ptr() if colnorms is not None else None
     return lib().spd_residual_static(_stream_ptr(stream), n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
+
+
+def spd_batch_create(h, As, Bs, Xs):
+    """Plan for len(As) systems: As[i] (n_i, n_i) float64 device tensors
+    (symmetric), Bs[i] and Xs[i] (n_i,) float64 device tensors."""
+    import numpy as np
+    cnt = len(As)
+    n = np.array([a.shape[0] for a in As], dtype=np.int32)
+    lda = np.array([a.stride(0) if a.is_contiguous() and a.shape[0] > 1 else max(a.shape[0], 1) for a in As],
+                   dtype=np.int32)
+    pa = np.array([a.data_ptr() for a in As], dtype=np.uint64)
+    pb = np.array([b.data_ptr() for b in Bs], dtype=np.uint64)
+    px = np.array([x.data_ptr() for x in Xs], dtype=np.uint64)
+    plan = C.c_void_p()
+    st = lib().spd_batch_create(h, cnt, n.ctypes.data, pa.ctypes.data, lda.ctypes.data, pb.ctypes.data,
+                                px.ctypes.data, C.byref(plan))
+    return st, (plan if st == SPD_OK else None)
+
+
+def spd_batch_solve(plan, method="chol_ir", prec="fp32", opts=None, count=None):
+    """Returns (status, summary SpdReport, per-system status, berr, iters)."""
+    import numpy as np
+    m = BATCH[method] if isinstance(method, str) else int(method)
+    rep = SpdReport()
+    cnt = int(count) if count is not None else 0
+    sts = np.zeros(max(cnt, 1), dtype=np.int32)
+    be = np.zeros(max(cnt, 1))
+    it = np.zeros(max(cnt, 1), dtype=np.int32)
+    args = (sts.ctypes.data, be.ctypes.data, it.ctypes.data) if cnt else (None, None, None)
+    st = lib().spd_batch_solve(plan, m, _prec(prec), _opts(opts), C.byref(rep), *args)
+    return st, rep, sts[:cnt], be[:cnt], it[:cnt]
+
+
+def spd_batch_info(plan, method="chol_ir"):
+    m = BATCH[method] if isinstance(method, str) else int(method)
+    t, c = C.c_int(), C.c_int()
+    ms = (C.c_float * 2)()
+    st = lib().spd_batch_info(plan, m, C.byref(t), C.byref(c), ms)
+    if st != SPD_OK:
+        raise SpdError(st, "spd_batch_info failed")
+    return {"threads_per_cta": t.value, "ctas": c.value, "tune_ms": [ms[0], ms[1]]}
+
+
+def spd_batch_destroy(plan):
+    return lib().spd_batch_destroy(plan)
