@@ -236,6 +236,142 @@ def reference_arm(args):
     return 0
 
 
+def batched_leg(args):
+    """Batched workload: 4096 systems, n_i ~ U{32..512}, A_i = G G^T / n_i +
+    0.05 I, one N(0,1) right-hand side each, in one persistent graph launch.
+    Matrices are drawn on the GPU (torch generator seeded 1000 + i; sizes
+    from the seeded host stream)."""
+    import numpy as np
+    import torch
+    import paper_1405_4644_gb300 as spd
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    h = spd.spd_create(torch.cuda.current_stream())
+    sizes = W.batched_sizes(args.count)
+    As, bs, xs = [], [], []
+    for i, n in enumerate(sizes):
+        g = torch.Generator(device=dev)
+        g.manual_seed(1000 + i)
+        G = torch.randn((int(n), int(n)), dtype=torch.float64, device=dev, generator=g)
+        A = G @ G.T / float(n)
+        A = 0.5 * (A + A.T)
+        A.diagonal().add_(0.05)
+        As.append(A.contiguous())
+        bs.append(torch.randn(int(n), dtype=torch.float64, device=dev, generator=g))
+        xs.append(torch.zeros(int(n), dtype=torch.float64, device=dev))
+    torch.cuda.synchronize()
+    st, plan = spd.spd_batch_create(h, As, bs, xs)
+    assert st == spd.SPD_OK, spd.spd_last_error_string(h)
+    out = {"leg": "batched", "metric": "batched FP64-accurate SPD solves/s (one persistent launch)", "unit": "systems/s",
+           "config": {"workload": f"batched: {args.count} systems, n ~ U{{32..512}}, A = G G^T/n + 0.05 I, 1 RHS",
+                      "sum_n2": int(np.sum(sizes.astype(np.int64) ** 2)),
+                      "sum_n3_over_3": float(np.sum(sizes.astype(np.float64) ** 3) / 3)}}
+    sum8n2 = 8.0 * float(np.sum(sizes.astype(np.float64) ** 2))
+    peaks, _ = load_peaks()
+    for method, prec in [("chol_ir", "fp32"), ("chol_ir", "bf16"), ("pcg_jacobi", "fp64")]:
+        st, rep, sts, be, it = spd.spd_batch_solve(plan, method, prec, count=len(sizes))  # warm-up (+ autotune)
+        assert st == spd.SPD_OK, spd.spd_last_error_string(h)
+        steps = max(1, args.steps if method == "chol_ir" else 1)
+        ms = []
+        for _ in range(steps):
+            st, rep, sts, be, it = spd.spd_batch_solve(plan, method, prec, count=len(sizes))
+            ms.append(rep.time_ms)
+        t = float(np.median(ms))
+        iters = float(np.mean(it))
+        passes = 1.0 + iters if method == "chol_ir" else iters + 2.0   # float64 passes over every A
+        fp64_flops = 2.0 * float(np.sum(sizes.astype(np.float64) ** 2)) * passes
+        hbm = sum8n2 * passes / (t * 1e-3) / 1e9
+        info = spd.spd_batch_info(plan, method)
+        out[f"{method}_{prec}"] = {
+            "value": len(sizes) / (t * 1e-3), "ms_per_launch": t, "max_berr": float(np.max(be)),
+            "mean_iters": iters, "all_ok": bool(np.all(sts == 0)), "threads_per_cta": info["threads_per_cta"],
+            "autotune_ms": info["tune_ms"],
+            "roofline": {"bound": "alu", "unit": "TFLOP/s", "achieved": fp64_flops / (t * 1e-3) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS, "frac": fp64_flops / (t * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "hbm_gbs": hbm, "hbm_frac": hbm / peaks["hbm_gbs"],
+                         "note": "float64 residual flops (2 n^2 per pass) and A bytes (8 n^2 per pass)"}}
+    # the plain baseline: float64 Cholesky + solve per system, a sample of 128 systems scaled to the batch
+    rng_ = np.random.default_rng(0)
+    idx = rng_.choice(len(sizes), size=min(128, len(sizes)), replace=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in idx:
+        stt, F, _ = spd.spd_factor(h, As[i], "fp64")
+        X = torch.zeros((1, int(sizes[i])), dtype=torch.float64, device=dev).t()
+        spd.spd_solve_ir(h, F, As[i], bs[i][:, None], X)
+        spd.spd_factor_destroy(F)
+    torch.cuda.synchronize()
+    tl = time.perf_counter() - t0
+    scale = float(np.sum(sizes.astype(np.float64) ** 3)) / float(np.sum(sizes[idx].astype(np.float64) ** 3))
+    out["fp64_per_system_loop"] = {"value": len(sizes) / (tl * scale), "unit": "systems/s",
+                                   "sample": f"{len(idx)} systems timed, scaled by sum n^3"}
+    spd.spd_batch_destroy(plan)
+    spd.spd_destroy(h)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def learned_leg(args):
+    """Learned preconditioner on the Matern-3/2 family (n points uniform in the
+    unit square, ell ~ U[0.02, 0.5], nugget ~ logU[1e-4, 1e-1]): train on
+    seeds 0.., test on held-out seeds 100000..; PCG iterations and time with
+    the learned M against Jacobi-PCG and float32 Cholesky-IR."""
+    import numpy as np
+    import torch
+    import paper_1405_4644_gb300 as spd
+    import workloads as W
+    from paper_1405_4644_gb300 import learned as trainer
+    dev = torch.device("cuda", 0)
+    h = spd.spd_create(torch.cuda.current_stream())
+    n = args.n_learned
+    st, net = spd.spd_mlp_create(h, 256, 11, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = trainer.train(h, net, n, range(args.train_systems), W, probes=8, lr=2e-3, wsup=0.1, use_factor=True)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    res = {"jacobi": [], "learned": [], "chol_ir": []}
+    opts = {"tol": 1e-14, "crit": "berr", "eta": 1e-12, "maxit_inner": 20000}
+    for seed in range(100000, 100000 + args.test_systems):
+        A, coords, ell, nug = trainer.make_system(n, seed, dev, W)
+        b = torch.from_numpy(W.gaussian_rhs(n, 1, seed)).to(dev)
+        X = torch.zeros((1, n), dtype=torch.float64, device=dev).t()
+        st, rep = spd.spd_cg(h, A, b, X, "fp64", "jacobi", opts=opts)
+        res["jacobi"].append((rep.iters_low, rep.time_ms, rep.berr, st))
+        F = trainer.features(h, A, coords, ell, nug)
+        tb0 = time.perf_counter()
+        st, P = spd.spd_lowrank_build(net, A, F)
+        torch.cuda.synchronize()
+        tb = 1e3 * (time.perf_counter() - tb0)
+        X.zero_()
+        st, rep = spd.spd_solve_learned(h, P, A, b, X, opts)
+        spd.spd_lowrank_destroy(P)
+        res["learned"].append((rep.iters_low, rep.time_ms + tb, rep.berr, rep.fell_back))
+        st, Fc, fr = spd.spd_factor(h, A, "fp32")
+        X.zero_()
+        st, rep = spd.spd_solve_ir(h, Fc, A, b, X)
+        spd.spd_factor_destroy(Fc)
+        res["chol_ir"].append((rep.iters_low, rep.time_ms + fr.time_ms, rep.berr, st))
+    spd.spd_mlp_destroy(net)
+    spd.spd_destroy(h)
+
+    def summ(rows):
+        a = np.array([r[:3] for r in rows], dtype=np.float64)
+        return {"median_iters": float(np.median(a[:, 0])), "mean_ms": float(np.mean(a[:, 1])),
+                "max_berr": float(np.max(a[:, 2]))}
+    out = {"leg": "learned", "metric": "PCG iterations and ms per FP64-accurate solve, learned vs Jacobi",
+           "config": {"workload": f"Matern-3/2 family, n={n}, {args.train_systems} training systems, "
+                                  f"{args.test_systems} held-out", "n": n},
+           "train": {"seconds": t_train, "systems_per_s": args.train_systems / t_train,
+                     "loss_first10": float(np.mean(hist[:10])), "loss_last10": float(np.mean(hist[-10:]))},
+           "jacobi_pcg": summ(res["jacobi"]), "learned_pcg": summ(res["learned"]),
+           "learned_fallbacks": int(sum(r[3] for r in res["learned"])), "chol_ir_fp32": summ(res["chol_ir"]),
+           "iteration_gain_median": float(np.median([j[0] / max(l[0], 1) for j, l in zip(res["jacobi"],
+                                                                                       res["learned"])]))}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +385,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--leg", default="main", choices=["main", "batched", "learned"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--n-learned", type=int, default=4096)
+    ap.add_argument("--train-systems", type=int, default=1000)
+    ap.add_argument("--test-systems", type=int, default=32)
     args = ap.parse_args()
     args.kappas = [float(k) for k in args.kappas.split(",")]
     precs = args.precs.split(",")
@@ -256,6 +397,10 @@ def main():
         precs = precs * len(args.kappas)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.leg == "batched":
+        return batched_leg(args)
+    if args.leg == "learned":
+        return learned_leg(args)
 
     import numpy as np
     import torch
@@ -333,7 +478,8 @@ def main():
         energy = {"j_per_solve": j / (len(systems) * args.steps), "avg_power_w": clocks["avg_power_w"],
                   "source": "nvidia-smi power.draw mean x time, gross"}
 
-    per_kappa = [{"kappa": k, "prec": p, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
+    per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
+                  "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
                   "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
 
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system

@@ -83,7 +83,8 @@ typedef enum spd_crit {
 typedef enum spd_precond {
     SPD_PC_NONE = 0,   /* Algorithm 2 as printed                           */
     SPD_PC_JACOBI = 1, /* M = diag(A)^{-1}                                  */
-    SPD_PC_FACTOR = 2  /* M = (R~^T R~)^{-1} from an spd_factor object      */
+    SPD_PC_FACTOR = 2, /* M = (R~^T R~)^{-1} from an spd_factor object      */
+    SPD_PC_LOWRANK = 3 /* learned M = S (Dh + Uh Uh^T)^{-1} S (spd_lowrank)  */
 } spd_precond;
 
 /* Arithmetic of the float64-accurate residual r = b - A x. */
@@ -227,12 +228,59 @@ spd_status spd_residual_static(void *stream, int n, int m, const double *A, int 
  * |i - j| <= opts->band when band >= 0 (Section 4.1) -- and rho, alpha,
  * beta and the vector updates in float64; then X += e.  beta is the
  * Fletcher-Reeves quotient r'^T r' / rho.  pc selects the preconditioner;
- * pc_data is the spd_factor_t* for SPD_PC_FACTOR, else NULL.  X starts
+ * pc_data is the spd_factor_t* for SPD_PC_FACTOR, the spd_lowrank* for
+ * SPD_PC_LOWRANK, else NULL.  X starts
  * from zero.  The m columns are independent CG runs sharing each pass
  * over A~. */
 spd_status spd_cg(spd_handle *h, int n, int m, const double *A, int lda, int matvec_prec,
                   int pc, const void *pc_data, const double *B, int ldb, double *X, int ldx,
                   const spd_opts *opts, spd_report *rep);
+
+/* ---- learned diagonal-plus-low-rank preconditioner for PCG -------------------
+ * (No passage of the paper: an extension of Algorithm 2's CG.)  A small
+ * network maps per-row features of A to Dh (diagonal, > 0) and Uh (n x 32),
+ * defining the SPD preconditioner  M = S (Dh + Uh Uh^T)^{-1} S  with
+ * S = diag(A)^{-1/2}, applied through the Woodbury identity in O(32 n).
+ * The network is 16 -> H -> H -> 33 with SiLU activations; with bf16 set,
+ * the forward products take bf16-rounded operands and activations
+ * (float32 accumulation and float32 master weights).  Training minimises
+ *   L = (1/p) sum_c ||A M z_c - z_c||^2 / ||z_c||^2
+ *       + w_sup ||M z_0 - t_0||^2 / ||t_0||^2
+ * over probe vectors z_c (device, n x p, column-major, ld n), where
+ * t_0 = A^{-1} z_0 comes from the system's own Cholesky factor (optional).
+ * All kernels (features, layers, loss, gradient, Adam, apply) run on the
+ * GPU.  Buffers are device pointers unless stated. */
+typedef struct spd_mlp spd_mlp;
+typedef struct spd_lowrank spd_lowrank;
+spd_status spd_mlp_create(spd_handle *h, int hidden, unsigned long long seed, int bf16, spd_mlp **net);
+spd_status spd_mlp_destroy(spd_mlp *net);
+/* Copy the flat float32 parameter vector out (out), in (in) and the
+ * gradient of the last spd_mlp_loss_grad out (grad_out); host or device
+ * pointers, each may be NULL; *count receives the parameter count. */
+spd_status spd_mlp_params(spd_mlp *net, float *out, const float *in, float *grad_out, long *count);
+/* F (n x 16 float32, row-major) = row features of A: point coordinates
+ * (coords, n x 2 float64 row-major), log ell, log nugget, Fourier terms of
+ * the coordinates, mean/rms/max-off-diagonal of the scaled row, 1. */
+spd_status spd_learned_features(spd_handle *h, int n, const double *A, int lda, const double *coords,
+                                double ell, double nugget, float *F);
+/* Loss L (host *loss) and its gradient with respect to every parameter
+ * (kept in the network for spd_mlp_adam).  T may be NULL (w_sup unused). */
+spd_status spd_mlp_loss_grad(spd_mlp *net, int n, const double *A, int lda, const float *F, int p,
+                             const double *Z, const double *T, double w_sup, double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) with learning rate lr. */
+spd_status spd_mlp_adam(spd_mlp *net, double lr);
+/* Inference: build the preconditioner of A from its features. */
+spd_status spd_lowrank_build(spd_mlp *net, int n, const double *A, int lda, const float *F,
+                             spd_lowrank **P);
+/* Z = M R for m columns (float64, column-major). */
+spd_status spd_lowrank_apply(spd_lowrank *P, int m, const double *R, int ldr, double *Z, int ldz);
+spd_status spd_lowrank_destroy(spd_lowrank *P);
+/* PCG on A in float64 with the learned M (spd_cg with SPD_PC_LOWRANK, at
+ * most opts->maxit_inner steps); if it misses the tolerance, float32
+ * Cholesky with iterative refinement takes over (report.fell_back = 1). */
+spd_status spd_solve_learned(spd_handle *h, const spd_lowrank *P, int n, int m, const double *A,
+                             int lda, const double *B, int ldb, double *X, int ldx,
+                             const spd_opts *opts, spd_report *rep);
 
 /* ---- batched solves ----------------------------------------------------------
  * Many independent systems A_i x_i = b_i (1 <= n_i <= 512, one right-hand

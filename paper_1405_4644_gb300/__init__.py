@@ -26,6 +26,8 @@ __all__ = [
     "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
     "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "BATCH",
     "spd_batch_create", "spd_batch_solve", "spd_batch_info", "spd_batch_destroy",
+    "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params", "spd_learned_features", "spd_mlp_loss_grad",
+    "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply", "spd_lowrank_destroy", "spd_solve_learned",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
@@ -34,7 +36,7 @@ SPD_ERR_SCRATCH = 8
 PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto": 6}
 PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
-PC = {"none": 0, "jacobi": 1, "factor": 2}
+PC = {"none": 0, "jacobi": 1, "factor": 2, "lowrank": 3}
 BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
@@ -44,7 +46,9 @@ EXPORTED = [
     "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
     "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_cg", "spd_profile_enable", "spd_profile_read",
     "spd_launch_count", "spd_gemm_update", "spd_residual_static", "spd_batch_create", "spd_batch_solve",
-    "spd_batch_info", "spd_batch_destroy",
+    "spd_batch_info", "spd_batch_destroy", "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params",
+    "spd_learned_features", "spd_mlp_loss_grad", "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply",
+    "spd_lowrank_destroy", "spd_solve_learned",
 ]
 
 
@@ -108,6 +112,16 @@ def lib():
         "spd_batch_solve": (I, [P, I, I, O, R, P, P, P]),
         "spd_batch_info": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float)]),
         "spd_batch_destroy": (I, [P]),
+        "spd_mlp_create": (I, [P, I, C.c_ulonglong, I, PP]),
+        "spd_mlp_destroy": (I, [P]),
+        "spd_mlp_params": (I, [P, P, P, P, C.POINTER(C.c_long)]),
+        "spd_learned_features": (I, [P, I, P, I, P, D, D, P]),
+        "spd_mlp_loss_grad": (I, [P, I, P, I, P, I, P, P, D, C.POINTER(C.c_double)]),
+        "spd_mlp_adam": (I, [P, D]),
+        "spd_lowrank_build": (I, [P, I, P, I, P, PP]),
+        "spd_lowrank_apply": (I, [P, I, P, I, P, I]),
+        "spd_lowrank_destroy": (I, [P]),
+        "spd_solve_learned": (I, [P, P, I, I, P, I, P, I, P, I, O, R]),
         "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
     }
@@ -372,3 +386,73 @@ def spd_batch_info(plan, method="chol_ir"):
 
 def spd_batch_destroy(plan):
     return lib().spd_batch_destroy(plan)
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+def spd_mlp_create(h, hidden=256, seed=0, bf16=True):
+    net = C.c_void_p()
+    st = lib().spd_mlp_create(h, int(hidden), int(seed), 1 if bf16 else 0, C.byref(net))
+    return st, (net if st == SPD_OK else None)
+
+
+def spd_mlp_destroy(net):
+    return lib().spd_mlp_destroy(net)
+
+
+def spd_mlp_params(net, out=None, inp=None, grad=None):
+    """Copy parameters out/in and the last gradient out; returns the count."""
+    cnt = C.c_long()
+    st = lib().spd_mlp_params(net, _ptr(out), _ptr(inp), _ptr(grad), C.byref(cnt))
+    if st != SPD_OK:
+        raise SpdError(st, "spd_mlp_params failed")
+    return cnt.value
+
+
+def spd_learned_features(h, A, coords, ell, nugget, F):
+    pA, lda, n = _sym(A)
+    return lib().spd_learned_features(h, n, pA, lda, coords.data_ptr(), float(ell), float(nugget), F.data_ptr())
+
+
+def spd_mlp_loss_grad(net, A, F, Z, T=None, wsup=0.0):
+    pA, lda, n = _sym(A)
+    pZ, ldz, _, p = colmajor(Z)
+    if ldz != n:
+        raise ValueError("probe block must have leading dimension n")
+    loss = C.c_double()
+    st = lib().spd_mlp_loss_grad(net, n, pA, lda, F.data_ptr(), p, pZ, _ptr(T), float(wsup), C.byref(loss))
+    return st, loss.value
+
+
+def spd_mlp_adam(net, lr):
+    return lib().spd_mlp_adam(net, float(lr))
+
+
+def spd_lowrank_build(net, A, F):
+    pA, lda, n = _sym(A)
+    P = C.c_void_p()
+    st = lib().spd_lowrank_build(net, n, pA, lda, F.data_ptr(), C.byref(P))
+    return st, (P if st == SPD_OK else None)
+
+
+def spd_lowrank_apply(P, R, Z):
+    pR, ldr, n, m = colmajor(R)
+    pZ, ldz, _, _ = colmajor(Z)
+    return lib().spd_lowrank_apply(P, m, pR, ldr, pZ, ldz)
+
+
+def spd_lowrank_destroy(P):
+    return lib().spd_lowrank_destroy(P)
+
+
+def spd_solve_learned(h, P, A, B, X, opts=None):
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = colmajor(B)
+    pX, ldx, _, _ = colmajor(X)
+    rep = SpdReport()
+    st = lib().spd_solve_learned(h, P, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), C.byref(rep))
+    return st, rep

@@ -169,3 +169,9 @@ struct ProfScope {
 // y <- (L L^T)^{-1} y for one float32 vector of the scaled system (no d
 // scaling); defined with the triangular-solve kernels.
 spd_status factor_apply_scaled_f32(spd_handle* h, const spd_factor_t* F, float* y);
+
+// learned low-rank preconditioner hooks for the CG driver (spd_learned.cu)
+struct spd_lowrank;
+int lowrank_order(const spd_lowrank* P);
+spd_status lowrank_apply_cg(spd_handle* h, const spd_lowrank* P, int n, int m, const double* R, long ldr, double* Z,
+                            long ldz);

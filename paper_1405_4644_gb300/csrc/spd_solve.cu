@@ -341,6 +341,7 @@ struct CgSetup {
     int band = -1;
     int pc = SPD_PC_NONE;
     const spd_factor_t* F = nullptr;
+    const spd_lowrank* LR = nullptr;
     const double* dinv = nullptr;
 };
 
@@ -473,11 +474,13 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
         ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
         ++(h)->launches, k_inner_target<<<ceil_div(m, 128), 128, 0, s>>>(w.b2, w.colnorms, w.anorm, m, o.crit, o.tol, n, w.target);
         const bool fac = (cs.pc == SPD_PC_FACTOR);
+        const bool lowrank = (cs.pc == SPD_PC_LOWRANK);
         ++(h)->launches, k_cg_start<<<gv, 256, 0, s>>>(n, m, w.R, n, w.E, w.Rr, w.Z, w.P, w.Pf,
-                                      cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, fac ? 0 : 1);
+                                      cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, (fac || lowrank) ? 0 : 1);
         LAUNCH_CHECK(h);
-        if (fac) {
-            st = lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0);
+        if (fac || lowrank) {
+            st = fac ? lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0)
+                     : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
             if (st != SPD_OK) return st;
             ++(h)->launches, k_copy_p<<<gv, 256, 0, s>>>(n, m, w.Z, w.P, w.Pf);
         }
@@ -501,8 +504,9 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             ++(h)->launches, k_cg_update<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.E, w.Rr, w.P, w.Q,
                                            cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, w.Z);
             LAUNCH_CHECK(h);
-            if (fac) {
-                st = lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0);
+            if (fac || lowrank) {
+                st = fac ? lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0)
+                         : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
                 if (st != SPD_OK) return st;
             }
             ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
@@ -642,7 +646,8 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (opts_in) o = *opts_in;
     if (rep) memset(rep, 0, sizeof(*rep));
     if (bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || o.maxit_inner < 1 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_FACTOR || (pc == SPD_PC_FACTOR && !pc_data))
+        o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_LOWRANK ||
+        ((pc == SPD_PC_FACTOR || pc == SPD_PC_LOWRANK) && !pc_data))
         return set_err(h, SPD_ERR_ARG, "spd_cg: bad arguments");
     if (matvec_prec != SPD_PREC_FP64 && matvec_prec != SPD_PREC_FP32 && matvec_prec != SPD_PREC_BF16)
         return set_err(h, SPD_ERR_UNSUPPORTED, "spd_cg: matrix-vector precision must be FP64, FP32 or BF16");
@@ -650,6 +655,8 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
         return set_err(h, SPD_ERR_UNSUPPORTED, "spd_cg: the banded inner matrix is stored in FP32");
     if (pc == SPD_PC_FACTOR && static_cast<const spd_factor_t*>(pc_data)->n != n)
         return set_err(h, SPD_ERR_ARG, "spd_cg: factor order differs from n");
+    if (pc == SPD_PC_LOWRANK && lowrank_order(static_cast<const spd_lowrank*>(pc_data)) != n)
+        return set_err(h, SPD_ERR_ARG, "spd_cg: preconditioner order differs from n");
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
     WsPlan p;
@@ -658,7 +665,8 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     cg_plan(p, h, n, m, o_, &S, &G2);
     CgSetup cs;
     cs.pc = pc;
-    cs.F = static_cast<const spd_factor_t*>(pc_data);
+    if (pc == SPD_PC_FACTOR) cs.F = static_cast<const spd_factor_t*>(pc_data);
+    if (pc == SPD_PC_LOWRANK) cs.LR = static_cast<const spd_lowrank*>(pc_data);
     size_t o_at = 0, o_dinv = 0;
     long ldt = round_up(n, 64);
     if (o.band >= 0) {

@@ -276,3 +276,43 @@ def test_cg_ir_relative_target_reaches_double_accuracy():
     assert ok
     assert np.linalg.norm(oracle.residual(A, b, X)) <= 1e-14 * np.linalg.norm(b)
     assert hi[0] >= 2  # single-precision inner matvecs cannot get there in one sweep
+
+
+# --------------------------------------------------------------------------
+# Learned preconditioner oracle (no paper counterpart): definitions pinned
+# against constructions whose answer is known
+# --------------------------------------------------------------------------
+def test_learned_oracle_exact_preconditioner_gives_zero_loss():
+    """If Dh + Uh Uh^T equals the scaled matrix exactly, M = A^{-1} and the
+    probe loss vanishes."""
+    from oracle import learned as LO
+    g = np.random.default_rng(0)
+    n, H = 40, 8
+    U = g.standard_normal((n, LO.RANK)) * 0.1
+    dh = 1.0 - np.sum(U * U, axis=1)           # unit diagonal: diag(Dh + U U^T) = 1
+    assert dh.min() > 0.2
+    Ah = np.diag(dh) + U @ U.T
+    t = 0.5 + g.random(n)
+    A = t[:, None] * Ah * t[None, :]           # S = diag(A)^{-1/2} = 1/t, so S A S = Ah
+    O = np.concatenate([np.log(np.expm1(dh - 1e-3))[:, None], U], axis=1)
+    M = LO.precond(O, A)
+    np.testing.assert_allclose(M @ A, np.eye(n), atol=1e-9)
+    # a network whose last layer outputs O through its bias only
+    count = H * LO.NFEAT + H + H * H + H + (1 + LO.RANK) * H + 1 + LO.RANK
+    p = np.zeros(count)
+    F = np.zeros((n, LO.NFEAT))
+    Z = g.standard_normal((n, 3))
+    assert LO.loss(p, H, A, F, Z) > 0.1            # M = S^2 here: not the inverse
+    assert np.all(np.linalg.eigvalsh(LO.precond(LO.forward(p, F, H), A)) > 0)
+
+
+def test_learned_oracle_features_on_a_known_matrix():
+    from oracle import learned as LO
+    A = np.array([[4.0, 2.0, 0.0], [2.0, 4.0, 1.0], [0.0, 1.0, 1.0]])
+    coords = np.array([[0.0, 0.5], [0.25, 1.0], [1.0, 0.0]])
+    F = LO.features(A, coords, 0.1, 1e-2)
+    # scaled |A|: rows [1, .5, 0], [.5, 1, .5], [0, .5, 1]
+    np.testing.assert_allclose(F[:, 12], [1.5 / 3, 2.0 / 3, 1.5 / 3])
+    np.testing.assert_allclose(F[:, 14], [0.5, 0.5, 0.5])
+    np.testing.assert_allclose(F[1, 4:8], [np.sin(np.pi / 4), np.cos(np.pi / 4), 0.0, -1.0], atol=1e-15)
+    assert F[0, 2] == np.log(0.1) and F[0, 15] == 1.0

@@ -230,3 +230,21 @@ def batched_gram(sizes, shift: float = 0.05, seed_base: int = 1000):
         As.append(A)
         bs.append(g.standard_normal(int(n)))
     return As, bs
+
+
+def matern32_torch(points, ell: float, nugget: float, device):
+    """Matern-3/2 covariance of the given points (numpy, n x dim) assembled
+    in float64 on a torch device; same formula as ``matern32_cov``."""
+    import torch
+    P = torch.from_numpy(np.asarray(points, dtype=np.float64)).to(device)
+    r = torch.cdist(P, P, compute_mode="donot_use_mm_for_euclid_dist")
+    s = (3.0 ** 0.5) * r / ell
+    A = (1.0 + s) * torch.exp(-s)
+    A = 0.5 * (A + A.T)
+    A.diagonal().add_(nugget)
+    return A
+
+
+def matern_points(n: int, seed: int, dim: int = 2):
+    """Uniform points in the unit square (cube) for Matern system ``seed``."""
+    return rng(seed).random((n, dim))
