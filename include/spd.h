@@ -94,9 +94,10 @@ typedef enum spd_resid {
 
 /* Flags of spd_factor. */
 #define SPD_SCALE_DIAG 1u /* factor D^{-1/2} A D^{-1/2} (D = diag A); default */
-#define SPD_FACTOR_CUDA_CORES 2u /* run the trailing updates of a TF32/BF16/FP16
-                                    factor on the CUDA cores (same rounded
-                                    operands, float32 accumulation): a
+#define SPD_FACTOR_CUDA_CORES 2u /* run the trailing updates of a FP32/TF32/
+                                    BF16/FP16 factor on the CUDA cores (same
+                                    rounded operands, float32 accumulation;
+                                    plain float32 products for FP32): a
                                     reference engine for validation       */
 
 typedef struct spd_opts {
@@ -323,7 +324,11 @@ spd_status spd_batch_destroy(spd_batch *plan);
  * the tensor cores: A (M x K) and B (N x K) float32 row-major are rounded
  * (RNE) to `prec` (SPD_PREC_TF32, BF16, FP16 or FP8 -- FP8 multiplies the
  * operands by 2^8 before rounding, so |entries| <= 1.75 stay in range)
- * and multiplied with float32 accumulation; C is float32 row-major
+ * and multiplied with float32 accumulation; C is float32 row-major.
+ * SPD_PREC_FP32 splits each operand exactly into three tf32 slices
+ * (s0 = tf32(x), s1 = tf32(x - s0), s2 = x - s0 - s1) and accumulates the
+ * six slice products of order <= 2, smallest first: float32 accuracy
+ * (dropped terms below 2^-32 |a||b|) at tf32 tensor-core speed / 6.
  * (ldc >= N).  lower != 0 (requires A == B, M == N, lda == ldb) updates
  * only entries with row >= column.  Device pointers; synchronous. */
 spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,

@@ -71,9 +71,19 @@ template <> struct OpConv<__nv_fp8_e4m3> {
 struct Mirror {
     void* ptr;     // n x ld elements of the operand type (nullptr = no mirror)
     long ld;       // leading dimension in elements (row-major)
-    int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3 (x SPD_FP8_SCALE)
-    const float* unused;
+    int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3 (x SPD_FP8_SCALE),
+                   // 5 float32 as three tf32 slices (planes of `plane` elements)
+    long plane;    // kind 5: elements per slice plane (n * ld)
 };
+
+// x = s0 + s1 + s2 exactly, each a tf32 value: s0 = tf32(x), s1 = tf32(x - s0),
+// s2 = x - s0 - s1 (at most 2 significant bits left)
+__device__ __forceinline__ void split_tf32x3(float x, float& s0, float& s1, float& s2) {
+    s0 = round_tf32(x);
+    const float r1 = x - s0;
+    s1 = round_tf32(r1);
+    s2 = r1 - s1;
+}
 
 __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, float v) {
     switch (m.kind) {
@@ -83,6 +93,15 @@ __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, fl
         case 4:  // fixed power-of-two scale: |entries| <= 1 after diagonal scaling
             ((__nv_fp8_e4m3*)m.ptr)[r * m.ld + c] = __nv_fp8_e4m3(v * SPD_FP8_SCALE);
             break;
+        case 5: {
+            float s0, s1, s2;
+            split_tf32x3(v, s0, s1, s2);
+            float* p = (float*)m.ptr + r * m.ld + c;
+            p[0] = s0;
+            p[m.plane] = s1;
+            p[2 * m.plane] = s2;
+            break;
+        }
         default: break;
     }
 }

@@ -42,7 +42,7 @@ template <int KIND>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
-              uint32_t idesc, float scale, DevStatus* st) {
+              uint32_t idesc, float scale, int nseg, uint32_t segs, DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
     constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -80,23 +80,26 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const int nk = K / BK;
+    const int nk = K / BK;       // K tiles per segment
+    const int ntiles = nk * nseg;  // segment s multiplies slice (segs >> 4s) & 3 of A by slice (segs >> 4s+2) & 3 of B
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            for (int kt = 0; kt < nk; ++kt) {
+            for (int kt = 0; kt < ntiles; ++kt) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1u;
+                const int seg = kt / nk, kin = kt - seg * nk;
+                const int za = (segs >> (4 * seg)) & 3, zb = (segs >> (4 * seg + 2)) & 3;
                 if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) break;
                 tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_2d(sA + s * A_STAGE, &mapA, k0 + kt * BK, a_row0 + bm * BM, &full[s]);
-                tc::tma_load_2d(sB + s * B_STAGE, &mapB, k0 + kt * BK, b_row0 + bn * BN, &full[s]);
+                tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
+                tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + kin * BK, b_row0 + bn * BN, zb, &full[s]);
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
-            for (int kt = 0; kt < nk; ++kt) {
+            for (int kt = 0; kt < ntiles; ++kt) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1u;
                 if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) break;
@@ -170,23 +173,25 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-int elem_bytes(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
+int elem_bytes(int kind) { return (kind == 1 || kind == 5) ? 4 : kind == 4 ? 1 : 2; }
+int slices_of(int kind) { return kind == 5 ? 3 : 1; }
 
-// 2-D map over a row-major (rows x cols, ld elements) operand array with a
-// box of (128 bytes of K) x box_rows, 128-byte swizzle, zero fill.
+// 3-D map over `planes` row-major (rows x cols, ld elements) operand planes
+// (plane stride rows*ld) with a box of (128 bytes of K) x box_rows x 1,
+// 128-byte swizzle, zero fill outside.
 bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols, long ld, int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
-    CUtensorMapDataType dt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+    CUtensorMapDataType dt = (kind == 1 || kind == 5) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                              : kind == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const int es = elem_bytes(kind);
-    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)(ld * es)};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)slices_of(kind)};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(rows * ld * es)};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -194,7 +199,8 @@ bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols
 
 uint32_t idesc_for(int kind) {
     switch (kind) {
-        case 1: return tc::idesc_f32acc(2, BM, BN);  // tf32
+        case 1:
+        case 5: return tc::idesc_f32acc(2, BM, BN);  // tf32
         case 2: return tc::idesc_f32acc(1, BM, BN);  // bf16
         case 3: return tc::idesc_f32acc(0, BM, BN);  // fp16
         default: return tc::idesc_f32acc(0, BM, BN); // e4m3 (kind::f8f6f4)
@@ -224,7 +230,7 @@ float tc_fp8_scale() { return SPD_FP8_SCALE; }
 spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
                                long b_ld, long cols, float* C, long ldc, int kind) {
     *out = nullptr;
-    if (kind < 1 || kind > 4) return SPD_ERR_UNSUPPORTED;
+    if (kind < 1 || kind > 5) return SPD_ERR_UNSUPPORTED;
     TcGemm* g = new TcGemm();
     memset(g, 0, sizeof(*g));
     if (!make_map(&g->mapA, Ah, kind, a_rows, cols, a_ld, BM) || !make_map(&g->mapB, Bh, kind, b_rows, cols, b_ld, BN)) {
@@ -245,23 +251,34 @@ spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, 
 
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
                           int k0, int lower, DevStatus* st) {
-    const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
+    const int bk = (g->kind == 1 || g->kind == 5) ? 32 : g->kind == 4 ? 128 : 64;
     if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
     const uint32_t idesc = idesc_for(g->kind);
+    // float32 as three tf32 slices: the six slice products of order <= 2,
+    // smallest first, into one accumulator (A slice in bits 4s..4s+1, B
+    // slice in bits 4s+2..4s+3 of segment s)
+    int nseg = 1;
+    uint32_t segs = 0;
+    if (g->kind == 5) {
+        const int pairs[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
+        nseg = 6;
+        for (int q = 0; q < 6; ++q) segs |= (uint32_t)(pairs[q][0] | (pairs[q][1] << 2)) << (4 * q);
+    }
     switch (g->kind) {
         case 1:
+        case 5:
             k_gemm_tc<1><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, st);
+                                                       idesc, scale, nseg, segs, st);
             break;
         case 4:
             k_gemm_tc<2><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, st);
+                                                       idesc, scale, nseg, segs, st);
             break;
         default:
             k_gemm_tc<0><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, st);
+                                                       idesc, scale, nseg, segs, st);
     }
     return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;
 }

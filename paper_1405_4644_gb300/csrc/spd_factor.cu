@@ -6,8 +6,8 @@
 //   trsm(B,L) : trsm(B1, L11); B2 -= X1 L21^T; trsm(B2, L22)
 //
 // with 128x128 leaves (k_potrf_leaf / k_trsm_leaf) and every off-leaf
-// update a GEMM on the working matrix (tensor cores for TF32/BF16/FP16/FP8,
-// CUDA cores for FP32/FP64).  Split points are multiples of 128, so only the
+// update a GEMM on the working matrix (tensor cores for TF32/BF16/FP16/FP8
+// and for FP32 as three tf32 slices; CUDA cores for FP64).  Split points are multiples of 128, so only the
 // very last leaf can be ragged.
 #include "engine.cuh"
 #include "k_convert.cuh"
@@ -65,7 +65,9 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower)
     // algorithmic work: lower-triangle SYRK or full GEMM; C read+written once
     // in T, each operand row read once in the operand type
     const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
-    const double opsz = sizeof(T) == 8 ? 8.0 : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
+    const double opsz = sizeof(T) == 8 ? 8.0
+                        : c.mir.kind == 5 ? 12.0
+                        : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
     ProfScope ps(c.h, SPD_PHASE_TRAILING, 2.0 * celems * K,
                  2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N));
     if constexpr (sizeof(T) == 8) {
@@ -81,6 +83,7 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower)
         dim3 grid(ceil_div(N, 128), ceil_div(M, 128));
         switch (c.mir.kind) {
             case 0:
+            case 5:  // float32: plain products of the working matrix
             ++(c.h)->launches, k_gemm_nt_simt<float, float, 8, 8, 8><<<grid, 256, 0, s>>>(F->W, F->ldw, F->W, F->ldw, r0, M, c0,
                                                                            N, k0, K, lower, c.h->dst);
                 break;
@@ -149,6 +152,7 @@ void free_factor(spd_factor_t* F) {
 
 int mirror_kind(int prec) {
     switch (prec) {
+        case SPD_PREC_FP32: return 5;
         case SPD_PREC_TF32: return 1;
         case SPD_PREC_BF16: return 2;
         case SPD_PREC_FP16: return 3;
@@ -156,7 +160,7 @@ int mirror_kind(int prec) {
         default: return 0;
     }
 }
-size_t mirror_elem(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
+size_t mirror_elem(int kind) { return kind == 5 ? 12 : kind == 1 ? 4 : kind == 4 ? 1 : 2; }
 
 // One factorisation attempt in a fixed precision.
 spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
@@ -168,7 +172,9 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
     F->ldw = round_up(std::max(n, 1), 64);
     F->nblk128 = ceil_div(n, SPD_LEAF);
     const size_t nW = (size_t)n * F->ldw;
-    const int kind = mirror_kind(prec);
+    // the float32 factor's mirror (three tf32 slices) is only needed by the
+    // tensor-core engine
+    const int kind = (prec == SPD_PREC_FP32 && (flags & SPD_FACTOR_CUDA_CORES)) ? 0 : mirror_kind(prec);
     auto fail = [&](spd_status s) {
         free_factor(F);
         return s;
@@ -206,7 +212,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         spd_status st = check_dev_status(h, rep, "spd_factor");
         if (st != SPD_OK) return fail(st);
 
-        FCtx c{h, F, Mirror{F->Wh, F->ldh, kind, nullptr}, nullptr};
+        FCtx c{h, F, Mirror{F->Wh, F->ldh, kind, (long)n * F->ldh}, nullptr};
         TcGemm* tc = nullptr;
         if (kind && !(flags & SPD_FACTOR_CUDA_CORES)) {
             st = tc_gemm_create(&tc, F->W, F->ldw, F->Wh, F->ldh, kind, n);

@@ -9,7 +9,7 @@ namespace {
 __global__ void k_to_mirror(const float* __restrict__ A, long lda, int rows, int K, int Kp, void* out, long ldo,
                             int kind) {
     long total = (long)rows * Kp;
-    Mirror m{out, ldo, kind, nullptr};
+    Mirror m{out, ldo, kind, (long)rows * ldo};
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         long r = e / Kp, k = e - r * Kp;
         float v = (k < K) ? A[r * lda + k] : 0.f;
@@ -19,6 +19,7 @@ __global__ void k_to_mirror(const float* __restrict__ A, long lda, int rows, int
 
 int kind_of(int prec) {
     switch (prec) {
+        case SPD_PREC_FP32: return 5;
         case SPD_PREC_TF32: return 1;
         case SPD_PREC_BF16: return 2;
         case SPD_PREC_FP16: return 3;
@@ -33,12 +34,13 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
                                       const float* B, int ldb, float* C, int ldc, int lower) {
     if (!h) return SPD_ERR_ARG;
     const int kind = kind_of(prec);
-    if (!kind) return set_err(h, SPD_ERR_UNSUPPORTED, "spd_gemm_update: precision must be TF32, BF16, FP16 or FP8");
+    if (!kind)
+        return set_err(h, SPD_ERR_UNSUPPORTED, "spd_gemm_update: precision must be FP32, TF32, BF16, FP16 or FP8");
     if (M < 0 || N < 0 || K < 0 || (M > 0 && K > 0 && (!A || lda < K)) || (N > 0 && K > 0 && (!B || ldb < K)) ||
         (M > 0 && N > 0 && (!C || ldc < N)) || (lower && (M != N || A != B || lda != ldb)))
         return set_err(h, SPD_ERR_ARG, "spd_gemm_update: bad arguments");
     if (M == 0 || N == 0 || K == 0) return SPD_OK;
-    const int es = kind == 1 ? 4 : kind == 4 ? 1 : 2;
+    const int es = kind == 5 ? 12 : kind == 1 ? 4 : kind == 4 ? 1 : 2;  // bytes per element over all slices
     const long Kp = round_up(K, 128);
     const long ldo = round_up(Kp, 64);
     WsPlan p;

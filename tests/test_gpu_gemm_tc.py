@@ -74,9 +74,30 @@ def test_gemm_update_lower_triangle(h, prec, M, K):
     assert np.all(np.abs(got[il] - ref[il]) <= bound[il])
 
 
+@pytest.mark.parametrize("M,N,K", [(128, 256, 32), (300, 500, 200), (1000, 1000, 1024), (513, 129, 640)])
+def test_gemm_update_fp32_three_tf32_slices(h, M, N, K):
+    """FP32 operands split exactly into three tf32 slices; the six slice
+    products of order <= 2 give the float32 product to float32 accuracy
+    (dropped terms are below 2^-32 |a||b|), far beyond one tf32 product."""
+    g = np.random.default_rng(M + 5 * N + 11 * K)
+    A = g.uniform(-1, 1, (M, K)) * 2.0
+    B = g.uniform(-1, 1, (N, K)) * 2.0
+    C0 = g.standard_normal((M, N)).astype(np.float32).astype(np.float64)
+    A32, B32 = rounded(A, "fp32"), rounded(B, "fp32")
+    ref = C0 - A32 @ B32.T
+    got = run(h, "fp32", A, B, C0)
+    mag = np.abs(A32) @ np.abs(B32).T
+    err = np.abs(got - ref)
+    bound = (K + 8) * 2.0 ** -24 * mag + 2.0 ** -24 * np.abs(C0)
+    assert np.all(err <= bound), float((err / bound).max())
+    tf = run(h, "tf32", A, B, C0)
+    if K >= 64:
+        assert np.max(np.abs(tf - ref)) > 16 * np.max(err)
+
+
 def test_gemm_update_rejects_bad_arguments(h):
     import torch
     A = torch.zeros(8, 8, dtype=torch.float32, device=DEV)
-    assert spd.spd_gemm_update(h, "fp32", A, A, A) == spd.SPD_ERR_UNSUPPORTED
+    assert spd.spd_gemm_update(h, "fp64", A, A, A) == spd.SPD_ERR_UNSUPPORTED
     assert spd.lib().spd_gemm_update(h, spd.PREC["bf16"], 8, 8, 8, A.data_ptr(), 4, A.data_ptr(), 8,
                                      A.data_ptr(), 8, 0) == spd.SPD_ERR_ARG
