@@ -89,7 +89,15 @@ typedef enum spd_precond {
 
 /* Arithmetic of the float64-accurate residual r = b - A x. */
 typedef enum spd_resid {
-    SPD_RESID_FP64 = 0 /* float64 fused multiply-adds */
+    SPD_RESID_FP64 = 0, /* float64 fused multiply-adds                        */
+    SPD_RESID_DF32 = 1  /* refinement loops: residuals of spd_residual_df32 (float32
+                           units, about 48-bit accurate) while the largest
+                           backward error is above 2^-36, float64 residuals
+                           from there on; a column is only ever accepted as
+                           converged on a float64 residual, so the stopping
+                           rule and its guarantee are those of SPD_RESID_FP64.
+                           The float64 products of the CG fallback use
+                           spd_residual_df32's arithmetic throughout.        */
 } spd_resid;
 
 /* Flags of spd_factor. */
@@ -202,6 +210,25 @@ spd_status spd_factor_solve(spd_handle *h, const spd_factor_t *F, int n, int m,
 spd_status spd_residual(spd_handle *h, int n, int m, const double *A, int lda,
                         const double *B, int ldb, const double *X, int ldx,
                         double *R, int ldr, double *colnorms);
+
+/* The residual of spd_residual computed on the float32 units (the
+ * high-precision residual of Alg. 1 lines 3/7 and Alg. 2 line 2, emulated;
+ * Section 3.1 only asks that it be more accurate than the factor).
+ * A's float64 entries are split by bit operations into two float32 parts
+ * (|a - ah - am| <= 2^-47 |a|), each column of X is scaled by a power of
+ * two and split into two float32 parts, the leading product ah*xh is kept
+ * exactly (FMA), the sums are float32 pairs updated by TwoSum and folded
+ * into float64 every 64 terms.  This is 48-bit arithmetic (float64: 53):
+ * products err by about 2^-47 |a_ij||x_j| and each run of 64 pair
+ * additions by up to ~2^-43 of its largest partial sum, so
+ * |computed - exact| stays below 2^-40 (|A||x|)_i per entry -- accurate
+ * enough to drive refinement, not to certify a 1e-14 backward error
+ * (SPD_RESID_DF32 hands that to a float64 residual).  Entries with |a| outside [2^-100, 2^100)
+ * (and Inf/NaN) take float64 FMAs; non-finite X gives NaN.  Same arguments,
+ * layout, ownership and errors as spd_residual. */
+spd_status spd_residual_df32(spd_handle *h, int n, int m, const double *A, int lda,
+                             const double *B, int ldb, const double *X, int ldx,
+                             double *R, int ldr, double *colnorms);
 
 /* The same float64 residual and norms as spd_residual, for callers that may
  * not allocate device memory at all (host callbacks, allocator hooks,

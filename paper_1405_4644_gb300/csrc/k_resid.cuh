@@ -203,17 +203,20 @@ struct IrSummary {
     int stagnated;    // columns whose stall count reached 2
     double max_berr;  // max over columns of the backward error
     double max_rel;   // max over columns of ||r||_2 / ||b||_2
+    int pending;      // columns that met the rule on a residual not allowed to accept
 };
 
 // One CTA: update per-column state from colnorms; crit as spd_crit.
 static __global__ void k_ir_check(const double* __restrict__ colnorms, const double* __restrict__ anorm,
                            const double* __restrict__ b2, int m, int crit, double tol,
-                           IrCol* __restrict__ cols, IrSummary* __restrict__ sum, int count_sweep, int polish) {
-    __shared__ int s_active, s_stag;
+                           IrCol* __restrict__ cols, IrSummary* __restrict__ sum, int count_sweep, int polish,
+                           int accept = 1) {
+    __shared__ int s_active, s_stag, s_pend;
     __shared__ double s_berr, s_rel;
     if (threadIdx.x == 0) {
         s_active = 0;
         s_stag = 0;
+        s_pend = 0;
         s_berr = 0.0;
         s_rel = 0.0;
     }
@@ -228,7 +231,14 @@ static __global__ void k_ir_check(const double* __restrict__ colnorms, const dou
         if (!st.conv) {
             if (count_sweep) st.iters += 1;
             bool ok = (crit == 2) ? (err < tol) : (err <= tol);
-            if (ok) {
+            if (ok && !accept) {
+                // a residual that may not decide convergence (float32 pairs):
+                // the next sweep, judged by a float64 residual, doubles as
+                // the polish sweep
+                st.stall = 0;
+                st.extra = 0;
+                atomicAdd(&s_pend, 1);
+            } else if (ok) {
                 if (st.extra > 0) st.extra -= 1;  // meets the rule: polish once more
                 else st.conv = 1;
                 st.stall = 0;
@@ -250,6 +260,7 @@ static __global__ void k_ir_check(const double* __restrict__ colnorms, const dou
     if (threadIdx.x == 0) {
         sum->active = s_active;
         sum->stagnated = s_stag;
+        sum->pending = s_pend;
         sum->max_berr = s_berr;
         sum->max_rel = s_rel;
     }
@@ -258,4 +269,153 @@ static __global__ void k_ir_check(const double* __restrict__ colnorms, const dou
 // frozen[c] = cols[c].conv
 static __global__ void k_frozen_from_cols(const IrCol* __restrict__ cols, int m, int* __restrict__ frozen) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) frozen[c] = cols[c].conv;
+}
+
+// ---------------------------------------------------------------------------
+// The same residual in float32 arithmetic, float64-accurate ("DF32"): the
+// float64 pipe of this GPU is a small fraction of its float32 pipe, so the
+// products run on the float32 units with error-free transformations.
+//
+// * Each float64 entry a of A is split by integer operations on its bits:
+//   ah = its 24 leading significand bits (truncated), am = the next 23 bits
+//   rounded to nearest, so |a - ah - am| <= 2^-47 |a|.  Entries outside
+//   [2^-100, 2^100) in magnitude (and Inf/NaN) are not split: they take a
+//   float64 FMA (a branch no ordinary matrix takes; zeros split to 0, 0).
+// * Column c of X is scaled by a power of two sc_c (max |x| in [1/2, 1))
+//   and each entry split as xh = fl32(x), xm = fl32(x - xh).
+// * a x = ah xh + (am xh + ah xm) + dropped terms below 2^-46 |a||x|; the
+//   leading product is kept exactly as p + e (e by FMA).
+// * Running sums are unevaluated float32 pairs (S, C): S <- S + p by
+//   TwoSum (exact), C collects the TwoSum errors, e and the cross terms;
+//   every RESID_FOLD terms the pair is added into a float64 accumulator, and
+//   the result is scaled back by 1/sc_c.  Each addition into C rounds at
+//   2^-24 |C| with |C| up to ~k 2^-25 |S| after k terms, so a run of 64
+//   terms errs by up to ~2^-43 of its largest partial sum: 48-bit pairs, not
+//   float64 (2^-53 per operation).
+// All float32 operations use explicit round-to-nearest intrinsics, so the
+// compiler cannot fuse a product into a sum and break the TwoSum.
+// ---------------------------------------------------------------------------
+#define RESID_FOLD 64
+
+// Split a float64 into two float32 values; returns false when a must take
+// the float64 path (|a| outside [2^-100, 2^100) and a != 0, or Inf/NaN).
+__device__ __forceinline__ bool df32_split(double a, float& ah, float& am) {
+    const unsigned hi = (unsigned)__double2hiint(a), lo = (unsigned)__double2loint(a);
+    const unsigned ex = (hi >> 20) & 0x7ffu;
+    const unsigned sg = hi & 0x80000000u;
+    if (ex - 923u >= 200u) {
+        ah = 0.f;
+        am = 0.f;
+        return ((hi & 0x7fffffffu) | lo) == 0u;
+    }
+    // ah: biased float32 exponent ex - 1023 + 127, mantissa = the 23 bits
+    // after the leading one
+    ah = __uint_as_float(sg | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+    // am: the remaining 29 bits rounded to 23 (a carry out simply bumps the
+    // exponent), built as (2^23 + r) 2^(E-150) - 2^23 2^(E-150), E = ex - 919
+    const unsigned r = ((lo & 0x1fffffffu) + 32u) >> 6;
+    const unsigned eb = (ex - 919u) << 23;
+    am = __fsub_rn(__uint_as_float(sg | (eb + r)), __uint_as_float(sg | eb));
+    return true;
+}
+
+// sc[c] = 2^-e_c and sc[m + c] = 2^e_c with max_i |X[i, c]| = f 2^e_c,
+// f in [1/2, 1); 1 for an all-zero or non-finite column.
+static __global__ void __launch_bounds__(256) k_xscale(const double* __restrict__ X, long ldx, int n, int m,
+                                                double* __restrict__ sc) {
+    __shared__ double red[8];
+    const int c = blockIdx.x;
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) mx = fmax(mx, fabs(X[(long)c * ldx + i]));
+    mx = warp_max(mx);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double v = 0.0;
+        for (int k = 0; k < 8; ++k) v = fmax(v, red[k]);
+        int e = 0;
+        if (v > 0.0 && isfinite(v)) {
+            frexp(v, &e);
+            e = max(-1000, min(1000, e));
+        }
+        sc[c] = ldexp(1.0, -e);
+        sc[m + c] = ldexp(1.0, e);
+    }
+}
+
+template <int MT>
+static __global__ void __launch_bounds__(RESID_ROWS, 2)
+    k_resid_partial_df32(const double* __restrict__ A, long lda, int n, const double* __restrict__ X, long ldx,
+                         int c0, int mc, int jchunk, int mtot, const double* __restrict__ sc,
+                         double* __restrict__ P, float* __restrict__ rowabs) {
+    __shared__ __align__(16) float2 xf[RESID_JT][MT];   // (xh, xm) of the scaled X
+    __shared__ __align__(16) double xd[RESID_JT][MT];   // the scaled X itself (float64 branch)
+    const int tid = threadIdx.x;
+    const int i = blockIdx.x * RESID_ROWS + tid;
+    const int j0 = blockIdx.y * jchunk;
+    const int j1 = min(n, j0 + jchunk);
+    float S[MT], C[MT];
+    double acc[MT];
+#pragma unroll
+    for (int c = 0; c < MT; ++c) {
+        S[c] = 0.f;
+        C[c] = 0.f;
+        acc[c] = 0.0;
+    }
+    float asum = 0.f;
+    const double* Ai = A + (i < n ? i : 0);
+    for (int jb = j0; jb < j1; jb += RESID_JT) {
+        const int jn = min(RESID_JT, j1 - jb);
+        __syncthreads();
+        for (int e = tid; e < RESID_JT * MT; e += RESID_ROWS) {
+            const int jj = e % RESID_JT, c = e / RESID_JT;
+            double v = 0.0;
+            if (jj < jn && c < mc) v = X[(long)(c0 + c) * ldx + jb + jj] * sc[c0 + c];
+            const float h = __double2float_rn(v);
+            xd[jj][c] = v;
+            xf[jj][c] = make_float2(h, __double2float_rn(v - (double)h));
+        }
+        __syncthreads();
+        if (i < n) {
+            const double* ap = Ai + (long)jb * lda;
+            for (int jf = 0; jf < jn; jf += RESID_FOLD) {
+                const int je = min(jn, jf + RESID_FOLD);
+#pragma unroll 2
+                for (int jj = jf; jj < je; ++jj) {
+                    const double a = __ldg(ap + (long)jj * lda);
+                    float ah, am;
+                    if (!df32_split(a, ah, am)) {
+#pragma unroll
+                        for (int c = 0; c < MT; ++c) acc[c] = fma(a, xd[jj][c], acc[c]);
+                        if (rowabs) asum += fabsf(__double2float_rn(a));
+                    }
+                    if (rowabs) asum += fabsf(ah);
+#pragma unroll
+                    for (int c = 0; c < MT; ++c) {
+                        const float2 x = xf[jj][c];
+                        const float p = __fmul_rn(ah, x.x);
+                        const float e = __fmaf_rn(ah, x.x, -p);
+                        const float cr = __fmaf_rn(ah, x.y, __fmaf_rn(am, x.x, e));
+                        const float s = __fadd_rn(S[c], p);
+                        const float bp = __fsub_rn(s, S[c]);
+                        const float t = __fadd_rn(__fsub_rn(S[c], __fsub_rn(s, bp)), __fsub_rn(p, bp));
+                        S[c] = s;
+                        C[c] = __fadd_rn(C[c], __fadd_rn(t, cr));
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < MT; ++c) {
+                    acc[c] += (double)S[c] + (double)C[c];
+                    S[c] = 0.f;
+                    C[c] = 0.f;
+                }
+            }
+        }
+    }
+    if (i < n) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c)
+            if (c < mc) P[((long)blockIdx.y * mtot + c0 + c) * n + i] = acc[c] * sc[mtot + c0 + c];
+        if (rowabs) rowabs[(long)blockIdx.y * n + i] = asum;
+    }
 }

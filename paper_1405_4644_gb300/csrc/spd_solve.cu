@@ -78,10 +78,12 @@ extern "C" const char* spd_last_error_string(const spd_handle* h) { return h ? h
 namespace {
 
 struct ResidWs {
-    double* P;      // S x m x n partial sums
-    float* rowabs;  // S x n
+    double* P;      // max(S, Sdf) x m x n partial sums
+    float* rowabs;  // max(S, Sdf) x n
     double* NP;     // G x m x 3
-    int S;
+    int S;          // column splits of the float64 kernel
+    double* xsc;    // 2 m column scales of the DF32 kernel
+    int Sdf;        // column splits of the DF32 kernel
 };
 
 int resid_splits(spd_handle* h, int n) {
@@ -91,26 +93,97 @@ int resid_splits(spd_handle* h, int n) {
     return std::min(want, maxs);
 }
 
+// The DF32 kernel holds two CTAs per SM: pick the split count whose grid
+// fills whole waves best (at least two waves when the size allows).
+int resid_splits_df32(spd_handle* h, int n) {
+    const int rowblk = ceil_div(n, RESID_ROWS);
+    const int slots = 2 * h->sms;
+    const int maxs = std::max(1, n / (2 * RESID_FOLD));
+    int best = 1;
+    double best_eff = -1.0;
+    for (int s = 1; s <= maxs; ++s) {
+        const long ctas = (long)rowblk * s;
+        const long waves = (ctas + slots - 1) / slots;
+        double eff = (double)ctas / ((double)waves * slots);
+        if (ctas < 2L * slots && s < maxs) eff *= 0.5;  // too few CTAs to hide latency
+        if (eff > best_eff + 1e-9) {
+            best_eff = eff;
+            best = s;
+        }
+        if (ctas >= 4L * slots) break;
+    }
+    return best;
+}
+
 size_t resid_plan(WsPlan& p, spd_handle* h, int n, int m, size_t* offs) {
     int S = resid_splits(h, n);
+    int Smax = std::max(S, resid_splits_df32(h, n));
     int G = ceil_div(n, 256);
-    offs[0] = p.add<double>((size_t)S * m * n);
-    offs[1] = p.add<float>((size_t)S * n);
+    offs[0] = p.add<double>((size_t)Smax * m * n);
+    offs[1] = p.add<float>((size_t)Smax * n);
     offs[2] = p.add<double>((size_t)G * m * 3);
+    offs[3] = p.add<double>((size_t)2 * m);
     return S;
+}
+
+ResidWs resid_ws(spd_handle* h, int n, const size_t* off, int S) {
+    return ResidWs{ws_at<double>(h, off[0]), ws_at<float>(h, off[1]), ws_at<double>(h, off[2]), S,
+                   ws_at<double>(h, off[3]), resid_splits_df32(h, n)};
 }
 
 // R = B - A X (mode 0) or R = A X (mode 1), float64; colnorms[3m]; if anorm
 // is non-null also ||A||_inf.
-spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda, const double* B,
-                     long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
-                     int mode) {
+// The DF32 variant of the partial-sum pass (same partial layout).
+spd_status resid_partial_df32(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda,
+                              const double* X, long ldx, bool with_rowabs) {
     cudaStream_t s = h->stream;
-    ProfScope ps(h, SPD_PHASE_RESID, 2.0 * n * (double)n * m, 8.0 * n * (double)n + 24.0 * n * (double)m);
-    const int S = w.S;
+    const int S = w.Sdf;
     const int jchunk = (int)round_up(ceil_div(n, S), RESID_JT);
     dim3 grid(ceil_div(n, RESID_ROWS), S);
+    ++(h)->launches, k_xscale<<<m, 256, 0, s>>>(X, ldx, n, m, w.xsc);
     for (int c0 = 0; c0 < m; c0 += 16) {
+        int mc = std::min(16, m - c0);
+        float* ra = (with_rowabs && c0 == 0) ? w.rowabs : nullptr;
+        if (mc == 1)
+            ++(h)->launches, k_resid_partial_df32<1><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        else if (mc == 2)
+            ++(h)->launches, k_resid_partial_df32<2><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        else if (mc <= 4)
+            ++(h)->launches, k_resid_partial_df32<4><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        else if (mc <= 8)
+            ++(h)->launches, k_resid_partial_df32<8><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        else
+            ++(h)->launches, k_resid_partial_df32<16><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        LAUNCH_CHECK(h);
+    }
+    return SPD_OK;
+}
+
+// SPD_RESID_DF32 in the refinement loops: float32-pair residuals while the
+// largest backward error is above 2^-36 (16 times their own error bound
+// 2^-40 |A||x|, so the correction they drive is as good as a float64 one),
+// float64 residuals from there on; only a float64 residual may accept a
+// column as converged.
+constexpr double DF32_SWITCH = 1.4551915228366852e-11;  // 2^-36
+
+int resid_kind_for(const spd_opts& o, double berr_now, int pending = 0) {
+    return (o.resid == SPD_RESID_DF32 && pending == 0 && !(berr_now <= DF32_SWITCH)) ? SPD_RESID_DF32
+                                                                                      : SPD_RESID_FP64;
+}
+
+spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda, const double* B,
+                     long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
+                     int mode, int kind = SPD_RESID_FP64) {
+    cudaStream_t s = h->stream;
+    ProfScope ps(h, SPD_PHASE_RESID, 2.0 * n * (double)n * m, 8.0 * n * (double)n + 24.0 * n * (double)m);
+    const int S = kind == SPD_RESID_DF32 ? w.Sdf : w.S;
+    const int jchunk = (int)round_up(ceil_div(n, S), RESID_JT);
+    dim3 grid(ceil_div(n, RESID_ROWS), S);
+    if (kind == SPD_RESID_DF32) {
+        spd_status st = resid_partial_df32(h, w, n, m, A, lda, X, ldx, anorm != nullptr);
+        if (st != SPD_OK) return st;
+    }
+    for (int c0 = 0; c0 < m && kind != SPD_RESID_DF32; c0 += 16) {
         int mc = std::min(16, m - c0);
         float* ra = (anorm && c0 == 0) ? w.rowabs : nullptr;
         if (mc == 1)
@@ -292,22 +365,33 @@ bool bad_args(int n, int m, const void* A, int lda, const void* B, int ldb, cons
 // ---------------------------------------------------------------------------
 // public building blocks
 // ---------------------------------------------------------------------------
-extern "C" spd_status spd_residual(spd_handle* h, int n, int m, const double* A, int lda, const double* B, int ldb,
-                                   const double* X, int ldx, double* R, int ldr, double* colnorms) {
+namespace {
+spd_status residual_entry(spd_handle* h, int kind, int n, int m, const double* A, int lda, const double* B, int ldb,
+                          const double* X, int ldx, double* R, int ldr, double* colnorms) {
     if (!h) return SPD_ERR_ARG;
     if (bad_args(n, m, A, lda, B, ldb, X, ldx) || (n > 0 && m > 0 && (!R || ldr < n)))
         return set_err(h, SPD_ERR_ARG, "spd_residual: bad arguments");
     if (n == 0 || m == 0) return SPD_OK;
     WsPlan p;
-    size_t off[3];
+    size_t off[4];
     int S = (int)resid_plan(p, h, n, m, off);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
-    ResidWs w{ws_at<double>(h, off[0]), ws_at<float>(h, off[1]), ws_at<double>(h, off[2]), S};
-    st = resid_run(h, w, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms, nullptr, 0);
+    st = resid_run(h, resid_ws(h, n, off, S), n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms, nullptr, 0, kind);
     if (st != SPD_OK) return st;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return SPD_OK;
+}
+}  // namespace
+
+extern "C" spd_status spd_residual(spd_handle* h, int n, int m, const double* A, int lda, const double* B, int ldb,
+                                   const double* X, int ldx, double* R, int ldr, double* colnorms) {
+    return residual_entry(h, SPD_RESID_FP64, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms);
+}
+
+extern "C" spd_status spd_residual_df32(spd_handle* h, int n, int m, const double* A, int lda, const double* B,
+                                        int ldb, const double* X, int ldx, double* R, int ldr, double* colnorms) {
+    return residual_entry(h, SPD_RESID_DF32, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms);
 }
 
 extern "C" spd_status spd_factor_solve(spd_handle* h, const spd_factor_t* F, int n, int m, const double* R, int ldr,
@@ -379,48 +463,48 @@ size_t cg_plan(WsPlan& p, spd_handle* h, int n, int m, size_t* o, int* S, int* G
     *S = (int)resid_plan(p, h, n, m, o);
     *G2 = std::max(1, std::min(2 * h->sms, ceil_div(n, 256)));
     size_t nm = (size_t)n * m;
-    o[3] = p.add<double>(nm);       // R
-    o[4] = p.add<double>(3 * m);    // colnorms
-    o[5] = p.add<double>(1);        // anorm
-    o[6] = p.add<double>(m);        // b2
-    o[7] = p.add<double>(m);        // target
-    o[8] = p.add<double>(nm);       // E
-    o[9] = p.add<double>(nm);       // Rr
-    o[10] = p.add<double>(nm);      // Z
-    o[11] = p.add<double>(nm);      // P
-    o[12] = p.add<double>(nm);      // Q
-    o[13] = p.add<double>((size_t)(*G2) * m * 2);  // part
-    o[14] = p.add<double>(nm);      // Yz (factor preconditioner scratch)
-    o[15] = p.add<float>(nm);       // Pf
-    o[16] = p.add<IrCol>(m);
-    o[17] = p.add<IrSummary>(1);
-    o[18] = p.add<CgCol>(m);
-    o[19] = p.add<int>(m);          // frozen
-    o[20] = p.add<int>(1);          // active
+    o[4] = p.add<double>(nm);       // R
+    o[5] = p.add<double>(3 * m);    // colnorms
+    o[6] = p.add<double>(1);        // anorm
+    o[7] = p.add<double>(m);        // b2
+    o[8] = p.add<double>(m);        // target
+    o[9] = p.add<double>(nm);       // E
+    o[10] = p.add<double>(nm);       // Rr
+    o[11] = p.add<double>(nm);      // Z
+    o[12] = p.add<double>(nm);      // P
+    o[13] = p.add<double>(nm);      // Q
+    o[14] = p.add<double>((size_t)(*G2) * m * 2);  // part
+    o[15] = p.add<double>(nm);      // Yz (factor preconditioner scratch)
+    o[16] = p.add<float>(nm);       // Pf
+    o[17] = p.add<IrCol>(m);
+    o[18] = p.add<IrSummary>(1);
+    o[19] = p.add<CgCol>(m);
+    o[20] = p.add<int>(m);          // frozen
+    o[21] = p.add<int>(1);          // active
     return p.bytes;
 }
 
-CgWs cg_bind(spd_handle* h, const size_t* o, int S, int G2) {
+CgWs cg_bind(spd_handle* h, int n, const size_t* o, int S, int G2) {
     CgWs w;
-    w.rw = ResidWs{ws_at<double>(h, o[0]), ws_at<float>(h, o[1]), ws_at<double>(h, o[2]), S};
-    w.R = ws_at<double>(h, o[3]);
-    w.colnorms = ws_at<double>(h, o[4]);
-    w.anorm = ws_at<double>(h, o[5]);
-    w.b2 = ws_at<double>(h, o[6]);
-    w.target = ws_at<double>(h, o[7]);
-    w.E = ws_at<double>(h, o[8]);
-    w.Rr = ws_at<double>(h, o[9]);
-    w.Z = ws_at<double>(h, o[10]);
-    w.P = ws_at<double>(h, o[11]);
-    w.Q = ws_at<double>(h, o[12]);
-    w.part = ws_at<double>(h, o[13]);
-    w.Yz = ws_at<double>(h, o[14]);
-    w.Pf = ws_at<float>(h, o[15]);
-    w.cols = ws_at<IrCol>(h, o[16]);
-    w.sum = ws_at<IrSummary>(h, o[17]);
-    w.cg = ws_at<CgCol>(h, o[18]);
-    w.frozen = ws_at<int>(h, o[19]);
-    w.active = ws_at<int>(h, o[20]);
+    w.rw = resid_ws(h, n, o, S);
+    w.R = ws_at<double>(h, o[4]);
+    w.colnorms = ws_at<double>(h, o[5]);
+    w.anorm = ws_at<double>(h, o[6]);
+    w.b2 = ws_at<double>(h, o[7]);
+    w.target = ws_at<double>(h, o[8]);
+    w.E = ws_at<double>(h, o[9]);
+    w.Rr = ws_at<double>(h, o[10]);
+    w.Z = ws_at<double>(h, o[11]);
+    w.P = ws_at<double>(h, o[12]);
+    w.Q = ws_at<double>(h, o[13]);
+    w.part = ws_at<double>(h, o[14]);
+    w.Yz = ws_at<double>(h, o[15]);
+    w.Pf = ws_at<float>(h, o[16]);
+    w.cols = ws_at<IrCol>(h, o[17]);
+    w.sum = ws_at<IrSummary>(h, o[18]);
+    w.cg = ws_at<CgCol>(h, o[19]);
+    w.frozen = ws_at<int>(h, o[20]);
+    w.active = ws_at<int>(h, o[21]);
     w.G2 = G2;
     return w;
 }
@@ -453,9 +537,11 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
         CUDA_TRY(h, cudaMemset2DAsync(X, sizeof(double) * ldx, 0, sizeof(double) * n, m, s));
         ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, 0);
         ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
-        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0);
+        const int rk = resid_kind_for(o, INFINITY);
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);
         if (st != SPD_OK) return st;
-        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0, 0);
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0, 0,
+                                                      rk == SPD_RESID_FP64);
         LAUNCH_CHECK(h);
     }
     CUDA_TRY(h, cudaMemsetAsync(w.cg, 0, sizeof(CgCol) * m, s));
@@ -496,7 +582,7 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                 ++(h)->launches, k_matvec_band<<<gv, 256, 0, s>>>(static_cast<const float*>(cs.At), n, cs.band, w.Pf, m, w.Q);
                     break;
                 default:
-                    st = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1);
+                    st = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1, o.resid);
                     if (st != SPD_OK) return st;
             }
             LAUNCH_CHECK(h);
@@ -520,9 +606,11 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             }
         }
         ++(h)->launches, k_add_cols<<<gv, 256, 0, s>>>(X, ldx, w.E, n, m, w.frozen);
-        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0);
+        const int rk = resid_kind_for(o, sm.max_berr, sm.pending);
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);
         if (st != SPD_OK) return st;
-        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1, 0);
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1, 0,
+                                                      rk == SPD_RESID_FP64);
         LAUNCH_CHECK(h);
         ++outer;
     }
@@ -551,17 +639,17 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     if (opts_in) o = *opts_in;
     if (rep) memset(rep, 0, sizeof(*rep));
     if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2)
+        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_DF32)
         return set_err(h, SPD_ERR_ARG, "spd_solve_ir: bad arguments");
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
     WsPlan p;
-    size_t o_[21];
+    size_t o_[22];
     int S, G2;
     cg_plan(p, h, n, m, o_, &S, &G2);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
-    CgWs w = cg_bind(h, o_, S, G2);
+    CgWs w = cg_bind(h, n, o_, S, G2);
     CUDA_TRY(h, cudaEventRecord(h->e0, s));
 
     ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, std::max(0, o.polish));
@@ -569,10 +657,11 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     LAUNCH_CHECK(h);
     st = lp_apply(h, F, n, m, B, ldb, w.Yz, X, ldx, nullptr, 0);  // line 2
     if (st != SPD_OK) return st;
-    st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0);  // line 3
+    int rk = resid_kind_for(o, INFINITY);
+    st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);  // line 3
     if (st != SPD_OK) return st;
     ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0,
-                                                  std::max(0, o.polish));
+                                                  std::max(0, o.polish), rk == SPD_RESID_FP64);
     LAUNCH_CHECK(h);
 
     int sweeps = 0, low = 1, high = 1, fell = 0;
@@ -607,10 +696,11 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
         ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
         st = lp_apply(h, F, n, m, w.R, n, w.Yz, X, ldx, w.frozen, 1);  // lines 5-6
         if (st != SPD_OK) return st;
-        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0);  // line 7
+        rk = resid_kind_for(o, sm.max_berr, sm.pending);
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);  // line 7
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1,
-                                                      std::max(0, o.polish));
+                                                      std::max(0, o.polish), rk == SPD_RESID_FP64);
         LAUNCH_CHECK(h);
         ++sweeps;
         ++low;
@@ -646,7 +736,8 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (opts_in) o = *opts_in;
     if (rep) memset(rep, 0, sizeof(*rep));
     if (bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || o.maxit_inner < 1 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_LOWRANK ||
+        o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_LOWRANK || o.resid < SPD_RESID_FP64 ||
+        o.resid > SPD_RESID_DF32 ||
         ((pc == SPD_PC_FACTOR || pc == SPD_PC_LOWRANK) && !pc_data))
         return set_err(h, SPD_ERR_ARG, "spd_cg: bad arguments");
     if (matvec_prec != SPD_PREC_FP64 && matvec_prec != SPD_PREC_FP32 && matvec_prec != SPD_PREC_BF16)
@@ -660,7 +751,7 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
     WsPlan p;
-    size_t o_[21];
+    size_t o_[22];
     int S, G2;
     cg_plan(p, h, n, m, o_, &S, &G2);
     CgSetup cs;
@@ -683,7 +774,7 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (pc == SPD_PC_JACOBI) o_dinv = p.add<double>(n);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
-    CgWs w = cg_bind(h, o_, S, G2);
+    CgWs w = cg_bind(h, n, o_, S, G2);
     CUDA_TRY(h, cudaEventRecord(h->e0, s));
     const int gbig = grid_for((long)n * n, 256, 16 * h->sms);
     if (cs.matvec == MV_BAND) {
