@@ -210,6 +210,53 @@ def cpu_oracle_sample(n_full, m, seconds_hint=20.0):
                       f"{t:.2f} s, scaled by (n/{ns})^3 to n={n_full}"}
 
 
+# FP32 instruction issue rate of the part: 152 SMs x 128 lanes x 2.07 GHz
+FP32_OPS_PEAK_T = 152 * 2.07e9 * 128 / 1e12
+# float32 instructions per multiply-add of the float32-pair residual
+# (1 FMUL, 3 FFMA, 8 FADD: product, exact error, cross terms, TwoSum, pair)
+DF32_OPS_PER_MADD = 12
+
+
+def roofline(phases, per_kappa):
+    """Roofline of the phase (kernel family) that took the most device time
+    in the timed region; achieved = its algorithmic work / its event time."""
+    peaks, src = load_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    dom = max(phases, key=lambda p: phases[p]["ms"])
+    ph = phases[dom]
+    sec = ph["ms"] * 1e-3
+    low = sorted({k["prec_used"] for k in per_kappa} & set(TENSOR_RATIO))
+    if dom == "trailing" and low:
+        ratio = min(TENSOR_RATIO[p] for p in low)
+        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": bf16 * ratio,
+             "peak_source": f"{src} bf16 sustained x nominal {'/'.join(low)} ratio {ratio}"}
+    elif dom == "trailing_x3":
+        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12,
+             "peak": bf16 * TENSOR_RATIO["tf32"] / 6,
+             "peak_source": f"{src} bf16 sustained x nominal tf32 ratio 0.5 / 6 tf32 products per float32 product"}
+    elif dom == "resid":
+        r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP64_PEAK_TFLOPS,
+             "peak_source": "nominal FP64 1.25 TFLOP/s of the part"}
+    elif dom == "resid_df32":
+        r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / 2 * DF32_OPS_PER_MADD / sec / 1e12,
+             "peak": FP32_OPS_PEAK_T,
+             "peak_source": "float32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz (one op per instruction)"}
+    elif dom in ("trailing", "leaf", "panel"):
+        r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
+             "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    else:
+        r = {"bound": "hbm", "unit": "GB/s", "achieved": ph["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
+             "peak_source": f"{src} copy bandwidth"}
+    work = ph["flops"] if r["unit"] == "TFLOP/s" else ph["bytes"]
+    if dom == "resid_df32":
+        work = ph["flops"] / 2 * DF32_OPS_PER_MADD
+    r.update({"frac": r["achieved"] / r["peak"], "kernel_phase": dom, "launches": ph["launches"],
+              "avg_launch_ms": ph["ms"] / max(ph["launches"], 1), "traffic": None,
+              "algorithmic_per_launch": work / max(ph["launches"], 1)})
+    return r
+
+
+
 def reference_arm(args):
     """The oracle as it stands on the host cores, timed like our arm."""
     rank = int(os.environ.get("RANK", "0"))
@@ -385,6 +432,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--resid", default="df32", choices=["fp64", "df32"],
+                    help="refinement residual: float64, or float32 pairs until berr < 2^-36 then float64")
     ap.add_argument("--leg", default="main", choices=["main", "batched", "learned"])
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n-learned", type=int, default=4096)
@@ -412,7 +461,7 @@ def main():
     h = spd.spd_create(stream)
     systems = make_systems(args.n, args.m, args.kappas, dev)
     X = torch.zeros(args.m, args.n, dtype=torch.float64, device=dev).t()
-    opts = {"tol": 1e-14, "crit": "berr"}
+    opts = {"tol": 1e-14, "crit": "berr", "resid": args.resid}
 
     for _ in range(args.warmup):
         run_step(spd, h, systems, precs, X, opts)
@@ -446,28 +495,10 @@ def main():
     value = solves / (ms_max / 1e3)
 
     # dominant phase and its roofline
-    peaks, peak_src = load_peaks()
-    dom = max(phases, key=lambda p: phases[p]["ms"])
-    ph = phases[dom]
-    per_launch_ms = ph["ms"] / max(ph["launches"], 1)
-    if dom == "trailing" and precs[0] in TENSOR_RATIO:
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TENSOR_RATIO[precs[0]]
-        roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / (ph["ms"] * 1e-3) / 1e12,
-                "peak": peak, "peak_source": f"{peak_src} bf16 sustained x nominal {precs[0]} ratio"}
-    elif dom in ("resid",):
-        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / (ph["ms"] * 1e-3) / 1e12,
-                "peak": FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 1.25 TFLOP/s (no measured FP64 peak)"}
-    elif dom in ("trailing", "leaf"):
-        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / (ph["ms"] * 1e-3) / 1e12,
-                "peak": FP32_SIMT_PEAK_TFLOPS, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    else:
-        roof = {"bound": "hbm", "unit": "GB/s", "achieved": ph["bytes"] / (ph["ms"] * 1e-3) / 1e9,
-                "peak": peaks["hbm_gbs"], "peak_source": f"{peak_src} copy bandwidth"}
-    roof.update({"frac": roof["achieved"] / roof["peak"], "kernel_phase": dom, "launches": ph["launches"],
-                 "avg_launch_ms": per_launch_ms, "traffic": None,
-                 "algorithmic_per_launch": (ph["flops"] if roof["unit"] == "TFLOP/s" else ph["bytes"])
-                 / max(ph["launches"], 1)})
-
+    per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
+                  "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
+                  "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
+    roof = roofline(phases, per_kappa)
     energy = None
     if e0 is not None and e1 is not None:
         j = (e1 - e0) / 1e3
@@ -478,17 +509,13 @@ def main():
         energy = {"j_per_solve": j / (len(systems) * args.steps), "avg_power_w": clocks["avg_power_w"],
                   "source": "nvidia-smi power.draw mean x time, gross"}
 
-    per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
-                  "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
-                  "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
-
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None
     if not args.no_fp64:
         kappa, A, B = systems[0]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        (fr, r), = run_step(spd, h, [systems[0]], ["fp64"], X, opts)
+        (fr, r), = run_step(spd, h, [systems[0]], ["fp64"], X, dict(opts, resid="fp64"))
         torch.cuda.synchronize()
         t_ours = time.perf_counter() - t0
         t0 = time.perf_counter()
@@ -537,7 +564,10 @@ def main():
                "data": "synthetic",
                "config": {"workload": f"precision sweep n={args.n} m={args.m} kappa in {args.kappas}",
                           "n": args.n, "m": args.m, "kappas": args.kappas, "factor_prec": precs,
-                          "l2": "inputs larger than L2 (3 x 8 n^2 bytes resident)", "tol_berr": 1e-14},
+                          "l2": "inputs larger than L2 (3 x 8 n^2 bytes resident)", "tol_berr": 1e-14,
+                          "residual": {"fp64": "float64 throughout",
+                                       "df32": "float32 pairs while berr > 2^-36, float64 to finish "
+                                               "(convergence only accepted on a float64 residual)"}[args.resid]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "energy": energy, "fp64_baseline": fp64, "per_kappa": per_kappa,
                "phases": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in phases.items()}}

@@ -377,7 +377,10 @@ typedef enum spd_phase {
     SPD_PHASE_VECTOR = 6,   /* A6/C2: float64 vector updates and dots    */
     SPD_PHASE_PANEL = 7,    /* A2: panel triangular solves (leaf TRSM)   */
     SPD_PHASE_BATCH = 8,    /* B1: persistent batched solves             */
-    SPD_PHASE_COUNT = 9
+    SPD_PHASE_TRAILING_X3 = 9, /* A3 of an FP32 factor: three tf32 slices
+                                  on the tensor cores (flops counted once) */
+    SPD_PHASE_RESID_DF32 = 10, /* A5/C3 on the float32 units (float32 pairs) */
+    SPD_PHASE_COUNT = 11
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

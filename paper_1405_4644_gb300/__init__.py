@@ -312,7 +312,8 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
     return st, rep
 
 
-PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch"]
+PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch", "trailing_x3",
+          "resid_df32"]
 
 
 def spd_profile_enable(h, on=True):

@@ -68,7 +68,7 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower)
     const double opsz = sizeof(T) == 8 ? 8.0
                         : c.mir.kind == 5 ? 12.0
                         : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
-    ProfScope ps(c.h, SPD_PHASE_TRAILING, 2.0 * celems * K,
+    ProfScope ps(c.h, (c.tc && c.mir.kind == 5) ? SPD_PHASE_TRAILING_X3 : SPD_PHASE_TRAILING, 2.0 * celems * K,
                  2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N));
     if constexpr (sizeof(T) == 8) {
         dim3 grid(ceil_div(N, 64), ceil_div(M, 64));

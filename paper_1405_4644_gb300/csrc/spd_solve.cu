@@ -175,7 +175,8 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
                      long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
                      int mode, int kind = SPD_RESID_FP64) {
     cudaStream_t s = h->stream;
-    ProfScope ps(h, SPD_PHASE_RESID, 2.0 * n * (double)n * m, 8.0 * n * (double)n + 24.0 * n * (double)m);
+    ProfScope ps(h, kind == SPD_RESID_DF32 ? SPD_PHASE_RESID_DF32 : SPD_PHASE_RESID, 2.0 * n * (double)n * m,
+                 8.0 * n * (double)n + 24.0 * n * (double)m);
     const int S = kind == SPD_RESID_DF32 ? w.Sdf : w.S;
     const int jchunk = (int)round_up(ceil_div(n, S), RESID_JT);
     dim3 grid(ceil_div(n, RESID_ROWS), S);

@@ -129,10 +129,14 @@ def test_table1_iteration_band_full_size(h, d):
     g = json.load(open(GOLDEN))
     row = next(r for r in g["rows"] if r[0] == "cg" and r[1] == d and r[2] == 1)
     n = g["n"]
+    # the model covariance of Section 4, assembled in row blocks so that the
+    # device holds A (39 GB) plus one 2 GB block of temporaries
     i = torch.arange(n, dtype=torch.float64, device="cuda")
-    k = (i[:, None] - i[None, :]).abs_()
-    A = torch.where(k > 0, 1.0 / k.clamp_min(1.0).pow(d), torch.zeros((), dtype=torch.float64, device="cuda"))
-    del k
+    A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    for r0 in range(0, n, 4096):
+        blk = A[r0:r0 + 4096]
+        torch.sub(i[r0:r0 + 4096, None], i[None, :], out=blk)
+        blk.abs_().clamp_min_(1.0).pow_(d).reciprocal_()
     A.diagonal().copy_(1.0 + torch.sqrt(i + 1.0))
     B = dev_cols(W.uniform_rhs(n, 1, 0))
     X = dev_zeros(n, 1)
