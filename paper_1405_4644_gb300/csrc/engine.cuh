@@ -48,6 +48,8 @@ struct spd_factor_t {
     double* d = nullptr;       // scaling
     double* Dinv64 = nullptr;  // float64 factor: 32x32 diagonal sub-block inverses
     float* LinvT = nullptr;    // float32 factor: (L_JJ^{-1})^T of every 128x128 block
+    float* Cpl = nullptr;      // float32 factor: sweep couplings M_J, N_J (2 x nblk128 blocks)
+    float* Dinv32 = nullptr;   // float32 factor: inverses of the 32x32 diagonal sub-blocks
     int nblk128 = 0;
 };
 
@@ -169,6 +171,7 @@ struct ProfScope {
 // y <- (L L^T)^{-1} y for one float32 vector of the scaled system (no d
 // scaling); defined with the triangular-solve kernels.
 spd_status factor_apply_scaled_f32(spd_handle* h, const spd_factor_t* F, float* y);
+spd_status factor_couplings(spd_handle* h, spd_factor_t* F);
 
 // learned low-rank preconditioner hooks for the CG driver (spd_learned.cu)
 struct spd_lowrank;

@@ -1,13 +1,19 @@
 // k_leaf32.cuh -- float32 leaves of the low-precision factorisation (steps
-// A1/A2 of Section 3.1's Cholesky), built around the full inverse of each
-// 128x128 diagonal block:
+// A1/A2 of Section 3.1's Cholesky) and the per-block inverses the
+// triangular sweeps use:
 //
-//   k_potrf_leaf32  factors W[k:k+nb, k:k+nb] = L L^T (four 32x32 sub-steps,
-//                   warp-level pivots) and forms X = L^{-1} by block rows,
-//                   X_i = I_ii (E_i - sum_{j<i} L_ij X_j), I_ii the 32x32
-//                   inverses; stores L (and its operand mirror) and X^T.
-//   k_trsm_leaf32   panel solve X L^T = B as the product B (L^{-1})^T, one
-//                   register-tiled 64 x 128 block of rows per CTA.
+//   k_potrf_leaf32   factors W[k:k+nb, k:k+nb] = L L^T in four 32-column
+//                    steps: one warp factors the 32x32 diagonal block
+//                    (warp-level pivots) and inverts it by right-looking
+//                    substitution with the pivots' reciprocals; all warps
+//                    form the sub-panel below it with that inverse and
+//                    update the rest of the block.  Stores L (and its
+//                    operand mirror) and the four 32x32 inverses.
+//   k_trsm_leaf32    panel solve X L^T = B for 64 rows per CTA in four
+//                    32-column steps with the same 32x32 inverses.
+//   k_block_inverse  after the whole factorisation, off the critical path
+//                    and one CTA per block: the full (L_JJ^{-1})^T of every
+//                    128x128 diagonal block, for the sweeps.
 //
 // The float64 baseline keeps the sub-block kernels of k_leaf.cuh.
 #pragma once
@@ -15,16 +21,16 @@
 
 #define LD32 129
 
-constexpr size_t potrf_leaf32_smem() { return (size_t)(2 * 128 * LD32 + 96 * 33) * sizeof(float); }
+// Dinv32 for block b lives at Dinv32 + b * 4096: four row-major 32x32
+// blocks, D_s[i][c] = (L_ss^{-1})[i][c] (lower triangular).
+constexpr size_t potrf_leaf32_smem() { return (size_t)(128 * LD32 + 32 * 33 + 96 * 33) * sizeof(float); }
 
-// Linv_T for block b lives at LinvT + b * 128 * 128, row-major:
-// LinvT[l][c] = (L^{-1})[c][l]  (upper triangular).
 __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, long ldw, int k, int nb,
-                                                      float* __restrict__ LinvT, Mirror mir, DevStatus* st) {
+                                                      float* __restrict__ Dinv32, Mirror mir, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* S = reinterpret_cast<float*>(smem_raw);  // [128][129] the block, then L
-    float* X = S + 128 * LD32;                      // [128][129] L^{-1}
-    float* Tmp = X + 128 * LD32;                    // [96][33] or [32][97] scratch
+    float* Dj = S + 128 * LD32;                     // [32][33] inverse of the current 32x32 diagonal block
+    float* Tmp = Dj + 32 * 33;                      // [96][33] sub-panel scratch
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
@@ -46,7 +52,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
             d[2] = (c4 + 2 <= r) ? v[q].z : 0.f;
             d[3] = (c4 + 3 <= r) ? v[q].w : 0.f;
         }
-    } else {
+    } else {  // ragged last block: identity beyond nb
         for (int e = tid; e < 128 * 128; e += 256) {
             int r = e >> 7, c = e & 127;
             float v;
@@ -55,14 +61,15 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
             S[r * LD32 + c] = v;
         }
     }
-    for (int e = tid; e < 128 * 128; e += 256) X[(e >> 7) * LD32 + (e & 127)] = 0.f;
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    float* Dout = Dinv32 + (long)(k / 128) * 4096;
 
     for (int J = 0; J < 4; ++J) {
         const int o = J * 32;
         if (warp == 0) {
-            float a[32];
+            // lane r holds row o + r of the diagonal block
+            float a[32], rd[32];
 #pragma unroll
             for (int c = 0; c < 32; ++c) a[c] = S[(o + lane) * LD32 + o + c];
             int badj = -1;
@@ -74,7 +81,8 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
                     piv = 1.f;
                 }
                 const float dj = sqrtf(piv);
-                const float inv = 1.f / dj;
+                const float inv = __frcp_rn(dj);
+                rd[j] = inv;
                 a[j] = (lane == j) ? dj : (lane > j ? a[j] * inv : a[j]);
 #pragma unroll
                 for (int l = 0; l < 32; ++l) {  // constant bounds: fully unrolled, a[] stays in registers
@@ -92,36 +100,38 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
                 dev_raise(st, SPD_DEV_BREAKDOWN);
             }
             __syncwarp();
-            // lane c: column c of the 32x32 inverse, by forward substitution;
-            // row i of L is broadcast from shared memory
+            // lane c: column c of the inverse, right-looking: x_i = s_i / L_ii,
+            // then s_r -= L_ri x_i for r > i (independent updates, short chain)
             float x[32];
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const float* li = S + (o + i) * LD32 + o;
-                float s = (i == lane) ? 1.f : 0.f;
+            for (int i = 0; i < 32; ++i) x[i] = (i == lane) ? 1.f : 0.f;
 #pragma unroll
-                for (int l = 0; l < 32; ++l)
-                    if (l < i) s = fmaf(-li[l], x[l], s);
-                x[i] = s / li[i];
+            for (int i = 0; i < 32; ++i) {
+                x[i] *= rd[i];
+#pragma unroll
+                for (int r = i + 1; r < 32; ++r) x[r] = fmaf(-S[(o + r) * LD32 + o + i], x[i], x[r]);
             }
 #pragma unroll
-            for (int i = 0; i < 32; ++i) X[(o + i) * LD32 + o + lane] = x[i];
+            for (int i = 0; i < 32; ++i) {
+                Dj[i * 33 + lane] = x[i];
+                Dout[J * 1024 + i * 32 + lane] = x[i];
+            }
         }
         __syncthreads();
         if (s_bad) return;
         const int rows = 128 - (o + 32);
         if (rows == 0) break;
-        // sub-panel below: L_iJ = A_iJ I_JJ^T, 4 outputs per thread-iteration
+        // sub-panel below: L_iJ = A_iJ D_J^T, 4 outputs per thread-iteration
         for (int e = tid; e < rows * 8; e += 256) {
             const int i = e >> 3, c4 = (e & 7) * 4;
             const float* brow = S + (o + 32 + i) * LD32 + o;
             float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             for (int l = 0; l <= c4 + 3; ++l) {
                 const float b = brow[l];
-                s0 += b * X[(o + c4 + 0) * LD32 + o + l];
-                s1 += b * X[(o + c4 + 1) * LD32 + o + l];
-                s2 += b * X[(o + c4 + 2) * LD32 + o + l];
-                s3 += b * X[(o + c4 + 3) * LD32 + o + l];
+                s0 = fmaf(b, Dj[(c4 + 0) * 33 + l], s0);
+                s1 = fmaf(b, Dj[(c4 + 1) * 33 + l], s1);
+                s2 = fmaf(b, Dj[(c4 + 2) * 33 + l], s2);
+                s3 = fmaf(b, Dj[(c4 + 3) * 33 + l], s3);
             }
             float* t = Tmp + i * 33 + c4;
             t[0] = s0;
@@ -162,33 +172,6 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
         }
         __syncthreads();
     }
-    // off-diagonal blocks of X = L^{-1}, block row by block row:
-    // T = L_i,0:i X_0:i,0:i  (into Tmp as [32][97]), then X_i,0:i = -I_ii T
-    for (int i = 1; i < 4; ++i) {
-        const int ri = i * 32, w = i * 32;  // rows ri..ri+31 of X, columns 0..w-1
-        for (int e = tid; e < 32 * w; e += 256) {
-            const int r = e / w, c = e - r * w;
-            const float* lr = S + (ri + r) * LD32;
-            float s = 0.f;
-            for (int l = (c >> 5) << 5; l < ri; ++l) s += lr[l] * X[l * LD32 + c];
-            Tmp[r * 97 + c] = s;
-        }
-        __syncthreads();
-        for (int e = tid; e < 32 * w; e += 256) {
-            const int r = e / w, c = e - r * w;
-            const float* ir = X + (ri + r) * LD32 + ri;
-            float s = 0.f;
-            for (int l = 0; l <= r; ++l) s += ir[l] * Tmp[l * 97 + c];
-            X[(ri + r) * LD32 + c] = -s;
-        }
-        __syncthreads();
-    }
-    // X^T to global: LinvT[l][c] = X[c][l]
-    float* out = LinvT + (long)(k / 128) * 128 * 128;
-    for (int e = tid; e < 128 * 128; e += 256) {
-        const int l = e >> 7, c = e & 127;
-        out[e] = X[c * LD32 + l];
-    }
     for (int e = tid; e < 128 * 128; e += 256) {
         int r = e >> 7, c = e & 127;
         if (r < nb && c <= r) {
@@ -200,78 +183,161 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
 }
 
 // Panel solve for rows [r0, r0 + m) against the factored diagonal block at
-// column c0 (order 128): X = B (L^{-1})^T, i.e. X[r][c] = sum_{l<=c} B[r][l]
-// LinvT[l][c].  CTA = 64 rows; thread = 4 rows x 8 columns; warp w covers
-// columns 16w..16w+15, so its loop stops at l = 16w + 15 (the inverse is
-// lower triangular).
-constexpr size_t trsm_leaf32_smem() { return (size_t)(128 * 68 + 128 * 132) * sizeof(float); }
+// column c0 (order 128): X L^T = B, in four 32-column steps s:
+//   X_s = B_s D_s^T,   B_s' -= X_s L_s's^T  (s' > s),
+// with D_s the 32x32 inverses the leaf stored.  CTA = 64 rows; each thread
+// owns a 4-row by (2 | 6 - 2 s)-column register tile of each step.
+constexpr size_t trsm_leaf32_smem() { return (size_t)(64 * 132 + 96 * LD32 + 4 * 32 * 33) * sizeof(float); }
 
-__global__ void __launch_bounds__(256) k_trsm_leaf32(float* __restrict__ W, long ldw, int r0, int m, int c0,
-                                                     const float* __restrict__ LinvT, Mirror mir,
+__global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, long ldw, int r0, int m, int c0,
+                                                     const float* __restrict__ Dinv32, Mirror mir,
                                                      const DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Bt = reinterpret_cast<float*>(smem_raw);  // [128][68]  Bt[l][r] = B[r][l]
-    float* Lt = Bt + 128 * 68;                       // [128][132] LinvT
+    float* Bs = reinterpret_cast<float*>(smem_raw);  // [64][132] B, becoming X
+    float* Ls = Bs + 64 * 132;                       // [96][129] rows 32..127 of L_kk, columns 0..95
+    float* Ds = Ls + 96 * LD32;                      // [4][32][33] D_s
     if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
     const int tid = threadIdx.x;
     const int rb0 = r0 + blockIdx.x * 64;
-    const float* Lg = LinvT + (long)(c0 / 128) * 128 * 128;
     {
-        float4 vb[8], vl[16];
+        float4 vb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {  // B: 64 rows x 128 columns
             const int e = tid + q * 256, r = e >> 5, c4 = (e & 31) * 4;
             vb[q] = (rb0 + r < r0 + m) ? *reinterpret_cast<const float4*>(W + (long)(rb0 + r) * ldw + c0 + c4)
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = tid + q * 256, l = e >> 5, c4 = (e & 31) * 4;
-            vl[q] = *reinterpret_cast<const float4*>(Lg + l * 128 + c4);
+        for (int e = tid; e < 96 * 96; e += 256) {  // the strictly-below-diagonal 32-blocks of L_kk
+            const int r = e / 96, c = e - r * 96;
+            Ls[r * LD32 + c] = (c < r + 32) ? W[(long)(c0 + 32 + r) * ldw + c0 + c] : 0.f;
         }
+        const float* dg = Dinv32 + (long)(c0 / 128) * 4096;
+        for (int e = tid; e < 4096; e += 256) Ds[(e >> 5) * 33 + (e & 31)] = dg[e];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int e = tid + q * 256, r = e >> 5, c4 = (e & 31) * 4;
-            Bt[(c4 + 0) * 68 + r] = vb[q].x;
-            Bt[(c4 + 1) * 68 + r] = vb[q].y;
-            Bt[(c4 + 2) * 68 + r] = vb[q].z;
-            Bt[(c4 + 3) * 68 + r] = vb[q].w;
-        }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int e = tid + q * 256, l = e >> 5, c4 = (e & 31) * 4;
-            *reinterpret_cast<float4*>(Lt + l * 132 + c4) = vl[q];
+            *reinterpret_cast<float4*>(Bs + r * 132 + c4) = vb[q];
         }
     }
     __syncthreads();
-    const int warp = tid >> 5, lane = tid & 31;
-    const int cb = warp * 16 + (lane >> 4) * 8;  // 8 columns
-    const int rr = (lane & 15) * 4;              // 4 rows
-    const int lmax = warp * 16 + 16;
-    float acc[4][8];
+    // thread tile: rows tr..tr+3 (16 row groups) x a column group (16 groups)
+    const int tr = (tid >> 4) * 4, cgp = tid & 15;
+    for (int s = 0; s < 4; ++s) {
+        const int o = s * 32;
+        const float* D = Ds + s * 32 * 33;
+        // X_s, columns o + c, o + c + 1 (D[c][l] = 0 for l > c)
+        const int c = 2 * cgp;
+        float x[4][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) x[j][0] = x[j][1] = 0.f;
+        for (int l = 0; l <= c + 1; ++l) {
+            const float d0 = D[c * 33 + l], d1 = D[(c + 1) * 33 + l];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-    for (int l = 0; l < lmax; ++l) {
-        const float4 a = *reinterpret_cast<const float4*>(Bt + l * 68 + rr);
-        const float4 b0 = *reinterpret_cast<const float4*>(Lt + l * 132 + cb);
-        const float4 b1 = *reinterpret_cast<const float4*>(Lt + l * 132 + cb + 4);
-        const float av[4] = {a.x, a.y, a.z, a.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            for (int j = 0; j < 4; ++j) {
+                const float b = Bs[(tr + j) * 132 + o + l];
+                x[j][0] = fmaf(b, d0, x[j][0]);
+                x[j][1] = fmaf(b, d1, x[j][1]);
+            }
+        }
+        __syncthreads();  // every read of B_s done
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            Bs[(tr + j) * 132 + o + c] = x[j][0];
+            Bs[(tr + j) * 132 + o + c + 1] = x[j][1];
+        }
+        __syncthreads();
+        if (s == 3) break;
+        // B_s' -= X_s L_s's^T for the 96 - 32 s columns to the right: CW each
+        const int CW = 6 - 2 * s;
+        const int cb = o + 32 + cgp * CW;  // first column (= row of L) of this thread
+        float acc[4][6];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 6; ++q) acc[j][q] = 0.f;
+#pragma unroll 2
+        for (int l = 0; l < 32; ++l) {
+            float xv[4], lv[6];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) xv[j] = Bs[(tr + j) * 132 + o + l];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) lv[q] = (q < CW) ? Ls[(cb + q - 32) * LD32 + o + l] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) acc[j][q] = fmaf(xv[j], lv[q], acc[j][q]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int q = 0; q < 6; ++q)
+                if (q < CW) Bs[(tr + j) * 132 + cb + q] -= acc[j][q];
+        __syncthreads();
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long row = rb0 + rr + i;
+    for (int e = tid; e < 64 * 128; e += 256) {
+        const int rr = e >> 7, c = e & 127;
+        const long row = rb0 + rr;
         if (row >= r0 + m) continue;
-        float* dst = W + row * ldw + c0 + cb;
-        *reinterpret_cast<float4*>(dst) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        *reinterpret_cast<float4*>(dst + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) mirror_store(mir, row, (long)(c0 + cb + j), acc[i][j]);
+        const float v = Bs[rr * 132 + c];
+        W[row * ldw + c0 + c] = v;
+        mirror_store(mir, row, (long)(c0 + c), v);
+    }
+}
+
+// (L_JJ^{-1})^T of every 128x128 diagonal block (one CTA per block, after
+// the factorisation): X = L^{-1} by block rows, X_ii = D_i (the leaf's 32x32
+// inverses) and X_i,0:i = -D_i (L_i,0:i X_0:i,0:i); LinvT[l][c] = X[c][l].
+// Rows past n are the identity, as in the leaf.
+constexpr size_t block_inverse_smem() { return (size_t)(2 * 128 * LD32 + 32 * 97) * sizeof(float); }
+
+__global__ void __launch_bounds__(256) k_block_inverse(const float* __restrict__ W, long ldw, int n,
+                                                       const float* __restrict__ Dinv32, float* __restrict__ LinvT) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* S = reinterpret_cast<float*>(smem_raw);  // [128][129] L_JJ
+    float* X = S + 128 * LD32;                      // [128][129] L_JJ^{-1}
+    float* Tmp = X + 128 * LD32;                    // [32][97]
+    const int tid = threadIdx.x;
+    const int J = blockIdx.x;
+    const long k = (long)J * 128;
+    const int nb = (int)min((long)128, n - k);
+    const float* dg = Dinv32 + (long)J * 4096;
+    for (int e = tid; e < 128 * 128; e += 256) {
+        const int r = e >> 7, c = e & 127;
+        float v;
+        if (r < nb && c < nb) v = (c <= r) ? W[(k + r) * ldw + k + c] : 0.f;
+        else v = (r == c) ? 1.f : 0.f;
+        S[r * LD32 + c] = v;
+        const int br = r >> 5, bc = c >> 5;
+        X[r * LD32 + c] = (br == bc) ? dg[br * 1024 + (r & 31) * 32 + (c & 31)] : 0.f;
+    }
+    __syncthreads();
+    for (int i = 1; i < 4; ++i) {
+        const int ri = i * 32, w = i * 32;  // rows ri..ri+31 of X, columns 0..w-1
+        for (int e = tid; e < 32 * w; e += 256) {
+            const int rr = e / w, c = e - rr * w;
+            const float* lr = S + (ri + rr) * LD32;
+            float s0 = 0.f, s1 = 0.f;
+            int l = (c >> 5) << 5;
+            for (; l + 1 < ri; l += 2) {  // two chains: shorter dependency
+                s0 = fmaf(lr[l], X[l * LD32 + c], s0);
+                s1 = fmaf(lr[l + 1], X[(l + 1) * LD32 + c], s1);
+            }
+            if (l < ri) s0 = fmaf(lr[l], X[l * LD32 + c], s0);
+            Tmp[rr * 97 + c] = s0 + s1;
+        }
+        __syncthreads();
+        for (int e = tid; e < 32 * w; e += 256) {
+            const int rr = e / w, c = e - rr * w;
+            const float* ir = X + (ri + rr) * LD32 + ri;
+            float s = 0.f;
+            for (int l = 0; l <= rr; ++l) s = fmaf(ir[l], Tmp[l * 97 + c], s);
+            X[(ri + rr) * LD32 + c] = -s;
+        }
+        __syncthreads();
+    }
+    float* out = LinvT + (long)J * 16384;
+    for (int e = tid; e < 128 * 128; e += 256) {
+        const int l = e >> 7, c = e & 127;
+        out[e] = X[c * LD32 + l];
     }
 }

@@ -2,25 +2,40 @@
 // triangular sweeps y = L^{-1} y (forward) and z = L^{-T} z (backward) over
 // 128-row blocks, in one persistent cooperative kernel per sweep.
 //
-// Block J is owned by CTA J mod G.  Its owner accumulates the contributions
-// of the finished blocks in a fixed order (forward: K = 0..J-1 with
-// L_JK y_K; backward: K = NB-1..J+1 with L_KJ^T z_K), waiting for each with a
-// bounded acquire-load of ready[K], then finishes the block with the full
-// inverse of the diagonal block (y_J = L_JJ^{-1} t, z_J = L_JJ^{-T} t) and
-// publishes it with a release-store.  Owners take their blocks in sweep
-// order, so a wait only ever targets an earlier block; the cooperative
-// launch keeps all CTAs resident.  A wait that exceeds its limit raises
-// SPD_DEV_TIMEOUT and the kernel winds down without publishing.
+// Block J is owned by CTA J mod G, which takes its blocks in sweep order.
+// Forward, with t_J = y_J - sum_{K < J-1} L_JK y_K and u_J = L_JJ^{-1} t_J,
+//
+//   y_J = u_J - M_J y_{J-1},          M_J = L_JJ^{-1} L_{J,J-1},
+//
+// and backward, with v_J = L_JJ^{-T} (z_J - sum_{K > J+1} L_KJ^T z_K),
+//
+//   z_J = v_J - N_J z_{J+1},          N_J = L_JJ^{-T} L_{J+1,J}^T,
+//
+// the couplings M_J, N_J being formed once per factor (k_trsv_couplings).
+// Everything but the last product happens while the neighbouring block is
+// still being solved, so one sweep step on the critical path is: acquire the
+// neighbour's flag, one 128x128 by 128xMC product, publish.  The far
+// contributions are summed in a fixed order (forward K = 0..J-2, backward
+// K = NB-1..J+2); each waits with a bounded acquire-load of ready[K].  A wait
+// that exceeds its limit raises SPD_DEV_TIMEOUT and the kernel winds down
+// without publishing.
+//
+// Thread (i, h) (i = tid / 2, h = tid % 2) owns row i of the block and the
+// half h of the reduction index: its 64 tile entries go from global memory
+// straight into registers (double-buffered across tiles), the right-hand
+// sides are broadcast from shared memory, and the two halves meet through a
+// shuffle.
 #pragma once
 #include "common.cuh"
 
-#define TV_LD 129
+#define TV_LD 132
 
 struct TrsvArgs {
     const float* W;      // factor rows (row-major, lower), ldw
     long ldw;
     int n, NB;
     const float* LinvT;  // per block: (L_JJ^{-1})^T, 128 x 128 row-major
+    const float* Cpl;    // couplings: M_J at J * 16384, N_J at (NB + J) * 16384
     float* Y;            // n x m, column-major (ld n), in place
     int c0, mc;          // columns [c0, c0 + mc) in this pass
     int* ready;          // NB flags
@@ -42,183 +57,319 @@ __device__ __forceinline__ uint64_t tv_globaltimer() {
     return t;
 }
 
+// row stride of the staged right-hand sides: the eight reduction slices read
+// rows s + 8 l' (s = 0..7) in one instruction; with this stride those rows
+// fall in distinct banks
+template <int MC>
+__host__ __device__ constexpr int tv_ys() { return MC >= 8 ? MC + 4 : MC; }
+
 template <int MC>
 constexpr size_t trsv32_smem() {
-    return (size_t)(2 * 128 * TV_LD + 2 * 128 * MC) * sizeof(float);
+    return (size_t)(128 * TV_LD + 128 * tv_ys<MC>() + 128 * MC) * sizeof(float);
 }
 
-// 128 x 128 tile (rows trow, columns tcol of L, zero outside the matrix) into
-// 16 float4 registers per thread: every load is issued before any use.
-__device__ __forceinline__ void tile_ld(float4* v, const TrsvArgs& a, int trow, int tcol) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = threadIdx.x + q * 256, r = e >> 5, c4 = (e & 31) * 4;
-        const int gr = trow * 128 + r, gc = tcol * 128 + c4;
-        v[q] = (gr < a.n && gc < a.n) ? *reinterpret_cast<const float4*>(a.W + (long)gr * a.ldw + gc)
-                                      : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gc + 3 >= a.n) {  // columns past n hold scratch (ldw > n): zero them
-            if (gc + 1 >= a.n) v[q].y = 0.f;
-            if (gc + 2 >= a.n) v[q].z = 0.f;
-            v[q].w = 0.f;
+// ---------------------------------------------------------------------------
+// couplings, once per factor
+// ---------------------------------------------------------------------------
+// blockIdx.y == 0: M_J for J = blockIdx.x + 1, M_J[i][l] = sum_k LinvT_J[k][i] L_{J,J-1}[k][l]
+// blockIdx.y == 1: N_J for J = blockIdx.x,     N_J[i][l] = sum_k LinvT_J[i][k] L_{J+1,J}[l][k]
+// Rows of L past n are zero.  Thread: row i = tid / 2, columns 64 (tid % 2) + 0..63.
+constexpr size_t trsv_couplings_smem() { return (size_t)(2 * 128 * 129) * sizeof(float); }
+
+static __global__ void __launch_bounds__(256) k_trsv_couplings(const float* __restrict__ W, long ldw, int n, int NB,
+                                                        const float* __restrict__ LinvT, float* __restrict__ Cpl) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Li = reinterpret_cast<float*>(smem_raw);  // [128][129] LinvT_J
+    float* Bt = Li + 128 * 129;                      // [128][129] Bt[k][l]
+    const bool fwd = blockIdx.y == 0;
+    const int J = fwd ? blockIdx.x + 1 : blockIdx.x;
+    const int tid = threadIdx.x;
+    const float* lg = LinvT + (long)J * 16384;
+    for (int e = tid; e < 16384; e += 256) Li[(e >> 7) * 129 + (e & 127)] = lg[e];
+    for (int e = tid; e < 16384; e += 256) {
+        const int r = e >> 7, c = e & 127;
+        if (fwd) {  // Bt[k][l] = L_{J,J-1}[k][l]: row J*128 + r, column (J-1)*128 + c
+            const long gr = (long)J * 128 + r;
+            Bt[r * 129 + c] = gr < n ? W[gr * ldw + (long)(J - 1) * 128 + c] : 0.f;
+        } else {    // Bt[k][l] = L_{J+1,J}[l][k]: row (J+1)*128 + r (= l), column J*128 + c (= k)
+            const long gr = (long)(J + 1) * 128 + r;
+            Bt[c * 129 + r] = gr < n ? W[gr * ldw + (long)J * 128 + c] : 0.f;
         }
     }
-}
-__device__ __forceinline__ void tile_ld_contig(float4* v, const float* src) {
+    __syncthreads();
+    const int i = tid >> 1, lb = (tid & 1) * 64;
+    float acc[64];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = threadIdx.x + q * 256;
-        v[q] = reinterpret_cast<const float4*>(src)[e];
-    }
-}
-__device__ __forceinline__ void tile_st(const float4* v, float* Ls) {
+    for (int q = 0; q < 64; ++q) acc[q] = 0.f;
+    for (int k = 0; k < 128; ++k) {
+        const float a = fwd ? Li[k * 129 + i] : Li[i * 129 + k];
+        const float* b = Bt + k * 129 + lb;
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int e = threadIdx.x + q * 256, r = e >> 5, c4 = (e & 31) * 4;
-        float* d = Ls + r * TV_LD + c4;
-        d[0] = v[q].x;
-        d[1] = v[q].y;
-        d[2] = v[q].z;
-        d[3] = v[q].w;
+        for (int q = 0; q < 64; ++q) acc[q] = fmaf(a, b[q], acc[q]);
     }
+    float* out = Cpl + ((long)(fwd ? J : NB + J) * 128 + i) * 128 + lb;
+#pragma unroll
+    for (int q = 0; q < 64; q += 4) *reinterpret_cast<float4*>(out + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
 }
 
-// acc[0..CPT) += x * p[0..CPT)  with vector shared-memory loads
-template <int CPT>
-__device__ __forceinline__ void axpy_row(float* acc, float x, const float* p) {
-    if constexpr (CPT % 4 == 0) {
-#pragma unroll
-        for (int q = 0; q < CPT / 4; ++q) {
-            const float4 v = reinterpret_cast<const float4*>(p)[q];
-            acc[4 * q + 0] = fmaf(x, v.x, acc[4 * q + 0]);
-            acc[4 * q + 1] = fmaf(x, v.y, acc[4 * q + 1]);
-            acc[4 * q + 2] = fmaf(x, v.z, acc[4 * q + 2]);
-            acc[4 * q + 3] = fmaf(x, v.w, acc[4 * q + 3]);
+// ---------------------------------------------------------------------------
+// the sweeps
+// ---------------------------------------------------------------------------
+// Wait (thread 0, bounded) until ready[K] carries this sweep's epoch; then
+// the whole CTA may read block K.  Returns false once the CTA has given up.
+__device__ __forceinline__ bool tv_wait(const TrsvArgs& a, int K, int* s_abort) {
+    if (threadIdx.x == 0 && !*s_abort) {
+        if (ld_acquire(a.ready + K) != a.epoch) {
+            const uint64_t t0 = tv_globaltimer();
+            while (ld_acquire(a.ready + K) != a.epoch) {
+                if (tv_globaltimer() - t0 > 1000000000ull) {
+                    *s_abort = 1;
+                    atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
+                    break;
+                }
+            }
         }
-    } else if constexpr (CPT == 2) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
-        acc[0] = fmaf(x, v.x, acc[0]);
-        acc[1] = fmaf(x, v.y, acc[1]);
+        __threadfence();
+    }
+    __syncthreads();
+    return !*s_abort;
+}
+
+// Tile products use a 4-row register tile: thread (q, s) = (tid / 8, tid % 8)
+// owns rows 4q..4q+3 of the block and the reduction slice l = s + 8 l'
+// (l' = 0..15); each right-hand-side row read from shared memory feeds 4 MC
+// multiply-adds, and the eight slices of a row quad (eight adjacent lanes)
+// meet by shuffles.
+//
+// 64 tile entries into registers, v[j * 16 + l'] = entry (row 4q + j,
+// column s + 8 l'): forward, rows of L_JK (eight adjacent lanes read 32
+// contiguous bytes); backward, L_KJ^T, i.e. v[j * 16 + l'] =
+// L_KJ[s + 8 l'][4 q + j] (float4 loads along a row of L_KJ).  Zero past n.
+template <bool FWD>
+__device__ __forceinline__ void tv_tile(float (&v)[64], const float* W, long ldw, int n, int J, int K, int q, int s) {
+    if (FWD) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long gr = (long)J * 128 + 4 * q + j;
+            const float* src = W + gr * ldw + (long)K * 128 + s;
+#pragma unroll
+            for (int l = 0; l < 16; ++l) v[j * 16 + l] = gr < n ? __ldg(src + 8 * l) : 0.f;
+        }
     } else {
-        acc[0] = fmaf(x, p[0], acc[0]);
+#pragma unroll
+        for (int l = 0; l < 16; ++l) {
+            const long gr = (long)K * 128 + s + 8 * l;
+            const float4 t = gr < n ? __ldg(reinterpret_cast<const float4*>(W + gr * ldw + (long)J * 128 + 4 * q))
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[l] = t.x;
+            v[16 + l] = t.y;
+            v[32 + l] = t.z;
+            v[48 + l] = t.w;
+        }
     }
+}
+
+// the coupling rows 4q..4q+3, slice s, of a row-major 128x128 matrix
+__device__ __forceinline__ void tv_rows(float (&v)[64], const float* C, int q, int s) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float* src = C + (4 * q + j) * 128 + s;
+#pragma unroll
+        for (int l = 0; l < 16; ++l) v[j * 16 + l] = __ldg(src + 8 * l);
+    }
+}
+
+// Yk[l][c] = Y[K*128 + l, c0 + c] (zero past n or past mc); all loads first
+template <int MC>
+__device__ __forceinline__ void tv_stage(float* Yk, const TrsvArgs& a, int K) {
+    constexpr int PER = (128 * MC + 255) / 256;
+    float v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+        const int r = K * 128 + l;
+        v[u] = (e < 128 * MC && c < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + c) * a.n + r) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+        if (e < 128 * MC) Yk[l * tv_ys<MC>() + c] = v[u];
+    }
+}
+
+// acc[j][c] += sum_l' v[j * 16 + l'] Yk[s + 8 l'][c]  (fully unrolled)
+template <int MC>
+__device__ __forceinline__ void tv_dot(float (&acc)[4][MC], const float (&v)[64], const float* Yk, int s) {
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const float* y = Yk + (s + 8 * l) * tv_ys<MC>();
+        float yv[MC];
+        if constexpr (MC % 4 == 0) {
+#pragma unroll
+            for (int c = 0; c < MC; c += 4) {
+                const float4 t = *reinterpret_cast<const float4*>(y + c);
+                yv[c] = t.x;
+                yv[c + 1] = t.y;
+                yv[c + 2] = t.z;
+                yv[c + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < MC; ++c) yv[c] = y[c];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[j][c] = fmaf(v[j * 16 + l], yv[c], acc[j][c]);
+    }
+}
+
+// sum over the eight reduction slices (adjacent lanes): every lane of the
+// group ends with the total
+template <int MC>
+__device__ __forceinline__ void tv_reduce8(float (&acc)[4][MC]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < MC; ++c) {
+            float x = acc[j][c];
+            x += __shfl_xor_sync(0xffffffffu, x, 1);
+            x += __shfl_xor_sync(0xffffffffu, x, 2);
+            x += __shfl_xor_sync(0xffffffffu, x, 4);
+            acc[j][c] = x;
+        }
 }
 
 template <int MC, bool FWD>
 __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
-    constexpr int LY = MC;                       // unpadded rows: vector reads of a thread's columns
-    constexpr int CPT = MC >= 2 ? MC / 2 : 1;    // columns per thread
-    constexpr int LSPLIT = MC >= 2 ? 1 : 2;      // the two threads of a row split l when MC == 1
-    constexpr int YPT = (128 * MC + 255) / 256;  // y elements loaded per thread
+    constexpr int CPT = MC >= 2 ? MC / 2 : 1;  // columns per thread in the diagonal step
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Ls = reinterpret_cast<float*>(smem_raw);  // [128][129] L tile of the current contribution
-    float* Lv = Ls + 128 * TV_LD;                    // [128][129] (L_JJ^{-1})^T
-    float* Yk = Lv + 128 * TV_LD;                    // [128][MC]
-    float* T = Yk + 128 * LY;                        // [128][MC]
+    float* Lv = reinterpret_cast<float*>(smem_raw);  // [128][TV_LD] (L_JJ^{-1})^T
+    float* Yk = Lv + 128 * TV_LD;                    // [128][tv_ys] right-hand sides of a finished block
+    float* T = Yk + 128 * tv_ys<MC>();               // [128][MC] t_J, then u_J
     __shared__ int s_abort;
     const int tid = threadIdx.x;
-    const int i = tid >> 1, half = tid & 1;
+    const int tq = tid >> 3, ts = tid & 7;            // tile products: row quad, reduction slice
+    const int i = tid >> 1, half = tid & 1;           // diagonal step: row, column half
     const int cbase = (MC >= 2) ? half * CPT : 0;
-    const int l0 = (LSPLIT == 2) ? half * 64 : 0, l1 = (LSPLIT == 2) ? l0 + 64 : 128;
     if (tid == 0) s_abort = 0;
     __syncthreads();
 
     for (int t = blockIdx.x; t < a.NB; t += gridDim.x) {
         const int J = FWD ? t : a.NB - 1 - t;
-        const int kcount = FWD ? J : a.NB - 1 - J;
-        float4 pre[16];
-        {  // (L_JJ^{-1})^T does not depend on any other block: fetch it first
-            tile_ld_contig(pre, a.LinvT + (long)J * 128 * 128);
-            tile_st(pre, Lv);
-        }
-        if (kcount > 0) {
-            const int K = FWD ? 0 : a.NB - 1;
-            tile_ld(pre, a, FWD ? J : K, FWD ? K : J);
-        }
-        float acc[CPT];
+        const int nfar = FWD ? max(J - 1, 0) : max(a.NB - 2 - J, 0);
+        const bool near = FWD ? J >= 1 : J <= a.NB - 2;
+        float ra[64], rb[64];
+        {  // (L_JJ^{-1})^T depends on no other block: into shared memory first
+            const float4* src = reinterpret_cast<const float4*>(a.LinvT + (long)J * 16384);
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) acc[c] = 0.f;
-        for (int q = 0; q < kcount; ++q) {
+            for (int u = 0; u < 16; ++u) {
+                const int e = tid + u * 256, r = e >> 5, c4 = (e & 31) * 4;
+                *reinterpret_cast<float4*>(Lv + r * TV_LD + c4) = __ldg(src + e);
+            }
+        }
+        float acc[4][MC];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
+        // far contributions, two tiles per trip so that the register buffers
+        // alternate without copies
+        if (nfar > 0) tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, FWD ? 0 : a.NB - 1, tq, ts);
+        for (int q = 0; q < nfar; q += 2) {
             const int K = FWD ? q : a.NB - 1 - q;
-            if (tid == 0 && !s_abort) {
-                if (ld_acquire(a.ready + K) != a.epoch) {
-                    const uint64_t t0 = tv_globaltimer();
-                    while (ld_acquire(a.ready + K) != a.epoch) {
-                        __nanosleep(20);
-                        if (tv_globaltimer() - t0 > 1000000000ull) {
-                            s_abort = 1;
-                            atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
-                            break;
-                        }
-                    }
-                }
-                __threadfence();
-            }
+            if (!tv_wait(a, K, &s_abort)) break;
+            tv_stage<MC>(Yk, a, K);
             __syncthreads();
-            if (s_abort) break;
-            float yv[YPT];
-#pragma unroll
-            for (int u = 0; u < YPT; ++u) {
-                const int e = tid + u * 256, l = e & 127, c = e >> 7;
-                const int r = K * 128 + l;
-                yv[u] = (e < 128 * MC && c < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + c) * a.n + r) : 0.f;
-            }
-            tile_st(pre, Ls);
-#pragma unroll
-            for (int u = 0; u < YPT; ++u) {
-                const int e = tid + u * 256, l = e & 127, c = e >> 7;
-                if (e < 128 * MC) Yk[l * LY + c] = yv[u];
-            }
+            if (q + 1 < nfar) tv_tile<FWD>(rb, a.W, a.ldw, a.n, J, FWD ? q + 1 : a.NB - 2 - q, tq, ts);
+            tv_dot<MC>(acc, ra, Yk, ts);
             __syncthreads();
-            if (q + 1 < kcount) {  // next tile in flight while this one is used
-                const int Kn = FWD ? q + 1 : a.NB - 2 - q;
-                tile_ld(pre, a, FWD ? J : Kn, FWD ? Kn : J);
-            }
-            if (FWD) {  // acc[c] += sum_l L_JK[i][l] y_K[l][c]
-                const float* lr = Ls + i * TV_LD;
-#pragma unroll 4
-                for (int l = l0; l < l1; ++l) axpy_row<CPT>(acc, lr[l], Yk + l * LY + cbase);
-            } else {  // acc[c] += sum_r L_KJ[r][i] z_K[r][c]
-#pragma unroll 4
-                for (int r = l0; r < l1; ++r) axpy_row<CPT>(acc, Ls[r * TV_LD + i], Yk + r * LY + cbase);
-            }
+            if (q + 1 >= nfar) break;
+            const int K1 = FWD ? q + 1 : a.NB - 2 - q;
+            if (!tv_wait(a, K1, &s_abort)) break;
+            tv_stage<MC>(Yk, a, K1);
+            __syncthreads();
+            if (q + 2 < nfar) tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, FWD ? q + 2 : a.NB - 3 - q, tq, ts);
+            tv_dot<MC>(acc, rb, Yk, ts);
             __syncthreads();
         }
         if (s_abort) break;
-        if (LSPLIT == 2) {
+        // the coupling rows for the last product do not depend on anything
+        // still outstanding: start their loads now
+        if (near) tv_rows(ra, a.Cpl + (long)(FWD ? J : a.NB + J) * 16384, tq, ts);
+        tv_reduce8<MC>(acc);
+        // t = y_J - far sum (this CTA is the only writer of block J)
+        if (ts == 0) {
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
-        }
-        // t = y_J - acc  (this CTA is the only writer of block J)
+            for (int j = 0; j < 4; ++j) {
+                const int r = J * 128 + 4 * tq + j;
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int cc = cbase + c;
-            const int r = J * 128 + i;
-            if (half == 0 || MC >= 2) {
-                float y = (cc < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + cc) * a.n + r) : 0.f;
-                T[i * LY + cc] = y - acc[c];
+                for (int c = 0; c < MC; ++c) {
+                    const float y = (c < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + c) * a.n + r) : 0.f;
+                    T[(4 * tq + j) * MC + c] = y - acc[j][c];
+                }
             }
         }
         __syncthreads();
+        // u = L_JJ^{-1} t (forward) or L_JJ^{-T} t (backward), CPT columns
         float out[CPT];
 #pragma unroll
         for (int c = 0; c < CPT; ++c) out[c] = 0.f;
-        if (FWD) {  // y[i] = sum_{l<=i} Linv[i][l] t[l] = sum_l LinvT[l][i] t[l]
-            const int lend = (LSPLIT == 2) ? min(l1, i + 1) : i + 1;
-            for (int l = l0; l < lend; ++l) axpy_row<CPT>(out, Lv[l * TV_LD + i], T + l * LY + cbase);
-        } else {  // z[i] = sum_{l>=i} Linv[l][i] t[l] = sum_l LinvT[i][l] t[l]
-            const int lbeg = (LSPLIT == 2) ? max(l0, i) : i;
-            const float* lr = Lv + i * TV_LD;
-            for (int l = lbeg; l < l1; ++l) axpy_row<CPT>(out, lr[l], T + l * LY + cbase);
-        }
-        if (LSPLIT == 2) {
+        if (MC >= 2) {
+            if (FWD) {  // u[i] = sum_{l<=i} LinvT[l][i] t[l]
+                for (int l = 0; l <= i; ++l) {
+                    const float w = Lv[l * TV_LD + i];
 #pragma unroll
-            for (int c = 0; c < CPT; ++c) out[c] += __shfl_xor_sync(0xffffffffu, out[c], 1);
-        }
+                    for (int c = 0; c < CPT; ++c) out[c] = fmaf(w, T[l * MC + cbase + c], out[c]);
+                }
+            } else {    // u[i] = sum_{l>=i} LinvT[i][l] t[l]
+                const float* lr = Lv + i * TV_LD;
+                for (int l = i; l < 128; ++l) {
+                    const float w = lr[l];
 #pragma unroll
-        for (int c = 0; c < CPT; ++c) {
-            const int cc = cbase + c;
-            const int r = J * 128 + i;
-            if ((half == 0 || MC >= 2) && cc < a.mc && r < a.n) a.Y[(long)(a.c0 + cc) * a.n + r] = out[c];
+                    for (int c = 0; c < CPT; ++c) out[c] = fmaf(w, T[l * MC + cbase + c], out[c]);
+                }
+            }
+        } else {  // one column: the two threads of a row split l
+            const int l0 = half * 64, l1 = l0 + 64;
+            if (FWD) {
+                for (int l = l0; l < min(l1, i + 1); ++l) out[0] = fmaf(Lv[l * TV_LD + i], T[l], out[0]);
+            } else {
+                const float* lr = Lv + i * TV_LD;
+                for (int l = max(l0, i); l < l1; ++l) out[0] = fmaf(lr[l], T[l], out[0]);
+            }
+            out[0] += __shfl_xor_sync(0xffffffffu, out[0], 1);
+        }
+        __syncthreads();  // every read of t done: T now takes u
+#pragma unroll
+        for (int c = 0; c < CPT; ++c)
+            if (half == 0 || MC >= 2) T[i * MC + cbase + c] = out[c];
+        if (near) {  // the step on the critical path: y_J = u - C_J y_neighbour
+            const int Kn = FWD ? J - 1 : J + 1;
+            if (!tv_wait(a, Kn, &s_abort)) break;  // (its barrier also publishes u)
+            tv_stage<MC>(Yk, a, Kn);
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
+            tv_dot<MC>(acc, ra, Yk, ts);
+            tv_reduce8<MC>(acc);
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
+        }
+        if (ts == 0) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int r = J * 128 + 4 * tq + j;
+#pragma unroll
+                for (int c = 0; c < MC; ++c)
+                    if (c < a.mc && r < a.n) a.Y[(long)(a.c0 + c) * a.n + r] = T[(4 * tq + j) * MC + c] - acc[j][c];
+            }
         }
         __threadfence();
         __syncthreads();

@@ -36,7 +36,7 @@ spd_status leaf_potrf(FCtx& c, int k, int nb) {
             F->W64, F->ldw, k, nb, F->Dinv64, c.mir, c.h->dst);
     } else {
         ++(c.h)->launches, k_potrf_leaf32<<<1, 256, potrf_leaf32_smem(), c.h->stream>>>(F->W, F->ldw, k, nb,
-                                                                                          F->LinvT, c.mir, c.h->dst);
+                                                                                          F->Dinv32, c.mir, c.h->dst);
     }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
@@ -51,7 +51,7 @@ spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
             F->W64, F->ldw, r0, m, c0, kb, F->Dinv64, c.mir, c.h->dst);
     } else {
         ++(c.h)->launches, k_trsm_leaf32<<<ceil_div(m, 64), 256, trsm_leaf32_smem(), c.h->stream>>>(
-            F->W, F->ldw, r0, m, c0, F->LinvT, c.mir, c.h->dst);
+            F->W, F->ldw, r0, m, c0, F->Dinv32, c.mir, c.h->dst);
     }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
@@ -146,6 +146,8 @@ void free_factor(spd_factor_t* F) {
     cudaFree(F->Wh);
     cudaFree(F->d);
     cudaFree(F->LinvT);
+    cudaFree(F->Cpl);
+    cudaFree(F->Dinv32);
     cudaFree(F->Dinv64);
     delete F;
 }
@@ -187,6 +189,8 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
     } else if (e == cudaSuccess) {
         e = cudaMalloc(&F->W, sizeof(float) * std::max<size_t>(nW, 1));
         if (e == cudaSuccess) e = cudaMalloc(&F->LinvT, sizeof(float) * 128 * 128 * std::max(F->nblk128, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&F->Cpl, sizeof(float) * 2 * 128 * 128 * std::max(F->nblk128, 1));
+        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv32, sizeof(float) * 4096 * std::max(F->nblk128, 1));
         if (e == cudaSuccess && kind) {
             F->ldh = F->ldw;
             e = cudaMalloc(&F->Wh, mirror_elem(kind) * std::max<size_t>(nW, 1));
@@ -221,6 +225,16 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         }
         if (prec == SPD_PREC_FP64) st = potrf_rec<double>(c, 0, n);
         else st = potrf_rec<float>(c, 0, n);
+        if (st == SPD_OK && prec != SPD_PREC_FP64) {
+            // per-block inverses and sweep couplings: off the factorisation's
+            // critical path, all blocks at once
+            ProfScope pinv(h, SPD_PHASE_LEAF, (double)F->nblk128 * 128.0 * 128.0 * 128.0 / 3.0,
+                           (double)F->nblk128 * (8.0 * 16384.0 + 16384.0));
+            ++h->launches, k_block_inverse<<<F->nblk128, 256, block_inverse_smem(), s>>>(F->W, F->ldw, n, F->Dinv32,
+                                                                                        F->LinvT);
+            if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "block inverse launch failed");
+        }
+        if (st == SPD_OK && prec != SPD_PREC_FP64) st = factor_couplings(h, F);
         if (st == SPD_OK) st = check_dev_status(h, rep, "spd_factor");
         if (tc) tc_gemm_destroy(tc);
         if (st != SPD_OK) return fail(st);
@@ -307,6 +321,7 @@ static void setup_leaf_attrs() {
     cudaFuncSetAttribute(k_potrf_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf32_smem());
     cudaFuncSetAttribute(k_potrf_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<double>());
     cudaFuncSetAttribute(k_trsm_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_leaf32_smem());
+    cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_inverse_smem());
     cudaFuncSetAttribute(k_trsm_leaf<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)trsm_leaf_smem<double, 32>());
 }

@@ -278,7 +278,7 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
         h->epoch = 0;
     }
     for (int dir = 0; dir < 2; ++dir) {
-        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, Y, c0, mc, h->ready, ++h->epoch, h->dst};
+        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst};
         void* args[] = {&a};
         const int grid = std::min(NB, max_ctas[dir]);
         ++h->launches;
@@ -287,6 +287,27 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
     }
     return SPD_OK;
 }
+
+}  // namespace
+
+// The sweep couplings of a float32 factor (M_J, N_J of k_trsv32.cuh).
+spd_status factor_couplings(spd_handle* h, spd_factor_t* F) {
+    const int NB = F->nblk128;
+    if (NB < 2) return SPD_OK;
+    static bool attr = false;
+    if (!attr) {
+        attr = true;
+        cudaFuncSetAttribute(k_trsv_couplings, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)trsv_couplings_smem());
+    }
+    ProfScope ps(h, SPD_PHASE_LEAF, 2.0 * 2.0 * (NB - 1) * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * (NB - 1) * 16384.0);
+    ++h->launches, k_trsv_couplings<<<dim3(NB - 1, 2), 256, trsv_couplings_smem(), h->stream>>>(
+        F->W, F->ldw, F->n, NB, F->LinvT, F->Cpl);
+    LAUNCH_CHECK(h);
+    return SPD_OK;
+}
+
+namespace {
 
 // Y <- (L L^T)^{-1} Y for a float32 factor (n x m, ld n).
 spd_status lp_sweeps32(spd_handle* h, const spd_factor_t* F, int n, int m, float* Y) {
