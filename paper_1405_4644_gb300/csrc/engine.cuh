@@ -34,6 +34,8 @@ struct spd_handle {
     int* ready = nullptr;       // block flags of the persistent triangular sweeps
     int ready_n = 0;
     int epoch = 0;              // last flag value handed out
+    cudaStream_t aux = nullptr; // second stream of the look-ahead factorisation
+    std::vector<cudaEvent_t> sync_ev;  // timing-free events for stream joins
 };
 
 struct spd_factor_t {
@@ -152,18 +154,20 @@ struct ProfScope {
         cudaEventCreate(&e);
         return e;
     }
-    ProfScope(spd_handle* hh, int phase, double flops, double bytes) : h(hh), on(hh->prof_on) {
+    cudaStream_t s;
+    ProfScope(spd_handle* hh, int phase, double flops, double bytes, cudaStream_t st = nullptr)
+        : h(hh), on(hh->prof_on), s(st ? st : hh->stream) {
         if (!on) return;
         r.a = get_event(h);
         r.b = get_event(h);
         r.phase = phase;
         r.flops = flops;
         r.bytes = bytes;
-        cudaEventRecord(r.a, h->stream);
+        cudaEventRecord(r.a, s);
     }
     ~ProfScope() {
         if (!on) return;
-        cudaEventRecord(r.b, h->stream);
+        cudaEventRecord(r.b, s);
         h->prof.push_back(r);
     }
 };

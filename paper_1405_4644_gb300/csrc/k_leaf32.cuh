@@ -80,8 +80,9 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
                     if (badj < 0) badj = j;
                     piv = 1.f;
                 }
-                const float dj = sqrtf(piv);
-                const float inv = __frcp_rn(dj);
+                // one MUFU op on the pivot chain: 1/sqrt, then sqrt = piv / sqrt
+                const float inv = rsqrtf(piv);
+                const float dj = piv * inv;
                 rd[j] = inv;
                 a[j] = (lane == j) ? dj : (lane > j ? a[j] * inv : a[j]);
 #pragma unroll
@@ -172,13 +173,19 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
         }
         __syncthreads();
     }
-    for (int e = tid; e < 128 * 128; e += 256) {
-        int r = e >> 7, c = e & 127;
-        if (r < nb && c <= r) {
-            float v = S[r * LD32 + c];
-            W[(long)(k + r) * ldw + k + c] = v;
-            mirror_store(mir, (long)(k + r), (long)(k + c), v);
+    // L (lower part, rows < nb) to W and its mirror, four columns per store
+    for (int e = tid; e < 128 * 32; e += 256) {
+        const int r = e >> 5, c4 = (e & 31) * 4;
+        if (r >= nb || c4 > r) continue;
+        const float* sr = S + r * LD32 + c4;
+        float v[4] = {sr[0], sr[1], sr[2], sr[3]};
+        float* dst = W + (long)(k + r) * ldw + k + c4;
+        if (c4 + 3 <= r) {
+            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+            for (int q = 0; c4 + q <= r; ++q) dst[q] = v[q];
         }
+        for (int q = 0; q < 4 && c4 + q <= r; ++q) mirror_store(mir, (long)(k + r), (long)(k + c4 + q), v[q]);
     }
 }
 
@@ -207,12 +214,35 @@ __global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, l
             vb[q] = (rb0 + r < r0 + m) ? *reinterpret_cast<const float4*>(W + (long)(rb0 + r) * ldw + c0 + c4)
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int e = tid; e < 96 * 96; e += 256) {  // the strictly-below-diagonal 32-blocks of L_kk
-            const int r = e / 96, c = e - r * 96;
-            Ls[r * LD32 + c] = (c < r + 32) ? W[(long)(c0 + 32 + r) * ldw + c0 + c] : 0.f;
+        // the strictly-below-diagonal 32-blocks of L_kk (rows 32..127, columns
+        // 0..95) and the four 32x32 inverses: every load in flight first
+        float4 vl[9], vd[4];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int e = tid + q * 256, r = e / 24, c4 = (e - r * 24) * 4;
+            vl[q] = *reinterpret_cast<const float4*>(W + (long)(c0 + 32 + r) * ldw + c0 + c4);
         }
-        const float* dg = Dinv32 + (long)(c0 / 128) * 4096;
-        for (int e = tid; e < 4096; e += 256) Ds[(e >> 5) * 33 + (e & 31)] = dg[e];
+        const float4* dg = reinterpret_cast<const float4*>(Dinv32 + (long)(c0 / 128) * 4096);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vd[q] = __ldg(dg + tid + q * 256);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int e = tid + q * 256, r = e / 24, c4 = (e - r * 24) * 4;
+            float* d = Ls + r * LD32 + c4;
+            d[0] = (c4 + 0 < r + 32) ? vl[q].x : 0.f;
+            d[1] = (c4 + 1 < r + 32) ? vl[q].y : 0.f;
+            d[2] = (c4 + 2 < r + 32) ? vl[q].z : 0.f;
+            d[3] = (c4 + 3 < r + 32) ? vl[q].w : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = (tid + q * 256) * 4, i = e >> 5, c = e & 31;
+            float* d = Ds + i * 33 + c;
+            d[0] = vd[q].x;
+            d[1] = vd[q].y;
+            d[2] = vd[q].z;
+            d[3] = vd[q].w;
+        }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int e = tid + q * 256, r = e >> 5, c4 = (e & 31) * 4;
@@ -274,13 +304,16 @@ __global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, l
                 if (q < CW) Bs[(tr + j) * 132 + cb + q] -= acc[j][q];
         __syncthreads();
     }
-    for (int e = tid; e < 64 * 128; e += 256) {
-        const int rr = e >> 7, c = e & 127;
+    for (int e = tid; e < 64 * 32; e += 256) {
+        const int rr = e >> 5, c4 = (e & 31) * 4;
         const long row = rb0 + rr;
         if (row >= r0 + m) continue;
-        const float v = Bs[rr * 132 + c];
-        W[row * ldw + c0 + c] = v;
-        mirror_store(mir, row, (long)(c0 + c), v);
+        const float4 v = *reinterpret_cast<const float4*>(Bs + rr * 132 + c4);
+        *reinterpret_cast<float4*>(W + row * ldw + c0 + c4) = v;
+        mirror_store(mir, row, (long)(c0 + c4), v.x);
+        mirror_store(mir, row, (long)(c0 + c4 + 1), v.y);
+        mirror_store(mir, row, (long)(c0 + c4 + 2), v.z);
+        mirror_store(mir, row, (long)(c0 + c4 + 3), v.w);
     }
 }
 

@@ -35,6 +35,7 @@ extern "C" spd_status spd_create(spd_handle** out, void* stream) {
     if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 4096);
     if (e == cudaSuccess) e = cudaEventCreate(&h->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess) {
         DevStatus clear{0, INT_MAX, {0, 0}};
         e = cudaMemcpy(h->dst, &clear, sizeof(clear), cudaMemcpyHostToDevice);
@@ -45,6 +46,7 @@ extern "C" spd_status spd_create(spd_handle** out, void* stream) {
         if (h->pinned) cudaFreeHost(h->pinned);
         if (h->e0) cudaEventDestroy(h->e0);
         if (h->e1) cudaEventDestroy(h->e1);
+        if (h->aux) cudaStreamDestroy(h->aux);
         delete h;
         return e == cudaErrorMemoryAllocation ? SPD_ERR_OOM : SPD_ERR_CUDA;
     }
@@ -61,6 +63,8 @@ extern "C" spd_status spd_destroy(spd_handle* h) {
     cudaEventDestroy(h->e0);
     cudaEventDestroy(h->e1);
     cudaFree(h->ready);
+    if (h->aux) cudaStreamDestroy(h->aux);
+    for (auto e : h->sync_ev) cudaEventDestroy(e);
     for (auto& r : h->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
