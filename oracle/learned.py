@@ -11,6 +11,8 @@ definition the GPU kernels are checked against).
 * ``loss``      (1/p) sum_c ||A M z_c - z_c||^2 / ||z_c||^2
                 + w_sup ||M z_0 - t_0||^2 / ||t_0||^2
 * ``fd_grad``   central finite differences of ``loss`` along given directions
+                (pinned against the complex-step derivative, which every step of
+                ``loss`` supports: parameters may be complex)
 """
 from __future__ import annotations
 
@@ -38,7 +40,9 @@ def features(A, coords, ell, nugget):
 
 
 def unpack(params, H):
-    p = np.asarray(params, dtype=np.float64)
+    p = np.asarray(params)
+    if not np.iscomplexobj(p):  # complex parameters: the complex-step derivative of the tests
+        p = p.astype(np.float64)
     o = 0
     W1 = p[o:o + H * NFEAT].reshape(H, NFEAT); o += H * NFEAT
     b1 = p[o:o + H]; o += H

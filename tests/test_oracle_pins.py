@@ -318,6 +318,26 @@ def test_learned_oracle_features_on_a_known_matrix():
     assert F[0, 2] == np.log(0.1) and F[0, 15] == 1.0
 
 
+def test_learned_oracle_fd_gradient_matches_complex_step():
+    """Central differences of the probe loss against the complex-step
+    derivative Im L(p + i h v) / h, exact to rounding for an analytic L."""
+    from oracle import learned as LO
+    g = np.random.default_rng(4)
+    n, H = 30, 6
+    A = W.gram_shifted(n, 3, shift=0.5)
+    F = g.standard_normal((n, LO.NFEAT))
+    count = H * LO.NFEAT + H + H * H + H + (1 + LO.RANK) * H + 1 + LO.RANK
+    p = g.standard_normal(count) * 0.2
+    Z = g.standard_normal((n, 2))
+    T = np.linalg.solve(A, Z[:, :1])
+    for seed in range(3):
+        v = np.random.default_rng(seed).standard_normal(count)
+        h = 1e-30
+        cs = np.imag(LO.loss(p + 1j * h * v, H, A, F, Z, T, 0.3)) / h
+        fd = LO.fd_grad(p, H, A, F, Z, [v], T, 0.3, h=1e-5)[0]
+        assert abs(fd - cs) <= 1e-6 * abs(cs) + 1e-12, (fd, cs)
+
+
 # ---------------------------------------------------------------------------
 # the correctly rounded residual (judge of the float32-pair residual)
 # ---------------------------------------------------------------------------
