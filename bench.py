@@ -177,18 +177,78 @@ def make_systems(n, m, kappas, dev):
     return systems
 
 
+def solve_one(spd, h, A, B, X, prec, opts, kappa):
+    st, F, frep = spd.spd_factor(h, A, prec)
+    if st != spd.SPD_OK:
+        raise RuntimeError(f"spd_factor({prec}, kappa={kappa}): {spd.spd_last_error_string(h)}")
+    st, rep = spd.spd_solve_ir(h, F, A, B, X, opts)
+    spd.spd_factor_destroy(F)
+    if st != spd.SPD_OK:
+        raise RuntimeError(f"spd_solve_ir kappa={kappa}: {spd.spd_last_error_string(h)}")
+    return frep, rep
+
+
 def run_step(spd, h, systems, precs, X, opts):
-    reps = []
-    for (kappa, A, B), prec in zip(systems, precs):
-        st, F, frep = spd.spd_factor(h, A, prec)
-        if st != spd.SPD_OK:
-            raise RuntimeError(f"spd_factor({prec}, kappa={kappa}): {spd.spd_last_error_string(h)}")
-        st, rep = spd.spd_solve_ir(h, F, A, B, X, opts)
-        spd.spd_factor_destroy(F)
-        if st != spd.SPD_OK:
-            raise RuntimeError(f"spd_solve_ir kappa={kappa}: {spd.spd_last_error_string(h)}")
-        reps.append((frep, rep))
-    return reps
+    """The systems one after another on one handle."""
+    return [solve_one(spd, h, A, B, X, p, opts, k) for (k, A, B), p in zip(systems, precs)]
+
+
+class Lanes:
+    """Independent systems solved concurrently: one handle, stream, solution
+    buffer and host thread per lane (the library calls release the GIL).  The
+    latency-bound factorisation of one system overlaps the residuals and
+    sweeps of another."""
+
+    def __init__(self, spd, count, n, m, dev):
+        import torch
+        self.spd = spd
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(count)]
+        self.handles = [spd.spd_create(s) for s in self.streams]
+        self.X = [torch.zeros(m, n, dtype=torch.float64, device=dev).t() for _ in range(count)]
+
+    def run(self, systems, precs, opts, steps):
+        """steps x len(systems) solves; system i goes to lane i mod count.
+        Returns the reports of the last step, in system order."""
+        import threading
+        out = [None] * len(systems)
+        err = []
+
+        def work(lane):
+            try:
+                for _ in range(steps):
+                    for i in range(lane, len(systems), len(self.handles)):
+                        k, A, B = systems[i]
+                        out[i] = solve_one(self.spd, self.handles[lane], A, B, self.X[lane], precs[i], opts, k)
+            except Exception as e:  # noqa: BLE001 -- re-raised on the main thread
+                err.append(e)
+
+        th = [threading.Thread(target=work, args=(j,)) for j in range(len(self.handles))]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
+        if err:
+            raise err[0]
+        return out
+
+    def fork(self, main_stream):
+        """Make every lane stream wait for work queued so far on main_stream."""
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(main_stream)
+        for s in self.streams:
+            s.wait_event(ev)
+
+    def join(self, main_stream):
+        import torch
+        for s in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            main_stream.wait_event(ev)
+
+    def destroy(self):
+        for h in self.handles:
+            self.spd.spd_destroy(h)
 
 
 def cpu_oracle_sample(n_full, m, seconds_hint=20.0):
@@ -432,6 +492,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--lanes", type=int, default=3,
+                    help="systems solved concurrently (one handle, stream and host thread each)")
     ap.add_argument("--resid", default="df32", choices=["fp64", "df32"],
                     help="refinement residual: float64, or float32 pairs until berr < 2^-36 then float64")
     ap.add_argument("--leg", default="main", choices=["main", "batched", "learned"])
@@ -463,14 +525,26 @@ def main():
     X = torch.zeros(args.m, args.n, dtype=torch.float64, device=dev).t()
     opts = {"tol": 1e-14, "crit": "berr", "resid": args.resid}
 
-    for _ in range(args.warmup):
-        run_step(spd, h, systems, precs, X, opts)
+    lanes = Lanes(spd, args.lanes, args.n, args.m, dev) if args.lanes > 1 else None
+    handles = lanes.handles if lanes else [h]
+
+    def step_all(k):
+        if lanes:
+            return lanes.run(systems, precs, opts, k)
+        out = []
+        for _ in range(k):
+            out = run_step(spd, h, systems, precs, X, opts)
+        return out
+
+    if args.warmup:
+        step_all(args.warmup)
     torch.cuda.synchronize()
 
     smi = SmiSampler(torch.cuda.current_device())
     nvml = Nvml(torch.cuda.current_device())
-    spd.spd_profile_enable(h, True)
-    launches0 = spd.spd_launch_count(h)
+    for hh in handles:
+        spd.spd_profile_enable(hh, True)
+    launches0 = sum(spd.spd_launch_count(hh) for hh in handles)
     barrier(world)
     torch.cuda.synchronize()
     smi.start()
@@ -478,18 +552,24 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    reps = []
-    for _ in range(args.steps):
-        reps = run_step(spd, h, systems, precs, X, opts)
+    if lanes:
+        lanes.fork(stream)
+    reps = step_all(args.steps)
+    if lanes:
+        lanes.join(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     e1 = nvml.energy_mj() if nvml.ok else None
     barrier(world)
     clocks = smi.stop()
     ms = ev0.elapsed_time(ev1)
-    launches = spd.spd_launch_count(h) - launches0
-    phases = {p: spd.spd_profile_read(h, p) for p in spd.PHASES}
-    spd.spd_profile_enable(h, False)
+    launches = sum(spd.spd_launch_count(hh) for hh in handles) - launches0
+    phases = {}
+    for p in spd.PHASES:
+        recs = [spd.spd_profile_read(hh, p) for hh in handles]
+        phases[p] = {k: sum(r[k] for r in recs) for k in recs[0]}
+    for hh in handles:
+        spd.spd_profile_enable(hh, False)
     ms_max = max_over_ranks(ms, world)
     solves = len(systems) * args.steps * world
     value = solves / (ms_max / 1e3)
@@ -498,7 +578,18 @@ def main():
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
                   "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
                   "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
-    roof = roofline(phases, per_kappa)
+    roof_phases, roof_note = phases, "phases of the timed region"
+    if lanes:
+        # Under concurrency a launch's event time includes sharing the SMs with
+        # the other lanes, so the kernel rooflines come from one more pass of
+        # the same workload on a single lane (CUDA events on its stream).
+        spd.spd_profile_enable(h, True)
+        run_step(spd, h, systems, precs, X, opts)
+        roof_phases = {p: spd.spd_profile_read(h, p) for p in spd.PHASES}
+        spd.spd_profile_enable(h, False)
+        roof_note = "phases of one extra single-lane step of the same workload (timed region ran concurrent lanes)"
+    roof = roofline(roof_phases, per_kappa)
+    roof["measured_on"] = roof_note
     energy = None
     if e0 is not None and e1 is not None:
         j = (e1 - e0) / 1e3
@@ -533,21 +624,38 @@ def main():
         import numpy as np
         hostA = [torch.empty((args.n, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
         hostB = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
-        hostX = torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True)
+        hostX = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in handles]
         for (k, A, B), ha, hb in zip(systems, hostA, hostB):
             ha.copy_(A)
             hb.copy_(B.t())
         torch.cuda.synchronize()
         e2e_steps = max(1, min(args.steps, 2))
+
+        def host_lane(j, errs):
+            hh = handles[j]
+            try:
+                for _ in range(e2e_steps):
+                    for i in range(j, len(systems), len(handles)):
+                        st = spd.lib().spd_solve_ir_host(hh, args.n, args.m, hostA[i].data_ptr(), args.n,
+                                                         hostB[i].data_ptr(), args.n, hostX[j].data_ptr(), args.n,
+                                                         spd.PREC[precs[i]], spd._opts(opts),
+                                                         ctypes.byref(spd.SpdReport()))
+                        if st != spd.SPD_OK:
+                            raise RuntimeError("e2e: " + spd.spd_last_error_string(hh))
+            except Exception as e:  # noqa: BLE001 -- re-raised below
+                errs.append(e)
+
+        import threading
+        errs = []
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            for (k, _, _), ha, hb, p in zip(systems, hostA, hostB, precs):
-                st = spd.lib().spd_solve_ir_host(h, args.n, args.m, ha.data_ptr(), args.n, hb.data_ptr(),
-                                                 args.n, hostX.data_ptr(), args.n, spd.PREC[p],
-                                                 spd._opts(opts), ctypes.byref(spd.SpdReport()))
-                if st != spd.SPD_OK:
-                    raise RuntimeError("e2e: " + spd.spd_last_error_string(h))
+        th = [threading.Thread(target=host_lane, args=(j, errs)) for j in range(len(handles))]
+        for x in th:
+            x.start()
+        for x in th:
+            x.join()
         t = time.perf_counter() - t0
+        if errs:
+            raise errs[0]
         t = max_over_ranks(t, world)
         e2e = {"value": len(systems) * e2e_steps * world / t, "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
@@ -565,6 +673,7 @@ def main():
                "config": {"workload": f"precision sweep n={args.n} m={args.m} kappa in {args.kappas}",
                           "n": args.n, "m": args.m, "kappas": args.kappas, "factor_prec": precs,
                           "l2": "inputs larger than L2 (3 x 8 n^2 bytes resident)", "tol_berr": 1e-14,
+                          "lanes": args.lanes,
                           "residual": {"fp64": "float64 throughout",
                                        "df32": "float32 pairs while berr > 2^-36, float64 to finish "
                                                "(convergence only accepted on a float64 residual)"}[args.resid]},
@@ -572,6 +681,8 @@ def main():
                "energy": energy, "fp64_baseline": fp64, "per_kappa": per_kappa,
                "phases": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in phases.items()}}
         print(json.dumps(out), flush=True)
+    if lanes:
+        lanes.destroy()
     spd.spd_destroy(h)
     if world > 1:
         import torch.distributed as dist

@@ -166,6 +166,10 @@ void spd_opts_default(spd_opts *o);
  * rep may be NULL. */
 spd_status spd_factor(spd_handle *h, int n, const double *A, int lda, int prec,
                       unsigned flags, spd_factor_t **F, spd_report *rep);
+/* Releases the factor's memory, ordered on the handle's stream (no
+ * device-wide synchronisation; factors come from the device's stream-ordered
+ * pool, which spd_create sets to keep freed blocks cached).  The factor must
+ * not be in use on another stream at that point. */
 spd_status spd_factor_destroy(spd_factor_t *F);
 
 /* Order and precision of a factor (either output may be NULL). */

@@ -35,14 +35,15 @@ void launch_batch(spd_batch* b, int method, const BatchArgs& a, cudaStream_t s) 
 }
 
 void set_batch_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    const int smem = (int)batch_smem_bytes();
-    cudaFuncSetAttribute(k_batch_chol_ir<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_batch_chol_ir<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_batch_pcg<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_batch_pcg<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    static const bool done = [] {  // once per process, thread-safe
+        const int smem = (int)batch_smem_bytes();
+        cudaFuncSetAttribute(k_batch_chol_ir<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_batch_chol_ir<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_batch_pcg<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_batch_pcg<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        return true;
+    }();
+    (void)done;
 }
 
 spd_status run_once(spd_batch* b, int method, int nt, const BatchArgs& a) {

@@ -141,14 +141,12 @@ spd_status potrf_rec(FCtx& c, int n0, int nn) {
 
 void free_factor(spd_factor_t* F) {
     if (!F) return;
-    cudaFree(F->W);
-    cudaFree(F->W64);
-    cudaFree(F->Wh);
-    cudaFree(F->d);
-    cudaFree(F->LinvT);
-    cudaFree(F->Cpl);
-    cudaFree(F->Dinv32);
-    cudaFree(F->Dinv64);
+    // stream-ordered frees: no device-wide synchronisation, so factors on
+    // other handles' streams keep running
+    cudaStream_t s = F->h ? F->h->stream : nullptr;
+    for (void* p : {(void*)F->W, (void*)F->W64, F->Wh, (void*)F->d, (void*)F->LinvT, (void*)F->Cpl, (void*)F->Dinv32,
+                    (void*)F->Dinv64})
+        if (p) cudaFreeAsync(p, s);
     delete F;
 }
 
@@ -182,18 +180,19 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         return s;
     };
     cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&F->d, sizeof(double) * std::max(n, 1));
+    cudaStream_t as = h->stream;  // stream-ordered allocations (see free_factor)
+    e = cudaMallocAsync(&F->d, sizeof(double) * std::max(n, 1), as);
     if (e == cudaSuccess && prec == SPD_PREC_FP64) {
-        e = cudaMalloc(&F->W64, sizeof(double) * std::max<size_t>(nW, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv64, sizeof(double) * 4096 * std::max(F->nblk128, 1));
+        e = cudaMallocAsync(&F->W64, sizeof(double) * std::max<size_t>(nW, 1), as);
+        if (e == cudaSuccess) e = cudaMallocAsync(&F->Dinv64, sizeof(double) * 4096 * std::max(F->nblk128, 1), as);
     } else if (e == cudaSuccess) {
-        e = cudaMalloc(&F->W, sizeof(float) * std::max<size_t>(nW, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&F->LinvT, sizeof(float) * 128 * 128 * std::max(F->nblk128, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&F->Cpl, sizeof(float) * 2 * 128 * 128 * std::max(F->nblk128, 1));
-        if (e == cudaSuccess) e = cudaMalloc(&F->Dinv32, sizeof(float) * 4096 * std::max(F->nblk128, 1));
+        e = cudaMallocAsync(&F->W, sizeof(float) * std::max<size_t>(nW, 1), as);
+        if (e == cudaSuccess) e = cudaMallocAsync(&F->LinvT, sizeof(float) * 128 * 128 * std::max(F->nblk128, 1), as);
+        if (e == cudaSuccess) e = cudaMallocAsync(&F->Cpl, sizeof(float) * 2 * 128 * 128 * std::max(F->nblk128, 1), as);
+        if (e == cudaSuccess) e = cudaMallocAsync(&F->Dinv32, sizeof(float) * 4096 * std::max(F->nblk128, 1), as);
         if (e == cudaSuccess && kind) {
             F->ldh = F->ldw;
-            e = cudaMalloc(&F->Wh, mirror_elem(kind) * std::max<size_t>(nW, 1));
+            e = cudaMallocAsync(&F->Wh, mirror_elem(kind) * std::max<size_t>(nW, 1), as);
         }
     }
     if (e != cudaSuccess) {
@@ -315,15 +314,17 @@ spd_status cond_estimate(spd_handle* h, const spd_factor_t* F, const double* A, 
 }  // namespace
 
 static void setup_leaf_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    cudaFuncSetAttribute(k_potrf_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf32_smem());
-    cudaFuncSetAttribute(k_potrf_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf_smem<double>());
-    cudaFuncSetAttribute(k_trsm_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_leaf32_smem());
-    cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_inverse_smem());
-    cudaFuncSetAttribute(k_trsm_leaf<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)trsm_leaf_smem<double, 32>());
+    static const bool done = [] {  // once per process, thread-safe
+        cudaFuncSetAttribute(k_potrf_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)potrf_leaf32_smem());
+        cudaFuncSetAttribute(k_potrf_leaf<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)potrf_leaf_smem<double>());
+        cudaFuncSetAttribute(k_trsm_leaf32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_leaf32_smem());
+        cudaFuncSetAttribute(k_block_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)block_inverse_smem());
+        cudaFuncSetAttribute(k_trsm_leaf<double, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)trsm_leaf_smem<double, 32>());
+        return true;
+    }();
+    (void)done;
 }
 
 extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,

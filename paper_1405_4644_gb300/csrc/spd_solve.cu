@@ -1,6 +1,8 @@
 // spd_solve.cu -- handle management, the float64 residual, the
 // low-precision triangular solves, Algorithm 1's refinement loop and
 // Algorithm 2's CG with iterative refinement.
+#include <mutex>
+
 #include "engine.cuh"
 #include "k_convert.cuh"
 #include "k_solve.cuh"
@@ -36,6 +38,17 @@ extern "C" spd_status spd_create(spd_handle** out, void* stream) {
     if (e == cudaSuccess) e = cudaEventCreate(&h->e0);
     if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // factors come from the device's stream-ordered pool: keep freed
+        // blocks cached in the pool (like a caching allocator) instead of
+        // returning them to the driver at every synchronisation
+        cudaMemPool_t pool = nullptr;
+        if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         DevStatus clear{0, INT_MAX, {0, 0}};
         e = cudaMemcpy(h->dst, &clear, sizeof(clear), cudaMemcpyHostToDevice);
@@ -219,14 +232,15 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
 
 template <typename T>
 void setup_solve_attrs() {
-    static bool done = false;
-    if (done) return;
-    done = true;
-    constexpr int MC = solve_mc<T>();
-    cudaFuncSetAttribute(k_trsv_fwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)solve_smem_bytes<T>());
-    cudaFuncSetAttribute(k_trsv_bwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)solve_smem_bytes<T>());
+    static const bool done = [] {  // once per process, thread-safe
+        constexpr int MC = solve_mc<T>();
+        cudaFuncSetAttribute(k_trsv_fwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solve_smem_bytes<T>());
+        cudaFuncSetAttribute(k_trsv_bwd_step<T, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)solve_smem_bytes<T>());
+        return true;
+    }();
+    (void)done;
 }
 
 // Y <- L^{-T} L^{-1} Y in place (n x m, ld n) with the factor's L and the
@@ -255,23 +269,49 @@ spd_status lp_sweeps(spd_handle* h, const T* W, long ldw, const T* Dinv, int n, 
     return SPD_OK;
 }
 
+// Cooperative launches from every stream of the process run one after
+// another: a cooperative grid needs all of its CTAs resident at once, and two
+// such grids sharing the SMs could each hold part of the machine while
+// waiting for the rest.  Ordinary kernels may overlap them (they always run
+// to completion and release their SMs).
+struct CoopGate {
+    std::mutex mu;
+    cudaEvent_t last = nullptr;
+};
+CoopGate& coop_gate() {
+    static CoopGate g;
+    return g;
+}
+cudaError_t coop_launch(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+    CoopGate& g = coop_gate();
+    std::lock_guard<std::mutex> lock(g.mu);
+    cudaError_t e = cudaSuccess;
+    if (!g.last) e = cudaEventCreateWithFlags(&g.last, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.last, 0);  // a never-recorded event: no wait
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s);
+    if (e == cudaSuccess) e = cudaEventRecord(g.last, s);
+    return e;
+}
+
 template <int MC>
 spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, int c0, int mc) {
-    static int max_ctas[2] = {0, 0};
     const size_t smem = trsv32_smem<MC>();
     auto fwd = k_trsv32<MC, true>;
     auto bwd = k_trsv32<MC, false>;
-    static bool attrs = false;
-    if (!attrs) {
-        attrs = true;
+    struct Occ {
+        int per_sm[2];
+    };
+    static const Occ occ = [&] {  // once per instantiation, thread-safe
+        Occ o{{1, 1}};
         cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd, 256, smem);
-        max_ctas[0] = std::max(1, per_sm) * h->sms;
+        o.per_sm[0] = std::max(1, per_sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bwd, 256, smem);
-        max_ctas[1] = std::max(1, per_sm) * h->sms;
-    }
+        o.per_sm[1] = std::max(1, per_sm);
+        return o;
+    }();
     const int NB = ceil_div(n, 128);
     if (h->ready_n < NB) {
         if (h->ready) CUDA_TRY(h, cudaFree(h->ready));
@@ -284,10 +324,10 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
     for (int dir = 0; dir < 2; ++dir) {
         TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst};
         void* args[] = {&a};
-        const int grid = std::min(NB, max_ctas[dir]);
+        const int grid = std::min(NB, occ.per_sm[dir] * h->sms);
         ++h->launches;
-        CUDA_TRY(h, cudaLaunchCooperativeKernel(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(grid),
-                                                dim3(256), args, smem, h->stream));
+        CUDA_TRY(h, coop_launch(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(grid), dim3(256), args, smem,
+                                h->stream));
     }
     return SPD_OK;
 }
@@ -298,12 +338,12 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
 spd_status factor_couplings(spd_handle* h, spd_factor_t* F) {
     const int NB = F->nblk128;
     if (NB < 2) return SPD_OK;
-    static bool attr = false;
-    if (!attr) {
-        attr = true;
+    static const bool attr = [] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_trsv_couplings, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)trsv_couplings_smem());
-    }
+        return true;
+    }();
+    (void)attr;
     ProfScope ps(h, SPD_PHASE_LEAF, 2.0 * 2.0 * (NB - 1) * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * (NB - 1) * 16384.0);
     ++h->launches, k_trsv_couplings<<<dim3(NB - 1, 2), 256, trsv_couplings_smem(), h->stream>>>(
         F->W, F->ldw, F->n, NB, F->LinvT, F->Cpl);
