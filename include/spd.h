@@ -107,6 +107,10 @@ typedef enum spd_resid {
                                     rounded operands, float32 accumulation;
                                     plain float32 products for FP32): a
                                     reference engine for validation       */
+#define SPD_FACTOR_RECURSIVE 4u  /* tensor-core factors: recursive blocking
+                                    (large updates, many small panels) instead
+                                    of the default left-looking 128-column
+                                    schedule                                */
 
 typedef struct spd_opts {
     double tol;      /* stopping threshold (default 1e-14)                    */

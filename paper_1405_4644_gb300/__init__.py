@@ -41,6 +41,7 @@ RESID = {"fp64": 0, "df32": 1}
 BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
+SPD_FACTOR_RECURSIVE = 4
 
 # every symbol include/spd.h declares
 EXPORTED = [

@@ -13,6 +13,7 @@
 // of the tile) and apply C -= scale * acc to float32 C in global memory.
 // Every wait is bounded; a wait that gives up raises SPD_DEV_TIMEOUT.
 #include <cudaTypedefs.h>
+#include <algorithm>
 #include <cstring>
 #include "gemm_tc.h"
 #include "tc_ptx.cuh"
@@ -20,11 +21,11 @@
 namespace {
 
 constexpr int BM = 128, BN = 256, STAGES = 4;
-constexpr int A_STAGE = BM * 128;               // bytes: 128 rows x 128 B
-constexpr int B_STAGE = BN * 128;               // bytes: 256 rows x 128 B
-constexpr int STAGE_BYTES = A_STAGE + B_STAGE;  // 48 KB
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 256;
-constexpr uint32_t TMEM_COLS = 256;
+constexpr int A_STAGE = BM * 128;  // bytes: 128 rows x 128 B
+// the tile width BNT is 256 (trailing updates) or 128 (one block column)
+template <int BNT> __host__ __device__ constexpr int b_stage() { return BNT * 128; }
+template <int BNT> __host__ __device__ constexpr int stage_bytes() { return A_STAGE + b_stage<BNT>(); }
+template <int BNT> constexpr size_t smem_bytes() { return (size_t)STAGES * stage_bytes<BNT>() + 1024 + 256; }
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 
 template <int KIND> struct KindTraits;
@@ -38,12 +39,19 @@ template <> struct KindTraits<2> {  // fp8 e4m3
     static constexpr int BK = 128, KMMA = 32;
 };
 
-template <int KIND>
+// Split-K (kslice > 0): CTA z handles K tiles [z kslice, (z+1) kslice) of every
+// segment and writes its raw accumulator to Cpart + z M ldp (no C update);
+// k_reduce_parts then subtracts the partials from C in a fixed order.
+template <int KIND, int BNT>
 __global__ void __launch_bounds__(128, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
-              uint32_t idesc, float scale, int nseg, uint32_t segs, DevStatus* st) {
+              uint32_t idesc, float scale, int nseg, uint32_t segs, int kslice, float* __restrict__ Cpart,
+              long ldp, DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
+    constexpr int B_STAGE = b_stage<BNT>();
+    constexpr int STAGE_BYTES = stage_bytes<BNT>();
+    constexpr uint32_t TMEM_COLS = BNT;
     constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -58,7 +66,7 @@ __global__ void __launch_bounds__(128, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bm = blockIdx.y, bn = blockIdx.x;
-    if (lower && (bm * BM + BM - 1 < bn * BN)) return;  // whole tile above the diagonal
+    if (lower && (bm * BM + BM - 1 < bn * BNT)) return;  // whole tile above the diagonal
     if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
 
     if (threadIdx.x == 0) {
@@ -80,7 +88,9 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const int nk = K / BK;       // K tiles per segment
+    const int nk_all = K / BK;  // K tiles per segment
+    const int kb = kslice > 0 ? (int)blockIdx.z * kslice : 0;
+    const int nk = kslice > 0 ? max(0, min(nk_all, kb + kslice) - kb) : nk_all;  // this CTA's share
     const int ntiles = nk * nseg;  // segment s multiplies slice (segs >> 4s) & 3 of A by slice (segs >> 4s+2) & 3 of B
 
     if (warp == 0) {
@@ -92,8 +102,8 @@ __global__ void __launch_bounds__(128, 1)
                 const int za = (segs >> (4 * seg)) & 3, zb = (segs >> (4 * seg + 2)) & 3;
                 if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) break;
                 tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
-                tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + kin * BK, b_row0 + bn * BN, zb, &full[s]);
+                tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + (kb + kin) * BK, a_row0 + bm * BM, za, &full[s]);
+                tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + (kb + kin) * BK, b_row0 + bn * BNT, zb, &full[s]);
             }
         }
         __syncwarp();
@@ -120,12 +130,30 @@ __global__ void __launch_bounds__(128, 1)
     bool ok = tc::mbar_wait(accf, 0, abort_flag, WAIT_NS) && !*abort_flag;
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     tc::fence_after_sync();
-    if (ok) {
+    if (ok && Cpart) {  // split-K partial: the raw accumulator (zero for an empty share)
+        const int row = bm * BM + warp * 32 + lane;
+        for (int ch = 0; ch < BNT / 32; ++ch) {
+            const int col0 = bn * BNT + ch * 32;
+            if (col0 >= N) break;
+            float v[32];
+            if (ntiles > 0) tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32, v);
+            else {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = 0.f;
+            }
+            if (row < M) {
+                float* prow = Cpart + ((long)blockIdx.z * M + row) * ldp + col0;
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (col0 + j < N) prow[j] = v[j];
+            }
+        }
+    } else if (ok) {
         const int rloc = warp * 32 + lane;
         const int row = bm * BM + rloc;
         const int rowmax_warp = bm * BM + warp * 32 + 31;
-        for (int ch = 0; ch < BN / 32; ++ch) {
-            const int col0 = bn * BN + ch * 32;
+        for (int ch = 0; ch < BNT / 32; ++ch) {
+            const int col0 = bn * BNT + ch * 32;
             if (col0 >= N) break;                         // warp-uniform
             if (lower && rowmax_warp < col0) continue;    // warp-uniform: chunk above the diagonal
             float v[32];
@@ -197,31 +225,46 @@ bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols
     return r == CUDA_SUCCESS;
 }
 
-uint32_t idesc_for(int kind) {
+uint32_t idesc_for(int kind, int bn) {
     switch (kind) {
         case 1:
-        case 5: return tc::idesc_f32acc(2, BM, BN);  // tf32
-        case 2: return tc::idesc_f32acc(1, BM, BN);  // bf16
-        case 3: return tc::idesc_f32acc(0, BM, BN);  // fp16
-        default: return tc::idesc_f32acc(0, BM, BN); // e4m3 (kind::f8f6f4)
+        case 5: return tc::idesc_f32acc(2, BM, bn);  // tf32
+        case 2: return tc::idesc_f32acc(1, BM, bn);  // bf16
+        case 3: return tc::idesc_f32acc(0, BM, bn);  // fp16
+        default: return tc::idesc_f32acc(0, BM, bn); // e4m3 (kind::f8f6f4)
     }
 }
 
 void set_attrs() {
     // once per process, thread-safe (function-local static)
     static const bool done = [] {
-        cudaFuncSetAttribute(k_gemm_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-        cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        cudaFuncSetAttribute(k_gemm_tc<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
+        cudaFuncSetAttribute(k_gemm_tc<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
+        cudaFuncSetAttribute(k_gemm_tc<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
+        cudaFuncSetAttribute(k_gemm_tc<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
+        cudaFuncSetAttribute(k_gemm_tc<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
+        cudaFuncSetAttribute(k_gemm_tc<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
         return true;
     }();
     (void)done;
 }
 
+// C[i][j] -= scale * sum_{z < S} P[z][i][j], z in increasing order
+__global__ void k_reduce_parts(float* __restrict__ C, long ldc, int M, int N, const float* __restrict__ P, long ldp,
+                               int S, float scale) {
+    const long total = (long)M * N;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / N), j = (int)(e - (long)i * N);
+        float acc = 0.f;
+        for (int z = 0; z < S; ++z) acc += P[((long)z * M + i) * ldp + j];
+        C[(long)i * ldc + j] -= scale * acc;
+    }
+}
+
 }  // namespace
 
 struct TcGemm {
-    CUtensorMap mapA, mapB;  // box heights 128 (A) and 256 (B)
+    CUtensorMap mapA, mapB, mapB128;  // box heights 128 (A), 256 and 128 (B)
     float* C;
     long ldc;
     int kind;
@@ -235,7 +278,8 @@ spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a
     if (kind < 1 || kind > 5) return SPD_ERR_UNSUPPORTED;
     TcGemm* g = new TcGemm();
     memset(g, 0, sizeof(*g));
-    if (!make_map(&g->mapA, Ah, kind, a_rows, cols, a_ld, BM) || !make_map(&g->mapB, Bh, kind, b_rows, cols, b_ld, BN)) {
+    if (!make_map(&g->mapA, Ah, kind, a_rows, cols, a_ld, BM) || !make_map(&g->mapB, Bh, kind, b_rows, cols, b_ld, BN) ||
+        !make_map(&g->mapB128, Bh, kind, b_rows, cols, b_ld, 128)) {
         delete g;
         return SPD_ERR_UNSUPPORTED;
     }
@@ -251,13 +295,40 @@ spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, 
     return tc_gemm_create_maps(out, Wh, n, ldh, Wh, n, ldh, n, W, ldw, kind);
 }
 
+namespace {
+
+template <int BNT>
+void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M, int N, int K, int a_row0,
+                 int b_row0, int k0, int lower, float scale, int nseg, uint32_t segs, int kslice, float* Cpart,
+                 long ldp, DevStatus* st) {
+    const CUtensorMap& mb = BNT == 128 ? g->mapB128 : g->mapB;
+    const uint32_t idesc = idesc_for(g->kind, BNT);
+    switch (g->kind) {
+        case 1:
+        case 5:
+            k_gemm_tc<1, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
+                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
+                                                                  st);
+            break;
+        case 4:
+            k_gemm_tc<2, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
+                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
+                                                                  st);
+            break;
+        default:
+            k_gemm_tc<0, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
+                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
+                                                                  st);
+    }
+}
+
+}  // namespace
+
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
-                          int k0, int lower, DevStatus* st) {
+                          int k0, int lower, DevStatus* st, int splits, float* Cpart) {
     const int bk = (g->kind == 1 || g->kind == 5) ? 32 : g->kind == 4 ? 128 : 64;
     if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
-    const uint32_t idesc = idesc_for(g->kind);
     // float32 as three tf32 slices: the six slice products of order <= 2,
     // smallest first, into one accumulator (A slice in bits 4s..4s+1, B
     // slice in bits 4s+2..4s+3 of segment s)
@@ -268,26 +339,32 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, 
         nseg = 6;
         for (int q = 0; q < 6; ++q) segs |= (uint32_t)(pairs[q][0] | (pairs[q][1] << 2)) << (4 * q);
     }
-    switch (g->kind) {
-        case 1:
-        case 5:
-            k_gemm_tc<1><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, nseg, segs, st);
-            break;
-        case 4:
-            k_gemm_tc<2><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, nseg, segs, st);
-            break;
-        default:
-            k_gemm_tc<0><<<grid, 128, SMEM_BYTES, s>>>(g->mapA, g->mapB, C, ldc, M, N, K, a_row0, b_row0, k0, lower,
-                                                       idesc, scale, nseg, segs, st);
+    const int nk = K / bk;
+    if (splits > nk) splits = nk;
+    const bool split = splits > 1 && Cpart && !lower;
+    const int kslice = split ? (nk + splits - 1) / splits : 0;
+    if (split) splits = (nk + kslice - 1) / kslice;  // no empty share
+    const int bnt = (N <= 128) ? 128 : 256;
+    dim3 grid((N + bnt - 1) / bnt, (M + BM - 1) / BM, split ? splits : 1);
+    const long ldp = N;
+    if (bnt == 128)
+        launch_kind<128>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, kslice,
+                         split ? Cpart : nullptr, ldp, st);
+    else
+        launch_kind<256>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, kslice,
+                         split ? Cpart : nullptr, ldp, st);
+    if (split) {
+        const long total = (long)M * N;
+        const int blocks = (int)std::min<long>((total + 255) / 256, 1024);
+        k_reduce_parts<<<blocks, 256, 0, s>>>(C, ldc, M, N, Cpart, ldp, splits, scale);
     }
     return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;
 }
 
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
-                       DevStatus* st) {
-    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st);
+                       DevStatus* st, int splits, float* Cpart) {
+    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st, splits,
+                          Cpart);
 }
 
 void tc_gemm_destroy(TcGemm* g) { delete g; }

@@ -22,7 +22,8 @@ struct FCtx {
     spd_handle* h;
     spd_factor_t* F;
     Mirror mir;
-    TcGemm* tc;   // tensor-core GEMM plan (nullptr: CUDA cores)
+    TcGemm* tc;          // tensor-core GEMM plan (nullptr: CUDA cores)
+    float* part = nullptr;  // split-K partials of the block-column updates
 };
 
 
@@ -58,7 +59,7 @@ spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
 }
 
 template <typename T>
-spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower) {
+spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower, int splits = 1) {
     if (M <= 0 || N <= 0 || K <= 0) return SPD_OK;
     spd_factor_t* F = c.F;
     cudaStream_t s = c.h->stream;
@@ -76,7 +77,7 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower)
                                                                      k0, K, lower, c.h->dst);
     } else {
         if (c.tc) {
-            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst);
+            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst, splits, c.part);
             if (st != SPD_OK) return set_err(c.h, st, "tensor-core trailing update failed");
             return SPD_OK;
         }
@@ -137,6 +138,31 @@ spd_status potrf_rec(FCtx& c, int n0, int nn) {
     TRY(trsm_rec<T>(c, n0 + n1, nn - n1, n0, n1));
     TRY(gemm<T>(c, n0 + n1, nn - n1, n0 + n1, nn - n1, n0, n1, 1));
     return potrf_rec<T>(c, n0 + n1, nn - n1);
+}
+
+// Left-looking block-column schedule (tensor-core factors): for each
+// 128-column block k, one update with everything to its left,
+//   W[k:, k] -= L[k:, 0:k] L[k, 0:k]^T      (M x 128 x 128k, split-K when
+//                                             the block column has few tiles)
+// then the leaf and the panel solve below it.  The critical path is one
+// update, one leaf and one panel per block (n/128 of each) instead of the
+// recursion's ~n/128 log2(n/128) panel solves and updates; the operands are
+// read once per block column (left-looking traffic ~n^3/(3*128) operand
+// elements in total), and C is read and written once per block.
+template <typename T>
+spd_status potrf_left(FCtx& c, int n) {
+    const int NB = ceil_div(n, SPD_LEAF);
+    for (int k = 0; k < NB; ++k) {
+        const int r0 = k * SPD_LEAF, nb = std::min(SPD_LEAF, n - r0);
+        if (k > 0) {
+            const int M = n - r0, tiles = ceil_div(M, 128);
+            const int splits = c.part ? std::max(1, std::min(16, c.h->sms / tiles)) : 1;
+            TRY(gemm<T>(c, r0, M, r0, nb, 0, r0, 0, splits));
+        }
+        TRY(leaf_potrf<T>(c, r0, nb));
+        if (r0 + nb < n) TRY(leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb));
+    }
+    return SPD_OK;
 }
 
 void free_factor(spd_factor_t* F) {
@@ -222,8 +248,20 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
             if (st == SPD_OK) c.tc = tc;
             else if (st != SPD_ERR_UNSUPPORTED) return fail(set_err(h, st, "tensor-core plan failed"));
         }
-        if (prec == SPD_PREC_FP64) st = potrf_rec<double>(c, 0, n);
-        else st = potrf_rec<float>(c, 0, n);
+        if (prec == SPD_PREC_FP64) {
+            st = potrf_rec<double>(c, 0, n);
+        } else if (c.tc && !(flags & SPD_FACTOR_RECURSIVE)) {
+            // split-K partials: at most sms x 128 x 128 floats (splits x tiles <= sms)
+            cudaError_t pe = cudaMallocAsync(&c.part, sizeof(float) * 128 * 128 * std::max(h->sms, 1), s);
+            if (pe != cudaSuccess) {
+                cudaGetLastError();
+                c.part = nullptr;  // the updates then run unsplit
+            }
+            st = potrf_left<float>(c, n);
+            if (c.part) cudaFreeAsync(c.part, s);
+        } else {
+            st = potrf_rec<float>(c, 0, n);
+        }
         if (st == SPD_OK && prec != SPD_PREC_FP64) {
             // per-block inverses and sweep couplings: off the factorisation's
             // critical path, all blocks at once

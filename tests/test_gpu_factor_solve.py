@@ -52,6 +52,31 @@ def test_factor_matches_oracle(h, n, prec):
     assert fw <= 8 * kappa * max(n, 8) ** 0.5 * u, fw
 
 
+@pytest.mark.parametrize("n", [129, 700, 2100])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16"])
+def test_left_looking_and_recursive_schedules_agree(h, n, prec):
+    """The default block-column (left-looking) schedule and the recursive
+    one compute the same factor up to rounding: both meet the backward bound
+    of the operand type, and they differ by no more than it allows."""
+    A = W.gram_shifted(n, seed=n + 1, shift=0.5)
+    d_ref, As = scaled(A)
+    Ls = []
+    for flags in [spd.SPD_SCALE_DIAG, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_RECURSIVE]:
+        st, F, rep = spd.spd_factor(h, dev_sym(A), prec, flags)
+        check(h, st)
+        try:
+            L, d, p = factor_L(F)
+        finally:
+            spd.spd_factor_destroy(F)
+        u = max(UNIT_ROUNDOFF[prec], 2.0 ** -24)
+        bw = np.linalg.norm(L @ L.T - As) / np.linalg.norm(As)
+        assert bw <= 4 * max(n, 8) ** 0.5 * u, (flags, bw)
+        Ls.append(L)
+    kappa = np.linalg.cond(As)
+    diff = np.max(np.abs(Ls[0] - Ls[1]))
+    assert diff <= 8 * kappa * max(n, 8) ** 0.5 * max(UNIT_ROUNDOFF[prec], 2.0 ** -24), diff
+
+
 @pytest.mark.parametrize("n", [3, 129, 700])
 @pytest.mark.parametrize("m", [1, 5, 40])
 def test_factor_solve_matches_oracle(h, n, m):
