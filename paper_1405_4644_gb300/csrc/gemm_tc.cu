@@ -20,12 +20,15 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 256, STAGES = 4;
+constexpr int BM = 128, BN = 256;
 constexpr int A_STAGE = BM * 128;  // bytes: 128 rows x 128 B
-// the tile width BNT is 256 (trailing updates) or 128 (one block column)
+// The tile width BNT is 256 (trailing updates) or 128 (one block column),
+// with ST pipeline stages: 4 stages and one CTA per SM, or (128-wide tf32
+// tiles, whose six-segment float32 updates are long) 3 stages of 32 KB and
+// two CTAs per SM, so that one CTA's epilogue overlaps the other's main loop.
 template <int BNT> __host__ __device__ constexpr int b_stage() { return BNT * 128; }
 template <int BNT> __host__ __device__ constexpr int stage_bytes() { return A_STAGE + b_stage<BNT>(); }
-template <int BNT> constexpr size_t smem_bytes() { return (size_t)STAGES * stage_bytes<BNT>() + 1024 + 256; }
+template <int BNT, int ST> constexpr size_t smem_bytes() { return (size_t)ST * stage_bytes<BNT>() + 1024 + 256; }
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 
 template <int KIND> struct KindTraits;
@@ -42,14 +45,15 @@ template <> struct KindTraits<2> {  // fp8 e4m3
 // Split-K (kslice > 0): CTA z handles K tiles [z kslice, (z+1) kslice) of every
 // segment and writes its raw accumulator to Cpart + z M ldp (no C update);
 // k_reduce_parts then subtracts the partials from C in a fixed order.
-template <int KIND, int BNT>
-__global__ void __launch_bounds__(128, 1)
+template <int KIND, int BNT, int ST>
+__global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
               uint32_t idesc, float scale, int nseg, uint32_t segs, int kslice, float* __restrict__ Cpart,
               long ldp, DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
     constexpr int B_STAGE = b_stage<BNT>();
+    constexpr int STAGES = ST;
     constexpr int STAGE_BYTES = stage_bytes<BNT>();
     constexpr uint32_t TMEM_COLS = BNT;
     constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
@@ -238,12 +242,12 @@ uint32_t idesc_for(int kind, int bn) {
 void set_attrs() {
     // once per process, thread-safe (function-local static)
     static const bool done = [] {
-        cudaFuncSetAttribute(k_gemm_tc<0, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
-        cudaFuncSetAttribute(k_gemm_tc<1, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
-        cudaFuncSetAttribute(k_gemm_tc<2, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256>());
-        cudaFuncSetAttribute(k_gemm_tc<0, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
-        cudaFuncSetAttribute(k_gemm_tc<1, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
-        cudaFuncSetAttribute(k_gemm_tc<2, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128>());
+        cudaFuncSetAttribute(k_gemm_tc<0, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
+        cudaFuncSetAttribute(k_gemm_tc<1, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
+        cudaFuncSetAttribute(k_gemm_tc<2, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
+        cudaFuncSetAttribute(k_gemm_tc<0, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
+        cudaFuncSetAttribute(k_gemm_tc<1, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 3>());
+        cudaFuncSetAttribute(k_gemm_tc<2, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
         return true;
     }();
     (void)done;
@@ -305,20 +309,22 @@ void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M
     const uint32_t idesc = idesc_for(g->kind, BNT);
     switch (g->kind) {
         case 1:
-        case 5:
-            k_gemm_tc<1, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
-                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
-                                                                  st);
+        case 5: {
+            constexpr int ST = BNT == 128 ? 3 : 4;
+            k_gemm_tc<1, BNT, ST><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(
+                g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
+                st);
             break;
+        }
         case 4:
-            k_gemm_tc<2, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
-                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
-                                                                  st);
+            k_gemm_tc<2, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
+                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
+                                                                        Cpart, ldp, st);
             break;
         default:
-            k_gemm_tc<0, BNT><<<grid, 128, smem_bytes<BNT>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0,
-                                                                  lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
-                                                                  st);
+            k_gemm_tc<0, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
+                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
+                                                                        Cpart, ldp, st);
     }
 }
 
@@ -340,6 +346,13 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, 
         for (int q = 0; q < 6; ++q) segs |= (uint32_t)(pairs[q][0] | (pairs[q][1] << 2)) << (4 * q);
     }
     const int nk = K / bk;
+    // splits < 0: choose from the SM count -splits, filling the machine once
+    // (two CTAs per SM for the 128-wide tf32 tiles)
+    if (splits < 0) {
+        const int tiles = ((N + 127) / 128 <= 1 && N <= 128 ? 1 : (N + BN - 1) / BN) * ((M + BM - 1) / BM);
+        const int occ = (N <= 128 && (g->kind == 1 || g->kind == 5)) ? 2 : 1;
+        splits = std::max(1, std::min(16, occ * (-splits) / std::max(tiles, 1)));
+    }
     if (splits > nk) splits = nk;
     const bool split = splits > 1 && Cpart && !lower;
     const int kslice = split ? (nk + splits - 1) / splits : 0;

@@ -13,7 +13,9 @@ struct TcGemm;
 // Returns SPD_ERR_UNSUPPORTED when the operand kind has no tensor-core path.
 spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n);
 // splits > 1 with a partial buffer Cpart (splits x M x N floats) splits K
-// across CTAs and reduces the partials in a fixed order (full, not lower).
+// across CTAs and reduces the partials in a fixed order (full, not lower);
+// splits = -S lets the GEMM pick the split count for S SMs (at most 16,
+// and then Cpart must hold 2 S x 128 x 128 floats).
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
                        DevStatus* st, int splits = 1, float* Cpart = nullptr);
 void tc_gemm_destroy(TcGemm* g);

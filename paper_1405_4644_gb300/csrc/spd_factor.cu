@@ -156,7 +156,8 @@ spd_status potrf_left(FCtx& c, int n) {
         const int r0 = k * SPD_LEAF, nb = std::min(SPD_LEAF, n - r0);
         if (k > 0) {
             const int M = n - r0, tiles = ceil_div(M, 128);
-            const int splits = c.part ? std::max(1, std::min(16, c.h->sms / tiles)) : 1;
+            (void)tiles;
+            const int splits = c.part ? -c.h->sms : 1;  // split-K chosen by the GEMM from the SM count
             TRY(gemm<T>(c, r0, M, r0, nb, 0, r0, 0, splits));
         }
         TRY(leaf_potrf<T>(c, r0, nb));
@@ -251,8 +252,8 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (prec == SPD_PREC_FP64) {
             st = potrf_rec<double>(c, 0, n);
         } else if (c.tc && !(flags & SPD_FACTOR_RECURSIVE)) {
-            // split-K partials: at most sms x 128 x 128 floats (splits x tiles <= sms)
-            cudaError_t pe = cudaMallocAsync(&c.part, sizeof(float) * 128 * 128 * std::max(h->sms, 1), s);
+            // split-K partials: at most 2 sms x 128 x 128 floats (splits x tiles <= 2 sms)
+            cudaError_t pe = cudaMallocAsync(&c.part, sizeof(float) * 128 * 128 * 2 * std::max(h->sms, 1), s);
             if (pe != cudaSuccess) {
                 cudaGetLastError();
                 c.part = nullptr;  // the updates then run unsplit
