@@ -292,8 +292,8 @@ def roofline(phases, per_kappa):
              "peak_source": f"{src} bf16 sustained x nominal {'/'.join(low)} ratio {ratio}"}
     elif dom == "trailing_x3":
         r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12,
-             "peak": bf16 * TENSOR_RATIO["tf32"] / 6,
-             "peak_source": f"{src} bf16 sustained x nominal tf32 ratio 0.5 / 6 tf32 products per float32 product"}
+             "peak": bf16 / 6,
+             "peak_source": f"{src} bf16 sustained / 6 bf16 slice products per float32 product"}
     elif dom == "resid":
         r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP64_PEAK_TFLOPS,
              "peak_source": "nominal FP64 1.25 TFLOP/s of the part"}

@@ -359,13 +359,15 @@ spd_status spd_batch_destroy(spd_batch *plan);
  * the tensor cores: A (M x K) and B (N x K) float32 row-major are rounded
  * (RNE) to `prec` (SPD_PREC_TF32, BF16, FP16 or FP8 -- FP8 multiplies the
  * operands by 2^8 before rounding, so |entries| <= 1.75 stay in range)
- * and multiplied with float32 accumulation; C is float32 row-major.
- * SPD_PREC_FP32 splits each operand exactly into three tf32 slices
- * (s0 = tf32(x), s1 = tf32(x - s0), s2 = x - s0 - s1) and accumulates the
- * six slice products of order <= 2, smallest first: float32 accuracy
- * (dropped terms below 2^-32 |a||b|) at tf32 tensor-core speed / 6.
+ * and multiplied with float32 accumulation; C is float32 row-major
  * (ldc >= N).  lower != 0 (requires A == B, M == N, lda == ldb) updates
- * only entries with row >= column.  Device pointers; synchronous. */
+ * only entries with row >= column.  SPD_PREC_FP32 splits each operand into
+ * three bf16 slices (s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 -
+ * s1), together x's 24 significant bits) and accumulates the six slice
+ * products of order <= 2, smallest first, in float32: float32-class
+ * accuracy (the dropped products are below 2^-23 |a||b|, the slices' last
+ * rounding below 2^-24 |x|) at one third of the bf16 tensor-core rate.
+ * Device pointers; synchronous. */
 spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,
                            const float *B, int ldb, float *C, int ldc, int lower);
 
@@ -385,7 +387,7 @@ typedef enum spd_phase {
     SPD_PHASE_VECTOR = 6,   /* A6/C2: float64 vector updates and dots    */
     SPD_PHASE_PANEL = 7,    /* A2: panel triangular solves (leaf TRSM)   */
     SPD_PHASE_BATCH = 8,    /* B1: persistent batched solves             */
-    SPD_PHASE_TRAILING_X3 = 9, /* A3 of an FP32 factor: three tf32 slices
+    SPD_PHASE_TRAILING_X3 = 9, /* A3 of an FP32 factor: three bf16 slices
                                   on the tensor cores (flops counted once) */
     SPD_PHASE_RESID_DF32 = 10, /* A5/C3 on the float32 units (float32 pairs) */
     SPD_PHASE_COUNT = 11

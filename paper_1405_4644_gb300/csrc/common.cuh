@@ -72,17 +72,19 @@ struct Mirror {
     void* ptr;     // n x ld elements of the operand type (nullptr = no mirror)
     long ld;       // leading dimension in elements (row-major)
     int kind;      // 0 none, 1 tf32 (float), 2 bf16, 3 fp16, 4 fp8 e4m3 (x SPD_FP8_SCALE),
-                   // 5 float32 as three tf32 slices (planes of `plane` elements)
+                   // 5 float32 as three bf16 slices (planes of `plane` elements)
     long plane;    // kind 5: elements per slice plane (n * ld)
 };
 
-// x = s0 + s1 + s2 exactly, each a tf32 value: s0 = tf32(x), s1 = tf32(x - s0),
-// s2 = x - s0 - s1 (at most 2 significant bits left)
-__device__ __forceinline__ void split_tf32x3(float x, float& s0, float& s1, float& s2) {
-    s0 = round_tf32(x);
-    const float r1 = x - s0;
-    s1 = round_tf32(r1);
-    s2 = r1 - s1;
+// x ~ s0 + s1 + s2 with bf16 slices: s0 = bf16(x), s1 = bf16(x - s0),
+// s2 = bf16(x - s0 - s1); the remainders are exact in float32, so the three
+// slices carry x's 24 significant bits up to a last rounding below 2^-24 |x|
+__device__ __forceinline__ void split_bf16x3(float x, __nv_bfloat16& s0, __nv_bfloat16& s1, __nv_bfloat16& s2) {
+    s0 = __float2bfloat16_rn(x);
+    const float r1 = __fsub_rn(x, __bfloat162float(s0));
+    s1 = __float2bfloat16_rn(r1);
+    const float r2 = __fsub_rn(r1, __bfloat162float(s1));
+    s2 = __float2bfloat16_rn(r2);
 }
 
 __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, float v) {
@@ -94,9 +96,9 @@ __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, fl
             ((__nv_fp8_e4m3*)m.ptr)[r * m.ld + c] = __nv_fp8_e4m3(v * SPD_FP8_SCALE);
             break;
         case 5: {
-            float s0, s1, s2;
-            split_tf32x3(v, s0, s1, s2);
-            float* p = (float*)m.ptr + r * m.ld + c;
+            __nv_bfloat16 s0, s1, s2;
+            split_bf16x3(v, s0, s1, s2);
+            __nv_bfloat16* p = (__nv_bfloat16*)m.ptr + r * m.ld + c;
             p[0] = s0;
             p[m.plane] = s1;
             p[2 * m.plane] = s2;

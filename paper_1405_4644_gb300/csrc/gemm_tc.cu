@@ -205,7 +205,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-int elem_bytes(int kind) { return (kind == 1 || kind == 5) ? 4 : kind == 4 ? 1 : 2; }
+int elem_bytes(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
 int slices_of(int kind) { return kind == 5 ? 3 : 1; }
 
 // 3-D map over `planes` row-major (rows x cols, ld elements) operand planes
@@ -214,8 +214,8 @@ int slices_of(int kind) { return kind == 5 ? 3 : 1; }
 bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols, long ld, int box_rows) {
     auto enc = get_encode();
     if (!enc) return false;
-    CUtensorMapDataType dt = (kind == 1 || kind == 5) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                             : kind == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+    CUtensorMapDataType dt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : (kind == 2 || kind == 5) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                              : kind == 3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                          : CU_TENSOR_MAP_DATA_TYPE_UINT8;
     const int es = elem_bytes(kind);
@@ -231,9 +231,9 @@ bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols
 
 uint32_t idesc_for(int kind, int bn) {
     switch (kind) {
-        case 1:
-        case 5: return tc::idesc_f32acc(2, BM, bn);  // tf32
-        case 2: return tc::idesc_f32acc(1, BM, bn);  // bf16
+        case 1: return tc::idesc_f32acc(2, BM, bn);  // tf32
+        case 2:
+        case 5: return tc::idesc_f32acc(1, BM, bn);  // bf16 (and float32 as bf16 slices)
         case 3: return tc::idesc_f32acc(0, BM, bn);  // fp16
         default: return tc::idesc_f32acc(0, BM, bn); // e4m3 (kind::f8f6f4)
     }
@@ -246,7 +246,8 @@ void set_attrs() {
         cudaFuncSetAttribute(k_gemm_tc<1, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
         cudaFuncSetAttribute(k_gemm_tc<2, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
         cudaFuncSetAttribute(k_gemm_tc<0, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<1, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 3>());
+        cudaFuncSetAttribute(k_gemm_tc<0, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 3>());
+        cudaFuncSetAttribute(k_gemm_tc<1, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
         cudaFuncSetAttribute(k_gemm_tc<2, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
         return true;
     }();
@@ -309,9 +310,13 @@ void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M
     const uint32_t idesc = idesc_for(g->kind, BNT);
     switch (g->kind) {
         case 1:
-        case 5: {
+            k_gemm_tc<1, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
+                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
+                                                                        Cpart, ldp, st);
+            break;
+        case 5: {  // float32 as bf16 slices: six-segment K loops, two CTAs per SM on 128-wide tiles
             constexpr int ST = BNT == 128 ? 3 : 4;
-            k_gemm_tc<1, BNT, ST><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(
+            k_gemm_tc<0, BNT, ST><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(
                 g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
                 st);
             break;
@@ -332,10 +337,10 @@ void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M
 
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
                           int k0, int lower, DevStatus* st, int splits, float* Cpart) {
-    const int bk = (g->kind == 1 || g->kind == 5) ? 32 : g->kind == 4 ? 128 : 64;
+    const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
     if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
-    // float32 as three tf32 slices: the six slice products of order <= 2,
+    // float32 as three bf16 slices: the six slice products of order <= 2,
     // smallest first, into one accumulator (A slice in bits 4s..4s+1, B
     // slice in bits 4s+2..4s+3 of segment s)
     int nseg = 1;
@@ -350,7 +355,7 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, 
     // (two CTAs per SM for the 128-wide tf32 tiles)
     if (splits < 0) {
         const int tiles = ((N + 127) / 128 <= 1 && N <= 128 ? 1 : (N + BN - 1) / BN) * ((M + BM - 1) / BM);
-        const int occ = (N <= 128 && (g->kind == 1 || g->kind == 5)) ? 2 : 1;
+        const int occ = (N <= 128 && g->kind == 5) ? 2 : 1;
         splits = std::max(1, std::min(16, occ * (-splits) / std::max(tiles, 1)));
     }
     if (splits > nk) splits = nk;

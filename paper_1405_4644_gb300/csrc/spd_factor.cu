@@ -7,7 +7,7 @@
 //
 // with 128x128 leaves (k_potrf_leaf / k_trsm_leaf) and every off-leaf
 // update a GEMM on the working matrix (tensor cores for TF32/BF16/FP16/FP8
-// and for FP32 as three tf32 slices; CUDA cores for FP64).  Split points are multiples of 128, so only the
+// and for FP32 as three bf16 slices; CUDA cores for FP64).  Split points are multiples of 128, so only the
 // very last leaf can be ragged.
 #include "engine.cuh"
 #include "k_convert.cuh"
@@ -67,7 +67,7 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower,
     // in T, each operand row read once in the operand type
     const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
     const double opsz = sizeof(T) == 8 ? 8.0
-                        : c.mir.kind == 5 ? 12.0
+                        : c.mir.kind == 5 ? 6.0
                         : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
     ProfScope ps(c.h, (c.tc && c.mir.kind == 5) ? SPD_PHASE_TRAILING_X3 : SPD_PHASE_TRAILING, 2.0 * celems * K,
                  2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N));
@@ -187,7 +187,7 @@ int mirror_kind(int prec) {
         default: return 0;
     }
 }
-size_t mirror_elem(int kind) { return kind == 5 ? 12 : kind == 1 ? 4 : kind == 4 ? 1 : 2; }
+size_t mirror_elem(int kind) { return kind == 5 ? 6 : kind == 1 ? 4 : kind == 4 ? 1 : 2; }
 
 // One factorisation attempt in a fixed precision.
 spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
@@ -199,7 +199,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
     F->ldw = round_up(std::max(n, 1), 64);
     F->nblk128 = ceil_div(n, SPD_LEAF);
     const size_t nW = (size_t)n * F->ldw;
-    // the float32 factor's mirror (three tf32 slices) is only needed by the
+    // the float32 factor's mirror (three bf16 slices) is only needed by the
     // tensor-core engine
     const int kind = (prec == SPD_PREC_FP32 && (flags & SPD_FACTOR_CUDA_CORES)) ? 0 : mirror_kind(prec);
     auto fail = [&](spd_status s) {

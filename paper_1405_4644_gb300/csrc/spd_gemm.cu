@@ -40,7 +40,7 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
         (M > 0 && N > 0 && (!C || ldc < N)) || (lower && (M != N || A != B || lda != ldb)))
         return set_err(h, SPD_ERR_ARG, "spd_gemm_update: bad arguments");
     if (M == 0 || N == 0 || K == 0) return SPD_OK;
-    const int es = kind == 5 ? 12 : kind == 1 ? 4 : kind == 4 ? 1 : 2;  // bytes per element over all slices
+    const int es = kind == 5 ? 6 : kind == 1 ? 4 : kind == 4 ? 1 : 2;  // bytes per element over all slices
     const long Kp = round_up(K, 128);
     const long ldo = round_up(Kp, 64);
     WsPlan p;

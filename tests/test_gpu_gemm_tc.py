@@ -75,10 +75,10 @@ def test_gemm_update_lower_triangle(h, prec, M, K):
 
 
 @pytest.mark.parametrize("M,N,K", [(128, 256, 32), (300, 500, 200), (1000, 1000, 1024), (513, 129, 640)])
-def test_gemm_update_fp32_three_tf32_slices(h, M, N, K):
-    """FP32 operands split exactly into three tf32 slices; the six slice
-    products of order <= 2 give the float32 product to float32 accuracy
-    (dropped terms are below 2^-32 |a||b|), far beyond one tf32 product."""
+def test_gemm_update_fp32_three_bf16_slices(h, M, N, K):
+    """FP32 operands split into three bf16 slices; the six slice products of
+    order <= 2 give the float32 product to float32-class accuracy (dropped
+    terms below 2^-23 |a||b|), far beyond one tf32 product."""
     g = np.random.default_rng(M + 5 * N + 11 * K)
     A = g.uniform(-1, 1, (M, K)) * 2.0
     B = g.uniform(-1, 1, (N, K)) * 2.0
