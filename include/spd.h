@@ -92,8 +92,10 @@ typedef enum spd_resid {
     SPD_RESID_FP64 = 0, /* float64 fused multiply-adds                        */
     SPD_RESID_DF32 = 1  /* refinement loops: residuals of spd_residual_df32 (float32
                            units, about 48-bit accurate) while the largest
-                           backward error is above 2^-36, float64 residuals
-                           from there on; a column is only ever accepted as
+                           backward error is above 2^-36 and, below that,
+                           while each sweep still shrinks it fourfold;
+                           float64 residuals from there on; a column is only
+                           ever accepted as
                            converged on a float64 residual, so the stopping
                            rule and its guarantee are those of SPD_RESID_FP64.
                            The float64 products of the CG fallback use

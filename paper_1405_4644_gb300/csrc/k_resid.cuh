@@ -210,7 +210,7 @@ struct IrSummary {
 static __global__ void k_ir_check(const double* __restrict__ colnorms, const double* __restrict__ anorm,
                            const double* __restrict__ b2, int m, int crit, double tol,
                            IrCol* __restrict__ cols, IrSummary* __restrict__ sum, int count_sweep, int polish,
-                           int accept = 1) {
+                           int accept = 1, int restart = 0) {
     __shared__ int s_active, s_stag, s_pend;
     __shared__ double s_berr, s_rel;
     if (threadIdx.x == 0) {
@@ -244,7 +244,10 @@ static __global__ void k_ir_check(const double* __restrict__ colnorms, const dou
                 st.stall = 0;
             } else {
                 st.extra = polish;
-                if (count_sweep) st.stall = (err > 0.5 * st.prev) ? st.stall + 1 : 0;
+                // restart: the first residual of another arithmetic is not
+                // compared with the last one of the previous arithmetic
+                if (restart) st.stall = 0;
+                else if (count_sweep) st.stall = (err > 0.5 * st.prev) ? st.stall + 1 : 0;
             }
             st.prev = err;
             st.err = err;

@@ -178,15 +178,35 @@ spd_status resid_partial_df32(spd_handle* h, const ResidWs& w, int n, int m, con
 
 // SPD_RESID_DF32 in the refinement loops: float32-pair residuals while the
 // largest backward error is above 2^-36 (16 times their own error bound
-// 2^-40 |A||x|, so the correction they drive is as good as a float64 one),
-// float64 residuals from there on; only a float64 residual may accept a
-// column as converged.
+// 2^-40 |A||x|, so the correction they drive is as good as a float64 one)
+// and, below that, while each sweep still shrinks it at least fourfold (the
+// pairs' rounding has not been reached); float64 residuals from the first
+// sweep that fails either test, or after a column met the rule on a pair
+// residual.  Only a float64 residual may accept a column as converged.
 constexpr double DF32_SWITCH = 1.4551915228366852e-11;  // 2^-36
 
-int resid_kind_for(const spd_opts& o, double berr_now, int pending = 0) {
-    return (o.resid == SPD_RESID_DF32 && pending == 0 && !(berr_now <= DF32_SWITCH)) ? SPD_RESID_DF32
-                                                                                      : SPD_RESID_FP64;
-}
+struct ResidPolicy {
+    bool df32;           // still on float32-pair residuals
+    double prev = -1.0;  // largest backward error of the previous residual
+    explicit ResidPolicy(const spd_opts& o) : df32(o.resid == SPD_RESID_DF32) {}
+    int first() const { return df32 ? SPD_RESID_DF32 : SPD_RESID_FP64; }
+    // kind of the next residual after one with summary sm; *restart = 1 when
+    // the arithmetic changes
+    int next(const IrSummary& sm, int* restart) {
+        *restart = 0;
+        if (df32) {
+            const double b = sm.max_berr;
+            const bool keep = sm.pending == 0 && b > 0.0 &&
+                              (b > DF32_SWITCH || (prev > 0.0 && b <= 0.25 * prev));
+            if (!keep) {
+                df32 = false;
+                *restart = 1;
+            }
+        }
+        prev = sm.max_berr;
+        return df32 ? SPD_RESID_DF32 : SPD_RESID_FP64;
+    }
+};
 
 spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda, const double* B,
                      long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
@@ -597,13 +617,16 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                       double* X, long ldx, const spd_opts& o, const CgSetup& cs, bool reuse_state, int* low,
                       int* high, IrSummary* last) {
     cudaStream_t s = h->stream;
+    // a refinement that falls back here after float64 residuals stays on them
+    ResidPolicy pol(o);
+    if (reuse_state) pol.df32 = false;
     const int gv = grid_for((long)n * m, 256, 8 * h->sms);
     spd_status st;
     if (!reuse_state) {
         CUDA_TRY(h, cudaMemset2DAsync(X, sizeof(double) * ldx, 0, sizeof(double) * n, m, s));
         ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, 0);
         ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
-        const int rk = resid_kind_for(o, INFINITY);
+        const int rk = pol.first();
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0, 0,
@@ -672,11 +695,12 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             }
         }
         ++(h)->launches, k_add_cols<<<gv, 256, 0, s>>>(X, ldx, w.E, n, m, w.frozen);
-        const int rk = resid_kind_for(o, sm.max_berr, sm.pending);
+        int restart = 0;
+        const int rk = pol.next(sm, &restart);
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1, 0,
-                                                      rk == SPD_RESID_FP64);
+                                                      rk == SPD_RESID_FP64, restart);
         LAUNCH_CHECK(h);
         ++outer;
     }
@@ -723,7 +747,8 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     LAUNCH_CHECK(h);
     st = lp_apply(h, F, n, m, B, ldb, w.Yz, X, ldx, nullptr, 0);  // line 2
     if (st != SPD_OK) return st;
-    int rk = resid_kind_for(o, INFINITY);
+    ResidPolicy pol(o);
+    int rk = pol.first(), restart = 0;
     st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);  // line 3
     if (st != SPD_OK) return st;
     ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0,
@@ -762,11 +787,11 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
         ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
         st = lp_apply(h, F, n, m, w.R, n, w.Yz, X, ldx, w.frozen, 1);  // lines 5-6
         if (st != SPD_OK) return st;
-        rk = resid_kind_for(o, sm.max_berr, sm.pending);
+        rk = pol.next(sm, &restart);
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);  // line 7
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1,
-                                                      std::max(0, o.polish), rk == SPD_RESID_FP64);
+                                                      std::max(0, o.polish), rk == SPD_RESID_FP64, restart);
         LAUNCH_CHECK(h);
         ++sweeps;
         ++low;
