@@ -109,6 +109,52 @@ __device__ __forceinline__ void mirror_store(const Mirror& m, long r, long c, fl
 }
 __device__ __forceinline__ void mirror_store(const Mirror&, long, long, double) {}
 
+// Four consecutive entries (c a multiple of 4) in one packed store per plane.
+__device__ __forceinline__ uint2 pack_bf16x4(float a, float b, float c, float d) {
+    __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    return make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+}
+__device__ __forceinline__ void mirror_store4(const Mirror& m, long r, long c, float4 v) {
+    const long o = r * m.ld + c;
+    switch (m.kind) {
+        case 1:
+            *reinterpret_cast<float4*>((float*)m.ptr + o) =
+                make_float4(round_tf32(v.x), round_tf32(v.y), round_tf32(v.z), round_tf32(v.w));
+            break;
+        case 2: *reinterpret_cast<uint2*>((__nv_bfloat16*)m.ptr + o) = pack_bf16x4(v.x, v.y, v.z, v.w); break;
+        case 3: {
+            __half2 lo = __floats2half2_rn(v.x, v.y), hi = __floats2half2_rn(v.z, v.w);
+            *reinterpret_cast<uint2*>((__half*)m.ptr + o) =
+                make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+            break;
+        }
+        case 5: {
+            __nv_bfloat16 s[4][3];
+            split_bf16x3(v.x, s[0][0], s[0][1], s[0][2]);
+            split_bf16x3(v.y, s[1][0], s[1][1], s[1][2]);
+            split_bf16x3(v.z, s[2][0], s[2][1], s[2][2]);
+            split_bf16x3(v.w, s[3][0], s[3][1], s[3][2]);
+            __nv_bfloat16* p = (__nv_bfloat16*)m.ptr + o;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                __nv_bfloat162 lo, hi;
+                lo.x = s[0][q];
+                lo.y = s[1][q];
+                hi.x = s[2][q];
+                hi.y = s[3][q];
+                *reinterpret_cast<uint2*>(p + q * m.plane) =
+                    make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+            }
+            break;
+        }
+        default:
+            mirror_store(m, r, c, v.x);
+            mirror_store(m, r, c + 1, v.y);
+            mirror_store(m, r, c + 2, v.z);
+            mirror_store(m, r, c + 3, v.w);
+    }
+}
+
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
 template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }

@@ -181,11 +181,15 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
         float v[4] = {sr[0], sr[1], sr[2], sr[3]};
         float* dst = W + (long)(k + r) * ldw + k + c4;
         if (c4 + 3 <= r) {
-            *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+            const float4 f = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst) = f;
+            mirror_store4(mir, (long)(k + r), (long)(k + c4), f);
         } else {
-            for (int q = 0; c4 + q <= r; ++q) dst[q] = v[q];
+            for (int q = 0; c4 + q <= r; ++q) {
+                dst[q] = v[q];
+                mirror_store(mir, (long)(k + r), (long)(k + c4 + q), v[q]);
+            }
         }
-        for (int q = 0; q < 4 && c4 + q <= r; ++q) mirror_store(mir, (long)(k + r), (long)(k + c4 + q), v[q]);
     }
 }
 
@@ -310,10 +314,7 @@ __global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, l
         if (row >= r0 + m) continue;
         const float4 v = *reinterpret_cast<const float4*>(Bs + rr * 132 + c4);
         *reinterpret_cast<float4*>(W + row * ldw + c0 + c4) = v;
-        mirror_store(mir, row, (long)(c0 + c4), v.x);
-        mirror_store(mir, row, (long)(c0 + c4 + 1), v.y);
-        mirror_store(mir, row, (long)(c0 + c4 + 2), v.z);
-        mirror_store(mir, row, (long)(c0 + c4 + 3), v.w);
+        mirror_store4(mir, row, (long)(c0 + c4), v);
     }
 }
 
