@@ -13,6 +13,7 @@
 //   partial norms.  Pass 3 (k_colnorms): per-column norms.
 #pragma once
 #include "common.cuh"
+#include "tc_ptx.cuh"
 
 #define RESID_ROWS 256
 #define RESID_JT 64
@@ -346,17 +347,61 @@ static __global__ void __launch_bounds__(256) k_xscale(const double* __restrict_
     }
 }
 
+// A reaches shared memory in 16-column chunks by bulk copies (one 2 KB copy
+// per column of the CTA's 256 rows, double-buffered, completing on an
+// mbarrier), so the loads in flight no longer depend on registers.  A CTA
+// whose rows are ragged (the last row block) or whose columns are not 16-byte
+// aligned reads A directly instead.
+#define DF_DJ 16
+template <int MT>
+constexpr size_t df32_smem() {
+    return (size_t)2 * DF_DJ * RESID_ROWS * sizeof(double)       // A chunks
+           + (size_t)RESID_JT * (MT + 1) * sizeof(float2)          // (xh, xm)
+           + (size_t)RESID_JT * (MT + 1) * sizeof(double) + 64;   // scaled X, barriers
+}
+
+template <int MT>
+__device__ __forceinline__ void df32_madd(double a, const float2* xfj, const double* xdj, float (&S)[MT],
+                                          float (&C)[MT], double (&acc)[MT], float& asum, bool with_abs) {
+    float ah, am;
+    if (!df32_split(a, ah, am)) {
+#pragma unroll
+        for (int c = 0; c < MT; ++c) acc[c] = fma(a, xdj[c], acc[c]);
+        if (with_abs) asum += fabsf(__double2float_rn(a));
+    }
+    if (with_abs) asum += fabsf(ah);
+#pragma unroll
+    for (int c = 0; c < MT; ++c) {
+        const float2 x = xfj[c];
+        const float p = __fmul_rn(ah, x.x);
+        const float e = __fmaf_rn(ah, x.x, -p);
+        const float cr = __fmaf_rn(ah, x.y, __fmaf_rn(am, x.x, e));
+        const float s = __fadd_rn(S[c], p);
+        const float bp = __fsub_rn(s, S[c]);
+        const float t = __fadd_rn(__fsub_rn(S[c], __fsub_rn(s, bp)), __fsub_rn(p, bp));
+        S[c] = s;
+        C[c] = __fadd_rn(C[c], __fadd_rn(t, cr));
+    }
+}
+
 template <int MT>
 static __global__ void __launch_bounds__(RESID_ROWS, 2)
     k_resid_partial_df32(const double* __restrict__ A, long lda, int n, const double* __restrict__ X, long ldx,
                          int c0, int mc, int jchunk, int mtot, const double* __restrict__ sc,
-                         double* __restrict__ P, float* __restrict__ rowabs) {
-    __shared__ __align__(16) float2 xf[RESID_JT][MT];   // (xh, xm) of the scaled X
-    __shared__ __align__(16) double xd[RESID_JT][MT];   // the scaled X itself (float64 branch)
+                         double* __restrict__ P, float* __restrict__ rowabs, DevStatus* st) {
+    extern __shared__ __align__(128) unsigned char df_smem[];
+    double* Ast = reinterpret_cast<double*>(df_smem);                                   // [2][DF_DJ][256]
+    float2* xf = reinterpret_cast<float2*>(Ast + 2 * DF_DJ * RESID_ROWS);              // [JT][MT+1]
+    double* xd = reinterpret_cast<double*>(xf + RESID_JT * (MT + 1));                   // [JT][MT+1]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(xd + RESID_JT * (MT + 1));              // [2]
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 2);
     const int tid = threadIdx.x;
-    const int i = blockIdx.x * RESID_ROWS + tid;
+    const int i0 = blockIdx.x * RESID_ROWS, i = i0 + tid;
     const int j0 = blockIdx.y * jchunk;
     const int j1 = min(n, j0 + jchunk);
+    const bool bulk = (i0 + RESID_ROWS <= n) && ((reinterpret_cast<uintptr_t>(A + i0) & 15) == 0) &&
+                      ((lda * (long)sizeof(double)) % 16 == 0);
+    const int nchunks = (j1 - j0 + DF_DJ - 1) / DF_DJ;
     float S[MT], C[MT];
     double acc[MT];
 #pragma unroll
@@ -366,7 +411,29 @@ static __global__ void __launch_bounds__(RESID_ROWS, 2)
         acc[c] = 0.0;
     }
     float asum = 0.f;
+    if (tid == 0) {
+        tc::mbar_init(&bar[0], 1);
+        tc::mbar_init(&bar[1], 1);
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    // issue chunk g (columns j0 + 16 g ..) into buffer g & 1
+    auto issue = [&](int g) {
+        const int jc = j0 + g * DF_DJ, w = min(DF_DJ, j1 - jc);
+        uint64_t* b = &bar[g & 1];
+        tc::mbar_arrive_expect_tx(b, (uint32_t)(w * RESID_ROWS * sizeof(double)));
+        for (int q = 0; q < w; ++q)
+            tc::bulk_g2s(Ast + ((g & 1) * DF_DJ + q) * RESID_ROWS, A + (long)(jc + q) * lda + i0,
+                         RESID_ROWS * sizeof(double), b);
+    };
+    if (bulk && tid == 0) {
+        if (nchunks > 0) issue(0);
+        if (nchunks > 1) issue(1);
+    }
     const double* Ai = A + (i < n ? i : 0);
+    bool ok = true;
+    int g = 0;
     for (int jb = j0; jb < j1; jb += RESID_JT) {
         const int jn = min(RESID_JT, j1 - jb);
         __syncthreads();
@@ -374,38 +441,32 @@ static __global__ void __launch_bounds__(RESID_ROWS, 2)
             const int jj = e % RESID_JT, c = e / RESID_JT;
             double v = 0.0;
             if (jj < jn && c < mc) v = X[(long)(c0 + c) * ldx + jb + jj] * sc[c0 + c];
-            const float h = __double2float_rn(v);
-            xd[jj][c] = v;
-            xf[jj][c] = make_float2(h, __double2float_rn(v - (double)h));
+            const float hx = __double2float_rn(v);
+            xd[jj * (MT + 1) + c] = v;
+            xf[jj * (MT + 1) + c] = make_float2(hx, __double2float_rn(v - (double)hx));
         }
         __syncthreads();
-        if (i < n) {
-            const double* ap = Ai + (long)jb * lda;
-            for (int jf = 0; jf < jn; jf += RESID_FOLD) {
-                const int je = min(jn, jf + RESID_FOLD);
-#pragma unroll 2
-                for (int jj = jf; jj < je; ++jj) {
-                    const double a = __ldg(ap + (long)jj * lda);
-                    float ah, am;
-                    if (!df32_split(a, ah, am)) {
-#pragma unroll
-                        for (int c = 0; c < MT; ++c) acc[c] = fma(a, xd[jj][c], acc[c]);
-                        if (rowabs) asum += fabsf(__double2float_rn(a));
-                    }
-                    if (rowabs) asum += fabsf(ah);
-#pragma unroll
-                    for (int c = 0; c < MT; ++c) {
-                        const float2 x = xf[jj][c];
-                        const float p = __fmul_rn(ah, x.x);
-                        const float e = __fmaf_rn(ah, x.x, -p);
-                        const float cr = __fmaf_rn(ah, x.y, __fmaf_rn(am, x.x, e));
-                        const float s = __fadd_rn(S[c], p);
-                        const float bp = __fsub_rn(s, S[c]);
-                        const float t = __fadd_rn(__fsub_rn(S[c], __fsub_rn(s, bp)), __fsub_rn(p, bp));
-                        S[c] = s;
-                        C[c] = __fadd_rn(C[c], __fadd_rn(t, cr));
-                    }
+        for (int jf = 0; jf < jn; jf += DF_DJ, ++g) {
+            const int je = min(jn, jf + DF_DJ);
+            if (bulk) {
+                ok = ok && tc::mbar_wait(&bar[g & 1], (uint32_t)((g >> 1) & 1), abort_flag, 2000000000ull);
+                if (ok) {
+                    const double* ac = Ast + (g & 1) * DF_DJ * RESID_ROWS + tid;
+#pragma unroll 4
+                    for (int jj = jf; jj < je; ++jj)
+                        df32_madd<MT>(ac[(jj - jf) * RESID_ROWS], xf + jj * (MT + 1), xd + jj * (MT + 1), S, C, acc,
+                                      asum, rowabs != nullptr);
                 }
+                __syncthreads();  // every thread is done with buffer g & 1
+                if (tid == 0 && ok && !*abort_flag && g + 2 < nchunks) issue(g + 2);
+            } else if (i < n) {
+                const double* ap = Ai + (long)jb * lda;
+#pragma unroll 2
+                for (int jj = jf; jj < je; ++jj)
+                    df32_madd<MT>(__ldg(ap + (long)jj * lda), xf + jj * (MT + 1), xd + jj * (MT + 1), S, C, acc,
+                                  asum, rowabs != nullptr);
+            }
+            if ((jf + DF_DJ) % RESID_FOLD == 0 || jf + DF_DJ >= jn) {  // fold the float32 pairs
 #pragma unroll
                 for (int c = 0; c < MT; ++c) {
                     acc[c] += (double)S[c] + (double)C[c];
@@ -415,6 +476,7 @@ static __global__ void __launch_bounds__(RESID_ROWS, 2)
             }
         }
     }
+    if (bulk && !ok && tid == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
     if (i < n) {
 #pragma unroll
         for (int c = 0; c < MT; ++c)

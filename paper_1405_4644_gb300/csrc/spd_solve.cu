@@ -151,6 +151,19 @@ ResidWs resid_ws(spd_handle* h, int n, const size_t* off, int S) {
 // R = B - A X (mode 0) or R = A X (mode 1), float64; colnorms[3m]; if anorm
 // is non-null also ||A||_inf.
 // The DF32 variant of the partial-sum pass (same partial layout).
+template <int MT>
+void launch_df32(spd_handle* h, dim3 grid, const double* A, long lda, int n, const double* X, long ldx, int c0, int mc,
+                 int jchunk, int m, const ResidWs& w, float* ra) {
+    static const bool attr = [] {  // once per instantiation, thread-safe
+        cudaFuncSetAttribute(k_resid_partial_df32<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)df32_smem<MT>());
+        return true;
+    }();
+    (void)attr;
+    ++(h)->launches, k_resid_partial_df32<MT><<<grid, RESID_ROWS, df32_smem<MT>(), h->stream>>>(
+        A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra, h->dst);
+}
+
 spd_status resid_partial_df32(spd_handle* h, const ResidWs& w, int n, int m, const double* A, long lda,
                               const double* X, long ldx, bool with_rowabs) {
     cudaStream_t s = h->stream;
@@ -161,16 +174,11 @@ spd_status resid_partial_df32(spd_handle* h, const ResidWs& w, int n, int m, con
     for (int c0 = 0; c0 < m; c0 += 16) {
         int mc = std::min(16, m - c0);
         float* ra = (with_rowabs && c0 == 0) ? w.rowabs : nullptr;
-        if (mc == 1)
-            ++(h)->launches, k_resid_partial_df32<1><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
-        else if (mc == 2)
-            ++(h)->launches, k_resid_partial_df32<2><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
-        else if (mc <= 4)
-            ++(h)->launches, k_resid_partial_df32<4><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
-        else if (mc <= 8)
-            ++(h)->launches, k_resid_partial_df32<8><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
-        else
-            ++(h)->launches, k_resid_partial_df32<16><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.xsc, w.P, ra);
+        if (mc == 1) launch_df32<1>(h, grid, A, lda, n, X, ldx, c0, mc, jchunk, m, w, ra);
+        else if (mc == 2) launch_df32<2>(h, grid, A, lda, n, X, ldx, c0, mc, jchunk, m, w, ra);
+        else if (mc <= 4) launch_df32<4>(h, grid, A, lda, n, X, ldx, c0, mc, jchunk, m, w, ra);
+        else if (mc <= 8) launch_df32<8>(h, grid, A, lda, n, X, ldx, c0, mc, jchunk, m, w, ra);
+        else launch_df32<16>(h, grid, A, lda, n, X, ldx, c0, mc, jchunk, m, w, ra);
         LAUNCH_CHECK(h);
     }
     return SPD_OK;
