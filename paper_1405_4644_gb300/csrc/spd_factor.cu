@@ -23,7 +23,8 @@ struct FCtx {
     spd_factor_t* F;
     Mirror mir;
     TcGemm* tc;          // tensor-core GEMM plan (nullptr: CUDA cores)
-    float* part = nullptr;  // split-K partials of the block-column updates
+    float* part = nullptr;   // split-K partials of the early block-column updates (second stream)
+    float* part2 = nullptr;  // partials of the rank-128 updates (main stream)
 };
 
 
@@ -59,10 +60,11 @@ spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
 }
 
 template <typename T>
-spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower, int splits = 1) {
+spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower, int splits = 1,
+                cudaStream_t strm = nullptr, float* part = nullptr) {
     if (M <= 0 || N <= 0 || K <= 0) return SPD_OK;
     spd_factor_t* F = c.F;
-    cudaStream_t s = c.h->stream;
+    cudaStream_t s = strm ? strm : c.h->stream;
     // algorithmic work: lower-triangle SYRK or full GEMM; C read+written once
     // in T, each operand row read once in the operand type
     const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
@@ -70,14 +72,14 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower,
                         : c.mir.kind == 5 ? 6.0
                         : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
     ProfScope ps(c.h, (c.tc && c.mir.kind == 5) ? SPD_PHASE_TRAILING_X3 : SPD_PHASE_TRAILING, 2.0 * celems * K,
-                 2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N));
+                 2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N), s);
     if constexpr (sizeof(T) == 8) {
         dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
         ++(c.h)->launches, k_gemm_nt_simt<double, double, 4, 4, 8><<<grid, 256, 0, s>>>(F->W64, F->ldw, F->W64, F->ldw, r0, M, c0, N,
                                                                      k0, K, lower, c.h->dst);
     } else {
         if (c.tc) {
-            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst, splits, c.part);
+            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst, splits, part ? part : c.part);
             if (st != SPD_OK) return set_err(c.h, st, "tensor-core trailing update failed");
             return SPD_OK;
         }
@@ -140,30 +142,63 @@ spd_status potrf_rec(FCtx& c, int n0, int nn) {
     return potrf_rec<T>(c, n0 + n1, nn - n1);
 }
 
-// Left-looking block-column schedule (tensor-core factors): for each
-// 128-column block k, one update with everything to its left,
-//   W[k:, k] -= L[k:, 0:k] L[k, 0:k]^T      (M x 128 x 128k, split-K when
-//                                             the block column has few tiles)
-// then the leaf and the panel solve below it.  The critical path is one
-// update, one leaf and one panel per block (n/128 of each) instead of the
-// recursion's ~n/128 log2(n/128) panel solves and updates; the operands are
-// read once per block column (left-looking traffic ~n^3/(3*128) operand
-// elements in total), and C is read and written once per block.
+// Left-looking block-column schedule with a look-ahead (tensor-core
+// factors).  Block column k needs everything to its left:
+//   W[k:, k] -= L[k:, 0:k-1] L[k, 0:k-1]^T   ("early": columns done two
+//                                            steps ago, on the second stream)
+//   W[k:, k] -= L[k:, k-1] L[k, k-1]^T       ("last": rank 128, main stream)
+// then the leaf and the panel solve below it (main stream).  The early part,
+// which holds nearly all of the tensor-core work, runs while the previous
+// block's leaf and panel run; the critical path per block is one rank-128
+// update, one leaf and one panel.  The early update of block k waits for the
+// panel of block k-2; the last update of block k waits for its early update
+// (both write W[k:, k]).
 template <typename T>
 spd_status potrf_left(FCtx& c, int n) {
+    spd_handle* h = c.h;
     const int NB = ceil_div(n, SPD_LEAF);
-    for (int k = 0; k < NB; ++k) {
-        const int r0 = k * SPD_LEAF, nb = std::min(SPD_LEAF, n - r0);
-        if (k > 0) {
-            const int M = n - r0, tiles = ceil_div(M, 128);
-            (void)tiles;
-            const int splits = c.part ? -c.h->sms : 1;  // split-K chosen by the GEMM from the SM count
-            TRY(gemm<T>(c, r0, M, r0, nb, 0, r0, 0, splits));
-        }
-        TRY(leaf_potrf<T>(c, r0, nb));
-        if (r0 + nb < n) TRY(leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb));
+    cudaStream_t P = h->stream, U = h->aux;
+    // two events per block: panel done (main), early update done (second)
+    const size_t need = 2 * (size_t)NB + 1;
+    while (h->sync_ev.size() < need) {
+        cudaEvent_t e = nullptr;
+        CUDA_TRY(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->sync_ev.push_back(e);
     }
-    return SPD_OK;
+    cudaEvent_t* evPanel = h->sync_ev.data();
+    cudaEvent_t* evEarly = h->sync_ev.data() + NB;
+    cudaEvent_t evStart = h->sync_ev[2 * NB];
+    CUDA_TRY(h, cudaEventRecord(evStart, P));  // the second stream starts after the conversion
+    CUDA_TRY(h, cudaStreamWaitEvent(U, evStart, 0));
+    spd_status st = SPD_OK;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < NB && st == SPD_OK && e == cudaSuccess; ++k) {
+        const int r0 = k * SPD_LEAF, nb = std::min(SPD_LEAF, n - r0), M = n - r0;
+        if (k >= 2) e = cudaStreamWaitEvent(P, evEarly[k], 0);
+        if (e == cudaSuccess && k >= 1)  // last: rank 128 with block column k-1
+            st = gemm<T>(c, r0, M, r0, nb, r0 - SPD_LEAF, SPD_LEAF, 0, 1, P, c.part2);
+        if (e == cudaSuccess && st == SPD_OK) st = leaf_potrf<T>(c, r0, nb);
+        if (e == cudaSuccess && st == SPD_OK && r0 + nb < n) st = leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb);
+        if (e != cudaSuccess || st != SPD_OK) break;
+        e = cudaEventRecord(evPanel[k], P);
+        // early update of block k+2 on the second stream: columns 0..k
+        if (e == cudaSuccess && k + 2 < NB) {
+            e = cudaStreamWaitEvent(U, evPanel[k], 0);
+            const int r2 = (k + 2) * SPD_LEAF, nb2 = std::min(SPD_LEAF, n - r2);
+            if (e == cudaSuccess)
+                st = gemm<T>(c, r2, n - r2, r2, nb2, 0, (k + 1) * SPD_LEAF, 0, c.part ? -h->sms : 1, U, c.part);
+            if (e == cudaSuccess) e = cudaEventRecord(evEarly[k + 2], U);
+        }
+    }
+    // join, on every path: the main stream continues (and frees the partial
+    // buffers) only after everything queued on the second stream
+    cudaEvent_t evEnd = h->sync_ev[2 * NB];
+    cudaError_t e2 = cudaEventRecord(evEnd, U);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(P, evEnd, 0);
+    if (e2 != cudaSuccess) cudaStreamSynchronize(U);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess && st == SPD_OK) st = set_err(h, SPD_ERR_CUDA, "look-ahead schedule: %s", cudaGetErrorString(e));
+    return st;
 }
 
 void free_factor(spd_factor_t* F) {
@@ -258,8 +293,14 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                 cudaGetLastError();
                 c.part = nullptr;  // the updates then run unsplit
             }
+            if (c.part && cudaMallocAsync(&c.part2, sizeof(float) * 128 * 128 * 2 * std::max(h->sms, 1), s) !=
+                              cudaSuccess) {
+                cudaGetLastError();
+                c.part2 = nullptr;
+            }
             st = potrf_left<float>(c, n);
             if (c.part) cudaFreeAsync(c.part, s);
+            if (c.part2) cudaFreeAsync(c.part2, s);
         } else {
             st = potrf_rec<float>(c, 0, n);
         }
