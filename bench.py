@@ -579,15 +579,23 @@ def main():
                   "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
                   "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
     roof_phases, roof_note = phases, "phases of the timed region"
-    if lanes:
-        # Under concurrency a launch's event time includes sharing the SMs with
-        # the other lanes, so the kernel rooflines come from one more pass of
-        # the same workload on a single lane (CUDA events on its stream).
+    if True:
+        # A launch's event time under concurrency (the lanes, and the factor's
+        # look-ahead stream) includes sharing the SMs, so the kernel rooflines
+        # come from one more step of the same workload with every kernel
+        # running alone: one lane, the factor's serial schedule (CUDA events on
+        # the launching stream).
         spd.spd_profile_enable(h, True)
-        run_step(spd, h, systems, precs, X, opts)
+        for (k, A, B), p in zip(systems, precs):
+            st, F, _ = spd.spd_factor(h, A, p, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SERIAL)
+            if st != spd.SPD_OK:
+                raise RuntimeError("roofline pass: " + spd.spd_last_error_string(h))
+            st, _ = spd.spd_solve_ir(h, F, A, B, X, opts)
+            spd.spd_factor_destroy(F)
         roof_phases = {p: spd.spd_profile_read(h, p) for p in spd.PHASES}
         spd.spd_profile_enable(h, False)
-        roof_note = "phases of one extra single-lane step of the same workload (timed region ran concurrent lanes)"
+        roof_note = ("phases of one extra step of the same workload with every kernel alone (one lane, serial "
+                     "factor schedule); the timed region ran concurrent lanes and the look-ahead")
     roof = roofline(roof_phases, per_kappa)
     roof["measured_on"] = roof_note
     energy = None

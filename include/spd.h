@@ -113,6 +113,10 @@ typedef enum spd_resid {
                                     (large updates, many small panels) instead
                                     of the default left-looking 128-column
                                     schedule                                */
+#define SPD_FACTOR_SERIAL 8u     /* left-looking schedule without its
+                                    look-ahead: every kernel on the handle's
+                                    stream in order (kernels then run alone,
+                                    e.g. to time them)                      */
 
 typedef struct spd_opts {
     double tol;      /* stopping threshold (default 1e-14)                    */

@@ -42,6 +42,7 @@ BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
 SPD_FACTOR_RECURSIVE = 4
+SPD_FACTOR_SERIAL = 8
 
 # every symbol include/spd.h declares
 EXPORTED = [

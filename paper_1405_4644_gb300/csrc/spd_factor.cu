@@ -154,10 +154,11 @@ spd_status potrf_rec(FCtx& c, int n0, int nn) {
 // panel of block k-2; the last update of block k waits for its early update
 // (both write W[k:, k]).
 template <typename T>
-spd_status potrf_left(FCtx& c, int n) {
+spd_status potrf_left(FCtx& c, int n, bool lookahead) {
     spd_handle* h = c.h;
     const int NB = ceil_div(n, SPD_LEAF);
-    cudaStream_t P = h->stream, U = h->aux;
+    // without the look-ahead both parts run in order on the main stream
+    cudaStream_t P = h->stream, U = lookahead ? h->aux : h->stream;
     // two events per block: panel done (main), early update done (second)
     const size_t need = 2 * (size_t)NB + 1;
     while (h->sync_ev.size() < need) {
@@ -298,7 +299,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                 cudaGetLastError();
                 c.part2 = nullptr;
             }
-            st = potrf_left<float>(c, n);
+            st = potrf_left<float>(c, n, !(flags & SPD_FACTOR_SERIAL));
             if (c.part) cudaFreeAsync(c.part, s);
             if (c.part2) cudaFreeAsync(c.part2, s);
         } else {

@@ -55,13 +55,15 @@ def test_factor_matches_oracle(h, n, prec):
 @pytest.mark.parametrize("n", [129, 700, 2100])
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16"])
 def test_left_looking_and_recursive_schedules_agree(h, n, prec):
-    """The default block-column (left-looking) schedule and the recursive
-    one compute the same factor up to rounding: both meet the backward bound
-    of the operand type, and they differ by no more than it allows."""
+    """The default block-column (left-looking) schedule, its serial form and
+    the recursive one compute the same factor up to rounding: all meet the
+    backward bound of the operand type, the recursive one differs by no more
+    than it allows, and the serial one is identical."""
     A = W.gram_shifted(n, seed=n + 1, shift=0.5)
     d_ref, As = scaled(A)
     Ls = []
-    for flags in [spd.SPD_SCALE_DIAG, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_RECURSIVE]:
+    for flags in [spd.SPD_SCALE_DIAG, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_RECURSIVE,
+                  spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SERIAL]:
         st, F, rep = spd.spd_factor(h, dev_sym(A), prec, flags)
         check(h, st)
         try:
@@ -75,6 +77,9 @@ def test_left_looking_and_recursive_schedules_agree(h, n, prec):
     kappa = np.linalg.cond(As)
     diff = np.max(np.abs(Ls[0] - Ls[1]))
     assert diff <= 8 * kappa * max(n, 8) ** 0.5 * max(UNIT_ROUNDOFF[prec], 2.0 ** -24), diff
+    # the look-ahead only reorders independent work: the serial schedule
+    # gives the same factor bit for bit
+    assert np.array_equal(Ls[0], Ls[2])
 
 
 @pytest.mark.parametrize("n", [3, 129, 700])
