@@ -301,6 +301,9 @@ def roofline(phases, per_kappa):
         r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / 2 * DF32_OPS_PER_MADD / sec / 1e12,
              "peak": FP32_OPS_PEAK_T,
              "peak_source": "float32 instructions/s: 152 SMs x 128 lanes x 2.07 GHz (one op per instruction)"}
+    elif dom == "resid_tc":
+        r = {"bound": "hbm", "unit": "GB/s", "achieved": ph["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
+             "peak_source": f"{src} copy bandwidth (the digit planes stream from HBM)"}
     elif dom in ("trailing", "leaf", "panel"):
         r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
              "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
@@ -494,8 +497,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--lanes", type=int, default=3,
                     help="systems solved concurrently (one handle, stream and host thread each)")
-    ap.add_argument("--resid", default="df32", choices=["fp64", "df32"],
-                    help="refinement residual: float64, or float32 pairs until berr < 2^-36 then float64")
+    ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc"],
+                    help="refinement residual: float64; float32 pairs until berr < 2^-36 then float64; "
+                         "or exact bf16 digit products on the tensor cores")
     ap.add_argument("--leg", default="main", choices=["main", "batched", "learned"])
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n-learned", type=int, default=4096)
@@ -684,7 +688,9 @@ def main():
                           "lanes": args.lanes,
                           "residual": {"fp64": "float64 throughout",
                                        "df32": "float32 pairs while berr > 2^-36, float64 to finish "
-                                               "(convergence only accepted on a float64 residual)"}[args.resid]},
+                                               "(convergence only accepted on a float64 residual)",
+                                       "tc": "exact products of bf16 digits on the tensor cores (ten 7-bit "
+                                             "digits per entry, 55 digit products), every residual"}[args.resid]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "energy": energy, "fp64_baseline": fp64, "per_kappa": per_kappa,
                "phases": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in phases.items()}}

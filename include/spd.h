@@ -90,7 +90,7 @@ typedef enum spd_precond {
 /* Arithmetic of the float64-accurate residual r = b - A x. */
 typedef enum spd_resid {
     SPD_RESID_FP64 = 0, /* float64 fused multiply-adds                        */
-    SPD_RESID_DF32 = 1  /* refinement loops: residuals of spd_residual_df32 (float32
+    SPD_RESID_DF32 = 1, /* refinement loops: residuals of spd_residual_df32 (float32
                            units, about 48-bit accurate) while the largest
                            backward error is above 2^-36 and, below that,
                            while each sweep still shrinks it fourfold;
@@ -100,6 +100,12 @@ typedef enum spd_resid {
                            rule and its guarantee are those of SPD_RESID_FP64.
                            The float64 products of the CG fallback use
                            spd_residual_df32's arithmetic throughout.        */
+    SPD_RESID_TC = 2    /* every residual (and every float64 product of the
+                           CG fallback) from spd_residual_tc: exact products
+                           of bf16 digits on the tensor cores; columns may be
+                           accepted on it.  The digit planes of A (20 bytes
+                           per entry of A) are formed once per solve and stay
+                           in the handle's workspace.                        */
 } spd_resid;
 
 /* Flags of spd_factor. */
@@ -243,6 +249,26 @@ spd_status spd_residual(spd_handle *h, int n, int m, const double *A, int lda,
 spd_status spd_residual_df32(spd_handle *h, int n, int m, const double *A, int lda,
                              const double *B, int ldb, const double *X, int ldx,
                              double *R, int ldr, double *colnorms);
+
+/* The residual of spd_residual from exact integer products on the bf16
+ * tensor cores (the error-free splitting of Ozaki, Ogita, Oishi and Rump,
+ * 2012; Section 3.1 asks only for a residual more accurate than the
+ * factor).  Row i of A is cut into ten signed 7-bit digits below 2^e_i
+ * (e_i = ilogb(max_j |a_ij|) + 2), column c of X likewise (f_c); entries
+ * lose only their bits below 2^{e_i - 70} (2^{f_c - 70}).  The 55 digit
+ * products of total weight <= 11 are summed exactly (float32 on the tensor
+ * cores over 64-wide chunks of j, each sum an integer of magnitude < 2^22,
+ * then integers), combined with their power-of-two scales in double-double,
+ * and b - (A x) is rounded once.  The dropped digit products and the
+ * truncation add less than 2^-64.5 max_j|a_ij| max|x_c| per term, so
+ *   |computed - exact| <= 2^-53 |r_i| + n 2^-64 max_j |a_ij| max_j |x_jc|
+ * (at n = 16384, 2^-50 ||A||_inf ||x||_inf at worst).  Rows of A with a
+ * non-finite entry and columns of X with one give NaN.  Workspace: 20 bytes
+ * per entry of A for the digit planes, plus O(n m).  Same arguments,
+ * layout, ownership and errors as spd_residual. */
+spd_status spd_residual_tc(spd_handle *h, int n, int m, const double *A, int lda,
+                           const double *B, int ldb, const double *X, int ldx,
+                           double *R, int ldr, double *colnorms);
 
 /* The same float64 residual and norms as spd_residual, for callers that may
  * not allocate device memory at all (host callbacks, allocator hooks,
@@ -396,7 +422,8 @@ typedef enum spd_phase {
     SPD_PHASE_TRAILING_X3 = 9, /* A3 of an FP32 factor: three bf16 slices
                                   on the tensor cores (flops counted once) */
     SPD_PHASE_RESID_DF32 = 10, /* A5/C3 on the float32 units (float32 pairs) */
-    SPD_PHASE_COUNT = 11
+    SPD_PHASE_RESID_TC = 11,   /* A5/C3 on the tensor cores (bf16 digits)     */
+    SPD_PHASE_COUNT = 12
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

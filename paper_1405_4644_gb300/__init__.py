@@ -24,7 +24,7 @@ __all__ = [
     "SPD_ERR_OOM", "SPD_ERR_UNSUPPORTED", "PREC", "SPD_SCALE_DIAG", "SpdOpts", "SpdReport", "SpdError",
     "lib", "colmajor", "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor",
     "spd_factor_destroy", "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve",
-    "spd_residual", "spd_residual_df32", "RESID", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "BATCH",
+    "spd_residual", "spd_residual_df32", "spd_residual_tc", "RESID", "spd_cg", "spd_profile_enable", "spd_profile_read", "PHASES", "EXPORTED", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "BATCH",
     "spd_batch_create", "spd_batch_solve", "spd_batch_info", "spd_batch_destroy",
     "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params", "spd_learned_features", "spd_mlp_loss_grad",
     "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply", "spd_lowrank_destroy", "spd_solve_learned",
@@ -37,7 +37,7 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto":
 PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
 PC = {"none": 0, "jacobi": 1, "factor": 2, "lowrank": 3}
-RESID = {"fp64": 0, "df32": 1}
+RESID = {"fp64": 0, "df32": 1, "tc": 2}
 BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
@@ -47,8 +47,8 @@ SPD_FACTOR_SERIAL = 8
 # every symbol include/spd.h declares
 EXPORTED = [
     "spd_create", "spd_destroy", "spd_last_error_string", "spd_opts_default", "spd_factor", "spd_factor_destroy",
-    "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_residual_df32", "spd_cg", "spd_profile_enable", "spd_profile_read",
-    "spd_launch_count", "spd_gemm_update", "spd_residual_static", "spd_batch_create", "spd_batch_solve",
+    "spd_factor_info", "spd_factor_copy", "spd_solve_ir", "spd_solve_ir_host", "spd_factor_solve", "spd_residual", "spd_residual_df32", "spd_residual_tc", "spd_cg", "spd_profile_enable",
+    "spd_profile_read", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "spd_batch_create", "spd_batch_solve",
     "spd_batch_info", "spd_batch_destroy", "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params",
     "spd_learned_features", "spd_mlp_loss_grad", "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply",
     "spd_lowrank_destroy", "spd_solve_learned",
@@ -107,6 +107,7 @@ def lib():
         "spd_factor_solve": (I, [P, P, I, I, P, I, P, I]),
         "spd_residual": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
         "spd_residual_df32": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
+        "spd_residual_tc": (I, [P, I, I, P, I, P, I, P, I, P, I, P]),
         "spd_cg": (I, [P, I, I, P, I, I, I, P, P, I, P, I, O, R]),
         "spd_profile_enable": (I, [P, I]),
         "spd_launch_count": (I, [P, C.POINTER(C.c_longlong)]),
@@ -303,6 +304,16 @@ def spd_residual_df32(h, A, B, X, R, colnorms=None):
     return lib().spd_residual_df32(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
 
 
+def spd_residual_tc(h, A, B, X, R, colnorms=None):
+    """R = B - A X from exact bf16 digit products on the tensor cores."""
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = colmajor(B)
+    pX, ldx, _, _ = colmajor(X)
+    pR, ldr, _, _ = colmajor(R)
+    pc = colnorms.data_ptr() if colnorms is not None else None
+    return lib().spd_residual_tc(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
+
+
 def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
     pA, lda, n = _sym(A)
     pB, ldb, _, m = colmajor(B)
@@ -315,7 +326,7 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
 
 
 PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch", "trailing_x3",
-          "resid_df32"]
+          "resid_df32", "resid_tc"]
 
 
 def spd_profile_enable(h, on=True):

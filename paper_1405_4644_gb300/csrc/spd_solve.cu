@@ -9,6 +9,7 @@
 #include "k_trsv32.cuh"
 #include "k_resid.cuh"
 #include "k_cg.cuh"
+#include "resid_tc.h"
 
 // ---------------------------------------------------------------------------
 // handle
@@ -101,7 +102,33 @@ struct ResidWs {
     int S;          // column splits of the float64 kernel
     double* xsc;    // 2 m column scales of the DF32 kernel
     int Sdf;        // column splits of the DF32 kernel
+    const TcResidWs* tc = nullptr;  // prepared digit planes (SPD_RESID_TC)
 };
+
+// The tensor-core residual's workspace, planned beside a solver's and
+// prepared (digit planes of A) once per call when opts.resid asks for it.
+struct TcSetup {
+    bool on = false;
+    size_t off[6] = {0, 0, 0, 0, 0, 0};
+    TcResidWs ws;
+};
+
+void tc_plan_if(WsPlan& p, spd_handle* h, int n, int m, int resid, TcSetup& t) {
+    if (resid != SPD_RESID_TC) return;
+    t.on = true;
+    tc_resid_plan(p, h, n, m, t.off);
+}
+
+spd_status tc_bind_prepare(spd_handle* h, TcSetup& t, int n, int m, const double* A, long lda, ResidWs& rw) {
+    if (!t.on) return SPD_OK;
+    spd_status st = tc_resid_bind(h, &t.ws, n, m, t.off);
+    if (st != SPD_OK) return st;
+    ProfScope ps(h, SPD_PHASE_RESID_TC, 0.0, 36.0 * n * (double)n);  // A twice, 20 bytes of digits per entry
+    st = tc_resid_prepare(h, &t.ws, A, lda);
+    if (st != SPD_OK) return st;
+    rw.tc = &t.ws;
+    return SPD_OK;
+}
 
 int resid_splits(spd_handle* h, int n) {
     int rowblk = ceil_div(n, RESID_ROWS);
@@ -195,9 +222,11 @@ constexpr double DF32_SWITCH = 1.4551915228366852e-11;  // 2^-36
 
 struct ResidPolicy {
     bool df32;           // still on float32-pair residuals
+    int last;            // the float64-accurate kind: SPD_RESID_FP64 or SPD_RESID_TC
     double prev = -1.0;  // largest backward error of the previous residual
-    explicit ResidPolicy(const spd_opts& o) : df32(o.resid == SPD_RESID_DF32) {}
-    int first() const { return df32 ? SPD_RESID_DF32 : SPD_RESID_FP64; }
+    explicit ResidPolicy(const spd_opts& o)
+        : df32(o.resid == SPD_RESID_DF32), last(o.resid == SPD_RESID_TC ? SPD_RESID_TC : SPD_RESID_FP64) {}
+    int first() const { return df32 ? SPD_RESID_DF32 : last; }
     // kind of the next residual after one with summary sm; *restart = 1 when
     // the arithmetic changes
     int next(const IrSummary& sm, int* restart) {
@@ -212,7 +241,7 @@ struct ResidPolicy {
             }
         }
         prev = sm.max_berr;
-        return df32 ? SPD_RESID_DF32 : SPD_RESID_FP64;
+        return df32 ? SPD_RESID_DF32 : last;
     }
 };
 
@@ -220,6 +249,23 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
                      long ldb, const double* X, long ldx, double* R, long ldr, double* colnorms, double* anorm,
                      int mode, int kind = SPD_RESID_FP64) {
     cudaStream_t s = h->stream;
+    if (kind == SPD_RESID_TC) {
+        if (!w.tc || w.tc->n != n || w.tc->m != m) return set_err(h, SPD_ERR_ARG, "tensor-core residual not prepared");
+        // algorithmic work: 55 digit products of 2 n^2 m; bytes: the ten digit planes
+        ProfScope ps(h, SPD_PHASE_RESID_TC, 110.0 * n * (double)n * m, 20.0 * n * (double)n + 24.0 * n * (double)m);
+        spd_status st = tc_resid_run(h, w.tc, B, ldb, X, ldx, R, ldr, w.NP, mode);
+        if (st != SPD_OK) return st;
+        const int G = ceil_div(n, 256);
+        if (colnorms) {
+            ++(h)->launches, k_colnorms<<<m, 256, 0, s>>>(w.NP, G, m, colnorms);
+            LAUNCH_CHECK(h);
+        }
+        if (anorm) {
+            ++(h)->launches, k_anorm<<<1, 1024, 0, s>>>(w.tc->rowabs, w.tc->RS, n, anorm);
+            LAUNCH_CHECK(h);
+        }
+        return SPD_OK;
+    }
     ProfScope ps(h, kind == SPD_RESID_DF32 ? SPD_PHASE_RESID_DF32 : SPD_PHASE_RESID, 2.0 * n * (double)n * m,
                  8.0 * n * (double)n + 24.0 * n * (double)m);
     const int S = kind == SPD_RESID_DF32 ? w.Sdf : w.S;
@@ -469,9 +515,14 @@ spd_status residual_entry(spd_handle* h, int kind, int n, int m, const double* A
     WsPlan p;
     size_t off[4];
     int S = (int)resid_plan(p, h, n, m, off);
+    TcSetup tcs;
+    tc_plan_if(p, h, n, m, kind, tcs);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
-    st = resid_run(h, resid_ws(h, n, off, S), n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms, nullptr, 0, kind);
+    ResidWs rw = resid_ws(h, n, off, S);
+    st = tc_bind_prepare(h, tcs, n, m, A, lda, rw);
+    if (st != SPD_OK) return st;
+    st = resid_run(h, rw, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms, nullptr, 0, kind);
     if (st != SPD_OK) return st;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return SPD_OK;
@@ -486,6 +537,11 @@ extern "C" spd_status spd_residual(spd_handle* h, int n, int m, const double* A,
 extern "C" spd_status spd_residual_df32(spd_handle* h, int n, int m, const double* A, int lda, const double* B,
                                         int ldb, const double* X, int ldx, double* R, int ldr, double* colnorms) {
     return residual_entry(h, SPD_RESID_DF32, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms);
+}
+
+extern "C" spd_status spd_residual_tc(spd_handle* h, int n, int m, const double* A, int lda, const double* B,
+                                      int ldb, const double* X, int ldx, double* R, int ldr, double* colnorms) {
+    return residual_entry(h, SPD_RESID_TC, n, m, A, lda, B, ldb, X, ldx, R, ldr, colnorms);
 }
 
 extern "C" spd_status spd_factor_solve(spd_handle* h, const spd_factor_t* F, int n, int m, const double* R, int ldr,
@@ -638,7 +694,7 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0, 0,
-                                                      rk == SPD_RESID_FP64);
+                                                      rk != SPD_RESID_DF32);
         LAUNCH_CHECK(h);
     }
     CUDA_TRY(h, cudaMemsetAsync(w.cg, 0, sizeof(CgCol) * m, s));
@@ -708,7 +764,7 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1, 0,
-                                                      rk == SPD_RESID_FP64, restart);
+                                                      rk != SPD_RESID_DF32, restart);
         LAUNCH_CHECK(h);
         ++outer;
     }
@@ -737,7 +793,7 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     if (opts_in) o = *opts_in;
     if (rep) memset(rep, 0, sizeof(*rep));
     if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_DF32)
+        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_TC)
         return set_err(h, SPD_ERR_ARG, "spd_solve_ir: bad arguments");
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
@@ -745,10 +801,14 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     size_t o_[22];
     int S, G2;
     cg_plan(p, h, n, m, o_, &S, &G2);
+    TcSetup tcs;
+    tc_plan_if(p, h, n, m, o.resid, tcs);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
     CgWs w = cg_bind(h, n, o_, S, G2);
     CUDA_TRY(h, cudaEventRecord(h->e0, s));
+    st = tc_bind_prepare(h, tcs, n, m, A, lda, w.rw);
+    if (st != SPD_OK) return st;
 
     ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, std::max(0, o.polish));
     ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
@@ -760,7 +820,7 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, rk);  // line 3
     if (st != SPD_OK) return st;
     ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0,
-                                                  std::max(0, o.polish), rk == SPD_RESID_FP64);
+                                                  std::max(0, o.polish), rk != SPD_RESID_DF32);
     LAUNCH_CHECK(h);
 
     int sweeps = 0, low = 1, high = 1, fell = 0;
@@ -799,7 +859,7 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
         st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, rk);  // line 7
         if (st != SPD_OK) return st;
         ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1,
-                                                      std::max(0, o.polish), rk == SPD_RESID_FP64, restart);
+                                                      std::max(0, o.polish), rk != SPD_RESID_DF32, restart);
         LAUNCH_CHECK(h);
         ++sweeps;
         ++low;
@@ -836,7 +896,7 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (rep) memset(rep, 0, sizeof(*rep));
     if (bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || o.maxit_inner < 1 || !(o.tol >= 0.0) ||
         o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_LOWRANK || o.resid < SPD_RESID_FP64 ||
-        o.resid > SPD_RESID_DF32 ||
+        o.resid > SPD_RESID_TC ||
         ((pc == SPD_PC_FACTOR || pc == SPD_PC_LOWRANK) && !pc_data))
         return set_err(h, SPD_ERR_ARG, "spd_cg: bad arguments");
     if (matvec_prec != SPD_PREC_FP64 && matvec_prec != SPD_PREC_FP32 && matvec_prec != SPD_PREC_BF16)
@@ -871,10 +931,14 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
         o_at = p.add<__nv_bfloat16>((size_t)n * ldt);
     }
     if (pc == SPD_PC_JACOBI) o_dinv = p.add<double>(n);
+    TcSetup tcs;
+    tc_plan_if(p, h, n, m, o.resid, tcs);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
     CgWs w = cg_bind(h, n, o_, S, G2);
     CUDA_TRY(h, cudaEventRecord(h->e0, s));
+    st = tc_bind_prepare(h, tcs, n, m, A, lda, w.rw);
+    if (st != SPD_OK) return st;
     const int gbig = grid_for((long)n * n, 256, 16 * h->sms);
     if (cs.matvec == MV_BAND) {
         float* Ab = ws_at<float>(h, o_at);

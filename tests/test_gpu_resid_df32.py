@@ -175,7 +175,7 @@ def test_resid_option_out_of_range_is_rejected(h):
     st, F, _ = spd.spd_factor(h, A, "fp32")
     check(h, st)
     try:
-        st, _ = spd.spd_solve_ir(h, F, A, dev_cols(np.ones((n, 1))), dev_zeros(n, 1), {"resid": 2})
+        st, _ = spd.spd_solve_ir(h, F, A, dev_cols(np.ones((n, 1))), dev_zeros(n, 1), {"resid": 3})
         assert st == spd.SPD_ERR_ARG
     finally:
         spd.spd_factor_destroy(F)
