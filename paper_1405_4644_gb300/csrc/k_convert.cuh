@@ -26,16 +26,51 @@ static __global__ void k_diag_scale(const double* __restrict__ A, long lda, int 
     d[i] = scale ? 1.0 / sqrt(a) : 1.0;
 }
 
+// |x| = m 2^e for a finite, nonzero float64 x (magnitude bits b): m in [1, 2]
+// is the mantissa rounded to 24 bits (half up), formed with integer
+// operations only (subnormal x normalised first)
+__device__ __forceinline__ float f64_mant24(unsigned long long b, int& e) {
+    int ef = (int)(b >> 52);
+    unsigned long long M = b & 0xFFFFFFFFFFFFFull;
+    if (ef == 0) {  // subnormal: shift the leading one to bit 52
+        const int sh = __clzll((long long)M) - 11;
+        M = (M << sh) & 0xFFFFFFFFFFFFFull;
+        ef = 1 - sh;
+    }
+    e = ef - 1023;
+    const uint32_t m = (uint32_t)((M + (1ull << 28)) >> 29);  // 2^23 carries to 2.0
+    return __uint_as_float(0x3F800000u + m);
+}
+
+// d_i a d_j rounded to float32 without float64 arithmetic, which runs at a
+// small fraction of the float32 rate on this part: the three 24-bit
+// mantissas are multiplied in float32 and the exponents added (scalbnf).
+// Five roundings of 2^-24 at most: |error| <= 2^-21.6 |d_i a d_j| for normal
+// results.
+__device__ __forceinline__ float scaled_f32(double a, double di, double dj) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    if (mag == 0ull) return (b >> 63) ? -0.f : 0.f;
+    int ea, ei, ej;
+    const float ma = f64_mant24(mag, ea);
+    const float mi = f64_mant24((unsigned long long)__double_as_longlong(di), ei);
+    const float mj = f64_mant24((unsigned long long)__double_as_longlong(dj), ej);
+    const float v = scalbnf(ma * mi * mj, ea + ei + ej);
+    return (b >> 63) ? -v : v;
+}
+
 // W (row-major, ldw) lower triangle <- d_i A_ij d_j for i >= j, rounded to
 // T.  A is column-major (lda); element (i, j) lives at A[i + j*lda].  A
 // 32x32 tile is read along i (coalesced in A) and written along j
 // (coalesced in W) through shared memory.  Tiles strictly above the
-// diagonal are skipped.  Non-finite entries raise SPD_DEV_NONFINITE.
+// diagonal are skipped.  Non-finite entries raise SPD_DEV_NONFINITE.  For
+// float32 W the scaling avoids float64 arithmetic (scaled_f32; d is positive
+// and normal).
 template <typename T>
 static __global__ void k_scale_convert(const double* __restrict__ A, long lda, int n,
                                 const double* __restrict__ d, T* __restrict__ W, long ldw,
                                 DevStatus* st) {
-    __shared__ double tile[32][33];
+    __shared__ T tile[32][33];
     int bi = blockIdx.y, bj = blockIdx.x;  // tile row (i) and column (j)
     if (bj > bi) return;
     int i0 = bi * 32, j0 = bj * 32;
@@ -44,11 +79,13 @@ static __global__ void k_scale_convert(const double* __restrict__ A, long lda, i
     // read: columns j0+jj, rows i0+tx (contiguous in A)
     for (int jj = ty; jj < 32; jj += 8) {
         int i = i0 + tx, j = j0 + jj;
-        double v = 0.0;
+        T v = T(0);
         if (i < n && j < n && j <= i) {
-            v = A[(long)j * lda + i];
-            if (!isfinite(v)) bad = true;
-            v = d[i] * v * d[j];
+            const double a = A[(long)j * lda + i];
+            if (((unsigned long long)__double_as_longlong(a) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
+                bad = true;
+            if constexpr (sizeof(T) == 8) v = d[i] * a * d[j];
+            else v = scaled_f32(a, d[i], d[j]);
         }
         tile[tx][jj] = v;  // tile[i_local][j_local]
     }
@@ -57,7 +94,7 @@ static __global__ void k_scale_convert(const double* __restrict__ A, long lda, i
     // write: rows i0+ii, columns j0+tx (contiguous in W)
     for (int ii = ty; ii < 32; ii += 8) {
         int i = i0 + ii, j = j0 + tx;
-        if (i < n && j < n && j <= i) W[(long)i * ldw + j] = (T)tile[ii][tx];
+        if (i < n && j < n && j <= i) W[(long)i * ldw + j] = tile[ii][tx];
     }
 }
 

@@ -2,7 +2,8 @@
 // triangular sweeps y = L^{-1} y (forward) and z = L^{-T} z (backward) over
 // 128-row blocks, in one persistent cooperative kernel per sweep.
 //
-// Block J is owned by CTA J mod G, which takes its blocks in sweep order.
+// Block J (in sweep order t) is owned by the CTA of rank t mod G among the G
+// CTAs ordered by SM id, which takes its blocks in sweep order.
 // Forward, with t_J = y_J - sum_{K < J-1} L_JK y_K and u_J = L_JJ^{-1} t_J,
 //
 //   y_J = u_J - M_J y_{J-1},          M_J = L_JJ^{-1} L_{J,J-1},
@@ -41,7 +42,11 @@ struct TrsvArgs {
     int* ready;          // NB flags
     int epoch;           // value that marks a block finished in this sweep
     DevStatus* st;
+    unsigned long long* slots;  // one per CTA: (epoch << 32) | SM id of the CTA in this sweep
 };
+
+// largest grid of the sweeps (CTAs), the size of the slot table
+#define TV_SLOTS 1024
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
@@ -50,6 +55,14 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 }
 __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 __device__ __forceinline__ uint64_t tv_globaltimer() {
     uint64_t t;
@@ -247,15 +260,50 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
     float* Lv = reinterpret_cast<float*>(smem_raw);  // [128][TV_LD] (L_JJ^{-1})^T
     float* Yk = Lv + 128 * TV_LD;                    // [128][tv_ys] right-hand sides of a finished block
     float* T = Yk + 128 * tv_ys<MC>();               // [128][MC] t_J, then u_J
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_rank;
+    __shared__ unsigned s_sm;
     const int tid = threadIdx.x;
     const int tq = tid >> 3, ts = tid & 7;            // tile products: row quad, reduction slice
     const int i = tid >> 1, half = tid & 1;           // diagonal step: row, column half
     const int cbase = (MC >= 2) ? half * CPT : 0;
-    if (tid == 0) s_abort = 0;
+    if (tid == 0) {
+        s_abort = 0;
+        s_rank = 0;
+        unsigned sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        s_sm = sm;
+        st_release64(a.slots + blockIdx.x, ((unsigned long long)(unsigned)a.epoch << 32) | sm);
+    }
     __syncthreads();
+    // This CTA's rank among all CTAs ordered by SM id: blocks go to ranks in
+    // sweep order, so consecutive blocks mostly run on neighbouring SMs (the
+    // same TPC or GPC), where handing a finished block over is several times
+    // faster than across the chip.  Every CTA is resident (cooperative
+    // launch); the wait for the others' slots is bounded.
+    {
+        int before = 0;
+        for (int b = tid; b < (int)gridDim.x; b += blockDim.x) {
+            unsigned long long v = ld_acquire64(a.slots + b);
+            if ((unsigned)(v >> 32) != (unsigned)a.epoch) {
+                const uint64_t t0 = tv_globaltimer();
+                while ((unsigned)((v = ld_acquire64(a.slots + b)) >> 32) != (unsigned)a.epoch) {
+                    if (tv_globaltimer() - t0 > 1000000000ull) {
+                        s_abort = 1;
+                        atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
+                        break;
+                    }
+                }
+            }
+            const unsigned smb = (unsigned)v;
+            before += (smb < s_sm || (smb == s_sm && b < (int)blockIdx.x)) ? 1 : 0;
+        }
+        if (before) atomicAdd(&s_rank, before);
+    }
+    __syncthreads();
+    if (s_abort) return;
+    const int rank = s_rank;
 
-    for (int t = blockIdx.x; t < a.NB; t += gridDim.x) {
+    for (int t = rank; t < a.NB; t += gridDim.x) {
         const int J = FWD ? t : a.NB - 1 - t;
         const int nfar = FWD ? max(J - 1, 0) : max(a.NB - 2 - J, 0);
         const bool near = FWD ? J >= 1 : J <= a.NB - 2;

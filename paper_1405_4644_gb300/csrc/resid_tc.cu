@@ -47,10 +47,13 @@ constexpr uint32_t TCR_MAGIC_BITS = 0x4B400000u;
 
 // exponent of a row or column from the bits of its largest magnitude: 2^e
 // bounds every entry by a factor 4 (e = ilogb + 2); 0 for an all-zero row
+// (integer operations only: float64 arithmetic is slow on this part)
 __device__ __forceinline__ int tcr_exp(unsigned long long mx) {
     if (mx >= 0x7FF0000000000000ull) return TCR_NONFINITE;
     if (mx == 0ull) return 0;
-    return ilogb(__longlong_as_double((long long)mx)) + 2;
+    const int ef = (int)(mx >> 52);
+    const int lg = ef > 0 ? ef - 1023 : (63 - __clzll((long long)mx)) - 1074;  // ilogb, subnormals included
+    return lg + 2;
 }
 
 // the ten signed digits of a / 2^e: a = 2^e sum_{p<10} d[p] 2^{-7(p+1)} up
@@ -66,14 +69,23 @@ __device__ __forceinline__ void tcr_digits(double a, int e, int (&d)[TCR_S], boo
     unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
     if (ef) M |= 1ull << 52;
     else ef = 1;
-    const int sh = ef - 1005 - e;  // F = M 2^sh
-    uint32_t c[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int o = 21 * k - sh;  // F bit 21 k is M bit o
-        const unsigned long long w = o >= 0 ? (o < 64 ? M >> o : 0ull) : M << (-o);
-        c[k] = (uint32_t)w & 0x1FFFFFu;
+    const int sh = ef - 1005 - e;  // F = M 2^sh (sh <= 16 for normal a, up to 68 in subnormal rows)
+    // F as its low 64 bits and the (at most five) bits above them
+    unsigned long long lo = 0ull;
+    uint32_t hi = 0;
+    if (sh >= 64) {
+        hi = (uint32_t)(M << (sh - 64));
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = (uint32_t)(M >> (64 - sh));
+    } else if (sh > -64) {
+        lo = M >> (-sh);
     }
+    uint32_t c[4];
+    c[0] = (uint32_t)lo & 0x1FFFFFu;
+    c[1] = (uint32_t)(lo >> 21) & 0x1FFFFFu;
+    c[2] = (uint32_t)(lo >> 42) & 0x1FFFFFu;
+    c[3] = (uint32_t)(lo >> 63) | (hi << 1);
     constexpr uint32_t K3 = 64u | (64u << 7) | (64u << 14);
     uint32_t carry = 0;
 #pragma unroll
@@ -86,6 +98,18 @@ __device__ __forceinline__ void tcr_digits(double a, int e, int (&d)[TCR_S], boo
     }
     d[0] = (int)(c[3] + carry);
     neg = (bits >> 63) != 0;
+}
+
+// |a| as a float from the bits of a (magnitude bits b), truncating the
+// mantissa: no float64 arithmetic or conversion, which run at a small
+// fraction of the float32 rate on this part; below 2^-126 counts as 0 and
+// above float range as infinity (a row sum of |a| that large overflows anyway)
+__device__ __forceinline__ float tcr_absf(unsigned long long b) {
+    const uint32_t hi = (uint32_t)(b >> 32);
+    const int e = (int)(hi >> 20);  // biased float64 exponent (sign already cleared)
+    if (e < 1023 - 126) return 0.f;
+    if (e > 1023 + 127) return __uint_as_float(0x7F800000u);
+    return __uint_as_float(((uint32_t)(e - 1023 + 127) << 23) | (uint32_t)((b >> 29) & 0x7FFFFFu));
 }
 
 // bf16 bits of a small integer (exact): through the float magic number
@@ -113,18 +137,87 @@ __global__ void __launch_bounds__(256) k_tcr_rowscan(const double* __restrict__ 
         for (int u = 0; u < 8; ++u) {
             const unsigned long long b = (unsigned long long)__double_as_longlong(a[u]) & 0x7FFFFFFFFFFFFFFFull;
             mx[u & 3] = b > mx[u & 3] ? b : mx[u & 3];
-            asum[u & 3] += fabsf((float)a[u]);
+            asum[u & 3] += tcr_absf(b);
         }
     }
     for (; j < j1; ++j) {
         const double a = __ldg(ap + (long)j * lda);
         const unsigned long long b = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
         mx[0] = b > mx[0] ? b : mx[0];
-        asum[0] += fabsf((float)a);
+        asum[0] += tcr_absf(b);
     }
     const unsigned long long m01 = mx[0] > mx[1] ? mx[0] : mx[1], m23 = mx[2] > mx[3] ? mx[2] : mx[3];
     if (j1 > j0) atomicMax(rowmax + i, m01 > m23 ? m01 : m23);
     rowabs[(long)s * n + i] = (asum[0] + asum[1]) + (asum[2] + asum[3]);
+}
+
+// The same scan with A streamed by TMA: CTA (row block of 256, column
+// chunk) loads 256 x 16 tiles (32 KB) into a 3-stage ring; thread t owns row
+// t of the block.  Waits are bounded; a wait that gives up raises
+// SPD_DEV_TIMEOUT and the CTA stops.
+constexpr int TRS_COLS = 16, TRS_ST = 3;
+constexpr int TRS_TILE = 256 * TRS_COLS * 8;
+constexpr size_t TRS_SMEM = (size_t)TRS_ST * TRS_TILE + 128;
+__global__ void __launch_bounds__(256) k_tcr_rowscan_tma(const __grid_constant__ CUtensorMap mapA, int n, int jchunk,
+                                                         unsigned long long* __restrict__ rowmax,
+                                                         float* __restrict__ rowabs, DevStatus* st) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const double* buf = reinterpret_cast<const double*>(smem_raw);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + TRS_ST * TRS_TILE);
+    uint64_t* empty = full + TRS_ST;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + TRS_ST);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int i0 = blockIdx.x * 256, s = blockIdx.y;
+    const int j0 = s * jchunk, j1 = min(n, j0 + jchunk);  // jchunk is a multiple of 16
+    const int ntile = j1 > j0 ? (j1 - j0 + TRS_COLS - 1) / TRS_COLS : 0;
+    if (tid == 0) {
+        for (int k = 0; k < TRS_ST; ++k) {
+            tc::mbar_init(&full[k], 1);
+            tc::mbar_init(&empty[k], 8);
+        }
+        *abort_flag = 0;
+        tc::fence_barrier_init();
+        tc::prefetch_tmap(&mapA);
+        for (int t = 0; t < TRS_ST && t < ntile; ++t) {
+            tc::mbar_arrive_expect_tx(&full[t], TRS_TILE);
+            tc::tma_load_2d(smem_raw + t * TRS_TILE, &mapA, i0, j0 + t * TRS_COLS, &full[t]);
+        }
+    }
+    __syncthreads();
+    unsigned long long mx0 = 0ull, mx1 = 0ull;
+    float as0 = 0.f, as1 = 0.f;
+    for (int t = 0; t < ntile; ++t) {
+        const int k = t % TRS_ST;
+        const uint32_t ph = (t / TRS_ST) & 1u;
+        if (!tc::mbar_wait(&full[k], ph, abort_flag, TCR_WAIT_NS)) break;
+        const double* col = buf + (size_t)k * 256 * TRS_COLS + tid;
+#pragma unroll
+        for (int c = 0; c < TRS_COLS; c += 2) {
+            const double a = col[c * 256], b = col[(c + 1) * 256];
+            const unsigned long long ba = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+            const unsigned long long bb = (unsigned long long)__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFull;
+            mx0 = ba > mx0 ? ba : mx0;
+            mx1 = bb > mx1 ? bb : mx1;
+            as0 += tcr_absf(ba);
+            as1 += tcr_absf(bb);
+        }
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&empty[k]);
+        if (tid == 0 && t + TRS_ST < ntile) {  // refill this stage once every warp has read it
+            if (!tc::mbar_wait(&empty[k], ph, abort_flag, TCR_WAIT_NS)) break;
+            tc::mbar_arrive_expect_tx(&full[k], TRS_TILE);
+            tc::tma_load_2d(smem_raw + k * TRS_TILE, &mapA, i0, j0 + (t + TRS_ST) * TRS_COLS, &full[k]);
+        }
+    }
+    if (*abort_flag) {
+        if (tid == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
+        return;
+    }
+    const int i = i0 + tid;
+    if (i < n) {
+        if (ntile > 0) atomicMax(rowmax + i, mx0 > mx1 ? mx0 : mx1);
+        rowabs[(long)s * n + i] = as0 + as1;
+    }
 }
 
 // 64 x 64 tile: element (i0 + r, j0 + c) of column-major A goes to
@@ -507,6 +600,20 @@ bool tcr_map(CUtensorMap* map, const void* base, long planes, long rows, long co
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// column-major float64 A (n x n, ld lda) in 256-row x 16-column boxes; needs a
+// 16-byte aligned A and lda a multiple of 2
+bool tcr_map_a64(CUtensorMap* map, const double* A, int n, long lda) {
+    auto enc = tcr_encoder();
+    if (!enc || (reinterpret_cast<uintptr_t>(A) & 15) || (lda & 1)) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+    cuuint64_t strides[1] = {(cuuint64_t)(lda * 8)};
+    cuuint32_t box[2] = {256, (cuuint32_t)TRS_COLS};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(A), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct TcrSchedule {
     int RB, CB, Nkc, G;
     long T;
@@ -562,9 +669,23 @@ spd_status tc_resid_prepare(spd_handle* h, TcResidWs* w, const double* A, long l
     cudaStream_t s = h->stream;
     const int n = w->n;
     CUDA_TRY(h, cudaMemsetAsync(w->rowmax, 0, sizeof(unsigned long long) * n, s));
-    const int jchunk = ceil_div(n, w->RS);
-    ++(h)->launches, k_tcr_rowscan<<<dim3(ceil_div(n, 256), w->RS), 256, 0, s>>>(A, lda, n, jchunk, w->rowmax,
-                                                                                w->rowabs);
+    CUtensorMap mapA64;
+    if (tcr_map_a64(&mapA64, A, n, lda)) {  // stream A by TMA
+        static const bool attr = [] {  // once per process, thread-safe
+            cudaFuncSetAttribute(k_tcr_rowscan_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TRS_SMEM);
+            return true;
+        }();
+        (void)attr;
+        w->RS = 8;
+        const int jchunk = (int)round_up(ceil_div(n, w->RS), TRS_COLS);
+        ++(h)->launches, k_tcr_rowscan_tma<<<dim3(ceil_div(n, 256), w->RS), 256, TRS_SMEM, s>>>(
+            mapA64, n, jchunk, w->rowmax, w->rowabs, h->dst);
+    } else {
+        w->RS = TCR_RS;
+        const int jchunk = ceil_div(n, w->RS);
+        ++(h)->launches, k_tcr_rowscan<<<dim3(ceil_div(n, 256), w->RS), 256, 0, s>>>(A, lda, n, jchunk, w->rowmax,
+                                                                                    w->rowabs);
+    }
     LAUNCH_CHECK(h);
     ++(h)->launches, k_tcr_digits_a<<<dim3(ceil_div(n, 64), ceil_div(n, 64)), 256, 0, s>>>(A, lda, n, w->rowmax,
                                                                                           w->Ad, w->ldp);

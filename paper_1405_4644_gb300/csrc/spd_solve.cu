@@ -387,18 +387,24 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
         return o;
     }();
     const int NB = ceil_div(n, 128);
+    // flags (NB ints) and, after them, the CTA slot table; both restart at
+    // epoch 0 (all zero) whenever they are reallocated
+    const size_t slot_off = (size_t)round_up((long)sizeof(int) * NB, 256);
     if (h->ready_n < NB) {
         if (h->ready) CUDA_TRY(h, cudaFree(h->ready));
         h->ready = nullptr;
-        CUDA_TRY(h, cudaMalloc(&h->ready, sizeof(int) * NB));
-        CUDA_TRY(h, cudaMemsetAsync(h->ready, 0, sizeof(int) * NB, h->stream));
+        const size_t bytes = slot_off + sizeof(unsigned long long) * TV_SLOTS;
+        CUDA_TRY(h, cudaMalloc(&h->ready, bytes));
+        CUDA_TRY(h, cudaMemsetAsync(h->ready, 0, bytes, h->stream));
         h->ready_n = NB;
         h->epoch = 0;
     }
+    unsigned long long* slots = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->ready) +
+                                                                      round_up((long)sizeof(int) * h->ready_n, 256));
     for (int dir = 0; dir < 2; ++dir) {
-        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst};
+        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst, slots};
         void* args[] = {&a};
-        const int grid = std::min(NB, occ.per_sm[dir] * h->sms);
+        const int grid = std::min({NB, occ.per_sm[dir] * h->sms, TV_SLOTS});
         ++h->launches;
         CUDA_TRY(h, coop_launch(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(grid), dim3(256), args, smem,
                                 h->stream));
