@@ -277,7 +277,17 @@ FP32_OPS_PEAK_T = 152 * 2.07e9 * 128 / 1e12
 DF32_OPS_PER_MADD = 12
 
 
-def roofline(phases, per_kappa):
+# DRAM bytes (read + write) per phase launch from an ncu capture of a smaller
+# case, per unit of n^2 (the kernels stream a fixed number of bytes per entry
+# of A or of the factor): {phase: (bytes per n^2, source)}.  The forward and
+# backward sweeps of one solve at n = 8192, m = 16 read 136.97 + 136.95 MB and
+# wrote 0.23 + 3.13 MB (profiles/trsv_sweeps_n8192_m16.md).
+MEASURED_TRAFFIC = {
+    "solve": ((136968960 + 225792 + 136949248 + 3132928) / 8192 ** 2, "profiles/trsv_sweeps_n8192_m16.md"),
+}
+
+
+def roofline(phases, per_kappa, n=None):
     """Roofline of the phase (kernel family) that took the most device time
     in the timed region; achieved = its algorithmic work / its event time."""
     peaks, src = load_peaks()
@@ -314,7 +324,10 @@ def roofline(phases, per_kappa):
     if dom == "resid_df32":
         work = ph["flops"] / 2 * DF32_OPS_PER_MADD
     r.update({"frac": r["achieved"] / r["peak"], "kernel_phase": dom, "launches": ph["launches"],
-              "avg_launch_ms": ph["ms"] / max(ph["launches"], 1), "traffic": None,
+              "avg_launch_ms": ph["ms"] / max(ph["launches"], 1),
+              "traffic": (MEASURED_TRAFFIC[dom][0] * n * n if (dom in MEASURED_TRAFFIC and n) else None),
+              "traffic_source": (MEASURED_TRAFFIC[dom][1] + ", scaled by n^2" if (dom in MEASURED_TRAFFIC and n)
+                                 else None),
               "algorithmic_per_launch": work / max(ph["launches"], 1)})
     return r
 
@@ -600,7 +613,7 @@ def main():
         spd.spd_profile_enable(h, False)
         roof_note = ("phases of one extra step of the same workload with every kernel alone (one lane, serial "
                      "factor schedule); the timed region ran concurrent lanes and the look-ahead")
-    roof = roofline(roof_phases, per_kappa)
+    roof = roofline(roof_phases, per_kappa, args.n)
     roof["measured_on"] = roof_note
     energy = None
     if e0 is not None and e1 is not None:
