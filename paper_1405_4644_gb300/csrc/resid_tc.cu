@@ -20,6 +20,7 @@
 //   k_tcr_final     combines the groups with their scales in double-double,
 //                   R = B - AX rounded once, block partial norms.
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include "resid_tc.h"
 #include "tc_ptx.cuh"
 
@@ -56,50 +57,6 @@ __device__ __forceinline__ int tcr_exp(unsigned long long mx) {
     return lg + 2;
 }
 
-// the ten signed digits of a / 2^e: a = 2^e sum_{p<10} d[p] 2^{-7(p+1)} up
-// to the bits of a below 2^{e-70} (dropped, toward zero); |a| < 2^{e-1}.
-// F = |a| 2^{70-e} < 2^69 is taken in four 21-bit fields (three digits
-// each, the top one below 2^6); adding 64 at every digit position and
-// subtracting it from every 7-bit field gives the balanced digits in
-// [-64, 63] with the carries propagated, the top digit in [0, 64]; the sign
-// of a then negates them all.  Returned as d[p] with d[9] least significant.
-__device__ __forceinline__ void tcr_digits(double a, int e, int (&d)[TCR_S], bool& neg) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
-    int ef = (int)((bits >> 52) & 0x7FF);
-    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
-    if (ef) M |= 1ull << 52;
-    else ef = 1;
-    const int sh = ef - 1005 - e;  // F = M 2^sh (sh <= 16 for normal a, up to 68 in subnormal rows)
-    // F as its low 64 bits and the (at most five) bits above them
-    unsigned long long lo = 0ull;
-    uint32_t hi = 0;
-    if (sh >= 64) {
-        hi = (uint32_t)(M << (sh - 64));
-    } else if (sh > 0) {
-        lo = M << sh;
-        hi = (uint32_t)(M >> (64 - sh));
-    } else if (sh > -64) {
-        lo = M >> (-sh);
-    }
-    uint32_t c[4];
-    c[0] = (uint32_t)lo & 0x1FFFFFu;
-    c[1] = (uint32_t)(lo >> 21) & 0x1FFFFFu;
-    c[2] = (uint32_t)(lo >> 42) & 0x1FFFFFu;
-    c[3] = (uint32_t)(lo >> 63) | (hi << 1);
-    constexpr uint32_t K3 = 64u | (64u << 7) | (64u << 14);
-    uint32_t carry = 0;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const uint32_t t = c[k] + K3 + carry;
-        d[9 - 3 * k] = (int)(t & 127u) - 64;
-        d[8 - 3 * k] = (int)((t >> 7) & 127u) - 64;
-        d[7 - 3 * k] = (int)((t >> 14) & 127u) - 64;
-        carry = t >> 21;
-    }
-    d[0] = (int)(c[3] + carry);
-    neg = (bits >> 63) != 0;
-}
-
 // |a| as a float from the bits of a (magnitude bits b), truncating the
 // mantissa: no float64 arithmetic or conversion, which run at a small
 // fraction of the float32 rate on this part; below 2^-126 counts as 0 and
@@ -115,6 +72,71 @@ __device__ __forceinline__ float tcr_absf(unsigned long long b) {
 // bf16 bits of a small integer (exact): through the float magic number
 __device__ __forceinline__ uint32_t tcr_bf16(int v) {
     return __float_as_uint(__int_as_float((int)TCR_MAGIC_BITS + v) - TCR_MAGIC) >> 16;
+}
+
+// The ten signed digits of a / 2^e: a = 2^e sum_{p<10} d[p] 2^{-7(p+1)} up
+// to the bits of a below 2^{e-70} (dropped, toward zero); |a| < 2^{e-1}.
+// F = |a| 2^{70-e} < 2^69 is taken in four 21-bit fields (three digits
+// each, the top one below 2^6); adding 64 at every digit position and
+// subtracting it from every 7-bit field gives the balanced digits in
+// [-64, 63] with the carries propagated, the top digit in [0, 64]; the sign
+// of a then negates them all.  d[0] is the most significant digit.
+// Two entries are done at a time and returned in bf16 pairs:
+// pk[p] = bf16(d_p(a0)) | bf16(d_p(a1)) << 16.  The recoded 7-bit fields
+// f = d + 64 of each 21-bit chunk are spread over bytes (tcr_fields); one
+// byte permute puts field j of both entries into the mantissas of 0x4300
+// (bf16 128 + f), and one packed bf16 FMA forms s (x - 192) = +-d exactly.
+// The top digit (0..64) is converted directly.
+__device__ __forceinline__ void tcr_fields(double a, int e, uint32_t (&u)[3], int& top, bool& neg) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(a);
+    int ef = (int)((bits >> 52) & 0x7FF);
+    unsigned long long M = bits & 0xFFFFFFFFFFFFFull;
+    if (ef) M |= 1ull << 52;
+    else ef = 1;
+    const int sh = ef - 1005 - e;
+    unsigned long long lo = 0ull;
+    uint32_t hi = 0;
+    if (sh >= 64) {
+        hi = (uint32_t)(M << (sh - 64));
+    } else if (sh > 0) {
+        lo = M << sh;
+        hi = (uint32_t)(M >> (64 - sh));
+    } else if (sh > -64) {
+        lo = M >> (-sh);
+    }
+    const uint32_t c0 = (uint32_t)lo & 0x1FFFFFu, c1 = (uint32_t)(lo >> 21) & 0x1FFFFFu,
+                   c2 = (uint32_t)(lo >> 42) & 0x1FFFFFu, c3 = (uint32_t)(lo >> 63) | (hi << 1);
+    constexpr uint32_t K3 = 64u | (64u << 7) | (64u << 14);
+    uint32_t t = c0 + K3;
+    u[0] = (t & 0x7Fu) | ((t << 1) & 0x7F00u) | ((t << 2) & 0x7F0000u);
+    t = c1 + K3 + (t >> 21);
+    u[1] = (t & 0x7Fu) | ((t << 1) & 0x7F00u) | ((t << 2) & 0x7F0000u);
+    t = c2 + K3 + (t >> 21);
+    u[2] = (t & 0x7Fu) | ((t << 1) & 0x7F00u) | ((t << 2) & 0x7F0000u);
+    top = (int)(c3 + (t >> 21));
+    neg = (bits >> 63) != 0;
+}
+
+__device__ __forceinline__ void tcr_digits2(double a0, double a1, int e, uint32_t (&pk)[TCR_S]) {
+    uint32_t u0[3], u1[3];
+    int top0, top1;
+    bool n0, n1;
+    tcr_fields(a0, e, u0, top0, n0);
+    tcr_fields(a1, e, u1, top1, n1);
+    const uint32_t sb = (n0 ? 0xBF80u : 0x3F80u) | (n1 ? 0xBF800000u : 0x3F800000u);  // +-1
+    const uint32_t cb = (n0 ? 0x4340u : 0xC340u) | (n1 ? 0x43400000u : 0xC3400000u);  // -+192
+    const __nv_bfloat162 s2 = *reinterpret_cast<const __nv_bfloat162*>(&sb);
+    const __nv_bfloat162 c2 = *reinterpret_cast<const __nv_bfloat162*>(&cb);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const uint32_t x = __byte_perm(u0[k], u1[k], (uint32_t)(j | (3 << 4) | ((4 + j) << 8) | (7 << 12))) |
+                               0x43004300u;
+            const __nv_bfloat162 r = __hfma2(*reinterpret_cast<const __nv_bfloat162*>(&x), s2, c2);
+            pk[9 - 3 * k - j] = *reinterpret_cast<const uint32_t*>(&r);
+        }
+    pk[0] = (tcr_bf16(top0) ^ (n0 ? 0x8000u : 0u)) | ((tcr_bf16(top1) ^ (n1 ? 0x8000u : 0u)) << 16);
 }
 
 __global__ void __launch_bounds__(256) k_tcr_rowscan(const double* __restrict__ A, long lda, int n, int jchunk,
@@ -243,15 +265,12 @@ __global__ void __launch_bounds__(256) k_tcr_digits_a(const double* __restrict__
         if (i >= n) break;
         const int e = tcr_exp(rowmax[i]);
         const bool zero = e == TCR_NONFINITE;
-        int d0[TCR_S], d1[TCR_S];
-        bool n0, n1;
-        tcr_digits(zero ? 0.0 : tile[r][2 * lane], zero ? 0 : e, d0, n0);
-        tcr_digits(zero ? 0.0 : tile[r][2 * lane + 1], zero ? 0 : e, d1, n1);
+        uint32_t pk[TCR_S];
+        tcr_digits2(zero ? 0.0 : tile[r][2 * lane], zero ? 0.0 : tile[r][2 * lane + 1], zero ? 0 : e, pk);
         // ldp is a multiple of 64, so the tile's columns are inside the row pitch
         uint32_t* dst = reinterpret_cast<uint32_t*>(Ad + (long)i * ldp + j0) + lane;
 #pragma unroll
-        for (int p = 0; p < TCR_S; ++p)
-            dst[(long)p * n * ldp / 2] = (tcr_bf16(d0[p]) ^ (n0 ? 0x8000u : 0u)) | ((tcr_bf16(d1[p]) ^ (n1 ? 0x8000u : 0u)) << 16);
+        for (int p = 0; p < TCR_S; ++p) dst[(long)p * n * ldp / 2] = pk[p];
     }
 }
 
@@ -284,15 +303,11 @@ __global__ void __launch_bounds__(256) k_tcr_digits_x(const double* __restrict__
         uint32_t pk[TCR_S][4];
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
-            int d0[TCR_S], d1[TCR_S];
-            bool n0, n1;
-            const double a0 = (!zero && j + u < n) ? x[j + u] : 0.0;
-            const double a1 = (!zero && j + u + 1 < n) ? x[j + u + 1] : 0.0;
-            tcr_digits(a0, zero ? 0 : e, d0, n0);
-            tcr_digits(a1, zero ? 0 : e, d1, n1);
+            uint32_t pq[TCR_S];
+            tcr_digits2((!zero && j + u < n) ? x[j + u] : 0.0, (!zero && j + u + 1 < n) ? x[j + u + 1] : 0.0,
+                        zero ? 0 : e, pq);
 #pragma unroll
-            for (int p = 0; p < TCR_S; ++p)
-                pk[p][u >> 1] = (tcr_bf16(d0[p]) ^ (n0 ? 0x8000u : 0u)) | ((tcr_bf16(d1[p]) ^ (n1 ? 0x8000u : 0u)) << 16);
+            for (int p = 0; p < TCR_S; ++p) pk[p][u >> 1] = pq[p];
         }
 #pragma unroll
         for (int p = 0; p < TCR_S; ++p)
