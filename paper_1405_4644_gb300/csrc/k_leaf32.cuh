@@ -25,6 +25,29 @@
 // blocks, D_s[i][c] = (L_ss^{-1})[i][c] (lower triangular).
 constexpr size_t potrf_leaf32_smem() { return (size_t)(128 * LD32 + 32 * 33 + 96 * 33) * sizeof(float); }
 
+// Entries of L in columns [c0, c0 + 32), rows c0 .. nb - 1, from the leaf's
+// shared copy S to W and its mirror, four columns per store; thread t of nt.
+__device__ __forceinline__ void leaf_store_cols(const float* S, float* W, long ldw, int k, int nb, int c0,
+                                                const Mirror& mir, int t, int nt) {
+    for (int e = t; e < (128 - c0) * 8; e += nt) {
+        const int r = c0 + (e >> 3), c4 = c0 + (e & 7) * 4;
+        if (r >= nb || c4 > r) continue;
+        const float* sr = S + r * LD32 + c4;
+        float v[4] = {sr[0], sr[1], sr[2], sr[3]};
+        float* dst = W + (long)(k + r) * ldw + k + c4;
+        if (c4 + 3 <= r) {
+            const float4 f = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(dst) = f;
+            mirror_store4(mir, (long)(k + r), (long)(k + c4), f);
+        } else {
+            for (int q = 0; c4 + q <= r; ++q) {
+                dst[q] = v[q];
+                mirror_store(mir, (long)(k + r), (long)(k + c4 + q), v[q]);
+            }
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, long ldw, int k, int nb,
                                                       float* __restrict__ Dinv32, Mirror mir, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -117,6 +140,10 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
                 Dj[i * 33 + lane] = x[i];
                 Dout[J * 1024 + i * 32 + lane] = x[i];
             }
+        } else if (J > 0) {
+            // block column J - 1 is final: the other warps write it out while
+            // warp 0 factors the next diagonal block
+            leaf_store_cols(S, W, ldw, k, nb, o - 32, mir, tid - 32, 224);
         }
         __syncthreads();
         if (s_bad) return;
@@ -173,24 +200,8 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
         }
         __syncthreads();
     }
-    // L (lower part, rows < nb) to W and its mirror, four columns per store
-    for (int e = tid; e < 128 * 32; e += 256) {
-        const int r = e >> 5, c4 = (e & 31) * 4;
-        if (r >= nb || c4 > r) continue;
-        const float* sr = S + r * LD32 + c4;
-        float v[4] = {sr[0], sr[1], sr[2], sr[3]};
-        float* dst = W + (long)(k + r) * ldw + k + c4;
-        if (c4 + 3 <= r) {
-            const float4 f = make_float4(v[0], v[1], v[2], v[3]);
-            *reinterpret_cast<float4*>(dst) = f;
-            mirror_store4(mir, (long)(k + r), (long)(k + c4), f);
-        } else {
-            for (int q = 0; c4 + q <= r; ++q) {
-                dst[q] = v[q];
-                mirror_store(mir, (long)(k + r), (long)(k + c4 + q), v[q]);
-            }
-        }
-    }
+    // the last block column (the others went out during the next diagonal step)
+    leaf_store_cols(S, W, ldw, k, nb, 96, mir, tid, 256);
 }
 
 // Panel solve for rows [r0, r0 + m) against the factored diagonal block at
