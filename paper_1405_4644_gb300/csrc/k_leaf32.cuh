@@ -48,6 +48,37 @@ __device__ __forceinline__ void leaf_store_cols(const float* S, float* W, long l
     }
 }
 
+// Part of the leaf's trailing update after step o: S[i][j] -= sum_{l<32}
+// S[i][o+l] S[j][o+l] for the 2x2 blocks (bi, bj), bj <= bi, of the region
+// from row/column base = o + 32 with bi in [bi0, bi1) (bi1 <= (128 - base) /
+// 2); thread t of nt.
+__device__ __forceinline__ void leaf_trailing(float* S, int o, int bi0, int bi1, int t, int nt) {
+    const int base = o + 32;
+    const int nc = bi1;  // columns bj < bi1 cover every bj <= bi
+    for (int e = t; e < (bi1 - bi0) * nc; e += nt) {
+        const int bi = bi0 + e / nc, bj = e % nc;
+        if (bj > bi) continue;
+        const int i = base + 2 * bi, j = base + 2 * bj;
+        const float* r0 = S + i * LD32 + o;
+        const float* r1 = r0 + LD32;
+        const float* q0 = S + j * LD32 + o;
+        const float* q1 = q0 + LD32;
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+#pragma unroll 8
+        for (int l = 0; l < 32; ++l) {
+            const float a0 = r0[l], a1 = r1[l], b0 = q0[l], b1 = q1[l];
+            s00 += a0 * b0;
+            s01 += a0 * b1;
+            s10 += a1 * b0;
+            s11 += a1 * b1;
+        }
+        S[i * LD32 + j] -= s00;
+        S[(i + 1) * LD32 + j] -= s10;
+        S[(i + 1) * LD32 + j + 1] -= s11;
+        if (j + 1 <= i) S[i * LD32 + j + 1] -= s01;
+    }
+}
+
 __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, long ldw, int k, int nb,
                                                       float* __restrict__ Dinv32, Mirror mir, DevStatus* st) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -141,9 +172,12 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
                 Dout[J * 1024 + i * 32 + lane] = x[i];
             }
         } else if (J > 0) {
-            // block column J - 1 is final: the other warps write it out while
-            // warp 0 factors the next diagonal block
+            // while warp 0 factors this diagonal block, the other warps write
+            // out block column J - 1 (final) and finish step J - 1's trailing
+            // update below this diagonal block (rows o + 32 .., read only
+            // after the next barrier)
             leaf_store_cols(S, W, ldw, k, nb, o - 32, mir, tid - 32, 224);
+            leaf_trailing(S, o - 32, 16, (128 - o) >> 1, tid - 32, 224);
         }
         __syncthreads();
         if (s_bad) return;
@@ -173,31 +207,9 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
             S[(o + 32 + i) * LD32 + o + c] = Tmp[i * 33 + c];
         }
         __syncthreads();
-        // trailing update of the rest of the leaf: 2x2 outputs per thread-iteration
-        const int base = o + 32;
-        const int hr = rows >> 1;
-        for (int e = tid; e < hr * hr; e += 256) {
-            const int bi = e / hr, bj = e - bi * hr;
-            if (bj > bi) continue;
-            const int i = base + 2 * bi, j = base + 2 * bj;
-            const float* r0 = S + i * LD32 + o;
-            const float* r1 = r0 + LD32;
-            const float* q0 = S + j * LD32 + o;
-            const float* q1 = q0 + LD32;
-            float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-#pragma unroll 8
-            for (int l = 0; l < 32; ++l) {
-                const float a0 = r0[l], a1 = r1[l], b0 = q0[l], b1 = q1[l];
-                s00 += a0 * b0;
-                s01 += a0 * b1;
-                s10 += a1 * b0;
-                s11 += a1 * b1;
-            }
-            S[i * LD32 + j] -= s00;
-            S[(i + 1) * LD32 + j] -= s10;
-            S[(i + 1) * LD32 + j + 1] -= s11;
-            if (j + 1 <= i) S[i * LD32 + j + 1] -= s01;
-        }
+        // trailing update of the next diagonal block only (rows and columns
+        // o + 32 .. o + 63); the rest of it runs during the next diagonal step
+        leaf_trailing(S, o, 0, 16, tid, 256);
         __syncthreads();
     }
     // the last block column (the others went out during the next diagonal step)
