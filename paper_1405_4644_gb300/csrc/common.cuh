@@ -168,3 +168,10 @@ __device__ __forceinline__ bool spin_until_geq(const volatile int* flag, int wan
     }
     return false;
 }
+
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization waits here until the previous kernel in its stream has
+// completed and its writes are visible; the previous kernel may let it be
+// scheduled earlier with pdl_trigger().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }

@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
 
     // epilogue: TMEM -> registers -> C -= scale * acc
     bool ok = tc::mbar_wait(accf, 0, abort_flag, WAIT_NS) && !*abort_flag;
+    if (threadIdx.x == 0) pdl_trigger();  // a dependent kernel (the next leaf) may be scheduled
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     tc::fence_after_sync();
     if (ok && Cpart) {  // split-K partial: the raw accumulator (zero for an empty share)

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
     float* Tmp = Dj + 32 * 33;                      // [96][33] sub-panel scratch
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    pdl_wait();  // the update of this diagonal block is the previous kernel
     if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
 
     if (nb == 128) {
@@ -121,6 +122,7 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
 
     for (int J = 0; J < 4; ++J) {
         const int o = J * 32;
+        if (J == 2 && tid == 0) pdl_trigger();  // the panel solve may start loading its rows
         if (warp == 0) {
             // lane r holds row o + r of the diagonal block
             float a[32], rd[32];
@@ -223,17 +225,19 @@ __global__ void __launch_bounds__(256, 1) k_potrf_leaf32(float* __restrict__ W, 
 // owns a 4-row by (2 | 6 - 2 s)-column register tile of each step.
 constexpr size_t trsm_leaf32_smem() { return (size_t)(64 * 132 + 96 * LD32 + 4 * 32 * 33) * sizeof(float); }
 
+// b_ready: the previous kernel in the stream (the leaf) does not write B,
+// so B is loaded before waiting for it (programmatic dependent launch).
 __global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, long ldw, int r0, int m, int c0,
                                                      const float* __restrict__ Dinv32, Mirror mir,
-                                                     const DevStatus* st) {
+                                                     const DevStatus* st, int b_ready) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Bs = reinterpret_cast<float*>(smem_raw);  // [64][132] B, becoming X
     float* Ls = Bs + 64 * 132;                       // [96][129] rows 32..127 of L_kk, columns 0..95
     float* Ds = Ls + 96 * LD32;                      // [4][32][33] D_s
-    if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
     const int tid = threadIdx.x;
     const int rb0 = r0 + blockIdx.x * 64;
     {
+        if (!b_ready) pdl_wait();
         float4 vb[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {  // B: 64 rows x 128 columns
@@ -241,6 +245,8 @@ __global__ void __launch_bounds__(256, 2) k_trsm_leaf32(float* __restrict__ W, l
             vb[q] = (rb0 + r < r0 + m) ? *reinterpret_cast<const float4*>(W + (long)(rb0 + r) * ldw + c0 + c4)
                                        : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        if (b_ready) pdl_wait();  // L_kk and its inverses come from the previous kernel
+        if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
         // the strictly-below-diagonal 32-blocks of L_kk (rows 32..127, columns
         // 0..95) and the four 32x32 inverses: every load in flight first
         float4 vl[9], vd[4];

@@ -29,6 +29,24 @@ struct FCtx {
 
 
 
+// Launch with programmatic stream serialization: the kernel may be scheduled
+// before the previous kernel in the stream finishes and waits for it itself
+// (pdl_wait), which hides the launch gap on the factorisation's critical path.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 spd_status leaf_potrf(FCtx& c, int k, int nb) {
     spd_factor_t* F = c.F;
@@ -37,23 +55,28 @@ spd_status leaf_potrf(FCtx& c, int k, int nb) {
         ++(c.h)->launches, k_potrf_leaf<double><<<1, 256, potrf_leaf_smem<double>(), c.h->stream>>>(
             F->W64, F->ldw, k, nb, F->Dinv64, c.mir, c.h->dst);
     } else {
-        ++(c.h)->launches, k_potrf_leaf32<<<1, 256, potrf_leaf32_smem(), c.h->stream>>>(F->W, F->ldw, k, nb,
-                                                                                          F->Dinv32, c.mir, c.h->dst);
+        ++(c.h)->launches;
+        CUDA_TRY(c.h, launch_pdl(k_potrf_leaf32, dim3(1), dim3(256), potrf_leaf32_smem(), c.h->stream, F->W, F->ldw, k,
+                                 nb, F->Dinv32, c.mir, c.h->dst));
     }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
 }
 
+// b_ready: B (rows r0 .., block column c0) is final before the previous
+// kernel in the stream, which is then the leaf of block c0
 template <typename T>
-spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb) {
+spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb, bool b_ready = false) {
     spd_factor_t* F = c.F;
     ProfScope ps(c.h, SPD_PHASE_PANEL, (double)m * kb * kb, 2.0 * m * kb * sizeof(T));
     if constexpr (sizeof(T) == 8) {
         ++(c.h)->launches, k_trsm_leaf<double, 32><<<ceil_div(m, 32), 256, trsm_leaf_smem<double, 32>(), c.h->stream>>>(
             F->W64, F->ldw, r0, m, c0, kb, F->Dinv64, c.mir, c.h->dst);
     } else {
-        ++(c.h)->launches, k_trsm_leaf32<<<ceil_div(m, 64), 256, trsm_leaf32_smem(), c.h->stream>>>(
-            F->W, F->ldw, r0, m, c0, F->Dinv32, c.mir, c.h->dst);
+        ++(c.h)->launches;
+        CUDA_TRY(c.h, launch_pdl(k_trsm_leaf32, dim3(ceil_div(m, 64)), dim3(256), trsm_leaf32_smem(), c.h->stream,
+                                 F->W, F->ldw, r0, m, c0, (const float*)F->Dinv32, c.mir, (const DevStatus*)c.h->dst,
+                                 b_ready ? 1 : 0));
     }
     LAUNCH_CHECK(c.h);
     return SPD_OK;
@@ -179,7 +202,8 @@ spd_status potrf_left(FCtx& c, int n, bool lookahead) {
         if (e == cudaSuccess && k >= 1)  // last: rank 128 with block column k-1
             st = gemm<T>(c, r0, M, r0, nb, r0 - SPD_LEAF, SPD_LEAF, 0, 1, P, c.part2);
         if (e == cudaSuccess && st == SPD_OK) st = leaf_potrf<T>(c, r0, nb);
-        if (e == cudaSuccess && st == SPD_OK && r0 + nb < n) st = leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb);
+        if (e == cudaSuccess && st == SPD_OK && r0 + nb < n)
+            st = leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb, true);  // right after the leaf
         if (e != cudaSuccess || st != SPD_OK) break;
         e = cudaEventRecord(evPanel[k], P);
         // early update of block k+2 on the second stream: columns 0..k
