@@ -50,7 +50,7 @@ struct spd_factor_t {
     double* d = nullptr;       // scaling
     double* Dinv64 = nullptr;  // float64 factor: 32x32 diagonal sub-block inverses
     float* LinvT = nullptr;    // float32 factor: (L_JJ^{-1})^T of every 128x128 block
-    float* Cpl = nullptr;      // float32 factor: sweep couplings M_J, N_J (2 x nblk128 blocks)
+    float* Cpl = nullptr;      // float32 factor: sweep couplings M_J, N_J, P_J, Q_J (4 x nblk128 blocks)
     float* Dinv32 = nullptr;   // float32 factor: inverses of the 32x32 diagonal sub-blocks
     int nblk128 = 0;
 };

@@ -36,7 +36,7 @@ struct TrsvArgs {
     long ldw;
     int n, NB;
     const float* LinvT;  // per block: (L_JJ^{-1})^T, 128 x 128 row-major
-    const float* Cpl;    // couplings: M_J at J * 16384, N_J at (NB + J) * 16384
+    const float* Cpl;    // couplings: M_J, N_J, P_J, Q_J at (J, NB + J, 2 NB + J, 3 NB + J) * 16384
     float* Y;            // n x m, column-major (ld n), in place
     int c0, mc;          // columns [c0, c0 + mc) in this pass
     int* ready;          // NB flags
@@ -84,9 +84,13 @@ constexpr size_t trsv32_smem() {
 // ---------------------------------------------------------------------------
 // couplings, once per factor
 // ---------------------------------------------------------------------------
-// blockIdx.y == 0: M_J for J = blockIdx.x + 1, M_J[i][l] = sum_k LinvT_J[k][i] L_{J,J-1}[k][l]
-// blockIdx.y == 1: N_J for J = blockIdx.x,     N_J[i][l] = sum_k LinvT_J[i][k] L_{J+1,J}[l][k]
-// Rows of L past n are zero.  Thread: row i = tid / 2, columns 64 (tid % 2) + 0..63.
+// Couplings at distance d = 1 (blockIdx.y 0, 1) and d = 2 (blockIdx.y 2, 3):
+//   forward  (y even): C[i][l] = sum_k LinvT_J[k][i] L_{J,J-d}[k][l],  J = blockIdx.x + d
+//            (M_J for d = 1, P_J for d = 2);
+//   backward (y odd):  C[i][l] = sum_k LinvT_J[i][k] L_{J+d,J}[l][k],  J = blockIdx.x
+//            (N_J for d = 1, Q_J for d = 2).
+// Stored at Cpl + (y NB + J) 16384.  Rows of L past n are zero.  Thread: row
+// i = tid / 2, columns 64 (tid % 2) + 0..63.
 constexpr size_t trsv_couplings_smem() { return (size_t)(2 * 128 * 129) * sizeof(float); }
 
 static __global__ void __launch_bounds__(256) k_trsv_couplings(const float* __restrict__ W, long ldw, int n, int NB,
@@ -94,18 +98,20 @@ static __global__ void __launch_bounds__(256) k_trsv_couplings(const float* __re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* Li = reinterpret_cast<float*>(smem_raw);  // [128][129] LinvT_J
     float* Bt = Li + 128 * 129;                      // [128][129] Bt[k][l]
-    const bool fwd = blockIdx.y == 0;
-    const int J = fwd ? blockIdx.x + 1 : blockIdx.x;
+    const bool fwd = (blockIdx.y & 1) == 0;
+    const int d = (int)(blockIdx.y >> 1) + 1;
+    const int J = fwd ? (int)blockIdx.x + d : (int)blockIdx.x;
+    if ((fwd ? J : J + d) > NB - 1) return;
     const int tid = threadIdx.x;
     const float* lg = LinvT + (long)J * 16384;
     for (int e = tid; e < 16384; e += 256) Li[(e >> 7) * 129 + (e & 127)] = lg[e];
     for (int e = tid; e < 16384; e += 256) {
         const int r = e >> 7, c = e & 127;
-        if (fwd) {  // Bt[k][l] = L_{J,J-1}[k][l]: row J*128 + r, column (J-1)*128 + c
+        if (fwd) {  // Bt[k][l] = L_{J,J-d}[k][l]: row J*128 + r, column (J-d)*128 + c
             const long gr = (long)J * 128 + r;
-            Bt[r * 129 + c] = gr < n ? W[gr * ldw + (long)(J - 1) * 128 + c] : 0.f;
-        } else {    // Bt[k][l] = L_{J+1,J}[l][k]: row (J+1)*128 + r (= l), column J*128 + c (= k)
-            const long gr = (long)(J + 1) * 128 + r;
+            Bt[r * 129 + c] = gr < n ? W[gr * ldw + (long)(J - d) * 128 + c] : 0.f;
+        } else {    // Bt[k][l] = L_{J+d,J}[l][k]: row (J+d)*128 + r (= l), column J*128 + c (= k)
+            const long gr = (long)(J + d) * 128 + r;
             Bt[c * 129 + r] = gr < n ? W[gr * ldw + (long)J * 128 + c] : 0.f;
         }
     }
@@ -120,7 +126,7 @@ static __global__ void __launch_bounds__(256) k_trsv_couplings(const float* __re
 #pragma unroll
         for (int q = 0; q < 64; ++q) acc[q] = fmaf(a, b[q], acc[q]);
     }
-    float* out = Cpl + ((long)(fwd ? J : NB + J) * 128 + i) * 128 + lb;
+    float* out = Cpl + ((long)(blockIdx.y * NB + J) * 128 + i) * 128 + lb;
 #pragma unroll
     for (int q = 0; q < 64; q += 4) *reinterpret_cast<float4*>(out + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
 }
@@ -305,8 +311,9 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
 
     for (int t = rank; t < a.NB; t += gridDim.x) {
         const int J = FWD ? t : a.NB - 1 - t;
-        const int nfar = FWD ? max(J - 1, 0) : max(a.NB - 2 - J, 0);
-        const bool near = FWD ? J >= 1 : J <= a.NB - 2;
+        const int nfar = FWD ? max(J - 2, 0) : max(a.NB - 3 - J, 0);
+        const bool near = FWD ? J >= 1 : J <= a.NB - 2;   // a neighbour at distance 1
+        const bool near2 = FWD ? J >= 2 : J <= a.NB - 3;  // and at distance 2
         float ra[64], rb[64];
         {  // (L_JJ^{-1})^T depends on no other block: into shared memory first
             const float4* src = reinterpret_cast<const float4*>(a.LinvT + (long)J * 16384);
@@ -342,9 +349,12 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
             __syncthreads();
         }
         if (s_abort) break;
-        // the coupling rows for the last product do not depend on anything
-        // still outstanding: start their loads now
-        if (near) tv_rows(ra, a.Cpl + (long)(FWD ? J : a.NB + J) * 16384, tq, ts);
+        // the coupling rows for the last two products do not depend on
+        // anything still outstanding: start the first one's loads now
+        const float* cp1 = a.Cpl + (long)(FWD ? J : a.NB + J) * 16384;           // M_J or N_J
+        const float* cp2 = a.Cpl + (long)(FWD ? 2 * a.NB + J : 3 * a.NB + J) * 16384;  // P_J or Q_J
+        if (near2) tv_rows(rb, cp2, tq, ts);
+        else if (near) tv_rows(ra, cp1, tq, ts);
         tv_reduce8<MC>(acc);
         // t = y_J - far sum (this CTA is the only writer of block J)
         if (ts == 0) {
@@ -392,23 +402,27 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
 #pragma unroll
         for (int c = 0; c < CPT; ++c)
             if (half == 0 || MC >= 2) T[i * MC + cbase + c] = out[c];
-        if (near) {  // the step on the critical path: y_J = u - C_J y_neighbour
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
+        if (near2) {  // the neighbour at distance 2: acc = P_J y_{J-2} (Q_J z_{J+2})
+            tv_rows(ra, cp1, tq, ts);
+            const int K2 = FWD ? J - 2 : J + 2;
+            if (!tv_wait(a, K2, &s_abort)) break;  // (its barrier also publishes u)
+            tv_stage<MC>(Yk, a, K2);
+            __syncthreads();
+            tv_dot<MC>(acc, rb, Yk, ts);
+        }
+        if (near) {  // the step on the critical path: y_J = u - acc - C_J y_neighbour
             const int Kn = FWD ? J - 1 : J + 1;
             if (!tv_wait(a, Kn, &s_abort)) break;  // (its barrier also publishes u)
             tv_stage<MC>(Yk, a, Kn);
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
             tv_dot<MC>(acc, ra, Yk, ts);
             tv_reduce8<MC>(acc);
         } else {
             __syncthreads();
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int c = 0; c < MC; ++c) acc[j][c] = 0.f;
         }
         if (ts == 0) {
 #pragma unroll

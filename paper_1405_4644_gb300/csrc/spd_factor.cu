@@ -275,7 +275,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
     } else if (e == cudaSuccess) {
         e = cudaMallocAsync(&F->W, sizeof(float) * std::max<size_t>(nW, 1), as);
         if (e == cudaSuccess) e = cudaMallocAsync(&F->LinvT, sizeof(float) * 128 * 128 * std::max(F->nblk128, 1), as);
-        if (e == cudaSuccess) e = cudaMallocAsync(&F->Cpl, sizeof(float) * 2 * 128 * 128 * std::max(F->nblk128, 1), as);
+        if (e == cudaSuccess) e = cudaMallocAsync(&F->Cpl, sizeof(float) * 4 * 128 * 128 * std::max(F->nblk128, 1), as);
         if (e == cudaSuccess) e = cudaMallocAsync(&F->Dinv32, sizeof(float) * 4096 * std::max(F->nblk128, 1), as);
         if (e == cudaSuccess && kind) {
             F->ldh = F->ldw;

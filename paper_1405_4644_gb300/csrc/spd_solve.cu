@@ -424,8 +424,10 @@ spd_status factor_couplings(spd_handle* h, spd_factor_t* F) {
         return true;
     }();
     (void)attr;
-    ProfScope ps(h, SPD_PHASE_LEAF, 2.0 * 2.0 * (NB - 1) * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * (NB - 1) * 16384.0);
-    ++h->launches, k_trsv_couplings<<<dim3(NB - 1, 2), 256, trsv_couplings_smem(), h->stream>>>(
+    // distance 1 (NB - 1 per direction) and distance 2 (NB - 2 per direction)
+    const int ncp = (NB - 1) + std::max(NB - 2, 0);
+    ProfScope ps(h, SPD_PHASE_LEAF, 2.0 * 2.0 * ncp * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * ncp * 16384.0);
+    ++h->launches, k_trsv_couplings<<<dim3(NB - 1, NB >= 3 ? 4 : 2), 256, trsv_couplings_smem(), h->stream>>>(
         F->W, F->ldw, F->n, NB, F->LinvT, F->Cpl);
     LAUNCH_CHECK(h);
     return SPD_OK;
