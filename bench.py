@@ -285,8 +285,17 @@ DF32_OPS_PER_MADD = 12
 # of A or of the factor): {phase: (bytes per n^2, source)}.  The forward and
 # backward sweeps of one solve at n = 8192, m = 16 read 136.97 + 136.95 MB and
 # wrote 0.23 + 3.13 MB (profiles/trsv_sweeps_n8192_m16.md).
+# DRAM bytes (ncu) of a phase's launches.  "solve": one forward + backward
+# pair, bytes per n^2 (n = 8192 capture, scaled by n^2).  "trailing_x3": the
+# ratio of DRAM bytes to algorithmic bytes over every update (and split-K
+# reduction) of one n = 8192 FP32 factorisation; a launch's traffic is that
+# ratio times its algorithmic bytes.
 MEASURED_TRAFFIC = {
-    "solve": ((136968960 + 225792 + 136949248 + 3132928) / 8192 ** 2, "profiles/trsv_sweeps_n8192_m16.md"),
+    "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2, "profiles/trsv_sweeps_n8192_m16.md, scaled by n^2"),
+}
+MEASURED_TRAFFIC_RATIO = {
+    "trailing_x3": (5595882752 / 5.012324e9, "profiles/gemm_x3_fp32_factor_n8192.md, DRAM/algorithmic bytes x this "
+                    "phase's algorithmic bytes per launch"),
 }
 
 
@@ -328,9 +337,11 @@ def roofline(phases, per_kappa, n=None):
         work = ph["flops"] / 2 * DF32_OPS_PER_MADD
     r.update({"frac": r["achieved"] / r["peak"], "kernel_phase": dom, "launches": ph["launches"],
               "avg_launch_ms": ph["ms"] / max(ph["launches"], 1),
-              "traffic": (MEASURED_TRAFFIC[dom][0] * n * n if (dom in MEASURED_TRAFFIC and n) else None),
-              "traffic_source": (MEASURED_TRAFFIC[dom][1] + ", scaled by n^2" if (dom in MEASURED_TRAFFIC and n)
-                                 else None),
+              "traffic": (MEASURED_TRAFFIC[dom][0] * n * n if (dom in MEASURED_TRAFFIC and n)
+                          else MEASURED_TRAFFIC_RATIO[dom][0] * ph["bytes"] / max(ph["launches"], 1)
+                          if dom in MEASURED_TRAFFIC_RATIO else None),
+              "traffic_source": (MEASURED_TRAFFIC[dom][1] if (dom in MEASURED_TRAFFIC and n)
+                                 else MEASURED_TRAFFIC_RATIO[dom][1] if dom in MEASURED_TRAFFIC_RATIO else None),
               "algorithmic_per_launch": work / max(ph["launches"], 1)})
     return r
 
@@ -640,10 +651,10 @@ def main():
         torch.cuda.synchronize()
         e2e_steps = max(1, min(args.steps, 2))
 
-        def host_lane(j, errs):
+        def host_lane(j, errs, steps):
             hh = handles[j]
             try:
-                for _ in range(e2e_steps):
+                for _ in range(steps):
                     for i in range(j, len(systems), len(handles)):
                         st = spd.lib().spd_solve_ir_host(hh, args.n, args.m, hostA[i].data_ptr(), args.n,
                                                          hostB[i].data_ptr(), args.n, hostX[j].data_ptr(), args.n,
@@ -655,20 +666,35 @@ def main():
                 errs.append(e)
 
         import threading
-        errs = []
+
+        def host_steps(steps):
+            errs = []
+            th = [threading.Thread(target=host_lane, args=(j, errs, steps)) for j in range(len(handles))]
+            for x in th:
+                x.start()
+            for x in th:
+                x.join()
+            if errs:
+                raise errs[0]
+
+        host_steps(1)  # untimed: the handles' device copies of A, B, X are allocated here
+        # the host link's rate for one pinned copy of A, alone (untimed; context for the number)
+        tmp = torch.empty((args.n, args.n), dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        c0 = time.perf_counter()
+        tmp.copy_(hostA[0], non_blocking=True)
+        torch.cuda.synchronize()
+        h2d_gbs = 8.0 * args.n * args.n / (time.perf_counter() - c0) / 1e9
+        del tmp
+        barrier(world)
         t0 = time.perf_counter()
-        th = [threading.Thread(target=host_lane, args=(j, errs)) for j in range(len(handles))]
-        for x in th:
-            x.start()
-        for x in th:
-            x.join()
+        host_steps(e2e_steps)
         t = time.perf_counter() - t0
-        if errs:
-            raise errs[0]
         t = max_over_ranks(t, world)
         e2e = {"value": len(systems) * e2e_steps * world / t, "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
-               "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m}
+               "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
+               "h2d_gbs_one_copy": h2d_gbs}
 
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None

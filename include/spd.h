@@ -214,7 +214,10 @@ spd_status spd_solve_ir(spd_handle *h, const spd_factor_t *F, int n, int m,
 
 /* Factor and refine in one call on HOST buffers: copies A and B to the
  * device, runs spd_factor + spd_solve_ir, copies X back (column-major,
- * lda/ldb/ldx >= n).  The device buffers are the library's. */
+ * lda/ldb/ldx >= n).  The device copies of A, B and X are the handle's: they
+ * grow to the largest call and stay allocated until spd_destroy, so repeated
+ * calls neither allocate nor free device memory for them.  Host buffers in
+ * pinned memory copy at the link's full rate.  Returns after X is on the host. */
 spd_status spd_solve_ir_host(spd_handle *h, int n, int m, const double *A_host, int lda,
                              const double *B_host, int ldb, double *X_host, int ldx,
                              int prec, const spd_opts *opts, spd_report *rep);

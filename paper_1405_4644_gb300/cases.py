@@ -8,7 +8,9 @@ time (each case repeats its call so that a profiler can skip the first one):
     python -m paper_1405_4644_gb300.cases convert     # scale + convert and factor, FP32, n = 8192
 
 Inputs are seeded and synthetic (workloads); nothing is checked beyond the
-status codes.
+status codes.  With --phases the library's per-phase records (launches, event
+time, algorithmic flops and bytes, summed over the repetitions) are printed at
+the end, for comparing a profiler's DRAM bytes with the algorithmic bytes.
 """
 from __future__ import annotations
 
@@ -23,6 +25,7 @@ def main(argv=None) -> int:
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--phases", action="store_true")
     a = ap.parse_args(argv)
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import torch
@@ -33,6 +36,8 @@ def main(argv=None) -> int:
     dev = torch.device("cuda", 0)
     h = spd.spd_create(torch.cuda.current_stream())
     n, m = a.n, a.m
+    if a.phases:
+        spd.spd_profile_enable(h, True)
 
     def ok(st):
         if st != spd.SPD_OK:
@@ -69,6 +74,12 @@ def main(argv=None) -> int:
                 ok(spd.spd_factor_solve(h, F, B, R))
             spd.spd_factor_destroy(F)
     torch.cuda.synchronize()
+    if a.phases:
+        for p in spd.PHASES:
+            r = spd.spd_profile_read(h, p)
+            if r["launches"]:
+                print(f"phase {p}: launches {r['launches']} ms {r['ms']:.3f} flops {r['flops']:.6e} "
+                      f"bytes {r['bytes']:.6e} (sum over {a.reps} repetitions)")
     spd.spd_destroy(h)
     print("ok", a.case, n, m)
     return 0

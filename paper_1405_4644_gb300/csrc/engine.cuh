@@ -36,6 +36,8 @@ struct spd_handle {
     int epoch = 0;              // last flag value handed out
     cudaStream_t aux = nullptr; // second stream of the look-ahead factorisation
     std::vector<cudaEvent_t> sync_ev;  // timing-free events for stream joins
+    void* stage = nullptr;      // grow-only device copies of spd_solve_ir_host's A, B, X
+    size_t stage_bytes = 0;
 };
 
 struct spd_factor_t {

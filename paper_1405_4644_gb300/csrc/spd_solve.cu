@@ -77,6 +77,7 @@ extern "C" spd_status spd_destroy(spd_handle* h) {
     cudaEventDestroy(h->e0);
     cudaEventDestroy(h->e1);
     cudaFree(h->ready);
+    cudaFree(h->stage);
     if (h->aux) cudaStreamDestroy(h->aux);
     for (auto e : h->sync_ev) cudaEventDestroy(e);
     for (auto& r : h->prof) {
@@ -1006,17 +1007,20 @@ extern "C" spd_status spd_solve_ir_host(spd_handle* h, int n, int m, const doubl
     if (rep) memset(rep, 0, sizeof(*rep));
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
-    double *dA = nullptr, *dB = nullptr, *dX = nullptr;
-    size_t bytesA = sizeof(double) * (size_t)n * n, bytesB = sizeof(double) * (size_t)n * m;
-    CUDA_TRY(h, cudaMallocAsync(&dA, bytesA, s));
-    CUDA_TRY(h, cudaMallocAsync(&dB, bytesB, s));
-    CUDA_TRY(h, cudaMallocAsync(&dX, bytesB, s));
-    auto release = [&]() {
-        cudaFreeAsync(dA, s);
-        cudaFreeAsync(dB, s);
-        cudaFreeAsync(dX, s);
-        cudaStreamSynchronize(s);
-    };
+    const size_t bytesA = (size_t)round_up((long)(sizeof(double) * (size_t)n * n), 256);
+    const size_t bytesB = (size_t)round_up((long)(sizeof(double) * (size_t)n * m), 256);
+    if (h->stage_bytes < bytesA + 2 * bytesB) {  // grow (the previous call ended synchronised)
+        CUDA_TRY(h, cudaStreamSynchronize(s));
+        cudaFree(h->stage);
+        h->stage = nullptr;
+        h->stage_bytes = 0;
+        CUDA_TRY(h, cudaMalloc(&h->stage, bytesA + 2 * bytesB));
+        h->stage_bytes = bytesA + 2 * bytesB;
+    }
+    double* dA = static_cast<double*>(h->stage);
+    double* dB = reinterpret_cast<double*>(static_cast<char*>(h->stage) + bytesA);
+    double* dX = reinterpret_cast<double*>(static_cast<char*>(h->stage) + bytesA + bytesB);
+    auto release = [&]() { cudaStreamSynchronize(s); };
     cudaError_t e = cudaMemcpy2DAsync(dA, sizeof(double) * n, A_host, sizeof(double) * lda, sizeof(double) * n, n,
                                       cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)

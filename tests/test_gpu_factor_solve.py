@@ -158,6 +158,28 @@ def test_solve_ir_host_buffers(h):
     assert oracle.berr(A, B, X) <= 1e-14
 
 
+def test_solve_ir_host_buffers_grow_and_shrink():
+    """The handle keeps the device copies between host-buffer calls: sizes
+    that grow (the copies are reallocated), shrink (a prefix is reused) and
+    grow again all solve correctly, with strided host A (lda > n)."""
+    import torch
+    hh = spd.spd_create(torch.cuda.current_stream())
+    try:
+        for n, m, seed in [(200, 1, 1), (700, 5, 2), (129, 3, 3), (700, 9, 4), (1000, 2, 5)]:
+            A = W.gram_shifted(n, seed=seed, shift=0.1)
+            # column-major with lda = n + 7: row j of Acm holds column j of A, then 7 pad entries
+            Acm = np.zeros((n, n + 7))
+            Acm[:, :n] = A.T
+            B = np.asfortranarray(W.gaussian_rhs(n, m, seed + 10))
+            X = np.zeros((n, m), order="F")
+            st = spd.lib().spd_solve_ir_host(hh, n, m, Acm.ctypes.data, n + 7, B.ctypes.data, n,
+                                             X.ctypes.data, n, spd.PREC["fp32"], None, None)
+            check(hh, st)
+            assert oracle.berr(A, B, X) <= 1e-14, (n, m)
+    finally:
+        spd.spd_destroy(hh)
+
+
 def test_not_spd_reports_failing_column(h):
     n = 300
     for k in (30, 130, 255):
