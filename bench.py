@@ -132,14 +132,20 @@ class Nvml:
 # distributed plumbing (replicas only: no collective on the data path)
 # ---------------------------------------------------------------------------
 def dist_setup(n_gpus):
+    """rank, world size and local rank from the launcher's environment; for
+    world > 1 a process group over NCCL (one GPU per rank), or over gloo
+    where no GPU is visible (host-side tests of this plumbing)."""
     import torch
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group("gloo")
     elif torch.cuda.is_available():
         torch.cuda.set_device(0)
     return rank, world, local
@@ -156,9 +162,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, world, seconds_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank does the same work)."""
+    return units_per_rank * world / seconds_max
 
 
 # ---------------------------------------------------------------------------
@@ -602,8 +615,7 @@ def main():
     for hh in handles:
         spd.spd_profile_enable(hh, False)
     ms_max = max_over_ranks(ms, world)
-    solves = len(systems) * args.steps * world
-    value = solves / (ms_max / 1e3)
+    value = job_rate(len(systems) * args.steps, world, ms_max / 1e3)
 
     # dominant phase and its roofline
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
@@ -691,7 +703,7 @@ def main():
         host_steps(e2e_steps)
         t = time.perf_counter() - t0
         t = max_over_ranks(t, world)
-        e2e = {"value": len(systems) * e2e_steps * world / t, "unit": UNIT,
+        e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
                "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
                "h2d_gbs_one_copy": h2d_gbs}
