@@ -21,6 +21,10 @@ Every function states the passage of the paper it follows:
 * ``cg``             textbook CG in float64.
 * ``cg_ir``          Algorithm 2 in its nested low/high reading, optionally
   with the banded inner matrix of Section 4.1.
+* ``spectral_solve`` the exact solution of A X = B for a matrix given by its
+  eigendecomposition A = Q diag(lam) Q^T, Q a product of Householder
+  reflections (the Section 5 test matrices with a prescribed spectrum): an
+  O(n k m) reference at sizes where the dense oracle is too slow.
 """
 from __future__ import annotations
 
@@ -203,6 +207,24 @@ def cg_ir(A, B, At=None, band=-1, tol=1e-14, crit="rel", eta=1e-3, maxit_in=5000
                              _p(X), n, float(tol), c, float(eta), int(maxit_in), int(maxit_out),
                              _p(lo), _p(hi), _p(fe))
     return X, lo, hi, fe, not bad
+
+
+def spectral_solve(V, lam, B):
+    """X = Q diag(lam)^{-1} Q^T B for Q = H_1 H_2 ... H_k, H_i = I - 2 v_i v_i^T
+    (v_i the unit columns of V): Q^T B = H_k ... H_1 B, a division by the
+    eigenvalues, then Q Y = H_1 ... H_k Y.  Each reflection is applied as
+    y - 2 v (v^T y), so the result errs by a few k units of roundoff relative
+    to ||X||, whatever the condition number."""
+    V = np.asarray(V, dtype=np.float64)
+    Y = np.array(B, dtype=np.float64).reshape(V.shape[0], -1)
+    for i in range(V.shape[1]):
+        v = V[:, i:i + 1]
+        Y -= 2.0 * v @ (v.T @ Y)
+    Y /= np.asarray(lam, dtype=np.float64)[:, None]
+    for i in reversed(range(V.shape[1])):
+        v = V[:, i:i + 1]
+        Y -= 2.0 * v @ (v.T @ Y)
+    return Y
 
 
 def cpu_threads() -> int:

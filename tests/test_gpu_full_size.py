@@ -1,0 +1,65 @@
+"""Parity at the benchmark's full size, in the configuration it times: n =
+16384, m = 16, the three prescribed-spectrum systems of Section 5 (A = Q
+diag(lambda) Q^T, Q a product of 32 Householder reflections, lambda
+log-spaced in [1, kappa], kappa = 1e2, 1e4, 1e6; right-hand sides N(0, 1)),
+precision AUTO, every residual of Algorithm 1 on the tensor cores, the three
+systems solved concurrently on three handles and high-priority streams.
+
+The dense oracle is too slow at this size, so each solution is judged by:
+- the library's reported normwise backward error (<= 1e-14, the stopping
+  tolerance);
+- the exact residual b - A x of 66 sampled rows (first, last and 64 random
+  ones), correctly rounded by the oracle, whose backward error must meet the
+  same tolerance (a lower bound of the true one);
+- the oracle's solution from the known eigendecomposition (an O(n k m)
+  computation accurate to roundoff whatever kappa is): the forward error may
+  not exceed 1e-12 kappa (the assembly error of A, a few k units of roundoff
+  of ||A||, amplified by kappa, stays far below; a float32-accurate solution
+  would miss it by four orders of magnitude).
+"""
+import numpy as np
+import pytest
+import torch
+
+import bench
+import oracle
+import paper_1405_4644_gb300 as spd
+import workloads as W
+from oracle import exact as E
+
+pytestmark = pytest.mark.gpu
+
+N, M, KAPPAS, K = 16384, 16, (1e2, 1e4, 1e6), 32
+
+
+def test_benchmark_workload_three_lanes():
+    dev = torch.device("cuda", 0)
+    systems, spectra = [], []
+    for i, kappa in enumerate(KAPPAS):  # the benchmark's recipe: seed i, right-hand sides seed 100 + i
+        A, lam, V = W.householder_spectrum(N, kappa, k=K, seed=i, device=dev)
+        B = torch.from_numpy(np.ascontiguousarray(W.gaussian_rhs(N, M, 100 + i).T)).to(dev).t()
+        systems.append((kappa, A, B))
+        spectra.append((lam, V))
+    torch.cuda.synchronize()
+    lanes = bench.Lanes(spd, len(KAPPAS), N, M, dev)
+    try:
+        reps = lanes.run(systems, ["auto"] * len(KAPPAS), {"tol": 1e-14, "crit": "berr", "resid": "tc"}, 1)
+        torch.cuda.synchronize()
+        Xs = [lanes.X[i].cpu().numpy() for i in range(len(KAPPAS))]  # lane i solved system i
+    finally:
+        lanes.destroy()
+    g = np.random.default_rng(7)
+    rows = np.unique(np.concatenate([[0, N - 1], g.choice(N, 64, replace=False)]))
+    for (kappa, A, B), (lam, V), (frep, rep), X in zip(systems, spectra, reps, Xs):
+        assert rep.berr <= 1e-14, (kappa, rep.berr)
+        assert spd.PREC_NAME.get(frep.prec_used) in ("fp16", "fp32"), (kappa, frep.prec_used)
+        Ah = A.cpu().numpy()
+        b = B.cpu().numpy()
+        norm_a = float(np.max(np.sum(np.abs(Ah), axis=1)))
+        r = E.residual_exact(Ah[rows], b[rows], X)
+        berr_rows = np.max(np.max(np.abs(r), axis=0) / (norm_a * np.max(np.abs(X), axis=0)))
+        assert berr_rows <= 1e-14, (kappa, berr_rows)
+        del Ah
+        Xr = oracle.spectral_solve(V, lam, b)
+        fwd = np.max(np.abs(X - Xr)) / np.max(np.abs(Xr))
+        assert fwd <= 1e-12 * kappa, (kappa, fwd)

@@ -379,3 +379,35 @@ def test_exact_residual_beats_float64_residual():
     assert np.max(np.abs(r_64 - r_ex)) > 0  # the float64 residual really rounds
     i = 11
     assert r_ex[i, 0] == E.residual_fraction(A[i:i + 1], b[i:i + 1], x)[0, 0]
+
+
+# --------------------------------------------------------------------------
+# Reference solution from a known eigendecomposition (the prescribed-spectrum
+# test matrices): pinned to LAPACK's solve and to two closed forms
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,k,kappa", [(300, 8, 1e4), (257, 32, 1e2), (64, 1, 1e6)])
+def test_spectral_solve_matches_lapack(n, k, kappa):
+    A, lam, V = W.householder_spectrum(n, kappa, k=k, seed=n)
+    B = W.gaussian_rhs(n, 3, n + 1)
+    X = oracle.spectral_solve(V, lam, B)
+    Xl = np.linalg.solve(A, B)
+    # both solve the assembled A up to its assembly error (a few k u ||A||),
+    # amplified by kappa
+    assert np.max(np.abs(X - Xl)) <= 1e-13 * kappa * np.max(np.abs(Xl))
+    # and the residual against the assembled matrix is at that level too
+    assert np.max(np.abs(B - A @ X)) <= 1e-13 * kappa * np.max(np.abs(B))
+
+
+def test_spectral_solve_closed_forms():
+    n = 50
+    V = W.householder_vectors(n, 4, seed=3)
+    B = W.gaussian_rhs(n, 2, 4)
+    # all eigenvalues 1: A = Q Q^T = I
+    assert np.allclose(oracle.spectral_solve(V, np.ones(n), B), B, rtol=0, atol=1e-14)
+    # a single reflection H = I - 2 v v^T with eigenvalues lam: H diag(lam) H;
+    # its inverse applied to B is H diag(1/lam) H B, formed densely here
+    v = V[:, :1]
+    H = np.eye(n) - 2.0 * v @ v.T
+    lam = np.linspace(1.0, 7.0, n)
+    ref = H @ (np.diag(1.0 / lam) @ (H @ B))
+    assert np.allclose(oracle.spectral_solve(v, lam, B), ref, rtol=0, atol=1e-14 * np.max(np.abs(ref)))
