@@ -15,7 +15,11 @@ The dense oracle is too slow at this size, so each solution is judged by:
   computation accurate to roundoff whatever kappa is): the forward error may
   not exceed 1e-12 kappa (the assembly error of A, a few k units of roundoff
   of ||A||, amplified by kappa, stays far below; a float32-accurate solution
-  would miss it by four orders of magnitude).
+  would miss it by four orders of magnitude);
+- a float64 Cholesky solve of the same assembled matrix on the host (LAPACK):
+  the two solutions may differ by at most 10 kappa 1e-16 max(1, sqrt(n)/8),
+  the bound of the smaller parity tests (two float64 solvers, Cholesky and
+  LU, already differ by 1.7e-15 kappa at n = 8192).
 """
 import numpy as np
 import pytest
@@ -28,6 +32,7 @@ import workloads as W
 from oracle import exact as E
 
 pytestmark = pytest.mark.gpu
+sl = pytest.importorskip("scipy.linalg")
 
 N, M, KAPPAS, K = 16384, 16, (1e2, 1e4, 1e6), 32
 
@@ -59,7 +64,11 @@ def test_benchmark_workload_three_lanes():
         r = E.residual_exact(Ah[rows], b[rows], X)
         berr_rows = np.max(np.max(np.abs(r), axis=0) / (norm_a * np.max(np.abs(X), axis=0)))
         assert berr_rows <= 1e-14, (kappa, berr_rows)
-        del Ah
         Xr = oracle.spectral_solve(V, lam, b)
         fwd = np.max(np.abs(X - Xr)) / np.max(np.abs(Xr))
         assert fwd <= 1e-12 * kappa, (kappa, fwd)
+        c = sl.cho_factor(Ah, lower=True, overwrite_a=True, check_finite=False)
+        Xo = sl.cho_solve(c, b, check_finite=False)
+        del Ah, c
+        fwo = np.max(np.abs(X - Xo)) / np.max(np.abs(Xo))
+        assert fwo <= 10 * kappa * 1e-16 * max(1.0, np.sqrt(N) / 8), (kappa, fwo)
