@@ -158,7 +158,13 @@ typedef struct spd_factor_t spd_factor_t;
 
 /* ---- handle ------------------------------------------------------------ */
 /* Create a handle bound to the current CUDA device and `stream`
- * (a cudaStream_t; NULL = the legacy default stream). */
+ * (a cudaStream_t; NULL = the legacy default stream).  The handle also owns
+ * a second, non-blocking stream at the default (lowest) priority, on which
+ * the factorisation's look-ahead issues its bulk trailing updates; every
+ * call joins it back into `stream` before returning.  Callers that run
+ * several handles concurrently get the most throughput when their own
+ * streams have a higher priority: each solve's critical chain then goes
+ * ahead of the other solves' bulk updates. */
 spd_status spd_create(spd_handle **h, void *stream);
 spd_status spd_destroy(spd_handle *h);
 /* Text of the last failure on h (static storage owned by h; never NULL). */
