@@ -52,3 +52,15 @@ def test_header_compiles_as_c(tmp_path):
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
                         str(tmp_path / "t.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No fallback: with libspd.so absent every entry point raises instead of
+    computing anything elsewhere."""
+    import paper_1405_4644_gb300 as spd
+    monkeypatch.setattr(spd, "_lib", None)
+    monkeypatch.setattr(spd, "_LIB_PATH", os.path.join(os.path.dirname(spd.__file__), "_absent", "libspd.so"))
+    with pytest.raises(spd.SpdError, match="not built"):
+        spd.lib()
+    with pytest.raises(spd.SpdError, match="not built"):
+        spd.spd_create(None)
