@@ -175,9 +175,14 @@ void spd_opts_default(spd_opts *o);
 /* ---- Algorithm 1, step 1: low-precision Cholesky --------------------------
  * Factor A ~= R~^T R~ (Section 3.1, eq. (cholesky), Alg. 1 line 1) in
  * precision `prec`, after the symmetric diagonal scaling D^{-1/2} A D^{-1/2}
- * when flags has SPD_SCALE_DIAG.  Blocked right-looking Cholesky with
- * recursive blocking: 128x128 diagonal-block factorisations, panel
- * triangular solves, and trailing updates A22 -= L21 L21^T.
+ * when flags has SPD_SCALE_DIAG.  Blocked Cholesky over 128-column block
+ * columns: 128x128 diagonal-block factorisations, panel triangular solves
+ * and trailing updates (A22 -= L21 L21^T, as block-column updates).  The
+ * tensor-core precisions use a left-looking schedule whose bulk updates run
+ * one block column ahead on the handle's second stream (SPD_FACTOR_SERIAL:
+ * the same schedule on one stream, bit-identical; SPD_FACTOR_RECURSIVE:
+ * right-looking recursive blocking); FP64 and the CUDA-core engine use the
+ * recursive form.
  * A: n x n, lda >= n, read-only, lower triangle read.  On success *F owns
  * the factor (release with spd_factor_destroy).  AUTO keeps the cheapest
  * factor whose estimated ||A^{-1} dA|| keeps refinement convergent

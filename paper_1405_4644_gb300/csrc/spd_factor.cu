@@ -1,14 +1,20 @@
 // spd_factor.cu -- Algorithm 1 line 1: the low-precision Cholesky
-// factorisation A ~= R~^T R~ (Section 3.1, eq. (cholesky)), blocked
-// right-looking with recursive blocking:
+// factorisation A ~= R~^T R~ (Section 3.1, eq. (cholesky)), in one of two
+// blocked schedules with 128x128 leaves (k_potrf_leaf32 / k_trsm_leaf32;
+// k_potrf_leaf / k_trsm_leaf for FP64):
 //
-//   chol(A)   : chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; chol(A22)
-//   trsm(B,L) : trsm(B1, L11); B2 -= X1 L21^T; trsm(B2, L22)
+// - left-looking over 128-column block columns (potrf_left; the tensor-core
+//   precisions by default): W[k:, k] -= L[k:, 0:k] L[k, 0:k]^T, leaf, panel
+//   solve, with the bulk of each update issued one block column ahead on the
+//   handle's second stream;
+// - recursive (potrf_rec; FP64, the CUDA-core engine, SPD_FACTOR_RECURSIVE):
+//     chol(A)   : chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; chol(A22)
+//     trsm(B,L) : trsm(B1, L11); B2 -= X1 L21^T; trsm(B2, L22)
 //
-// with 128x128 leaves (k_potrf_leaf / k_trsm_leaf) and every off-leaf
-// update a GEMM on the working matrix (tensor cores for TF32/BF16/FP16/FP8
-// and for FP32 as three bf16 slices; CUDA cores for FP64).  Split points are multiples of 128, so only the
-// very last leaf can be ragged.
+// Every off-leaf update is a GEMM on the working matrix (tensor cores for
+// TF32/BF16/FP16/FP8 and for FP32 as three bf16 slices; CUDA cores for
+// FP64).  Split points are multiples of 128, so only the very last leaf can
+// be ragged.
 #include "engine.cuh"
 #include "k_convert.cuh"
 #include "k_leaf.cuh"
