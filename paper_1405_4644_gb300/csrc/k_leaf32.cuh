@@ -7,8 +7,12 @@
 //                    (warp-level pivots) and inverts it by right-looking
 //                    substitution with the pivots' reciprocals; all warps
 //                    form the sub-panel below it with that inverse and
-//                    update the rest of the block.  Stores L (and its
-//                    operand mirror) and the four 32x32 inverses.
+//                    update the rest of the block; only the next diagonal
+//                    block's part of that update precedes the next pivot
+//                    step, and while warp 0 factors it the other warps
+//                    store the finished block column of L (and its operand
+//                    mirror) and finish the update.  Also stores the four
+//                    32x32 inverses.
 //   k_trsm_leaf32    panel solve X L^T = B for 64 rows per CTA in four
 //                    32-column steps with the same 32x32 inverses.
 //   k_block_inverse  after the whole factorisation, off the critical path

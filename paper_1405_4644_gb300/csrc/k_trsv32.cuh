@@ -4,22 +4,25 @@
 //
 // Block J (in sweep order t) is owned by the CTA of rank t mod G among the G
 // CTAs ordered by SM id, which takes its blocks in sweep order.
-// Forward, with t_J = y_J - sum_{K < J-1} L_JK y_K and u_J = L_JJ^{-1} t_J,
+// Forward, with t_J = y_J - sum_{K < J-2} L_JK y_K and u_J = L_JJ^{-1} t_J,
 //
-//   y_J = u_J - M_J y_{J-1},          M_J = L_JJ^{-1} L_{J,J-1},
+//   y_J = u_J - P_J y_{J-2} - M_J y_{J-1},
+//   M_J = L_JJ^{-1} L_{J,J-1},  P_J = L_JJ^{-1} L_{J,J-2},
 //
-// and backward, with v_J = L_JJ^{-T} (z_J - sum_{K > J+1} L_KJ^T z_K),
+// and backward, with v_J = L_JJ^{-T} (z_J - sum_{K > J+2} L_KJ^T z_K),
 //
-//   z_J = v_J - N_J z_{J+1},          N_J = L_JJ^{-T} L_{J+1,J}^T,
+//   z_J = v_J - Q_J z_{J+2} - N_J z_{J+1},
+//   N_J = L_JJ^{-T} L_{J+1,J}^T,  Q_J = L_JJ^{-T} L_{J+2,J}^T,
 //
-// the couplings M_J, N_J being formed once per factor (k_trsv_couplings).
-// Everything but the last product happens while the neighbouring block is
-// still being solved, so one sweep step on the critical path is: acquire the
-// neighbour's flag, one 128x128 by 128xMC product, publish.  The far
-// contributions are summed in a fixed order (forward K = 0..J-2, backward
-// K = NB-1..J+2); each waits with a bounded acquire-load of ready[K].  A wait
-// that exceeds its limit raises SPD_DEV_TIMEOUT and the kernel winds down
-// without publishing.
+// the couplings being formed once per factor (k_trsv_couplings).  The far
+// sum and the diagonal solve happen while the two nearest blocks are still
+// being solved; once block J-2 is published one product is left before
+// block J-1 can be taken, and one sweep step on the critical path is:
+// acquire the neighbour's flag, one 128x128 by 128xMC product, publish.  The
+// far contributions are summed in a fixed order (forward K = 0..J-3,
+// backward K = NB-1..J+3); each waits with a bounded acquire-load of
+// ready[K].  A wait that exceeds its limit raises SPD_DEV_TIMEOUT and the
+// kernel winds down without publishing.
 //
 // Thread (i, h) (i = tid / 2, h = tid % 2) owns row i of the block and the
 // half h of the reduction index: its 64 tile entries go from global memory
