@@ -461,6 +461,65 @@ def batched_leg(args):
     return 0
 
 
+def cg_leg(args):
+    """CG (Algorithm 2, nested reading) on the paper's model covariance of
+    Section 4: A(i,j) = 1/|i-j|^d off the diagonal, 1 + sqrt(i) on it (i
+    1-based), d in {1, 2, 4}; 1 and 32 right-hand sides U[0, 1] (seed 0);
+    stop at ||r||_2 <= 1e-5 as in Table 1; float32 matrix products, float64
+    outer residual.  Per case: solves/s (library device time), the low and
+    high iteration counts, and the matrix products' HBM rate (4 n^2 bytes of
+    the float32 copy per product) against the measured copy bandwidth."""
+    import numpy as np
+    import torch
+    import paper_1405_4644_gb300 as spd
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    h = spd.spd_create(torch.cuda.current_stream())
+    n = args.n_cg
+    peaks, src = load_peaks()
+    idx = torch.arange(n, dtype=torch.float64, device=dev)
+    A = torch.empty((n, n), dtype=torch.float64, device=dev)
+    opts = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000}
+    out = {"leg": "cg", "metric": "CG solves/s (Algorithm 2, float32 products, float64 outer residual)",
+           "unit": "solves/s", "config": {"workload": f"model covariance (Section 4), n={n}, d in (1, 2, 4), "
+                                                      "m in (1, 32), ||r||_2 <= 1e-5", "n": n}}
+    for d in (1, 2, 4):
+        for r0 in range(0, n, 4096):  # assembled in row blocks on the device (untimed)
+            blk = A[r0:r0 + 4096]
+            torch.sub(idx[r0:r0 + 4096, None], idx[None, :], out=blk)
+            blk.abs_().clamp_min_(1.0).pow_(d).reciprocal_()
+        A.diagonal().copy_(1.0 + torch.sqrt(idx + 1.0))
+        for m in (1, 32):
+            B = torch.from_numpy(np.ascontiguousarray(W.uniform_rhs(n, m, 0).T)).to(dev).t()
+            X = torch.zeros(m, n, dtype=torch.float64, device=dev).t()
+            st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)  # warm-up
+            if st != spd.SPD_OK:
+                raise RuntimeError(f"spd_cg d={d} m={m}: {spd.spd_last_error_string(h)}")
+            ms = []
+            spd.spd_profile_enable(h, True)
+            for _ in range(max(1, args.steps)):
+                X.zero_()
+                st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
+                if st != spd.SPD_OK:
+                    raise RuntimeError(f"spd_cg d={d} m={m}: {spd.spd_last_error_string(h)}")
+                ms.append(rep.time_ms)
+            mv = spd.spd_profile_read(h, "matvec")
+            spd.spd_profile_enable(h, False)
+            t = float(np.median(ms))
+            gbs = mv["bytes"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] > 0 else None
+            out[f"d{d}_m{m}"] = {
+                "value": 1e3 / t, "ms_per_solve": t, "iters_low": rep.iters_low, "iters_high": rep.iters_high,
+                "rel_resid": rep.rel_resid,
+                "matvec": {"launches": mv["launches"], "avg_launch_ms": mv["ms"] / max(mv["launches"], 1),
+                           "share_of_solve": mv["ms"] / (t * len(ms)),
+                           "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                                        "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                                        "peak_source": f"{src} copy bandwidth; 4 n^2 bytes per product"}}}
+    spd.spd_destroy(h)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def learned_leg(args):
     """Learned preconditioner on the Matern-3/2 family (n points uniform in the
     unit square, ell ~ U[0.02, 0.5], nugget ~ logU[1e-4, 1e-1]): train on
@@ -540,7 +599,8 @@ def main():
     ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc"],
                     help="refinement residual: float64; float32 pairs until berr < 2^-36 then float64; "
                          "or exact bf16 digit products on the tensor cores")
-    ap.add_argument("--leg", default="main", choices=["main", "batched", "learned"])
+    ap.add_argument("--leg", default="main", choices=["main", "batched", "learned", "cg"])
+    ap.add_argument("--n-cg", type=int, default=16384)
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n-learned", type=int, default=4096)
     ap.add_argument("--train-systems", type=int, default=1000)
@@ -554,6 +614,8 @@ def main():
         return reference_arm(args)
     if args.leg == "batched":
         return batched_leg(args)
+    if args.leg == "cg":
+        return cg_leg(args)
     if args.leg == "learned":
         return learned_leg(args)
 
