@@ -479,10 +479,12 @@ def cg_leg(args):
     peaks, src = load_peaks()
     idx = torch.arange(n, dtype=torch.float64, device=dev)
     A = torch.empty((n, n), dtype=torch.float64, device=dev)
-    opts = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000}
+    base = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000}
+    nvml = Nvml(torch.cuda.current_device())
     out = {"leg": "cg", "metric": "CG solves/s (Algorithm 2, float32 products, float64 outer residual)",
            "unit": "solves/s", "config": {"workload": f"model covariance (Section 4), n={n}, d in (1, 2, 4), "
-                                                      "m in (1, 32), ||r||_2 <= 1e-5", "n": n}}
+                                                      "m in (1, 32), ||r||_2 <= 1e-5; dense and banded "
+                                                      "(half-width 16, Section 4.1) inner products", "n": n}}
     for d in (1, 2, 4):
         for r0 in range(0, n, 4096):  # assembled in row blocks on the device (untimed)
             blk = A[r0:r0 + 4096]
@@ -492,29 +494,35 @@ def cg_leg(args):
         for m in (1, 32):
             B = torch.from_numpy(np.ascontiguousarray(W.uniform_rhs(n, m, 0).T)).to(dev).t()
             X = torch.zeros(m, n, dtype=torch.float64, device=dev).t()
-            st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)  # warm-up
-            if st != spd.SPD_OK:
-                raise RuntimeError(f"spd_cg d={d} m={m}: {spd.spd_last_error_string(h)}")
-            ms = []
-            spd.spd_profile_enable(h, True)
-            for _ in range(max(1, args.steps)):
-                X.zero_()
-                st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
+            for kind, opts in (("dense", base), ("band16", dict(base, band=16))):
+                st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)  # warm-up
                 if st != spd.SPD_OK:
-                    raise RuntimeError(f"spd_cg d={d} m={m}: {spd.spd_last_error_string(h)}")
-                ms.append(rep.time_ms)
-            mv = spd.spd_profile_read(h, "matvec")
-            spd.spd_profile_enable(h, False)
-            t = float(np.median(ms))
-            gbs = mv["bytes"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] > 0 else None
-            out[f"d{d}_m{m}"] = {
-                "value": 1e3 / t, "ms_per_solve": t, "iters_low": rep.iters_low, "iters_high": rep.iters_high,
-                "rel_resid": rep.rel_resid,
-                "matvec": {"launches": mv["launches"], "avg_launch_ms": mv["ms"] / max(mv["launches"], 1),
-                           "share_of_solve": mv["ms"] / (t * len(ms)),
-                           "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peaks["hbm_gbs"],
-                                        "frac": gbs / peaks["hbm_gbs"] if gbs else None,
-                                        "peak_source": f"{src} copy bandwidth; 4 n^2 bytes per product"}}}
+                    raise RuntimeError(f"spd_cg d={d} m={m} {kind}: {spd.spd_last_error_string(h)}")
+                ms = []
+                spd.spd_profile_enable(h, True)
+                torch.cuda.synchronize()
+                e0 = nvml.energy_mj() if nvml.ok else None
+                for _ in range(max(1, args.steps)):
+                    X.zero_()
+                    st, rep = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
+                    if st != spd.SPD_OK:
+                        raise RuntimeError(f"spd_cg d={d} m={m} {kind}: {spd.spd_last_error_string(h)}")
+                    ms.append(rep.time_ms)
+                torch.cuda.synchronize()
+                e1 = nvml.energy_mj() if nvml.ok else None
+                mv = spd.spd_profile_read(h, "matvec")
+                spd.spd_profile_enable(h, False)
+                t = float(np.median(ms))
+                gbs = mv["bytes"] / (mv["ms"] * 1e-3) / 1e9 if mv["ms"] > 0 else None
+                out[f"d{d}_m{m}_{kind}"] = {
+                    "value": 1e3 / t, "ms_per_solve": t, "iters_low": rep.iters_low, "iters_high": rep.iters_high,
+                    "rel_resid": rep.rel_resid,
+                    "j_per_solve": (e1 - e0) / 1e3 / len(ms) if e0 is not None and e1 is not None else None,
+                    "matvec": {"launches": mv["launches"], "avg_launch_ms": mv["ms"] / max(mv["launches"], 1),
+                               "share_of_solve": mv["ms"] / (t * len(ms)),
+                               "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs,
+                                            "peak": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"] if gbs else None,
+                                            "peak_source": f"{src} copy bandwidth; float32 entries read per product"}}}
     spd.spd_destroy(h)
     print(json.dumps(out), flush=True)
     return 0

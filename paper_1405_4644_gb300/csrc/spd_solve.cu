@@ -740,9 +740,13 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             switch (cs.matvec) {
                 case MV_FP32: mv_dispatch<float>(h, cs, n, m, w.Pf, w.Q); break;
                 case MV_BF16: mv_dispatch<__nv_bfloat16>(h, cs, n, m, w.Pf, w.Q); break;
-                case MV_BAND:
-                ++(h)->launches, k_matvec_band<<<gv, 256, 0, s>>>(static_cast<const float*>(cs.At), n, cs.band, w.Pf, m, w.Q);
+                case MV_BAND: {  // (2b + 1) n float32 entries of the band per product
+                    ProfScope ps(h, SPD_PHASE_MATVEC, 2.0 * (2.0 * cs.band + 1.0) * n * m,
+                                 4.0 * (2.0 * cs.band + 1.0) * n, s);
+                    ++(h)->launches, k_matvec_band<<<gv, 256, 0, s>>>(static_cast<const float*>(cs.At), n, cs.band,
+                                                                       w.Pf, m, w.Q);
                     break;
+                }
                 default:
                     st = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1, o.resid);
                     if (st != SPD_OK) return st;
