@@ -6,6 +6,10 @@
 // row-major with the panel rows K-contiguous; products and sums are in T.
 // With `lower` set (a SYRK on a diagonal block, r0 == c0) only entries with
 // r >= c are updated and tiles entirely above the diagonal are skipped.
+// W and Op may be the same array: the columns written, [c0, c0 + N), and the
+// columns read, [k0, k0 + K), are disjoint (the panel lies left of the block
+// it updates, k0 + K <= c0), so no element is reached through both
+// restrict-qualified pointers.
 #pragma once
 #include "common.cuh"
 

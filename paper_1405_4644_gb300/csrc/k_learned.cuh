@@ -113,9 +113,11 @@ __device__ __forceinline__ float silu_grad(float x) {
     return s * (1.f + x * (1.f - s));
 }
 
-// Z (pre-activation, rows x N) += bias; H = silu(Z) (optionally bf16-rounded)
-static __global__ void k_bias_act(float* __restrict__ Z, const float* __restrict__ b, float* __restrict__ H, int rows,
-                                  int N, int act, int bf16) {
+// Z (pre-activation, rows x N) += bias; H = silu(Z) (act = 1) or Z, optionally
+// rounded to bf16.  H may be Z (the output layer works in place), so neither
+// is restrict-qualified.
+static __global__ void k_bias_act(float* Z, const float* __restrict__ b, float* H, int rows, int N, int act,
+                                  int bf16) {
     long total = (long)rows * N;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
         const int c = (int)(e % N);
