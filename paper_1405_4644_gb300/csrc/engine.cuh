@@ -96,7 +96,7 @@ struct WsPlan {
     }
 };
 
-static spd_status ws_reserve(spd_handle* h, size_t bytes) {
+static inline spd_status ws_reserve(spd_handle* h, size_t bytes) {
     if (bytes <= h->ws_bytes) return SPD_OK;
     if (h->ws) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -122,7 +122,7 @@ static inline int grid_for(long work, int threads, int cap) {
 }
 
 // Read and clear the device status word; map to spd_status.
-static spd_status check_dev_status(spd_handle* h, spd_report* rep, const char* what) {
+static inline spd_status check_dev_status(spd_handle* h, spd_report* rep, const char* what) {
     DevStatus* hs = static_cast<DevStatus*>(h->pinned);
     CUDA_TRY(h, cudaMemcpyAsync(hs, h->dst, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
