@@ -293,22 +293,20 @@ FP32_OPS_PEAK_T = 152 * 2.07e9 * 128 / 1e12
 DF32_OPS_PER_MADD = 12
 
 
-# DRAM bytes (read + write) per phase launch from an ncu capture of a smaller
-# case, per unit of n^2 (the kernels stream a fixed number of bytes per entry
-# of A or of the factor): {phase: (bytes per n^2, source)}.  The forward and
-# backward sweeps of one solve at n = 8192, m = 16 read 136.97 + 136.95 MB and
-# wrote 0.23 + 3.13 MB (profiles/trsv_sweeps_n8192_m16.md).
-# DRAM bytes (ncu) of a phase's launches.  "solve": one forward + backward
-# pair, bytes per n^2 (n = 8192 capture, scaled by n^2).  "trailing_x3": the
-# ratio of DRAM bytes to algorithmic bytes over every update (and split-K
-# reduction) of one n = 8192 FP32 factorisation; a launch's traffic is that
-# ratio times its algorithmic bytes.
+# DRAM bytes (read + write, ncu) of a phase's launches, measured on a smaller
+# case of the same kernels.  "solve": one forward + backward sweep pair at
+# n = 8192, m = 16 read 137.10 + 136.97 MB and wrote 0.22 + 3.12 MB; the
+# sweeps stream the factor once each, so the bytes scale with n^2.
+# "trailing_x3": the ratio of DRAM bytes to algorithmic bytes over every
+# update (and split-K reduction) of one n = 8192 FP32 factorisation; a
+# launch's traffic is that ratio times its algorithmic bytes.
 MEASURED_TRAFFIC = {
-    "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2, "profiles/trsv_sweeps_n8192_m16.md, scaled by n^2"),
+    "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2,
+              "ncu DRAM bytes of one forward + backward sweep pair at n = 8192, m = 16, scaled by n^2"),
 }
 MEASURED_TRAFFIC_RATIO = {
-    "trailing_x3": (5595882752 / 5.012324e9, "profiles/gemm_x3_fp32_factor_n8192.md, DRAM/algorithmic bytes x this "
-                    "phase's algorithmic bytes per launch"),
+    "trailing_x3": (5595882752 / 5.012324e9, "ncu DRAM bytes / algorithmic bytes over one n = 8192 FP32 "
+                    "factorisation's updates, times this phase's algorithmic bytes per launch"),
 }
 
 
@@ -589,6 +587,78 @@ def learned_leg(args):
     return 0
 
 
+def case_leg(args):
+    """One kernel family at a time, for profilers (each case repeats its call
+    so that a profiler can skip the first one); seeded synthetic inputs,
+    nothing checked beyond the status codes.  With --phases the library's
+    per-phase records (launches, event time, algorithmic flops and bytes,
+    summed over the repetitions) are printed, for comparing a profiler's DRAM
+    bytes with the algorithmic bytes.
+      gemm        tcgen05 update C -= A B^T, BF16 operands, M = N = K = n
+      resid_fp64  float64 residual, n x n, m right-hand sides
+      resid_tc    tensor-core residual (digit planes and products)
+      sweeps      triangular sweeps of an FP16 factor, m right-hand sides
+      convert     scale + convert and the whole FP32 factorisation
+      factor      the factorisation in --precs (serial schedule: kernels alone)"""
+    import torch
+    import paper_1405_4644_gb300 as spd
+    import workloads as W
+
+    dev = torch.device("cuda", 0)
+    h = spd.spd_create(torch.cuda.current_stream())
+    n, m = args.n, args.m
+    if args.phases:
+        spd.spd_profile_enable(h, True)
+
+    def ok(st):
+        if st != spd.SPD_OK:
+            raise RuntimeError(spd.spd_last_error_string(h))
+
+    g = torch.Generator(device=dev).manual_seed(0)
+    if args.case == "gemm":
+        A = torch.rand(n, n, device=dev, generator=g) - 0.5
+        C = torch.zeros(n, n, device=dev)
+        for _ in range(args.reps):
+            ok(spd.spd_gemm_update(h, "bf16", A, A, C))
+    else:
+        if args.case == "resid_fp64":
+            A = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+            A = A + A.T
+        else:
+            A, _, _ = W.householder_spectrum(n, args.kappas[0], k=16, seed=0, device=dev)
+        X = torch.randn(m, n, dtype=torch.float64, device=dev, generator=g).t()
+        B = torch.randn(m, n, dtype=torch.float64, device=dev, generator=g).t()
+        R = torch.zeros(m, n, dtype=torch.float64, device=dev).t()
+        for _ in range(args.reps):
+            if args.case == "resid_fp64":
+                ok(spd.spd_residual(h, A, B, X, R))
+            elif args.case == "resid_tc":
+                ok(spd.spd_residual_tc(h, A, B, X, R))
+            elif args.case in ("convert", "factor"):
+                prec = "fp32" if args.case == "convert" else args.precs.split(",")[0]
+                flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_SERIAL if args.case == "factor" else 0)
+                st, F, rep = spd.spd_factor(h, A, prec, flags)
+                ok(st)
+                print(f"factor {prec} n={n}: {rep.time_ms:.3f} ms")
+                spd.spd_factor_destroy(F)
+        if args.case == "sweeps":
+            st, F, _ = spd.spd_factor(h, A, "fp16")
+            ok(st)
+            for _ in range(args.reps):
+                ok(spd.spd_factor_solve(h, F, B, R))
+            spd.spd_factor_destroy(F)
+    torch.cuda.synchronize()
+    if args.phases:
+        for p in spd.PHASES:
+            r = spd.spd_profile_read(h, p)
+            if r["launches"]:
+                print(f"phase {p}: launches {r['launches']} ms {r['ms']:.3f} flops {r['flops']:.6e} "
+                      f"bytes {r['bytes']:.6e} (sum over {args.reps} repetitions)")
+    spd.spd_destroy(h)
+    print("ok", args.case, n, m)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -613,6 +683,11 @@ def main():
     ap.add_argument("--n-learned", type=int, default=4096)
     ap.add_argument("--train-systems", type=int, default=1000)
     ap.add_argument("--test-systems", type=int, default=32)
+    ap.add_argument("--case", default=None,
+                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "convert", "factor"],
+                    help="run one kernel family on a fixed case (for profilers) and exit")
+    ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
+    ap.add_argument("--phases", action="store_true", help="--case: print the library's phase records")
     args = ap.parse_args()
     args.kappas = [float(k) for k in args.kappas.split(",")]
     precs = args.precs.split(",")
@@ -620,6 +695,8 @@ def main():
         precs = precs * len(args.kappas)
     if args.impl == "reference":
         return reference_arm(args)
+    if args.case:
+        return case_leg(args)
     if args.leg == "batched":
         return batched_leg(args)
     if args.leg == "cg":

@@ -56,11 +56,15 @@ typedef enum spd_status {
 
 /* Precision of the low-precision work (Section 3.1, "~" quantities).
  * FP64 is the plain baseline: the whole factorisation in float64.
- * FP32 keeps the factor and its updates in float32 (SIMT).
+ * FP32 keeps the factor in float32 and computes its trailing updates to
+ * float32 accuracy on the tensor cores, each float32 operand split into
+ * three bf16 slices (see spd_gemm_update); SPD_FACTOR_CUDA_CORES runs them
+ * as plain float32 products on the CUDA cores instead.
  * TF32/BF16/FP16/FP8 keep the factor in float32 but feed the trailing
  * updates to the tensor cores with operands rounded (RNE) to that type and
- * float32 accumulation; FP8 is OCP E4M3 with one power-of-two scale per
- * 128-row tile.  AUTO picks per matrix (see spd_factor). */
+ * float32 accumulation; FP8 is OCP E4M3 with one fixed power-of-two operand
+ * scale (2^8: every entry of the scaled factor has magnitude <= 1).  AUTO
+ * picks per matrix (see spd_factor). */
 typedef enum spd_prec {
     SPD_PREC_FP64 = 0,
     SPD_PREC_FP32 = 1,
@@ -150,7 +154,9 @@ typedef struct spd_report {
     double rel_resid;/* final max-over-columns ||r||_2 / ||b||_2             */
     double time_ms;  /* device time of the call (CUDA events)                */
     double cond_est; /* spd_factor with AUTO: estimated 1-norm condition
-                        number of the scaled matrix (Hager's estimator), or 0 */
+                        number of the scaled matrix (Hager's estimator);
+                        -1 when the FP16 factor broke down before it could
+                        be estimated; 0 for the other precisions           */
 } spd_report;
 
 typedef struct spd_handle spd_handle;
@@ -292,12 +298,15 @@ spd_status spd_residual_tc(spd_handle *h, int n, int m, const double *A, int lda
  * library keeps until exit.  Limit: n*m + 3*m*ceil(n/256) float64 values
  * must fit in that array (n*m up to about 2.09 million); larger problems
  * return SPD_ERR_SCRATCH.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make it
- * before any stream capture.  All calls share the array and it keeps the
- * last call's contents (no part of it has to start at zero); calls that
- * overlap on the GPU race on it and must be serialised by the caller.
- * Ordered on `stream` (a cudaStream_t, NULL = legacy default stream);
- * synchronous.  This entry point has no counterpart in the paper. */
+ * device address (cudaGetSymbolAddress) with that device current and keeps
+ * it for the life of the process; make that first call before any stream
+ * capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of it.  All calls share the array and it keeps the last
+ * call's contents (no part of it has to start at zero); calls that overlap
+ * on the GPU race on it and must be serialised by the caller.  Ordered on
+ * `stream` (a cudaStream_t, NULL = legacy default stream); returns after
+ * that stream has drained.  This entry point has no counterpart in the
+ * paper. */
 spd_status spd_residual_static(void *stream, int n, int m, const double *A, int lda,
                                const double *B, int ldb, const double *X, int ldx, double *R,
                                int ldr, double *colnorms);

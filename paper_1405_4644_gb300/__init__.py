@@ -154,10 +154,46 @@ def colmajor(t):
     return t.data_ptr(), t.stride(1), n, m
 
 
-def _sym(A):
+def _need_dev(t, name, dtype="float64"):
+    """Reject what the kernels would misread: a host tensor, another dtype,
+    or a tensor on a device other than the current one."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a torch tensor on the GPU")
+    want = getattr(torch, dtype)
+    if t.dtype != want:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.device.type != "cuda":
+        raise ValueError(f"{name} must be on a CUDA device")
+    if t.device.index is not None and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
+def _cols(t, name, n, m=None, dtype="float64"):
+    """colmajor() of a device block that must have n rows (and m columns)."""
+    _need_dev(t, name, dtype)
+    p, ld, rows, cols = colmajor(t)
+    if rows != n or (m is not None and cols != m):
+        raise ValueError(f"{name} has shape ({rows}, {cols}), expected ({n}, {m if m is not None else cols})")
+    return p, ld, rows, cols
+
+
+def _norms(colnorms, m):
+    """Pointer of the optional per-column norm buffer: 3*m float64 values."""
+    if colnorms is None:
+        return None
+    _need_dev(colnorms, "colnorms")
+    if not colnorms.is_contiguous() or colnorms.numel() < 3 * m:
+        raise ValueError(f"colnorms must be contiguous with at least 3*m = {3 * m} float64 values")
+    return colnorms.data_ptr()
+
+
+def _sym(A, dtype="float64"):
     """Pointer and lda of a symmetric matrix given as a C- or F-contiguous tensor."""
+    _need_dev(A, "A", dtype)
     n = A.shape[0]
-    if A.shape != (n, n):
+    if A.dim() != 2 or A.shape != (n, n):
         raise ValueError("A must be square")
     if A.is_contiguous():
         return A.data_ptr(), max(A.stride(0), 1) if n > 1 else 1, n
@@ -254,8 +290,8 @@ def spd_factor_copy(F, L=None, d=None):
 
 def spd_solve_ir(h, F, A, B, X, opts=None):
     pA, lda, n = _sym(A)
-    pB, ldb, nb, m = colmajor(B)
-    pX, ldx, nx, mx = colmajor(X)
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
     rep = SpdReport()
     st = lib().spd_solve_ir(h, F, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), C.byref(rep))
     return st, rep
@@ -280,44 +316,45 @@ def spd_solve_ir_host(h, A, B, X, prec="fp32", opts=None):
 
 
 def spd_factor_solve(h, F, R, Z):
-    pR, ldr, n, m = colmajor(R)
-    pZ, ldz, _, _ = colmajor(Z)
+    n_f, _ = spd_factor_info(F)
+    pR, ldr, n, m = _cols(R, "R", n_f)
+    pZ, ldz, _, _ = _cols(Z, "Z", n, m)
     return lib().spd_factor_solve(h, F, n, m, pR, ldr, pZ, ldz)
 
 
 def spd_residual(h, A, B, X, R, colnorms=None):
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
-    pR, ldr, _, _ = colmajor(R)
-    pc = colnorms.data_ptr() if colnorms is not None else None
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
+    pR, ldr, _, _ = _cols(R, "R", n, m)
+    pc = _norms(colnorms, m)
     return lib().spd_residual(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
 
 
 def spd_residual_df32(h, A, B, X, R, colnorms=None):
     """R = B - A X on the float32 units with error-free transformations."""
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
-    pR, ldr, _, _ = colmajor(R)
-    pc = colnorms.data_ptr() if colnorms is not None else None
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
+    pR, ldr, _, _ = _cols(R, "R", n, m)
+    pc = _norms(colnorms, m)
     return lib().spd_residual_df32(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
 
 
 def spd_residual_tc(h, A, B, X, R, colnorms=None):
     """R = B - A X from exact bf16 digit products on the tensor cores."""
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
-    pR, ldr, _, _ = colmajor(R)
-    pc = colnorms.data_ptr() if colnorms is not None else None
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
+    pR, ldr, _, _ = _cols(R, "R", n, m)
+    pc = _norms(colnorms, m)
     return lib().spd_residual_tc(h, n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
 
 
 def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
     rep = SpdReport()
     pcv = PC[pc] if isinstance(pc, str) else int(pc)
     st = lib().spd_cg(h, n, m, pA, lda, _prec(matvec_prec), pcv, pc_data, pB, ldb, pX, ldx, _opts(opts),
@@ -355,8 +392,14 @@ def spd_launch_count(h):
 def spd_gemm_update(h, prec, A, B, C, lower=False):
     """C -= round(A) round(B)^T on the tensor cores; float32 row-major device
     tensors A (M, K), B (N, K), C (M, N)."""
+    for t, nm in ((A, "A"), (B, "B"), (C, "C")):
+        _need_dev(t, nm, "float32")
+        if t.dim() != 2 or t.stride(1) != 1:
+            raise ValueError(f"{nm} must be a row-major 2-D float32 tensor")
     M, K = A.shape
     N = B.shape[0]
+    if B.shape[1] != K or tuple(C.shape) != (M, N):
+        raise ValueError(f"shapes A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)} do not match")
     return lib().spd_gemm_update(h, _prec(prec), M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                  C.data_ptr(), C.stride(0), 1 if lower else 0)
 
@@ -364,10 +407,10 @@ def spd_gemm_update(h, prec, A, B, C, lower=False):
 def spd_residual_static(stream, A, B, X, R, colnorms=None):
     """R = B - A X through the allocation-free entry point (fixed scratch)."""
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
-    pR, ldr, _, _ = colmajor(R)
-    pc = colnorms.data_ptr() if colnorms is not None else None
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
+    pR, ldr, _, _ = _cols(R, "R", n, m)
+    pc = _norms(colnorms, m)
     return lib().spd_residual_static(_stream_ptr(stream), n, m, pA, lda, pB, ldb, pX, ldx, pR, ldr, pc)
 
 
@@ -443,12 +486,23 @@ def spd_mlp_params(net, out=None, inp=None, grad=None):
 
 def spd_learned_features(h, A, coords, ell, nugget, F):
     pA, lda, n = _sym(A)
+    _need_dev(coords, "coords")
+    _need_dev(F, "F", "float32")
+    if not coords.is_contiguous() or coords.numel() < 2 * n or not F.is_contiguous() or F.numel() < 16 * n:
+        raise ValueError("coords must hold n x 2 float64 and F n x 16 float32 values, both contiguous")
     return lib().spd_learned_features(h, n, pA, lda, coords.data_ptr(), float(ell), float(nugget), F.data_ptr())
 
 
 def spd_mlp_loss_grad(net, A, F, Z, T=None, wsup=0.0):
     pA, lda, n = _sym(A)
-    pZ, ldz, _, p = colmajor(Z)
+    pZ, ldz, _, p = _cols(Z, "Z", n)
+    _need_dev(F, "F", "float32")
+    if not F.is_contiguous() or F.numel() < 16 * n:
+        raise ValueError("F must hold n x 16 contiguous float32 features")
+    if T is not None:
+        _need_dev(T, "T")
+        if not T.is_contiguous() or T.numel() < n:
+            raise ValueError("T must hold n contiguous float64 values")
     if ldz != n:
         raise ValueError("probe block must have leading dimension n")
     loss = C.c_double()
@@ -462,14 +516,18 @@ def spd_mlp_adam(net, lr):
 
 def spd_lowrank_build(net, A, F):
     pA, lda, n = _sym(A)
+    _need_dev(F, "F", "float32")
+    if not F.is_contiguous() or F.numel() < 16 * n:
+        raise ValueError("F must hold n x 16 contiguous float32 features")
     P = C.c_void_p()
     st = lib().spd_lowrank_build(net, n, pA, lda, F.data_ptr(), C.byref(P))
     return st, (P if st == SPD_OK else None)
 
 
 def spd_lowrank_apply(P, R, Z):
+    _need_dev(R, "R")
     pR, ldr, n, m = colmajor(R)
-    pZ, ldz, _, _ = colmajor(Z)
+    pZ, ldz, _, _ = _cols(Z, "Z", n, m)
     return lib().spd_lowrank_apply(P, m, pR, ldr, pZ, ldz)
 
 
@@ -479,8 +537,8 @@ def spd_lowrank_destroy(P):
 
 def spd_solve_learned(h, P, A, B, X, opts=None):
     pA, lda, n = _sym(A)
-    pB, ldb, _, m = colmajor(B)
-    pX, ldx, _, _ = colmajor(X)
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
     rep = SpdReport()
     st = lib().spd_solve_learned(h, P, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), C.byref(rep))
     return st, rep

@@ -460,12 +460,15 @@ extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda,
         // symmetric matrix).
         used = SPD_PREC_FP16;
         st = factor_once(h, n, A, lda, SPD_PREC_FP16, flags, F, rep);
+        if (st == SPD_ERR_NOT_SPD) kappa = -1.0;  // the FP16 factor broke down before any estimate
         if (st == SPD_OK && n > 0) {
             st = cond_estimate(h, *F, A, lda, &kappa);
-            if (st == SPD_OK && !(kappa / sqrt((double)n) * 0x1p-11 <= 0.25)) {
+            if (st != SPD_OK || !(kappa / sqrt((double)n) * 0x1p-11 <= 0.25)) {
+                // too ill-conditioned for FP16, or the estimate itself failed:
+                // no factor is handed out on either path
                 spd_factor_destroy(*F);
                 *F = nullptr;
-                st = SPD_ERR_NOT_SPD;
+                if (st == SPD_OK) st = SPD_ERR_NOT_SPD;
             }
         }
         if (st == SPD_ERR_NOT_SPD) {

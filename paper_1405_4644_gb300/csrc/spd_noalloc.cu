@@ -14,12 +14,15 @@
 // Every GPU that loads the library holds it until the process exits.  Host
 // code cannot use the array's name as a device address, so the first call on
 // each device looks the address up with cudaGetSymbolAddress (with that
-// device current) and caches it; make that first call before any stream
-// capture.  All calls share the array and it keeps the last call's partial
-// sums: calls whose work overlaps on the GPU (two streams, or two host
-// threads) race on it and must be serialised by the caller.  Nothing in the
-// array has to start at zero: each call writes every partial sum before it
-// reads it.
+// device current) and caches it for the life of the process; make that first
+// call before any stream capture.  The cache assumes the device's context
+// lives as long as the process: a program that calls cudaDeviceReset on a
+// device must not call this entry point on that device afterwards.  All calls
+// share the array and it keeps the last call's partial sums: calls whose work
+// overlaps on the GPU (two streams, or two host threads) race on it and must
+// be serialised by the caller.  Nothing in the array has to start at zero:
+// each call writes every partial sum before it reads it.  The call returns
+// after `stream` has drained.
 #include <mutex>
 #include "engine.cuh"
 #include "k_resid.cuh"
@@ -58,6 +61,9 @@ extern "C" spd_status spd_residual_static(void* stream, int n, int m, const doub
     if (n < 0 || m < 0) return SPD_ERR_ARG;
     if (n == 0 || m == 0) return SPD_OK;
     if (!A || !B || !X || !R || lda < n || ldb < n || ldx < n || ldr < n) return SPD_ERR_ARG;
+    // launch errors are read back below; clear one left by unrelated earlier
+    // work so that it is not reported as this call's
+    (void)cudaGetLastError();
     const size_t cap = SPD_NOALLOC_SCRATCH_BYTES / sizeof(double);
     const int G = ceil_div(n, 256);
     const size_t np = (size_t)G * m * 3;        // block partial norms

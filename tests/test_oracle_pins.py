@@ -63,6 +63,65 @@ def test_potrf_backward_invariant(n):
     np.testing.assert_allclose(R, L.T, rtol=0, atol=50 * n * U64 * np.abs(L).max())
 
 
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("n", [1, 7, 17, 64])
+def test_potrf_f32_min_matrix_closed_form(n):
+    # every step of the single-precision factor of min(i, j) is exact in float32
+    i = np.arange(1, n + 1)
+    A = np.minimum(i[:, None], i[None, :]).astype(float)
+    R = oracle.potrf_f32(A)
+    assert R.dtype == np.float32
+    assert np.array_equal(R, np.triu(np.ones((n, n), dtype=np.float32)))
+
+
+@pytest.mark.parametrize("n", [33, 200])
+def test_potrf_f32_backward_bound_and_lapack_single(n):
+    import scipy.linalg as sl
+    A = W.gram_shifted(n, seed=5)
+    R = oracle.potrf_f32(A).astype(np.float64)
+    # backward error of a single-precision Cholesky: ||R^T R - A|| <= c n u32 ||A||
+    rel = np.linalg.norm(R.T @ R - A) / np.linalg.norm(A)
+    assert rel <= 2 * n * U32
+    # and it is a single-precision factor, not a float64 one rounded at the end
+    R64 = oracle.potrf(A)
+    assert np.max(np.abs(R - R64)) > 4 * U64 * np.abs(R64).max()
+    # LAPACK's spotrf (scipy on a float32 matrix) agrees to the single-precision level
+    Rl = sl.cholesky(A.astype(np.float32), lower=False).astype(np.float64)
+    assert Rl.dtype == np.float64
+    kappa = np.linalg.cond(A)
+    np.testing.assert_allclose(R, Rl, rtol=0, atol=10 * n * U32 * kappa * np.abs(Rl).max())
+
+
+def test_potrs_f32_exact_on_integer_factor():
+    # R = triu(ones) (the factor of min(i, j)) with an integer right-hand side:
+    # both substitutions stay in small integers, exact in float32
+    n = 17
+    i = np.arange(1, n + 1)
+    A = np.minimum(i[:, None], i[None, :]).astype(float)
+    x = np.arange(-8, 9, dtype=float)[:, None] * np.array([[1.0, -2.0]])
+    R = np.triu(np.ones((n, n), dtype=np.float32))
+    X = oracle.potrs_f32(R, A @ x)
+    assert np.array_equal(X, x)
+
+
+@pytest.mark.parametrize("n", [50, 300])
+def test_potrs_f32_matches_float64_substitution_of_the_same_factor(n):
+    import scipy.linalg as sl
+    A = W.gram_shifted(n, seed=6)
+    R = oracle.potrf_f32(A)
+    B = W.gaussian_rhs(n, 3, 8)
+    X = oracle.potrs_f32(R, B)
+    R64 = R.astype(np.float64)
+    Y = sl.solve_triangular(R64, B, trans="T", lower=False)
+    X64 = sl.solve_triangular(R64, Y, lower=False)
+    kappa = np.linalg.cond(R64) ** 2
+    assert np.max(np.abs(X - X64)) <= 4 * n * U32 * kappa * np.max(np.abs(X64))
+    # single-precision solves: they are not float64-accurate either
+    assert np.max(np.abs(X - X64)) > 4 * U64 * np.max(np.abs(X64))
+
+
 def test_potrf_not_spd_reports_column():
     A = np.eye(5)
     A[3, 3] = -1.0
