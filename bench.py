@@ -599,7 +599,8 @@ def case_leg(args):
       resid_tc    tensor-core residual (digit planes and products)
       sweeps      triangular sweeps of an FP16 factor, m right-hand sides
       convert     scale + convert and the whole FP32 factorisation
-      factor      the factorisation in --precs (serial schedule: kernels alone)"""
+      factor      the factorisation in --precs (look-ahead schedule)
+      factor_serial  the same on one stream (every kernel alone, for phase rates)"""
     import torch
     import paper_1405_4644_gb300 as spd
     import workloads as W
@@ -634,9 +635,9 @@ def case_leg(args):
                 ok(spd.spd_residual(h, A, B, X, R))
             elif args.case == "resid_tc":
                 ok(spd.spd_residual_tc(h, A, B, X, R))
-            elif args.case in ("convert", "factor"):
+            elif args.case in ("convert", "factor", "factor_serial"):
                 prec = "fp32" if args.case == "convert" else args.precs.split(",")[0]
-                flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_SERIAL if args.case == "factor" else 0)
+                flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_SERIAL if args.case == "factor_serial" else 0)
                 st, F, rep = spd.spd_factor(h, A, prec, flags)
                 ok(st)
                 print(f"factor {prec} n={n}: {rep.time_ms:.3f} ms")
@@ -684,7 +685,7 @@ def main():
     ap.add_argument("--train-systems", type=int, default=1000)
     ap.add_argument("--test-systems", type=int, default=32)
     ap.add_argument("--case", default=None,
-                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "convert", "factor"],
+                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "convert", "factor", "factor_serial"],
                     help="run one kernel family on a fixed case (for profilers) and exit")
     ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
     ap.add_argument("--phases", action="store_true", help="--case: print the library's phase records")

@@ -446,7 +446,11 @@ typedef enum spd_phase {
                                   on the tensor cores (flops counted once) */
     SPD_PHASE_RESID_DF32 = 10, /* A5/C3 on the float32 units (float32 pairs) */
     SPD_PHASE_RESID_TC = 11,   /* A5/C3 on the tensor cores (bf16 digits)     */
-    SPD_PHASE_COUNT = 12
+    SPD_PHASE_TRAILING_LAST = 12, /* A3: the rank-128 updates on the
+                                     factorisation's critical path (the
+                                     last update of each block column before
+                                     its diagonal block is factored)        */
+    SPD_PHASE_COUNT = 13
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

@@ -3,14 +3,28 @@
 // eq. (cholesky); the O(n^3) part that "stresses the components to their
 // limits").
 //
-// One CTA computes a 128 x 256 tile of C.  Operand tiles (128 rows of A,
-// 256 rows of B, 128 bytes of K each) are fetched by TMA into shared memory
-// in the 128-byte swizzled K-major layout, through a 4-stage mbarrier
-// pipeline: warp 0 (one thread) issues the loads, warp 1 (one thread) issues
-// tcgen05.mma into a 128 x 256 float32 accumulator in tensor memory and
-// frees each stage with tcgen05.commit.  The four warps then read the
-// accumulator with tcgen05.ld (warp w owns TMEM lanes 32w..32w+31, i.e. rows
-// of the tile) and apply C -= scale * acc to float32 C in global memory.
+// One CTA computes a 128 x BNT tile of C (BNT = 256, or 128 for one block
+// column).  Operand tiles (128 rows of A, BNT rows of B, 128 bytes of K each)
+// are fetched by TMA into shared memory in the 128-byte swizzled K-major
+// layout, through a multi-stage mbarrier pipeline: warp 0 (one thread) issues
+// the loads, warp 1 (one thread) issues tcgen05.mma into float32
+// accumulators in tensor memory and frees each stage with tcgen05.commit.
+// The four warps then read the accumulators with tcgen05.ld (warp w owns
+// TMEM lanes 32w..32w+31, i.e. rows of the tile) and apply C -= scale * acc
+// to float32 C in global memory.
+//
+// Float32 operands given as three bf16 slices (s0 + s1 + s2) are multiplied
+// as the six slice products of order <= 2.  The products of one K tile are
+// issued back to back (K outer, slice pair inner), so the three reloads of a
+// slice tile within a K tile are served by L2 and each slice leaves HBM once;
+// the five small products go to one accumulator and s0*t0 to a second one,
+// added once in the epilogue, so no small product is ever rounded against
+// the large partial sums.
+//
+// Split K: CTA z of a tile takes K tiles [z kslice, (z+1) kslice) and writes
+// its raw accumulator to a partial buffer; the CTA that finishes a tile last
+// (a per-tile arrival counter) sums the partials in z order and updates C,
+// so the result does not depend on which CTA finished last.
 // Every wait is bounded; a wait that gives up raises SPD_DEV_TIMEOUT.
 #include <cudaTypedefs.h>
 #include <algorithm>
@@ -42,20 +56,58 @@ template <> struct KindTraits<2> {  // fp8 e4m3
     static constexpr int BK = 128, KMMA = 32;
 };
 
-// Split-K (kslice > 0): CTA z handles K tiles [z kslice, (z+1) kslice) of every
-// segment and writes its raw accumulator to Cpart + z M ldp (no C update);
-// k_reduce_parts then subtracts the partials from C in a fixed order.
-template <int KIND, int BNT, int ST>
+// v = acc (32 consecutive columns of one row of the tile) applied to C with
+// the lower-triangle and ragged-edge masks: C[row][col0 + j] -= scale * v[j]
+__device__ __forceinline__ void apply_chunk(float* __restrict__ crow, const float* v, int row, int col0, int N,
+                                            int lower, float scale) {
+    const bool full_chunk = (col0 + 32 <= N) && !(lower && row < col0 + 31) &&
+                            ((reinterpret_cast<uintptr_t>(crow) & 15) == 0);
+    if (full_chunk) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float4 c = reinterpret_cast<float4*>(crow)[q];
+            c.x -= scale * v[4 * q + 0];
+            c.y -= scale * v[4 * q + 1];
+            c.z -= scale * v[4 * q + 2];
+            c.w -= scale * v[4 * q + 3];
+            reinterpret_cast<float4*>(crow)[q] = c;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int col = col0 + j;
+            if (col < N && !(lower && row < col)) crow[j] -= scale * v[j];
+        }
+    }
+}
+
+// 32 columns of the accumulator(s) of this thread's row: acc0 (+ acc1)
+template <int NACC, int BNT>
+__device__ __forceinline__ void load_acc(uint32_t tmem, int warp, int ch, float* v) {
+    const uint32_t base = tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32;
+    tc::tmem_ld_32x32b_x32(base, v);
+    if constexpr (NACC == 2) {
+        float w[32];
+        tc::tmem_ld_32x32b_x32(base + BNT, w);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = v[j] + w[j];  // small products + s0*t0
+    }
+}
+
+// K loop: K tile kin of this CTA's share, slice pair q inner.  Segment q
+// multiplies slice (segs >> 4q) & 3 of A by slice (segs >> 4q+2) & 3 of B
+// into accumulator (accsel >> q) & 1.
+template <int KIND, int BNT, int ST, int NACC>
 __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
-              uint32_t idesc, float scale, int nseg, uint32_t segs, int kslice, float* __restrict__ Cpart,
-              long ldp, DevStatus* st) {
+              uint32_t idesc, float scale, int nseg, uint32_t segs, uint32_t accsel, int kslice,
+              float* __restrict__ Cpart, long ldp, int* __restrict__ tile_ctr, DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
     constexpr int B_STAGE = b_stage<BNT>();
     constexpr int STAGES = ST;
     constexpr int STAGE_BYTES = stage_bytes<BNT>();
-    constexpr uint32_t TMEM_COLS = BNT;
+    constexpr uint32_t TMEM_COLS = BNT * NACC;
     constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -67,6 +119,7 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     uint64_t* accf = empty + STAGES;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* last_flag = abort_flag + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bm = blockIdx.y, bn = blockIdx.x;
@@ -95,15 +148,15 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     const int nk_all = K / BK;  // K tiles per segment
     const int kb = kslice > 0 ? (int)blockIdx.z * kslice : 0;
     const int nk = kslice > 0 ? max(0, min(nk_all, kb + kslice) - kb) : nk_all;  // this CTA's share
-    const int ntiles = nk * nseg;  // segment s multiplies slice (segs >> 4s) & 3 of A by slice (segs >> 4s+2) & 3 of B
+    const int ntiles = nk * nseg;
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
             for (int kt = 0; kt < ntiles; ++kt) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1u;
-                const int seg = kt / nk, kin = kt - seg * nk;
-                const int za = (segs >> (4 * seg)) & 3, zb = (segs >> (4 * seg + 2)) & 3;
+                const int kin = kt / nseg, q = kt - kin * nseg;
+                const int za = (segs >> (4 * q)) & 3, zb = (segs >> (4 * q + 2)) & 3;
                 if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) break;
                 tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                 tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + (kb + kin) * BK, a_row0 + bm * BM, za, &full[s]);
@@ -113,16 +166,23 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {  // MMA issuer
+            // first segment (in issue order) of each accumulator starts it from zero
+            int first[2] = {-1, -1};
+            for (int q = nseg - 1; q >= 0; --q) first[(accsel >> q) & 1] = q;
             for (int kt = 0; kt < ntiles; ++kt) {
                 const int s = kt % STAGES;
                 const uint32_t ph = (kt / STAGES) & 1u;
+                const int kin = kt / nseg, q = kt - kin * nseg;
+                const int a = (accsel >> q) & 1;
                 if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) break;
                 tc::fence_after_sync();
                 const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_STAGE));
                 const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_STAGE));
+                const uint32_t d = tmem + (uint32_t)(a * BNT);
+                const bool fresh = kin == 0 && q == first[a];
 #pragma unroll
                 for (int k = 0; k < MMA_PER_STAGE; ++k)  // +32 bytes of K = +2 in the address field
-                    tc::mma<KIND>(tmem, ad + 2 * k, bd + 2 * k, idesc, (kt > 0 || k > 0) ? 1u : 0u);
+                    tc::mma<KIND>(d, ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
                 tc::mma_commit(&empty[s]);
             }
             tc::mma_commit(accf);
@@ -135,56 +195,82 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     if (threadIdx.x == 0) pdl_trigger();  // a dependent kernel (the next leaf) may be scheduled
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     tc::fence_after_sync();
-    if (ok && Cpart) {  // split-K partial: the raw accumulator (zero for an empty share)
-        const int row = bm * BM + warp * 32 + lane;
-        for (int ch = 0; ch < BNT / 32; ++ch) {
-            const int col0 = bn * BNT + ch * 32;
-            if (col0 >= N) break;
-            float v[32];
-            if (ntiles > 0) tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32, v);
-            else {
+    const int row = bm * BM + warp * 32 + lane;
+    const int rowmax_warp = bm * BM + warp * 32 + 31;
+    if (Cpart) {
+        // split K: this CTA's raw accumulator (zero for an empty share) ...
+        if (ok) {
+            for (int ch = 0; ch < BNT / 32; ++ch) {
+                const int col0 = bn * BNT + ch * 32;
+                if (col0 >= N) break;
+                float v[32];
+                if (ntiles > 0) load_acc<NACC, BNT>(tmem, warp, ch, v);
+                else {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = 0.f;
-            }
-            if (row < M) {
-                float* prow = Cpart + ((long)blockIdx.z * M + row) * ldp + col0;
+                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
+                }
+                if (row < M) {
+                    float* prow = Cpart + ((long)blockIdx.z * M + row) * ldp + col0;
+                    if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(prow) & 15) == 0)) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    if (col0 + j < N) prow[j] = v[j];
+                        for (int q = 0; q < 8; ++q)
+                            reinterpret_cast<float4*>(prow)[q] =
+                                make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (col0 + j < N) prow[j] = v[j];
+                    }
+                }
             }
         }
+        // ... then the tile's last CTA sums all partials in z order into C
+        __threadfence();
+        __syncthreads();
+        const int t = bm * gridDim.x + bn;
+        if (threadIdx.x == 0) *last_flag = (atomicAdd(&tile_ctr[t], 1) == (int)gridDim.z - 1) ? 1 : 0;
+        __syncthreads();
+        if (*last_flag) {
+            __threadfence();
+            if (ok && row < M) {
+                for (int ch = 0; ch < BNT / 32; ++ch) {
+                    const int col0 = bn * BNT + ch * 32;
+                    if (col0 >= N) break;
+                    if (lower && rowmax_warp < col0) continue;
+                    float acc[32];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+                    const bool vec = col0 + 32 <= N && (ldp & 3) == 0;
+                    for (int z = 0; z < (int)gridDim.z; ++z) {
+                        const float* prow = Cpart + ((long)z * M + row) * ldp + col0;
+                        if (vec) {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const float4 p = __ldcg(reinterpret_cast<const float4*>(prow) + q);
+                                acc[4 * q] += p.x;
+                                acc[4 * q + 1] += p.y;
+                                acc[4 * q + 2] += p.z;
+                                acc[4 * q + 3] += p.w;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (col0 + j < N) acc[j] += __ldcg(prow + j);
+                        }
+                    }
+                    apply_chunk(C + (long)row * ldc + col0, acc, row, col0, N, lower, scale);
+                }
+            }
+            if (threadIdx.x == 0) tile_ctr[t] = 0;  // reusable by the next launch on this stream
+        }
     } else if (ok) {
-        const int rloc = warp * 32 + lane;
-        const int row = bm * BM + rloc;
-        const int rowmax_warp = bm * BM + warp * 32 + 31;
         for (int ch = 0; ch < BNT / 32; ++ch) {
             const int col0 = bn * BNT + ch * 32;
             if (col0 >= N) break;                         // warp-uniform
             if (lower && rowmax_warp < col0) continue;    // warp-uniform: chunk above the diagonal
             float v[32];
-            tc::tmem_ld_32x32b_x32(tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32, v);
-            if (row < M) {
-                float* crow = C + (long)row * ldc + col0;
-                const bool full_chunk = (col0 + 32 <= N) && !(lower && row < col0 + 31) &&
-                                        ((reinterpret_cast<uintptr_t>(crow) & 15) == 0);
-                if (full_chunk) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float4 c = reinterpret_cast<float4*>(crow)[q];
-                        c.x -= scale * v[4 * q + 0];
-                        c.y -= scale * v[4 * q + 1];
-                        c.z -= scale * v[4 * q + 2];
-                        c.w -= scale * v[4 * q + 3];
-                        reinterpret_cast<float4*>(crow)[q] = c;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = col0 + j;
-                        if (col < N && !(lower && row < col)) crow[j] -= scale * v[j];
-                    }
-                }
-            }
+            load_acc<NACC, BNT>(tmem, warp, ch, v);
+            if (row < M) apply_chunk(C + (long)row * ldc + col0, v, row, col0, N, lower, scale);
         }
     }
     if (!ok && threadIdx.x == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
@@ -240,31 +326,26 @@ uint32_t idesc_for(int kind, int bn) {
     }
 }
 
+template <int KIND, int BNT, int ST, int NACC>
+void set_smem() {
+    cudaFuncSetAttribute(k_gemm_tc<KIND, BNT, ST, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes<BNT, ST>());
+}
+
 void set_attrs() {
     // once per process, thread-safe (function-local static)
     static const bool done = [] {
-        cudaFuncSetAttribute(k_gemm_tc<0, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<1, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<2, 256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<256, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<0, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<0, 128, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 3>());
-        cudaFuncSetAttribute(k_gemm_tc<1, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
-        cudaFuncSetAttribute(k_gemm_tc<2, 128, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<128, 4>());
+        set_smem<0, 256, 4, 1>();
+        set_smem<1, 256, 4, 1>();
+        set_smem<2, 256, 4, 1>();
+        set_smem<0, 256, 4, 2>();
+        set_smem<0, 128, 4, 1>();
+        set_smem<1, 128, 4, 1>();
+        set_smem<2, 128, 4, 1>();
+        set_smem<0, 128, 3, 2>();
         return true;
     }();
     (void)done;
-}
-
-// C[i][j] -= scale * sum_{z < S} P[z][i][j], z in increasing order
-__global__ void k_reduce_parts(float* __restrict__ C, long ldc, int M, int N, const float* __restrict__ P, long ldp,
-                               int S, float scale) {
-    const long total = (long)M * N;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / N), j = (int)(e - (long)i * N);
-        float acc = 0.f;
-        for (int z = 0; z < S; ++z) acc += P[((long)z * M + i) * ldp + j];
-        C[(long)i * ldc + j] -= scale * acc;
-    }
 }
 
 }  // namespace
@@ -305,85 +386,74 @@ namespace {
 
 template <int BNT>
 void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M, int N, int K, int a_row0,
-                 int b_row0, int k0, int lower, float scale, int nseg, uint32_t segs, int kslice, float* Cpart,
-                 long ldp, DevStatus* st) {
+                 int b_row0, int k0, int lower, float scale, int nseg, uint32_t segs, uint32_t accsel, int kslice,
+                 float* Cpart, long ldp, int* ctr, DevStatus* st) {
     const CUtensorMap& mb = BNT == 128 ? g->mapB128 : g->mapB;
     const uint32_t idesc = idesc_for(g->kind, BNT);
+#define SPD_GEMM_ARGS                                                                                              \
+    g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, segs, accsel, kslice, Cpart, ldp, \
+        ctr, st
     switch (g->kind) {
-        case 1:
-            k_gemm_tc<1, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
-                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
-                                                                        Cpart, ldp, st);
-            break;
-        case 5: {  // float32 as bf16 slices: six-segment K loops, two CTAs per SM on 128-wide tiles
+        case 1: k_gemm_tc<1, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+        case 5: {  // float32 as bf16 slices: two accumulators; two CTAs per SM on 128-wide tiles
             constexpr int ST = BNT == 128 ? 3 : 4;
-            k_gemm_tc<0, BNT, ST><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(
-                g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, segs, kslice, Cpart, ldp,
-                st);
+            k_gemm_tc<0, BNT, ST, 2><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(SPD_GEMM_ARGS);
             break;
         }
-        case 4:
-            k_gemm_tc<2, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
-                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
-                                                                        Cpart, ldp, st);
-            break;
-        default:
-            k_gemm_tc<0, BNT, 4><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0,
-                                                                        k0, lower, idesc, scale, nseg, segs, kslice,
-                                                                        Cpart, ldp, st);
+        case 4: k_gemm_tc<2, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+        default: k_gemm_tc<0, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS);
     }
+#undef SPD_GEMM_ARGS
 }
 
 }  // namespace
 
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
-                          int k0, int lower, DevStatus* st, int splits, float* Cpart) {
+                          int k0, int lower, DevStatus* st, int splits, const TcSplit* sb) {
     const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
     if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
-    // float32 as three bf16 slices: the six slice products of order <= 2,
-    // smallest first, into one accumulator (A slice in bits 4s..4s+1, B
-    // slice in bits 4s+2..4s+3 of segment s)
+    // float32 as three bf16 slices: the six slice products of order <= 2 (A
+    // slice in bits 4q..4q+1, B slice in bits 4q+2..4q+3 of segment q); the
+    // five small ones into accumulator 0, s0*t0 into accumulator 1
     int nseg = 1;
-    uint32_t segs = 0;
+    uint32_t segs = 0, accsel = 0;
     if (g->kind == 5) {
         const int pairs[6][2] = {{2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}, {0, 0}};
         nseg = 6;
         for (int q = 0; q < 6; ++q) segs |= (uint32_t)(pairs[q][0] | (pairs[q][1] << 2)) << (4 * q);
+        accsel = 1u << 5;
     }
     const int nk = K / bk;
+    const int bnt = (N <= 128) ? 128 : 256;
+    const int tiles = ((N + bnt - 1) / bnt) * ((M + BM - 1) / BM);
     // splits < 0: choose from the SM count -splits, filling the machine once
-    // (two CTAs per SM for the 128-wide tf32 tiles)
+    // (two CTAs per SM for the 128-wide float32 tiles)
     if (splits < 0) {
-        const int tiles = ((N + 127) / 128 <= 1 && N <= 128 ? 1 : (N + BN - 1) / BN) * ((M + BM - 1) / BM);
-        const int occ = (N <= 128 && g->kind == 5) ? 2 : 1;
+        const int occ = (bnt == 128 && g->kind == 5) ? 2 : 1;
         splits = std::max(1, std::min(16, occ * (-splits) / std::max(tiles, 1)));
     }
     if (splits > nk) splits = nk;
-    const bool split = splits > 1 && Cpart && !lower;
+    const bool split = splits > 1 && sb && sb->part && sb->ctr && tiles <= sb->ctr_cap &&
+                       (size_t)splits * M * N <= sb->part_cap;
     const int kslice = split ? (nk + splits - 1) / splits : 0;
     if (split) splits = (nk + kslice - 1) / kslice;  // no empty share
-    const int bnt = (N <= 128) ? 128 : 256;
     dim3 grid((N + bnt - 1) / bnt, (M + BM - 1) / BM, split ? splits : 1);
     const long ldp = N;
+    float* part = split ? sb->part : nullptr;
+    int* ctr = split ? sb->ctr : nullptr;
     if (bnt == 128)
-        launch_kind<128>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, kslice,
-                         split ? Cpart : nullptr, ldp, st);
+        launch_kind<128>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
+                         part, ldp, ctr, st);
     else
-        launch_kind<256>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, kslice,
-                         split ? Cpart : nullptr, ldp, st);
-    if (split) {
-        const long total = (long)M * N;
-        const int blocks = (int)std::min<long>((total + 255) / 256, 1024);
-        k_reduce_parts<<<blocks, 256, 0, s>>>(C, ldc, M, N, Cpart, ldp, splits, scale);
-    }
+        launch_kind<256>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
+                         part, ldp, ctr, st);
     return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;
 }
 
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
-                       DevStatus* st, int splits, float* Cpart) {
-    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st, splits,
-                          Cpart);
+                       DevStatus* st, int splits, const TcSplit* sb) {
+    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st, splits, sb);
 }
 
 void tc_gemm_destroy(TcGemm* g) { delete g; }

@@ -5,8 +5,8 @@
 //
 // - left-looking over 128-column block columns (potrf_left; the tensor-core
 //   precisions by default): W[k:, k] -= L[k:, 0:k] L[k, 0:k]^T, leaf, panel
-//   solve, with the bulk of each update issued one block column ahead on the
-//   handle's second stream;
+//   solve, with the bulk of the updates issued ahead, for two block columns
+//   at a time, on the handle's second stream;
 // - recursive (potrf_rec; FP64, the CUDA-core engine, SPD_FACTOR_RECURSIVE):
 //     chol(A)   : chol(A11); L21 = A21 L11^{-T}; A22 -= L21 L21^T; chol(A22)
 //     trsm(B,L) : trsm(B1, L11); B2 -= X1 L21^T; trsm(B2, L22)
@@ -28,9 +28,8 @@ struct FCtx {
     spd_handle* h;
     spd_factor_t* F;
     Mirror mir;
-    TcGemm* tc;          // tensor-core GEMM plan (nullptr: CUDA cores)
-    float* part = nullptr;   // split-K partials of the early block-column updates (second stream)
-    float* part2 = nullptr;  // partials of the rank-128 updates (main stream)
+    TcGemm* tc;               // tensor-core GEMM plan (nullptr: CUDA cores)
+    TcSplit* bulk = nullptr;  // split-K scratch of the bulk updates (second stream)
 };
 
 
@@ -88,19 +87,27 @@ spd_status leaf_trsm(FCtx& c, int r0, int m, int c0, int kb, bool b_ready = fals
     return SPD_OK;
 }
 
+// crit: a rank-128 update on the factorisation's critical path (recorded
+// as SPD_PHASE_TRAILING_LAST); otherwise a bulk update.  lower (r0 == c0):
+// only entries with row >= column are updated.
 template <typename T>
 spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower, int splits = 1,
-                cudaStream_t strm = nullptr, float* part = nullptr) {
+                cudaStream_t strm = nullptr, const TcSplit* sb = nullptr, bool crit = false) {
     if (M <= 0 || N <= 0 || K <= 0) return SPD_OK;
     spd_factor_t* F = c.F;
     cudaStream_t s = strm ? strm : c.h->stream;
-    // algorithmic work: lower-triangle SYRK or full GEMM; C read+written once
-    // in T, each operand row read once in the operand type
-    const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
+    // algorithmic work: the lower part of an M x N block on the diagonal
+    // (sum over its columns c < min(M, N) of M - c entries) or the full
+    // block; C read+written once in T, each operand row read once in the
+    // operand type (B's rows are A's first rows when lower)
+    const double w = (double)std::min(M, N);
+    const double celems = lower ? w * M - 0.5 * w * (w - 1.0) : (double)M * N;
     const double opsz = sizeof(T) == 8 ? 8.0
                         : c.mir.kind == 5 ? 6.0
                         : (c.mir.kind == 0 || c.mir.kind == 1 ? 4.0 : c.mir.kind == 4 ? 1.0 : 2.0);
-    ProfScope ps(c.h, (c.tc && c.mir.kind == 5) ? SPD_PHASE_TRAILING_X3 : SPD_PHASE_TRAILING, 2.0 * celems * K,
+    const int phase = crit ? SPD_PHASE_TRAILING_LAST
+                           : (c.tc && c.mir.kind == 5) ? SPD_PHASE_TRAILING_X3 : SPD_PHASE_TRAILING;
+    ProfScope ps(c.h, phase, 2.0 * celems * K,
                  2.0 * sizeof(T) * celems + opsz * (double)K * (lower ? M : (double)M + N), s);
     if constexpr (sizeof(T) == 8) {
         dim3 grid(ceil_div(N, 64), ceil_div(M, 64));
@@ -108,7 +115,7 @@ spd_status gemm(FCtx& c, int r0, int M, int c0, int N, int k0, int K, int lower,
                                                                      k0, K, lower, c.h->dst);
     } else {
         if (c.tc) {
-            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst, splits, part ? part : c.part);
+            spd_status st = tc_gemm_run(c.tc, s, r0, M, c0, N, k0, K, lower, c.h->dst, splits, sb);
             if (st != SPD_OK) return set_err(c.h, st, "tensor-core trailing update failed");
             return SPD_OK;
         }
@@ -172,23 +179,27 @@ spd_status potrf_rec(FCtx& c, int n0, int nn) {
 }
 
 // Left-looking block-column schedule with a look-ahead (tensor-core
-// factors).  Block column k needs everything to its left:
-//   W[k:, k] -= L[k:, 0:k-1] L[k, 0:k-1]^T   ("early": columns done two
-//                                            steps ago, on the second stream)
-//   W[k:, k] -= L[k:, k-1] L[k, k-1]^T       ("last": rank 128, main stream)
-// then the leaf and the panel solve below it (main stream).  The early part,
-// which holds nearly all of the tensor-core work, runs while the previous
-// block's leaf and panel run; the critical path per block is one rank-128
-// update, one leaf and one panel.  The early update of block k waits for the
-// panel of block k-2; the last update of block k waits for its early update
-// (both write W[k:, k]).
+// factors).  Block columns are taken in pairs P = (j, j+1), j even.  Block
+// column k needs every panel to its left applied:
+//   bulk (second stream): W[j:, j:j+2] -= L[j:, 0:j-1] L[j:j+2, 0:j-1]^T
+//        for the whole pair, as soon as panel j-2 is done; 256-wide tiles
+//        (entries above the diagonal are left alone);
+//   last (main stream, rank 128, on the critical path):
+//        block j:   W[j:, j:j+2] -= L[j:, j-1] L[j:j+2, j-1]^T  (both columns)
+//        block j+1: W[j+1:, j+1] -= L[j+1:, j] L[j+1, j]^T
+// each followed by the block's leaf and the panel solve below it.  The bulk
+// update of a pair, which holds nearly all of the tensor-core work, runs
+// while the previous block's last update, leaf and panel run; the bulk
+// update of pair P waits for panel j-2, the last update of block j for the
+// bulk update of its pair (both write W[j:, j:j+2]).
 template <typename T>
 spd_status potrf_left(FCtx& c, int n, bool lookahead) {
     spd_handle* h = c.h;
     const int NB = ceil_div(n, SPD_LEAF);
     // without the look-ahead both parts run in order on the main stream
     cudaStream_t P = h->stream, U = lookahead ? h->aux : h->stream;
-    // two events per block: panel done (main), early update done (second)
+    // two events per block: panel done (main), bulk update of the pair
+    // starting at this block done (second)
     const size_t need = 2 * (size_t)NB + 1;
     while (h->sync_ev.size() < need) {
         cudaEvent_t e = nullptr;
@@ -196,7 +207,7 @@ spd_status potrf_left(FCtx& c, int n, bool lookahead) {
         h->sync_ev.push_back(e);
     }
     cudaEvent_t* evPanel = h->sync_ev.data();
-    cudaEvent_t* evEarly = h->sync_ev.data() + NB;
+    cudaEvent_t* evBulk = h->sync_ev.data() + NB;
     cudaEvent_t evStart = h->sync_ev[2 * NB];
     CUDA_TRY(h, cudaEventRecord(evStart, P));  // the second stream starts after the conversion
     CUDA_TRY(h, cudaStreamWaitEvent(U, evStart, 0));
@@ -204,25 +215,32 @@ spd_status potrf_left(FCtx& c, int n, bool lookahead) {
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < NB && st == SPD_OK && e == cudaSuccess; ++k) {
         const int r0 = k * SPD_LEAF, nb = std::min(SPD_LEAF, n - r0), M = n - r0;
-        if (k >= 2) e = cudaStreamWaitEvent(P, evEarly[k], 0);
-        if (e == cudaSuccess && k >= 1)  // last: rank 128 with block column k-1
-            st = gemm<T>(c, r0, M, r0, nb, r0 - SPD_LEAF, SPD_LEAF, 0, 1, P, c.part2);
+        const bool pair_start = (k % 2) == 0;
+        if (pair_start && k >= 2) e = cudaStreamWaitEvent(P, evBulk[k], 0);
+        if (e == cudaSuccess && k >= 1) {  // last: rank 128 with block column k-1
+            if (pair_start)
+                st = gemm<T>(c, r0, M, r0, std::min(2 * SPD_LEAF, M), r0 - SPD_LEAF, SPD_LEAF, 1, 1, P, nullptr, true);
+            else
+                st = gemm<T>(c, r0, M, r0, nb, r0 - SPD_LEAF, SPD_LEAF, 0, 1, P, nullptr, true);
+        }
         if (e == cudaSuccess && st == SPD_OK) st = leaf_potrf<T>(c, r0, nb);
         if (e == cudaSuccess && st == SPD_OK && r0 + nb < n)
             st = leaf_trsm<T>(c, r0 + nb, n - r0 - nb, r0, nb, true);  // right after the leaf
         if (e != cudaSuccess || st != SPD_OK) break;
         e = cudaEventRecord(evPanel[k], P);
-        // early update of block k+2 on the second stream: columns 0..k
-        if (e == cudaSuccess && k + 2 < NB) {
+        // bulk update of the pair starting at block k+2 on the second stream:
+        // panels 0..k
+        if (e == cudaSuccess && pair_start && k + 2 < NB) {
             e = cudaStreamWaitEvent(U, evPanel[k], 0);
-            const int r2 = (k + 2) * SPD_LEAF, nb2 = std::min(SPD_LEAF, n - r2);
+            const int r2 = (k + 2) * SPD_LEAF, M2 = n - r2;
             if (e == cudaSuccess)
-                st = gemm<T>(c, r2, n - r2, r2, nb2, 0, (k + 1) * SPD_LEAF, 0, c.part ? -h->sms : 1, U, c.part);
-            if (e == cudaSuccess) e = cudaEventRecord(evEarly[k + 2], U);
+                st = gemm<T>(c, r2, M2, r2, std::min(2 * SPD_LEAF, M2), 0, (k + 1) * SPD_LEAF, 1,
+                             c.bulk ? -h->sms : 1, U, c.bulk);
+            if (e == cudaSuccess) e = cudaEventRecord(evBulk[k + 2], U);
         }
     }
-    // join, on every path: the main stream continues (and frees the partial
-    // buffers) only after everything queued on the second stream
+    // join, on every path: the main stream continues (and frees the split
+    // scratch) only after everything queued on the second stream
     cudaEvent_t evEnd = h->sync_ev[2 * NB];
     cudaError_t e2 = cudaEventRecord(evEnd, U);
     if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(P, evEnd, 0);
@@ -318,20 +336,22 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (prec == SPD_PREC_FP64) {
             st = potrf_rec<double>(c, 0, n);
         } else if (c.tc && !(flags & SPD_FACTOR_RECURSIVE)) {
-            // split-K partials: at most 2 sms x 128 x 128 floats (splits x tiles <= 2 sms)
-            cudaError_t pe = cudaMallocAsync(&c.part, sizeof(float) * 128 * 128 * 2 * std::max(h->sms, 1), s);
-            if (pe != cudaSuccess) {
-                cudaGetLastError();
-                c.part = nullptr;  // the updates then run unsplit
-            }
-            if (c.part && cudaMallocAsync(&c.part2, sizeof(float) * 128 * 128 * 2 * std::max(h->sms, 1), s) !=
-                              cudaSuccess) {
-                cudaGetLastError();
-                c.part2 = nullptr;
+            // split-K scratch of the bulk updates: at most 2 sms x 128 x 128
+            // partial floats and 2 sms tile counters (splits x tiles <= 2 sms)
+            const int S2 = 2 * std::max(h->sms, 1);
+            TcSplit sb{nullptr, (size_t)S2 * 128 * 128, nullptr, S2};
+            void* mem = nullptr;
+            if (cudaMallocAsync(&mem, sizeof(float) * sb.part_cap + sizeof(int) * S2, s) == cudaSuccess &&
+                cudaMemsetAsync(static_cast<float*>(mem) + sb.part_cap, 0, sizeof(int) * S2, s) == cudaSuccess) {
+                sb.part = static_cast<float*>(mem);
+                sb.ctr = reinterpret_cast<int*>(sb.part + sb.part_cap);
+                c.bulk = &sb;
+            } else {
+                cudaGetLastError();  // the bulk updates then run unsplit
             }
             st = potrf_left<float>(c, n, !(flags & SPD_FACTOR_SERIAL));
-            if (c.part) cudaFreeAsync(c.part, s);
-            if (c.part2) cudaFreeAsync(c.part2, s);
+            c.bulk = nullptr;
+            if (mem) cudaFreeAsync(mem, s);
         } else {
             st = potrf_rec<float>(c, 0, n);
         }
