@@ -21,10 +21,14 @@
 // added once in the epilogue, so no small product is ever rounded against
 // the large partial sums.
 //
+// Epilogue: each warp brings its 32 rows of the C tile into the (now idle)
+// stage buffers with TMA, as 32 x 32 boxes in the 128-byte swizzled layout
+// (a thread's row is then read and written without bank conflicts),
+// subtracts the accumulator and writes the boxes back with TMA stores.
 // Split K: CTA z of a tile takes K tiles [z kslice, (z+1) kslice) and writes
-// its raw accumulator to a partial buffer; the CTA that finishes a tile last
-// (a per-tile arrival counter) sums the partials in z order and updates C,
-// so the result does not depend on which CTA finished last.
+// its raw accumulator to a partial buffer; k_reduce_parts, launched as a
+// programmatic dependent of the GEMM, sums the partials of every entry in z
+// order and updates C.
 // Every wait is bounded; a wait that gives up raises SPD_DEV_TIMEOUT.
 #include <cudaTypedefs.h>
 #include <algorithm>
@@ -56,8 +60,9 @@ template <> struct KindTraits<2> {  // fp8 e4m3
     static constexpr int BK = 128, KMMA = 32;
 };
 
-// v = acc (32 consecutive columns of one row of the tile) applied to C with
-// the lower-triangle and ragged-edge masks: C[row][col0 + j] -= scale * v[j]
+// Without a tensor map of C (ldc * 4 bytes not a multiple of 16): v = acc
+// (32 consecutive columns of one row of the tile) applied to C directly with
+// the lower-triangle and ragged-edge masks, C[row][col0 + j] -= scale * v[j]
 __device__ __forceinline__ void apply_chunk(float* __restrict__ crow, const float* v, int row, int col0, int N,
                                             int lower, float scale) {
     const bool full_chunk = (col0 + 32 <= N) && !(lower && row < col0 + 31) &&
@@ -100,9 +105,9 @@ __device__ __forceinline__ void load_acc(uint32_t tmem, int warp, int ch, float*
 template <int KIND, int BNT, int ST, int NACC>
 __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              float* __restrict__ C, long ldc, int M, int N, int K, int a_row0, int b_row0, int k0, int lower,
-              uint32_t idesc, float scale, int nseg, uint32_t segs, uint32_t accsel, int kslice,
-              float* __restrict__ Cpart, long ldp, int* __restrict__ tile_ctr, DevStatus* st) {
+              const __grid_constant__ CUtensorMap mapC, float* __restrict__ C, long ldc, int cx0, int cy0, int M,
+              int N, int K, int a_row0, int b_row0, int k0, int lower, uint32_t idesc, float scale, int nseg,
+              uint32_t segs, uint32_t accsel, int kslice, float* __restrict__ Cpart, long ldp, DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
     constexpr int B_STAGE = b_stage<BNT>();
     constexpr int STAGES = ST;
@@ -117,9 +122,9 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* cbar = accf + 1;  // one per warp: its C boxes have landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cbar + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* last_flag = abort_flag + 1;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bm = blockIdx.y, bn = blockIdx.x;
@@ -132,10 +137,12 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
             tc::mbar_init(&empty[s], 1);
         }
         tc::mbar_init(accf, 1);
+        for (int w = 0; w < 4; ++w) tc::mbar_init(&cbar[w], 1);
         *abort_flag = 0;
         tc::fence_barrier_init();
         tc::prefetch_tmap(&mapA);
         tc::prefetch_tmap(&mapB);
+        if (!Cpart && !C) tc::prefetch_tmap(&mapC);
     }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -196,9 +203,9 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
     tc::fence_after_sync();
     const int row = bm * BM + warp * 32 + lane;
-    const int rowmax_warp = bm * BM + warp * 32 + 31;
+    const int row_w = bm * BM + warp * 32;  // first row of this warp's slab (warp-uniform)
     if (Cpart) {
-        // split K: this CTA's raw accumulator (zero for an empty share) ...
+        // split K: this CTA's raw accumulator (zero for an empty share)
         if (ok) {
             for (int ch = 0; ch < BNT / 32; ++ch) {
                 const int col0 = bn * BNT + ch * 32;
@@ -224,53 +231,75 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
                 }
             }
         }
-        // ... then the tile's last CTA sums all partials in z order into C
-        __threadfence();
-        __syncthreads();
-        const int t = bm * gridDim.x + bn;
-        if (threadIdx.x == 0) *last_flag = (atomicAdd(&tile_ctr[t], 1) == (int)gridDim.z - 1) ? 1 : 0;
-        __syncthreads();
-        if (*last_flag) {
-            __threadfence();
-            if (ok && row < M) {
-                for (int ch = 0; ch < BNT / 32; ++ch) {
-                    const int col0 = bn * BNT + ch * 32;
-                    if (col0 >= N) break;
-                    if (lower && rowmax_warp < col0) continue;
-                    float acc[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] = 0.f;
-                    const bool vec = col0 + 32 <= N && (ldp & 3) == 0;
-                    for (int z = 0; z < (int)gridDim.z; ++z) {
-                        const float* prow = Cpart + ((long)z * M + row) * ldp + col0;
-                        if (vec) {
-#pragma unroll
-                            for (int q = 0; q < 8; ++q) {
-                                const float4 p = __ldcg(reinterpret_cast<const float4*>(prow) + q);
-                                acc[4 * q] += p.x;
-                                acc[4 * q + 1] += p.y;
-                                acc[4 * q + 2] += p.z;
-                                acc[4 * q + 3] += p.w;
-                            }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (col0 + j < N) acc[j] += __ldcg(prow + j);
-                        }
-                    }
-                    apply_chunk(C + (long)row * ldc + col0, acc, row, col0, N, lower, scale);
-                }
-            }
-            if (threadIdx.x == 0) tile_ctr[t] = 0;  // reusable by the next launch on this stream
-        }
-    } else if (ok) {
+    } else if (ok && C) {  // C given directly (no tensor map): C is the block's origin
         for (int ch = 0; ch < BNT / 32; ++ch) {
             const int col0 = bn * BNT + ch * 32;
-            if (col0 >= N) break;                         // warp-uniform
-            if (lower && rowmax_warp < col0) continue;    // warp-uniform: chunk above the diagonal
+            if (col0 >= N) break;                           // warp-uniform
+            if (lower && row_w + 31 < col0) continue;       // warp-uniform: chunk above the diagonal
             float v[32];
             load_acc<NACC, BNT>(tmem, warp, ch, v);
             if (row < M) apply_chunk(C + (long)row * ldc + col0, v, row, col0, N, lower, scale);
+        }
+    } else if (ok && row_w < M) {
+        // C -= scale * acc through shared memory: the warp's 32 rows as
+        // 32 x 32 boxes (4 KB each, 128-byte swizzle: 16-byte chunk q of
+        // box row r sits at chunk q ^ (r & 7)), in the idle stage buffers
+        float* slab = reinterpret_cast<float*>(base) + warp * 32 * BNT;
+        int nbox = 0;
+        uint32_t need = 0;  // boxes inside N and not wholly above the diagonal
+        for (int ch = 0; ch < BNT / 32; ++ch) {
+            const int col0 = bn * BNT + ch * 32;
+            if (col0 >= N) break;
+            nbox = ch + 1;
+            if (!(lower && row_w + 31 < col0)) need |= 1u << ch;
+        }
+        if (lane == 0 && need) {
+            tc::mbar_arrive_expect_tx(&cbar[warp], 4096u * __popc(need));
+            for (int ch = 0; ch < nbox; ++ch)
+                if (need >> ch & 1u)
+                    tc::tma_load_2d(slab + ch * 1024, &mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, &cbar[warp]);
+        }
+        bool landed = !need || tc::mbar_wait(&cbar[warp], 0, abort_flag, WAIT_NS);
+        landed = __all_sync(0xffffffffu, landed);
+        if (landed) {
+            for (int ch = 0; ch < nbox; ++ch) {
+                if (!(need >> ch & 1u)) continue;  // warp-uniform
+                float v[32];
+                load_acc<NACC, BNT>(tmem, warp, ch, v);
+                float4* rp = reinterpret_cast<float4*>(slab + ch * 1024 + lane * 32);
+                const int col0 = bn * BNT + ch * 32;
+                // rows >= M, columns >= N and (lower) entries above the
+                // diagonal keep their value: the boxes may reach past the
+                // update's block, and the stores write every box entry back
+                const int lim = row < M ? (lower ? min(N - 1, row) : N - 1) : -1;  // last column to update
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    float4 c = rp[q ^ (lane & 7)];
+                    const int cq = col0 + 4 * q;
+                    if (cq + 3 <= lim) {
+                        c.x -= scale * v[4 * q];
+                        c.y -= scale * v[4 * q + 1];
+                        c.z -= scale * v[4 * q + 2];
+                        c.w -= scale * v[4 * q + 3];
+                    } else {
+                        if (cq <= lim) c.x -= scale * v[4 * q];
+                        if (cq + 1 <= lim) c.y -= scale * v[4 * q + 1];
+                        if (cq + 2 <= lim) c.z -= scale * v[4 * q + 2];
+                    }
+                    rp[q ^ (lane & 7)] = c;
+                }
+            }
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                for (int ch = 0; ch < nbox; ++ch)
+                    if (need >> ch & 1u) tc::tma_store_2d(&mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, slab + ch * 1024);
+                tc::bulk_commit();
+                tc::bulk_wait_all();
+            }
+            __syncwarp();
+        } else {
+            ok = false;
         }
     }
     if (!ok && threadIdx.x == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
@@ -316,6 +345,21 @@ bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols
     return r == CUDA_SUCCESS;
 }
 
+// 2-D map over a float32 row-major matrix (rows x cols, ld floats) with
+// 32 x 32 boxes in the 128-byte swizzled layout: the epilogue's view of C.
+bool make_map_c(CUtensorMap* map, float* C, long rows, long cols, long ld) {
+    auto enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * sizeof(float))};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 uint32_t idesc_for(int kind, int bn) {
     switch (kind) {
         case 1: return tc::idesc_f32acc(2, BM, bn);  // tf32
@@ -348,19 +392,62 @@ void set_attrs() {
     (void)done;
 }
 
+// C[i][j] -= scale * sum_{z < S} P[z][i][j] (z in increasing order), only
+// i >= j when lower.  Launched as a programmatic dependent of the split GEMM:
+// everything before pdl_wait overlaps the GEMM's last CTAs.
+__global__ void __launch_bounds__(256) k_reduce_parts(float* __restrict__ C, long ldc, int M, int N,
+                                                      const float* __restrict__ P, int S, float scale, int lower) {
+    pdl_wait();
+    if ((N & 3) == 0) {
+        const int n4 = N >> 2;
+        const long total = (long)M * n4;
+        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+            const int i = (int)(e / n4), j = (int)(e - (long)i * n4) * 4;
+            if (lower && i < j) continue;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int z = 0; z < S; ++z) {
+                const float4 p = __ldcg(reinterpret_cast<const float4*>(P + ((long)z * M + i) * N + j));
+                acc.x += p.x;
+                acc.y += p.y;
+                acc.z += p.z;
+                acc.w += p.w;
+            }
+            float4* cp = reinterpret_cast<float4*>(C + (long)i * ldc + j);
+            float4 c = *cp;
+            c.x -= scale * acc.x;
+            if (!lower || i >= j + 1) c.y -= scale * acc.y;
+            if (!lower || i >= j + 2) c.z -= scale * acc.z;
+            if (!lower || i >= j + 3) c.w -= scale * acc.w;
+            *cp = c;
+        }
+    } else {
+        const long total = (long)M * N;
+        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+            const int i = (int)(e / N), j = (int)(e - (long)i * N);
+            if (lower && i < j) continue;
+            float acc = 0.f;
+            for (int z = 0; z < S; ++z) acc += __ldcg(P + ((long)z * M + i) * N + j);
+            C[(long)i * ldc + j] -= scale * acc;
+        }
+    }
+}
+
 }  // namespace
 
 struct TcGemm {
     CUtensorMap mapA, mapB, mapB128;  // box heights 128 (A), 256 and 128 (B)
+    CUtensorMap mapC;                 // C in 32 x 32 boxes (when has_map_c)
+    bool has_map_c;
     float* C;
     long ldc;
     int kind;
+    int sms;
 };
 
 float tc_fp8_scale() { return SPD_FP8_SCALE; }
 
 spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
-                               long b_ld, long cols, float* C, long ldc, int kind) {
+                               long b_ld, long cols, float* C, long c_rows, long c_cols, long ldc, int kind) {
     *out = nullptr;
     if (kind < 1 || kind > 5) return SPD_ERR_UNSUPPORTED;
     TcGemm* g = new TcGemm();
@@ -370,29 +457,38 @@ spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a
         delete g;
         return SPD_ERR_UNSUPPORTED;
     }
+    // TMA needs 16-byte aligned rows of C; otherwise the epilogue writes C directly
+    g->has_map_c = (ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0) &&
+                   make_map_c(&g->mapC, C, c_rows, c_cols, ldc);
     g->C = C;
     g->ldc = ldc;
     g->kind = kind;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        g->sms = 148;
     set_attrs();
     *out = g;
     return SPD_OK;
 }
 
 spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n) {
-    return tc_gemm_create_maps(out, Wh, n, ldh, Wh, n, ldh, n, W, ldw, kind);
+    return tc_gemm_create_maps(out, Wh, n, ldh, Wh, n, ldh, n, W, n, n, ldw, kind);
 }
 
 namespace {
 
 template <int BNT>
-void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M, int N, int K, int a_row0,
+void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, int cx0, int cy0, int M, int N, int K, int a_row0,
                  int b_row0, int k0, int lower, float scale, int nseg, uint32_t segs, uint32_t accsel, int kslice,
-                 float* Cpart, long ldp, int* ctr, DevStatus* st) {
+                 float* Cpart, long ldp, DevStatus* st) {
     const CUtensorMap& mb = BNT == 128 ? g->mapB128 : g->mapB;
     const uint32_t idesc = idesc_for(g->kind, BNT);
-#define SPD_GEMM_ARGS                                                                                              \
-    g->mapA, mb, C, ldc, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, segs, accsel, kslice, Cpart, ldp, \
-        ctr, st
+    // without a tensor map of C the epilogue writes C (the block's origin) directly
+    float* Cdirect = g->has_map_c ? nullptr : g->C + (long)cy0 * g->ldc + cx0;
+#define SPD_GEMM_ARGS                                                                                            \
+    g->mapA, mb, g->mapC, Cdirect, g->ldc, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, \
+        segs, accsel, kslice, Cpart, ldp, st
     switch (g->kind) {
         case 1: k_gemm_tc<1, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
         case 5: {  // float32 as bf16 slices: two accumulators; two CTAs per SM on 128-wide tiles
@@ -408,10 +504,10 @@ void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, float* C, long ldc, int M
 
 }  // namespace
 
-spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
+spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, int N, int K, int a_row0, int b_row0,
                           int k0, int lower, DevStatus* st, int splits, const TcSplit* sb) {
     const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
-    if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0) return SPD_ERR_ARG;
+    if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0 || cx0 % 4 != 0) return SPD_ERR_ARG;
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
     // float32 as three bf16 slices: the six slice products of order <= 2 (A
     // slice in bits 4q..4q+1, B slice in bits 4q+2..4q+3 of segment q); the
@@ -434,26 +530,40 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, 
         splits = std::max(1, std::min(16, occ * (-splits) / std::max(tiles, 1)));
     }
     if (splits > nk) splits = nk;
-    const bool split = splits > 1 && sb && sb->part && sb->ctr && tiles <= sb->ctr_cap &&
-                       (size_t)splits * M * N <= sb->part_cap;
+    const bool split = splits > 1 && sb && sb->part && (size_t)splits * M * N <= sb->part_cap;
     const int kslice = split ? (nk + splits - 1) / splits : 0;
     if (split) splits = (nk + kslice - 1) / kslice;  // no empty share
     dim3 grid((N + bnt - 1) / bnt, (M + BM - 1) / BM, split ? splits : 1);
     const long ldp = N;
     float* part = split ? sb->part : nullptr;
-    int* ctr = split ? sb->ctr : nullptr;
     if (bnt == 128)
-        launch_kind<128>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
-                         part, ldp, ctr, st);
+        launch_kind<128>(g, s, grid, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
+                         part, ldp, st);
     else
-        launch_kind<256>(g, s, grid, C, ldc, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
-                         part, ldp, ctr, st);
+        launch_kind<256>(g, s, grid, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
+                         part, ldp, st);
+    if (split) {
+        cudaLaunchConfig_t cfg = {};
+        const long work = (long)M * ((N & 3) == 0 ? N / 4 : N);
+        cfg.gridDim = dim3((unsigned)std::max<long>(1, std::min<long>((work + 255) / 256, 4L * g->sms)));
+        cfg.blockDim = dim3(256);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        float* C = g->C + (long)cy0 * g->ldc + cx0;
+        if (cudaLaunchKernelEx(&cfg, k_reduce_parts, C, g->ldc, M, N, (const float*)part, splits, scale, lower) !=
+            cudaSuccess)
+            return SPD_ERR_CUDA;
+    }
     return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;
 }
 
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
                        DevStatus* st, int splits, const TcSplit* sb) {
-    return tc_gemm_launch(g, s, g->C + (long)r0 * g->ldc + c0, g->ldc, M, N, K, r0, c0, k0, lower, st, splits, sb);
+    return tc_gemm_launch(g, s, r0, c0, M, N, K, r0, c0, k0, lower, st, splits, sb);
 }
 
 void tc_gemm_destroy(TcGemm* g) { delete g; }

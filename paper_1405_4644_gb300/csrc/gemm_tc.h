@@ -9,30 +9,28 @@
 
 struct TcGemm;
 
-// Split-K scratch of one stream: partial sums (part_cap floats) and one
-// arrival counter per output tile (ctr_cap ints, zero before first use; each
-// launch leaves them zero again).
+// Split-K scratch of one stream: room for the partial sums (part_cap floats).
 struct TcSplit {
     float* part;
     size_t part_cap;
-    int* ctr;
-    int ctr_cap;
 };
 
 // Plan for one factor: tensor maps over Wh for the operand tiles.
 // Returns SPD_ERR_UNSUPPORTED when the operand kind has no tensor-core path.
 spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n);
-// splits > 1 with split scratch sb splits K across CTAs; the last CTA of
-// each tile sums the partials in a fixed order (lower masks apply as
-// without splitting); splits = -S lets the GEMM pick the split count for S
-// SMs (at most 16: splits x tiles <= 2 S, so 2 S x 128 x 128 partial floats
-// and 2 S counters always suffice).  Without room in sb the update runs
-// unsplit.
+// splits > 1 with split scratch sb splits K across CTAs and a dependent
+// kernel sums the partials in a fixed order (lower masks apply as without
+// splitting); splits = -S lets the GEMM pick the split count for S SMs (at
+// most 16: splits x tiles <= 2 S, so 2 S x 128 x 128 partial floats always
+// suffice).  Without room in sb the update runs unsplit.
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
                        DevStatus* st, int splits = 1, const TcSplit* sb = nullptr);
 void tc_gemm_destroy(TcGemm* g);
-// General form: separate operand arrays (rows x cols, ld elements each).
+// General form: separate operand arrays (rows x cols, ld elements each) and
+// C (c_rows x c_cols, ldc floats, row-major).
 spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
-                               long b_ld, long cols, float* C, long ldc, int kind);
-spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, float* C, long ldc, int M, int N, int K, int a_row0, int b_row0,
+                               long b_ld, long cols, float* C, long c_rows, long c_cols, long ldc, int kind);
+// C[cy0 + i][cx0 + j] -= sum_k A[a_row0 + i][k0 + k] B[b_row0 + j][k0 + k]
+// for i < M, j < N (cx0 a multiple of 4).
+spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, int N, int K, int a_row0, int b_row0,
                           int k0, int lower, DevStatus* st, int splits = 1, const TcSplit* sb = nullptr);

@@ -337,17 +337,15 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
             st = potrf_rec<double>(c, 0, n);
         } else if (c.tc && !(flags & SPD_FACTOR_RECURSIVE)) {
             // split-K scratch of the bulk updates: at most 2 sms x 128 x 128
-            // partial floats and 2 sms tile counters (splits x tiles <= 2 sms)
-            const int S2 = 2 * std::max(h->sms, 1);
-            TcSplit sb{nullptr, (size_t)S2 * 128 * 128, nullptr, S2};
+            // partial floats (splits x tiles <= 2 sms)
+            TcSplit sb{nullptr, (size_t)2 * std::max(h->sms, 1) * 128 * 128};
             void* mem = nullptr;
-            if (cudaMallocAsync(&mem, sizeof(float) * sb.part_cap + sizeof(int) * S2, s) == cudaSuccess &&
-                cudaMemsetAsync(static_cast<float*>(mem) + sb.part_cap, 0, sizeof(int) * S2, s) == cudaSuccess) {
+            if (cudaMallocAsync(&mem, sizeof(float) * sb.part_cap, s) == cudaSuccess) {
                 sb.part = static_cast<float*>(mem);
-                sb.ctr = reinterpret_cast<int*>(sb.part + sb.part_cap);
                 c.bulk = &sb;
             } else {
                 cudaGetLastError();  // the bulk updates then run unsplit
+                mem = nullptr;
             }
             st = potrf_left<float>(c, n, !(flags & SPD_FACTOR_SERIAL));
             c.bulk = nullptr;

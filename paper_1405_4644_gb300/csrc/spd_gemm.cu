@@ -58,14 +58,14 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
                                                                                             ldo, kind);
     LAUNCH_CHECK(h);
     TcGemm* g = nullptr;
-    st = tc_gemm_create_maps(&g, Ah, M, ldo, Bh, N, ldo, Kp, C, ldc, kind);
+    st = tc_gemm_create_maps(&g, Ah, M, ldo, Bh, N, ldo, Kp, C, M, N, ldc, kind);
     if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: tensor map creation failed");
     ++h->launches;
     {
         const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
         ProfScope ps(h, SPD_PHASE_TRAILING, 2.0 * celems * K,
                      8.0 * celems + (double)es * Kp * (lower ? M : (double)M + N));
-        st = tc_gemm_launch(g, s, C, ldc, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
+        st = tc_gemm_launch(g, s, 0, 0, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
     }
     tc_gemm_destroy(g);
     if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: launch failed");
