@@ -415,16 +415,23 @@ spd_status spd_batch_destroy(spd_batch *plan);
  * (RNE) to `prec` (SPD_PREC_TF32, BF16, FP16 or FP8 -- FP8 multiplies the
  * operands by 2^8 before rounding, so |entries| <= 1.75 stay in range)
  * and multiplied with float32 accumulation; C is float32 row-major
- * (ldc >= N).  lower != 0 (requires A == B, M == N, lda == ldb) updates
- * only entries with row >= column.  SPD_PREC_FP32 splits each operand into
- * three bf16 slices (s0 = bf16(x), s1 = bf16(x - s0), s2 = bf16(x - s0 -
- * s1), together x's 24 significant bits) and accumulates the six slice
- * products of order <= 2, smallest first, in float32: float32-class
- * accuracy (the dropped products are below 2^-23 |a||b|, the slices' last
- * rounding below 2^-24 |x|) at one third of the bf16 tensor-core rate.
- * Device pointers; synchronous. */
+ * (ldc >= N).  With SPD_GEMM_LOWER (requires A == B, M == N, lda == ldb)
+ * only entries with row >= column are updated.  SPD_PREC_FP32 splits each
+ * operand into three bf16 slices (s0 = bf16(x), s1 = bf16(x - s0), s2 =
+ * bf16(x - s0 - s1), together x's 24 significant bits) and accumulates the
+ * six slice products of order <= 2 in float32, the five small ones and
+ * s0*t0 in separate accumulators added at the end: float32-class accuracy
+ * (the dropped products are below 2^-23 |a||b|, the slices' last rounding
+ * below 2^-24 |x|) at one sixth of the bf16 tensor-core rate.
+ * flags: SPD_GEMM_LOWER as above; SPD_GEMM_STREAM_K schedules the tiles'
+ * K loops over all SMs in equal contiguous ranges of (tile, K tile) units
+ * ("stream-K", the schedule the factorisation picks for its long bulk
+ * updates; the pieces of shared tiles are added to C in K order, so the
+ * result does not depend on timing).  Device pointers; synchronous. */
+#define SPD_GEMM_LOWER 1
+#define SPD_GEMM_STREAM_K 2
 spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,
-                           const float *B, int ldb, float *C, int ldc, int lower);
+                           const float *B, int ldb, float *C, int ldc, int flags);
 
 /* ---- phase timing ---------------------------------------------------------
  * Code-phase markers in the spirit of the paper's instrumentation library

@@ -389,7 +389,10 @@ def spd_launch_count(h):
     return c.value
 
 
-def spd_gemm_update(h, prec, A, B, C, lower=False):
+SPD_GEMM_LOWER, SPD_GEMM_STREAM_K = 1, 2
+
+
+def spd_gemm_update(h, prec, A, B, C, lower=False, stream_k=False):
     """C -= round(A) round(B)^T on the tensor cores; float32 row-major device
     tensors A (M, K), B (N, K), C (M, N)."""
     for t, nm in ((A, "A"), (B, "B"), (C, "C")):
@@ -401,7 +404,8 @@ def spd_gemm_update(h, prec, A, B, C, lower=False):
     if B.shape[1] != K or tuple(C.shape) != (M, N):
         raise ValueError(f"shapes A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)} do not match")
     return lib().spd_gemm_update(h, _prec(prec), M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
-                                 C.data_ptr(), C.stride(0), 1 if lower else 0)
+                                 C.data_ptr(), C.stride(0),
+                                 (SPD_GEMM_LOWER if lower else 0) | (SPD_GEMM_STREAM_K if stream_k else 0))
 
 
 def spd_residual_static(stream, A, B, X, R, colnorms=None):

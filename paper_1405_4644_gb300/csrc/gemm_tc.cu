@@ -86,10 +86,11 @@ __device__ __forceinline__ void apply_chunk(float* __restrict__ crow, const floa
     }
 }
 
-// 32 columns of the accumulator(s) of this thread's row: acc0 (+ acc1)
+// 32 columns (chunk ch) of the accumulator(s) of this thread's row: acc0
+// (+ acc1); tacc addresses the warp's lane quadrant of the tile's accumulator
 template <int NACC, int BNT>
-__device__ __forceinline__ void load_acc(uint32_t tmem, int warp, int ch, float* v) {
-    const uint32_t base = tmem + (static_cast<uint32_t>(warp * 32) << 16) + ch * 32;
+__device__ __forceinline__ void load_acc(uint32_t tacc, int ch, float* v) {
+    const uint32_t base = tacc + ch * 32;
     tc::tmem_ld_32x32b_x32(base, v);
     if constexpr (NACC == 2) {
         float w[32];
@@ -99,21 +100,103 @@ __device__ __forceinline__ void load_acc(uint32_t tmem, int warp, int ch, float*
     }
 }
 
-// K loop: K tile kin of this CTA's share, slice pair q inner.  Segment q
-// multiplies slice (segs >> 4q) & 3 of A by slice (segs >> 4q+2) & 3 of B
-// into accumulator (accsel >> q) & 1.
+// C -= scale * acc for one warp's 32 rows through shared memory (the idle
+// stage buffers, once the CTA's main loop is over): the rows as 32 x 32 boxes
+// (4 KB each, 128-byte swizzle: 16-byte chunk q of box row r sits at chunk
+// q ^ (r & 7), so a thread's row is read without bank conflicts), loaded by
+// TMA, updated, stored back by TMA.  Rows >= M, columns >= N and (lower)
+// entries above the diagonal keep their value: the boxes may reach past the
+// update's block and every box entry is written back.  Returns false if the
+// loads did not land in time.
+template <int NACC, int BNT>
+__device__ __forceinline__ bool epilogue_tma(unsigned char* base, uint64_t* cbar, volatile int* abort_flag,
+                                             const CUtensorMap* mapC, uint32_t tacc, int cx0, int cy0, int M, int N,
+                                             int bm, int bn, int qd, int lane, int lower, float scale) {
+    float* slab = reinterpret_cast<float*>(base) + qd * 32 * BNT;
+    const int row_w = bm * BM + qd * 32, row = row_w + lane;
+    int nbox = 0;
+    uint32_t need = 0;  // boxes inside N and not wholly above the diagonal
+    for (int ch = 0; ch < BNT / 32; ++ch) {
+        const int col0 = bn * BNT + ch * 32;
+        if (col0 >= N) break;
+        nbox = ch + 1;
+        if (!(lower && row_w + 31 < col0)) need |= 1u << ch;
+    }
+    if (!need) return true;
+    if (lane == 0) {
+        tc::mbar_arrive_expect_tx(&cbar[qd], 4096u * __popc(need));
+        for (int ch = 0; ch < nbox; ++ch)
+            if (need >> ch & 1u)
+                tc::tma_load_2d(slab + ch * 1024, mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, &cbar[qd]);
+    }
+    bool landed = tc::mbar_wait(&cbar[qd], 0, abort_flag, WAIT_NS);
+    if (!__all_sync(0xffffffffu, landed)) return false;
+    const int lim = row < M ? (lower ? min(N - 1, row) : N - 1) : -1;  // last column to update
+    for (int ch = 0; ch < nbox; ++ch) {
+        if (!(need >> ch & 1u)) continue;  // warp-uniform
+        float v[32];
+        load_acc<NACC, BNT>(tacc, ch, v);
+        float4* rp = reinterpret_cast<float4*>(slab + ch * 1024 + lane * 32);
+        const int col0 = bn * BNT + ch * 32;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float4 c = rp[q ^ (lane & 7)];
+            const int cq = col0 + 4 * q;
+            if (cq + 3 <= lim) {
+                c.x -= scale * v[4 * q];
+                c.y -= scale * v[4 * q + 1];
+                c.z -= scale * v[4 * q + 2];
+                c.w -= scale * v[4 * q + 3];
+            } else {
+                if (cq <= lim) c.x -= scale * v[4 * q];
+                if (cq + 1 <= lim) c.y -= scale * v[4 * q + 1];
+                if (cq + 2 <= lim) c.z -= scale * v[4 * q + 2];
+            }
+            rp[q ^ (lane & 7)] = c;
+        }
+    }
+    tc::fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        for (int ch = 0; ch < nbox; ++ch)
+            if (need >> ch & 1u) tc::tma_store_2d(mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, slab + ch * 1024);
+        tc::bulk_commit();
+        tc::bulk_wait_all();
+    }
+    __syncwarp();
+    return true;
+}
+
+// The launch covers T = tiles_m x tiles_n output tiles of 128 x BNT with nk
+// K tiles each: W = T nk work units (tile t, K tile k) in tile-major order.
+// CTA g takes units [g W / G, (g+1) W / G): with G = T each CTA owns one
+// whole tile ("data-parallel"); with G < T ("stream-K") a CTA's range is cut
+// by tile boundaries into pieces, and a piece that is not a whole tile can
+// only be the CTA's first piece (partial slot 2g) or its last (slot 2g+1).
+__device__ __forceinline__ long unit_begin(int g, long W, int G) { return (long)g * W / G; }
+
+// Roles: warp 0 issues the TMA loads, warp 1 the MMAs, warps 2..5 run the
+// epilogue (warp w reads TMEM lanes 32 (w % 4) .. +31, i.e. those rows of the
+// tile).  K loop of a piece: K tile kin, slice pair q inner; segment q
+// multiplies slice (segs >> 4q) & 3 of A by slice (segs >> 4q+2) & 3 of B into
+// accumulator (accsel >> q) & 1.  With one accumulator per tile (NACC = 1)
+// the tensor memory holds two, so the epilogue of one piece overlaps the
+// main loop of the next.
 template <int KIND, int BNT, int ST, int NACC>
-__global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
+__global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-              const __grid_constant__ CUtensorMap mapC, float* __restrict__ C, long ldc, int cx0, int cy0, int M,
-              int N, int K, int a_row0, int b_row0, int k0, int lower, uint32_t idesc, float scale, int nseg,
-              uint32_t segs, uint32_t accsel, int kslice, float* __restrict__ Cpart, long ldp, DevStatus* st) {
+              const __grid_constant__ CUtensorMap mapC, int use_map_c, float* __restrict__ C, long ldc, int cx0,
+              int cy0, int M, int N, int a_row0, int b_row0, int k0, int lower, uint32_t idesc, float scale, int nseg,
+              uint32_t segs, uint32_t accsel, int tiles_n, int nk, long W, int G, float* __restrict__ Cpart,
+              DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
     constexpr int B_STAGE = b_stage<BNT>();
     constexpr int STAGES = ST;
     constexpr int STAGE_BYTES = stage_bytes<BNT>();
-    constexpr uint32_t TMEM_COLS = BNT * NACC;
-    constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 4: 32 bytes of K each
+    constexpr int NBUF = NACC == 1 ? 2 : 1;
+    constexpr uint32_t ACC_COLS = BNT * NACC;  // one tile's accumulator(s)
+    constexpr uint32_t TMEM_COLS = ACC_COLS * NBUF;
+    constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 32 bytes of K each
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
@@ -121,28 +204,32 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     unsigned char* sB = base + STAGES * A_STAGE;
     uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;
-    uint64_t* cbar = accf + 1;  // one per warp: its C boxes have landed
+    uint64_t* accfull = empty + STAGES;  // [NBUF] MMA -> epilogue
+    uint64_t* accempty = accfull + 2;    // [NBUF] epilogue -> MMA (4 arrivals)
+    uint64_t* cbar = accempty + 2;       // [4] C boxes of a quadrant have landed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cbar + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bm = blockIdx.y, bn = blockIdx.x;
-    if (lower && (bm * BM + BM - 1 < bn * BNT)) return;  // whole tile above the diagonal
     if (st->flags & (SPD_DEV_BREAKDOWN | SPD_DEV_NONFINITE | SPD_DEV_BADDIAG)) return;
+    const int g = blockIdx.x;
+    const long u0 = unit_begin(g, W, G), u1 = unit_begin(g + 1, W, G);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             tc::mbar_init(&full[s], 1);
             tc::mbar_init(&empty[s], 1);
         }
-        tc::mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&accfull[b], 1);
+            tc::mbar_init(&accempty[b], 4);
+        }
         for (int w = 0; w < 4; ++w) tc::mbar_init(&cbar[w], 1);
         *abort_flag = 0;
         tc::fence_barrier_init();
         tc::prefetch_tmap(&mapA);
         tc::prefetch_tmap(&mapB);
-        if (!Cpart && !C) tc::prefetch_tmap(&mapC);
+        if (use_map_c) tc::prefetch_tmap(&mapC);
     }
     if (warp == 1) {
         tc::tmem_alloc(tmem_slot, TMEM_COLS);
@@ -152,22 +239,37 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tmem_slot;
-    const int nk_all = K / BK;  // K tiles per segment
-    const int kb = kslice > 0 ? (int)blockIdx.z * kslice : 0;
-    const int nk = kslice > 0 ? max(0, min(nk_all, kb + kslice) - kb) : nk_all;  // this CTA's share
-    const int ntiles = nk * nseg;
+    bool ok = true;
+
+    // pieces of [u0, u1): tile t, K tiles [kb, ke); tiles wholly above the
+    // diagonal of a lower update are skipped by every role alike
+#define SPD_FOR_PIECES                                                         \
+    for (long u = u0, un = u0; u < u1; u = un)                                 \
+        if (const int t = (int)(u / nk), kb = (int)(u - (long)t * nk),         \
+            ke = (int)min((long)nk, kb + (u1 - u)), bm = t / tiles_n,          \
+            bn = t - (t / tiles_n) * tiles_n;                                  \
+            (un = u + (ke - kb)), (lower && (bm * BM + BM - 1 < bn * BNT)))    \
+            ;                                                                  \
+        else
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            for (int kt = 0; kt < ntiles; ++kt) {
-                const int s = kt % STAGES;
-                const uint32_t ph = (kt / STAGES) & 1u;
-                const int kin = kt / nseg, q = kt - kin * nseg;
-                const int za = (segs >> (4 * q)) & 3, zb = (segs >> (4 * q + 2)) & 3;
-                if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) break;
-                tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + (kb + kin) * BK, a_row0 + bm * BM, za, &full[s]);
-                tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + (kb + kin) * BK, b_row0 + bn * BNT, zb, &full[s]);
+            int kt = 0;
+            SPD_FOR_PIECES {
+                for (int kin = kb; kin < ke && ok; ++kin)
+                    for (int q = 0; q < nseg; ++q, ++kt) {
+                        const int s = kt % STAGES;
+                        const uint32_t ph = (kt / STAGES) & 1u;
+                        const int za = (segs >> (4 * q)) & 3, zb = (segs >> (4 * q + 2)) & 3;
+                        if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
+                        tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + kin * BK, b_row0 + bn * BNT, zb, &full[s]);
+                    }
+                if (!ok) break;
             }
         }
         __syncwarp();
@@ -176,133 +278,95 @@ __global__ void __launch_bounds__(128, ST == 3 ? 2 : 1)
             // first segment (in issue order) of each accumulator starts it from zero
             int first[2] = {-1, -1};
             for (int q = nseg - 1; q >= 0; --q) first[(accsel >> q) & 1] = q;
-            for (int kt = 0; kt < ntiles; ++kt) {
-                const int s = kt % STAGES;
-                const uint32_t ph = (kt / STAGES) & 1u;
-                const int kin = kt / nseg, q = kt - kin * nseg;
-                const int a = (accsel >> q) & 1;
-                if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) break;
-                tc::fence_after_sync();
-                const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_STAGE));
-                const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_STAGE));
-                const uint32_t d = tmem + (uint32_t)(a * BNT);
-                const bool fresh = kin == 0 && q == first[a];
+            int kt = 0, p = 0;
+            SPD_FOR_PIECES {
+                const int buf = p % NBUF;
+                if (p >= NBUF) {  // the epilogue has drained this accumulator
+                    if (!tc::mbar_wait(&accempty[buf], ((p / NBUF) - 1) & 1, abort_flag, WAIT_NS)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::fence_after_sync();
+                }
+                for (int kin = kb; kin < ke && ok; ++kin)
+                    for (int q = 0; q < nseg; ++q, ++kt) {
+                        const int s = kt % STAGES;
+                        const uint32_t ph = (kt / STAGES) & 1u;
+                        const int a = (accsel >> q) & 1;
+                        if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_STAGE));
+                        const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_STAGE));
+                        const uint32_t d = tmem + (uint32_t)(buf * ACC_COLS + a * BNT);
+                        const bool fresh = kin == kb && q == first[a];
 #pragma unroll
-                for (int k = 0; k < MMA_PER_STAGE; ++k)  // +32 bytes of K = +2 in the address field
-                    tc::mma<KIND>(d, ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
-                tc::mma_commit(&empty[s]);
+                        for (int k = 0; k < MMA_PER_STAGE; ++k)  // +32 bytes of K = +2 in the address field
+                            tc::mma<KIND>(d, ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
+                        tc::mma_commit(&empty[s]);
+                    }
+                if (!ok) break;
+                tc::mma_commit(&accfull[buf]);
+                ++p;
             }
-            tc::mma_commit(accf);
         }
         __syncwarp();
-    }
-
-    // epilogue: TMEM -> registers -> C -= scale * acc
-    bool ok = tc::mbar_wait(accf, 0, abort_flag, WAIT_NS) && !*abort_flag;
-    if (threadIdx.x == 0) pdl_trigger();  // a dependent kernel (the next leaf) may be scheduled
-    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-    tc::fence_after_sync();
-    const int row = bm * BM + warp * 32 + lane;
-    const int row_w = bm * BM + warp * 32;  // first row of this warp's slab (warp-uniform)
-    if (Cpart) {
-        // split K: this CTA's raw accumulator (zero for an empty share)
-        if (ok) {
-            for (int ch = 0; ch < BNT / 32; ++ch) {
-                const int col0 = bn * BNT + ch * 32;
-                if (col0 >= N) break;
-                float v[32];
-                if (ntiles > 0) load_acc<NACC, BNT>(tmem, warp, ch, v);
-                else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0.f;
-                }
-                if (row < M) {
-                    float* prow = Cpart + ((long)blockIdx.z * M + row) * ldp + col0;
-                    if (col0 + 32 <= N && ((reinterpret_cast<uintptr_t>(prow) & 15) == 0)) {
+    } else {  // epilogue warps
+        const int qd = warp & 3;  // TMEM lane quadrant = rows 32 qd .. 32 qd + 31 of the tile
+        int p = 0;
+        SPD_FOR_PIECES {
+            const int buf = p % NBUF;
+            ok = tc::mbar_wait(&accfull[buf], (p / NBUF) & 1, abort_flag, WAIT_NS);
+            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+            if (!ok) break;
+            tc::fence_after_sync();
+            const bool last = un >= u1;
+            if (last && warp == 2 && lane == 0) pdl_trigger();  // a dependent kernel may be scheduled
+            const uint32_t tacc = tmem + (static_cast<uint32_t>(qd * 32) << 16) + (uint32_t)(buf * ACC_COLS);
+            const int row_w = bm * BM + qd * 32;  // first row of this warp's slab (local, warp-uniform)
+            const int row = row_w + lane;
+            if (!(kb == 0 && ke == nk)) {
+                // part of a tile: raw accumulator into partial slot 2g (the
+                // CTA's first piece) or 2g + 1 (its last)
+                const int slot = 2 * g + (u == u0 ? 0 : 1);
+                float* prow = Cpart + ((long)slot * BM + qd * 32 + lane) * BNT;
+                for (int ch = 0; ch < BNT / 32; ++ch) {
+                    if (bn * BNT + ch * 32 >= N) break;  // warp-uniform
+                    float v[32];
+                    load_acc<NACC, BNT>(tacc, ch, v);
+                    if (row < M) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
-                            reinterpret_cast<float4*>(prow)[q] =
+                            reinterpret_cast<float4*>(prow + ch * 32)[q] =
                                 make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (col0 + j < N) prow[j] = v[j];
                     }
                 }
-            }
-        }
-    } else if (ok && C) {  // C given directly (no tensor map): C is the block's origin
-        for (int ch = 0; ch < BNT / 32; ++ch) {
-            const int col0 = bn * BNT + ch * 32;
-            if (col0 >= N) break;                           // warp-uniform
-            if (lower && row_w + 31 < col0) continue;       // warp-uniform: chunk above the diagonal
-            float v[32];
-            load_acc<NACC, BNT>(tmem, warp, ch, v);
-            if (row < M) apply_chunk(C + (long)row * ldc + col0, v, row, col0, N, lower, scale);
-        }
-    } else if (ok && row_w < M) {
-        // C -= scale * acc through shared memory: the warp's 32 rows as
-        // 32 x 32 boxes (4 KB each, 128-byte swizzle: 16-byte chunk q of
-        // box row r sits at chunk q ^ (r & 7)), in the idle stage buffers
-        float* slab = reinterpret_cast<float*>(base) + warp * 32 * BNT;
-        int nbox = 0;
-        uint32_t need = 0;  // boxes inside N and not wholly above the diagonal
-        for (int ch = 0; ch < BNT / 32; ++ch) {
-            const int col0 = bn * BNT + ch * 32;
-            if (col0 >= N) break;
-            nbox = ch + 1;
-            if (!(lower && row_w + 31 < col0)) need |= 1u << ch;
-        }
-        if (lane == 0 && need) {
-            tc::mbar_arrive_expect_tx(&cbar[warp], 4096u * __popc(need));
-            for (int ch = 0; ch < nbox; ++ch)
-                if (need >> ch & 1u)
-                    tc::tma_load_2d(slab + ch * 1024, &mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, &cbar[warp]);
-        }
-        bool landed = !need || tc::mbar_wait(&cbar[warp], 0, abort_flag, WAIT_NS);
-        landed = __all_sync(0xffffffffu, landed);
-        if (landed) {
-            for (int ch = 0; ch < nbox; ++ch) {
-                if (!(need >> ch & 1u)) continue;  // warp-uniform
-                float v[32];
-                load_acc<NACC, BNT>(tmem, warp, ch, v);
-                float4* rp = reinterpret_cast<float4*>(slab + ch * 1024 + lane * 32);
-                const int col0 = bn * BNT + ch * 32;
-                // rows >= M, columns >= N and (lower) entries above the
-                // diagonal keep their value: the boxes may reach past the
-                // update's block, and the stores write every box entry back
-                const int lim = row < M ? (lower ? min(N - 1, row) : N - 1) : -1;  // last column to update
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    float4 c = rp[q ^ (lane & 7)];
-                    const int cq = col0 + 4 * q;
-                    if (cq + 3 <= lim) {
-                        c.x -= scale * v[4 * q];
-                        c.y -= scale * v[4 * q + 1];
-                        c.z -= scale * v[4 * q + 2];
-                        c.w -= scale * v[4 * q + 3];
-                    } else {
-                        if (cq <= lim) c.x -= scale * v[4 * q];
-                        if (cq + 1 <= lim) c.y -= scale * v[4 * q + 1];
-                        if (cq + 2 <= lim) c.z -= scale * v[4 * q + 2];
-                    }
-                    rp[q ^ (lane & 7)] = c;
+            } else if (last && use_map_c) {
+                if (row_w < M && !epilogue_tma<NACC, BNT>(base, cbar, abort_flag, &mapC, tacc, cx0, cy0, M, N, bm,
+                                                            bn, qd, lane, lower, scale))
+                    ok = false;
+            } else {
+                for (int ch = 0; ch < BNT / 32; ++ch) {
+                    const int col0 = bn * BNT + ch * 32;
+                    if (col0 >= N) break;                      // warp-uniform
+                    if (lower && row_w + 31 < col0) continue;  // warp-uniform: chunk above the diagonal
+                    float v[32];
+                    load_acc<NACC, BNT>(tacc, ch, v);
+                    if (row < M) apply_chunk(C + (long)row * ldc + col0, v, row, col0, N, lower, scale);
                 }
             }
-            tc::fence_proxy_async_smem();
+            ok = __all_sync(0xffffffffu, ok);
+            tc::fence_before_sync();
             __syncwarp();
-            if (lane == 0) {
-                for (int ch = 0; ch < nbox; ++ch)
-                    if (need >> ch & 1u) tc::tma_store_2d(&mapC, cx0 + bn * BNT + ch * 32, cy0 + row_w, slab + ch * 1024);
-                tc::bulk_commit();
-                tc::bulk_wait_all();
-            }
-            __syncwarp();
-        } else {
-            ok = false;
+            if (lane == 0) tc::mbar_arrive(&accempty[buf]);
+            if (!ok) break;
+            ++p;
         }
     }
-    if (!ok && threadIdx.x == 0) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
+#undef SPD_FOR_PIECES
+    if (!ok && (lane == 0)) atomicOr(&st->flags, SPD_DEV_TIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tmem, TMEM_COLS);
@@ -392,43 +456,40 @@ void set_attrs() {
     (void)done;
 }
 
-// C[i][j] -= scale * sum_{z < S} P[z][i][j] (z in increasing order), only
-// i >= j when lower.  Launched as a programmatic dependent of the split GEMM:
-// everything before pdl_wait overlaps the GEMM's last CTAs.
+// Stream-K fix-up: for every entry of a tile that several CTAs share,
+// C[i][j] -= scale * (sum of their partial slots in CTA order, i.e. in K
+// order), only i >= j when lower.  Unit u belongs to CTA
+// owner(u) = floor(((u + 1) G - 1) / W) (the largest g with g W / G <= u);
+// tile t's piece of CTA g is g's first piece (slot 2g) when g's range starts
+// inside tile t, else its last (slot 2g + 1).  Launched as a programmatic
+// dependent of the GEMM: everything before pdl_wait overlaps its last CTAs.
 __global__ void __launch_bounds__(256) k_reduce_parts(float* __restrict__ C, long ldc, int M, int N,
-                                                      const float* __restrict__ P, int S, float scale, int lower) {
+                                                      const float* __restrict__ P, int bnt, int tiles_n, int nk,
+                                                      long W, int G, float scale, int lower) {
     pdl_wait();
-    if ((N & 3) == 0) {
-        const int n4 = N >> 2;
-        const long total = (long)M * n4;
-        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-            const int i = (int)(e / n4), j = (int)(e - (long)i * n4) * 4;
-            if (lower && i < j) continue;
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int z = 0; z < S; ++z) {
-                const float4 p = __ldcg(reinterpret_cast<const float4*>(P + ((long)z * M + i) * N + j));
-                acc.x += p.x;
-                acc.y += p.y;
-                acc.z += p.z;
-                acc.w += p.w;
-            }
-            float4* cp = reinterpret_cast<float4*>(C + (long)i * ldc + j);
-            float4 c = *cp;
-            c.x -= scale * acc.x;
-            if (!lower || i >= j + 1) c.y -= scale * acc.y;
-            if (!lower || i >= j + 2) c.z -= scale * acc.z;
-            if (!lower || i >= j + 3) c.w -= scale * acc.w;
-            *cp = c;
+    const int nq = (N + 3) >> 2;  // groups of four columns
+    const long total = (long)M * nq;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / nq), j = (int)(e - (long)i * nq) * 4;
+        if (lower && i < j) continue;
+        const int t = (i / BM) * tiles_n + j / bnt;
+        const long ut0 = (long)t * nk, ut1 = ut0 + nk;
+        const int glo = (int)(((ut0 + 1) * G - 1) / W), ghi = (int)((ut1 * G - 1) / W);
+        if (glo == ghi && unit_begin(glo, W, G) <= ut0 && unit_begin(glo + 1, W, G) >= ut1)
+            continue;  // the whole tile was one CTA's piece: already applied
+        const int r = i % BM, c = j % bnt;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int gg = glo; gg <= ghi; ++gg) {
+            const int slot = 2 * gg + (unit_begin(gg, W, G) / nk == t ? 0 : 1);
+            const float4 pv = __ldcg(reinterpret_cast<const float4*>(P + ((long)slot * BM + r) * bnt + c));
+            acc[0] += pv.x;
+            acc[1] += pv.y;
+            acc[2] += pv.z;
+            acc[3] += pv.w;
         }
-    } else {
-        const long total = (long)M * N;
-        for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-            const int i = (int)(e / N), j = (int)(e - (long)i * N);
-            if (lower && i < j) continue;
-            float acc = 0.f;
-            for (int z = 0; z < S; ++z) acc += __ldcg(P + ((long)z * M + i) * N + j);
-            C[(long)i * ldc + j] -= scale * acc;
-        }
+        float* cp = C + (long)i * ldc + j;
+        for (int q = 0; q < 4; ++q)
+            if (j + q < N && !(lower && i < j + q)) cp[q] -= scale * acc[q];
     }
 }
 
@@ -479,25 +540,24 @@ spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, 
 namespace {
 
 template <int BNT>
-void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, int cx0, int cy0, int M, int N, int K, int a_row0,
-                 int b_row0, int k0, int lower, float scale, int nseg, uint32_t segs, uint32_t accsel, int kslice,
-                 float* Cpart, long ldp, DevStatus* st) {
+void launch_kind(TcGemm* g, cudaStream_t s, int G, int cx0, int cy0, int M, int N, int a_row0, int b_row0, int k0,
+                 int lower, float scale, int nseg, uint32_t segs, uint32_t accsel, int tiles_n, int nk, long W,
+                 float* Cpart, DevStatus* st) {
     const CUtensorMap& mb = BNT == 128 ? g->mapB128 : g->mapB;
     const uint32_t idesc = idesc_for(g->kind, BNT);
-    // without a tensor map of C the epilogue writes C (the block's origin) directly
-    float* Cdirect = g->has_map_c ? nullptr : g->C + (long)cy0 * g->ldc + cx0;
+    float* Cb = g->C + (long)cy0 * g->ldc + cx0;  // the block's origin (epilogue without a tensor map)
 #define SPD_GEMM_ARGS                                                                                            \
-    g->mapA, mb, g->mapC, Cdirect, g->ldc, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, idesc, scale, nseg, \
-        segs, accsel, kslice, Cpart, ldp, st
+    g->mapA, mb, g->mapC, g->has_map_c ? 1 : 0, Cb, g->ldc, cx0, cy0, M, N, a_row0, b_row0, k0, lower, idesc, \
+        scale, nseg, segs, accsel, tiles_n, nk, W, G, Cpart, st
     switch (g->kind) {
-        case 1: k_gemm_tc<1, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+        case 1: k_gemm_tc<1, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
         case 5: {  // float32 as bf16 slices: two accumulators; two CTAs per SM on 128-wide tiles
             constexpr int ST = BNT == 128 ? 3 : 4;
-            k_gemm_tc<0, BNT, ST, 2><<<grid, 128, smem_bytes<BNT, ST>(), s>>>(SPD_GEMM_ARGS);
+            k_gemm_tc<0, BNT, ST, 2><<<G, 192, smem_bytes<BNT, ST>(), s>>>(SPD_GEMM_ARGS);
             break;
         }
-        case 4: k_gemm_tc<2, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
-        default: k_gemm_tc<0, BNT, 4, 1><<<grid, 128, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS);
+        case 4: k_gemm_tc<2, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+        default: k_gemm_tc<0, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS);
     }
 #undef SPD_GEMM_ARGS
 }
@@ -507,6 +567,7 @@ void launch_kind(TcGemm* g, cudaStream_t s, dim3 grid, int cx0, int cy0, int M, 
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, int N, int K, int a_row0, int b_row0,
                           int k0, int lower, DevStatus* st, int splits, const TcSplit* sb) {
     const int bk = g->kind == 1 ? 32 : g->kind == 4 ? 128 : 64;
+    if (M <= 0 || N <= 0 || K <= 0) return SPD_OK;
     if (K % bk != 0 || (k0 * elem_bytes(g->kind)) % 16 != 0 || cx0 % 4 != 0) return SPD_ERR_ARG;
     const float scale = g->kind == 4 ? 1.0f / (tc_fp8_scale() * tc_fp8_scale()) : 1.0f;
     // float32 as three bf16 slices: the six slice products of order <= 2 (A
@@ -522,29 +583,36 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
     }
     const int nk = K / bk;
     const int bnt = (N <= 128) ? 128 : 256;
-    const int tiles = ((N + bnt - 1) / bnt) * ((M + BM - 1) / BM);
-    // splits < 0: choose from the SM count -splits, filling the machine once
-    // (two CTAs per SM for the 128-wide float32 tiles)
-    if (splits < 0) {
-        const int occ = (bnt == 128 && g->kind == 5) ? 2 : 1;
-        splits = std::max(1, std::min(16, occ * (-splits) / std::max(tiles, 1)));
+    const int tiles_n = (N + bnt - 1) / bnt, tiles_m = (M + BM - 1) / BM;
+    const int T = tiles_n * tiles_m;
+    const long W = (long)T * nk;
+    // Data-parallel (one CTA per tile) or stream-K over `slots` CTAs, by an
+    // estimate of the launch's length: waves x K tiles per CTA x the time of
+    // one K tile, plus ~10 us of fix-up kernel for stream-K.  splits < 0
+    // allows stream-K on -splits SMs (two CTAs per SM for the 128-wide
+    // float32 tiles); splits = 1 keeps one CTA per tile.
+    int G = T;
+    if ((splits < 0 || splits == 0) && sb && sb->part && !(lower && tiles_n > 1)) {
+        const int sms = splits < 0 ? -splits : g->sms;
+        const int slots = (bnt == 128 && g->kind == 5 ? 2 : 1) * sms;
+        const int Gs = (int)std::min<long>(slots, W);
+        const double tk = nseg * (bnt == 256 ? 0.40 : 0.25);  // us per K tile (all segments)
+        const double dp = (double)((T + slots - 1) / slots) * nk * tk;
+        const double sk = (double)((W + Gs - 1) / Gs) * tk + 10.0;
+        // splits = 0: stream-K whenever it gives more CTAs than tiles
+        const bool want = splits == 0 ? Gs > T : sk < 0.9 * dp;
+        if (want && (size_t)2 * Gs * BM * bnt <= sb->part_cap) G = Gs;
     }
-    if (splits > nk) splits = nk;
-    const bool split = splits > 1 && sb && sb->part && (size_t)splits * M * N <= sb->part_cap;
-    const int kslice = split ? (nk + splits - 1) / splits : 0;
-    if (split) splits = (nk + kslice - 1) / kslice;  // no empty share
-    dim3 grid((N + bnt - 1) / bnt, (M + BM - 1) / BM, split ? splits : 1);
-    const long ldp = N;
-    float* part = split ? sb->part : nullptr;
+    float* part = (G < T) ? sb->part : nullptr;
     if (bnt == 128)
-        launch_kind<128>(g, s, grid, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
-                         part, ldp, st);
+        launch_kind<128>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
+                         W, part, st);
     else
-        launch_kind<256>(g, s, grid, cx0, cy0, M, N, K, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, kslice,
-                         part, ldp, st);
-    if (split) {
+        launch_kind<256>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
+                         W, part, st);
+    if (part) {
         cudaLaunchConfig_t cfg = {};
-        const long work = (long)M * ((N & 3) == 0 ? N / 4 : N);
+        const long work = (long)M * ((N + 3) / 4);
         cfg.gridDim = dim3((unsigned)std::max<long>(1, std::min<long>((work + 255) / 256, 4L * g->sms)));
         cfg.blockDim = dim3(256);
         cfg.stream = s;
@@ -554,8 +622,8 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
         cfg.attrs = at;
         cfg.numAttrs = 1;
         float* C = g->C + (long)cy0 * g->ldc + cx0;
-        if (cudaLaunchKernelEx(&cfg, k_reduce_parts, C, g->ldc, M, N, (const float*)part, splits, scale, lower) !=
-            cudaSuccess)
+        if (cudaLaunchKernelEx(&cfg, k_reduce_parts, C, g->ldc, M, N, (const float*)part, bnt, tiles_n, nk, W, G,
+                               scale, lower) != cudaSuccess)
             return SPD_ERR_CUDA;
     }
     return cudaGetLastError() == cudaSuccess ? SPD_OK : SPD_ERR_CUDA;

@@ -18,11 +18,13 @@ struct TcSplit {
 // Plan for one factor: tensor maps over Wh for the operand tiles.
 // Returns SPD_ERR_UNSUPPORTED when the operand kind has no tensor-core path.
 spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n);
-// splits > 1 with split scratch sb splits K across CTAs and a dependent
-// kernel sums the partials in a fixed order (lower masks apply as without
-// splitting); splits = -S lets the GEMM pick the split count for S SMs (at
-// most 16: splits x tiles <= 2 S, so 2 S x 128 x 128 partial floats always
-// suffice).  Without room in sb the update runs unsplit.
+// splits = -S with scratch sb lets the GEMM spread the tiles' K loops over
+// the S SMs ("stream-K": equal contiguous ranges of (tile, K tile) units per
+// CTA) when that is estimated faster than one CTA per tile; the pieces of
+// shared tiles go to partial slots (2 slots x 128 x 256 floats per CTA: 4 S x
+// 128 x 128 floats suffice) that a dependent kernel adds to C in K order.
+// splits = 0 takes stream-K whenever it gives more CTAs than tiles (on all
+// SMs).  Otherwise (splits = 1, or without room in sb) one CTA per tile.
 spd_status tc_gemm_run(TcGemm* g, cudaStream_t s, int r0, int M, int c0, int N, int k0, int K, int lower,
                        DevStatus* st, int splits = 1, const TcSplit* sb = nullptr);
 void tc_gemm_destroy(TcGemm* g);

@@ -336,9 +336,9 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (prec == SPD_PREC_FP64) {
             st = potrf_rec<double>(c, 0, n);
         } else if (c.tc && !(flags & SPD_FACTOR_RECURSIVE)) {
-            // split-K scratch of the bulk updates: at most 2 sms x 128 x 128
-            // partial floats (splits x tiles <= 2 sms)
-            TcSplit sb{nullptr, (size_t)2 * std::max(h->sms, 1) * 128 * 128};
+            // stream-K partial slots of the bulk updates: 2 per CTA, at most
+            // 2 sms CTAs of 128 x 128 or sms CTAs of 128 x 256
+            TcSplit sb{nullptr, (size_t)4 * std::max(h->sms, 1) * 128 * 128};
             void* mem = nullptr;
             if (cudaMallocAsync(&mem, sizeof(float) * sb.part_cap, s) == cudaSuccess) {
                 sb.part = static_cast<float*>(mem);

@@ -31,7 +31,10 @@ int kind_of(int prec) {
 }  // namespace
 
 extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int K, const float* A, int lda,
-                                      const float* B, int ldb, float* C, int ldc, int lower) {
+                                      const float* B, int ldb, float* C, int ldc, int flags) {
+    if ((unsigned)flags & ~3u) return set_err(h, SPD_ERR_ARG, "spd_gemm_update: unknown flags 0x%x", flags);
+    const int lower = flags & SPD_GEMM_LOWER;
+    const bool stream_k = (flags & SPD_GEMM_STREAM_K) != 0;
     if (!h) return SPD_ERR_ARG;
     const int kind = kind_of(prec);
     if (!kind)
@@ -46,6 +49,8 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
     WsPlan p;
     size_t oa = p.add<unsigned char>((size_t)M * ldo * es);
     size_t ob = lower ? oa : p.add<unsigned char>((size_t)N * ldo * es);
+    const size_t part_cap = (size_t)4 * std::max(h->sms, 1) * 128 * 128;  // stream-K partial slots
+    size_t op = stream_k ? p.add<float>(part_cap) : 0;
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
     void* Ah = ws_at<unsigned char>(h, oa);
@@ -65,7 +70,8 @@ extern "C" spd_status spd_gemm_update(spd_handle* h, int prec, int M, int N, int
         const double celems = lower ? 0.5 * (double)M * (M + 1) : (double)M * N;
         ProfScope ps(h, SPD_PHASE_TRAILING, 2.0 * celems * K,
                      8.0 * celems + (double)es * Kp * (lower ? M : (double)M + N));
-        st = tc_gemm_launch(g, s, 0, 0, M, N, (int)Kp, 0, 0, 0, lower, h->dst);
+        TcSplit sb{stream_k ? ws_at<float>(h, op) : nullptr, part_cap};
+        st = tc_gemm_launch(g, s, 0, 0, M, N, (int)Kp, 0, 0, 0, lower, h->dst, stream_k ? 0 : 1, &sb);
     }
     tc_gemm_destroy(g);
     if (st != SPD_OK) return set_err(h, st, "spd_gemm_update: launch failed");

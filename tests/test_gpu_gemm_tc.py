@@ -101,3 +101,54 @@ def test_gemm_update_rejects_bad_arguments(h):
     assert spd.spd_gemm_update(h, "fp64", A, A, A) == spd.SPD_ERR_UNSUPPORTED
     assert spd.lib().spd_gemm_update(h, spd.PREC["bf16"], 8, 8, 8, A.data_ptr(), 4, A.data_ptr(), 8,
                                      A.data_ptr(), 8, 0) == spd.SPD_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp16", "tf32", "fp8", "fp32"])
+@pytest.mark.parametrize("M,N,K", [(300, 500, 1024), (1000, 1000, 1024), (129, 256, 4096), (37, 100, 2048)])
+def test_gemm_update_stream_k_matches_rounded_product(h, prec, M, N, K):
+    """Stream-K schedule (equal (tile, K tile) ranges per CTA, pieces of
+    shared tiles added to C in K order by the fix-up kernel): same bounds as
+    one CTA per tile, and the same result for every launch."""
+    import torch
+    g = np.random.default_rng(M * 5 + N + K)
+    scale = 1.0 if prec == "fp8" else 2.0
+    A = g.uniform(-1, 1, (M, K)) * scale
+    B = g.uniform(-1, 1, (N, K)) * scale
+    C0 = g.standard_normal((M, N)).astype(np.float32).astype(np.float64)
+    Ar, Br = rounded(A, prec), rounded(B, prec)
+    ref = C0 - Ar @ Br.T
+    At = torch.from_numpy(A.astype(np.float32)).to(DEV)
+    Bt = torch.from_numpy(B.astype(np.float32)).to(DEV)
+    outs = []
+    for _ in range(2):
+        Ct = torch.from_numpy(C0.astype(np.float32)).to(DEV)
+        check(h, spd.spd_gemm_update(h, prec, At, Bt, Ct, stream_k=True))
+        outs.append(Ct.cpu().numpy().astype(np.float64))
+    got = outs[0]
+    assert np.array_equal(outs[0], outs[1])  # deterministic
+    mag = np.abs(Ar) @ np.abs(Br).T
+    if prec == "fp32":
+        bound = (K + 8) * 2.0 ** -24 * mag + 2.0 ** -24 * np.abs(C0)
+    else:
+        bound = 4 * K * 2.0 ** -23 * mag + 2.0 ** -22 * np.abs(C0) + 1e-30
+    err = np.abs(got - ref)
+    assert np.all(err <= bound), float((err / bound).max())
+
+
+@pytest.mark.parametrize("M,K", [(200, 2048), (256, 1024)])
+def test_gemm_update_stream_k_lower(h, M, K):
+    g = np.random.default_rng(M + 3 * K)
+    A = g.uniform(-1, 1, (M, K))
+    C0 = g.standard_normal((M, M)).astype(np.float32).astype(np.float64)
+    Ar = rounded(A, "bf16")
+    ref = C0 - Ar @ Ar.T
+    import torch
+    At = torch.from_numpy(A.astype(np.float32)).to(DEV)
+    Ct = torch.from_numpy(C0.astype(np.float32)).to(DEV)
+    check(h, spd.spd_gemm_update(h, "bf16", At, At, Ct, lower=True, stream_k=True))
+    got = Ct.cpu().numpy().astype(np.float64)
+    iu = np.triu_indices(M, 1)
+    assert np.array_equal(got[iu], C0[iu])
+    il = np.tril_indices(M)
+    bound = 4 * K * 2.0 ** -23 * (np.abs(Ar) @ np.abs(Ar).T) + 2.0 ** -22 * np.abs(C0)
+    assert np.all(np.abs(got[il] - ref[il]) <= bound[il])
