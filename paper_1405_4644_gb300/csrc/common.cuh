@@ -16,7 +16,8 @@ enum : int {
     SPD_DEV_NONFINITE = 1,   // NaN/Inf met in an input
     SPD_DEV_BREAKDOWN = 2,   // non-positive pivot
     SPD_DEV_TIMEOUT = 4,     // a bounded wait gave up
-    SPD_DEV_BADDIAG = 8      // non-positive diagonal entry (scaling impossible)
+    SPD_DEV_BADDIAG = 8,     // non-positive diagonal entry (scaling impossible)
+    SPD_DEV_INTERNAL = 16    // a kernel met launch arguments it cannot serve
 };
 
 struct DevStatus {

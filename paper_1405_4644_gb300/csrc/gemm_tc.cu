@@ -327,7 +327,9 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
             const uint32_t tacc = tmem + (static_cast<uint32_t>(qd * 32) << 16) + (uint32_t)(buf * ACC_COLS);
             const int row_w = bm * BM + qd * 32;  // first row of this warp's slab (local, warp-uniform)
             const int row = row_w + lane;
-            if (!(kb == 0 && ke == nk)) {
+            if (!(kb == 0 && ke == nk) && !Cpart) {
+                if (lane == 0) atomicOr(&st->flags, SPD_DEV_INTERNAL);  // a piece with nowhere to go
+            } else if (!(kb == 0 && ke == nk)) {
                 // part of a tile: raw accumulator into partial slot 2g (the
                 // CTA's first piece) or 2g + 1 (its last)
                 const int slot = 2 * g + (u == u0 ? 0 : 1);
@@ -603,7 +605,9 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
         const bool want = splits == 0 ? Gs > T : sk < 0.9 * dp;
         if (want && (size_t)2 * Gs * BM * bnt <= sb->part_cap) G = Gs;
     }
-    float* part = (G < T) ? sb->part : nullptr;
+    // stream-K (G != T: more or fewer CTAs than tiles) always writes partials
+    float* part = (G != T) ? sb->part : nullptr;
+    if (G != T && !part) return SPD_ERR_ARG;
     if (bnt == 128)
         launch_kind<128>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
                          W, part, st);
