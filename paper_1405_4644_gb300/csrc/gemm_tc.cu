@@ -468,30 +468,49 @@ void set_attrs() {
 __global__ void __launch_bounds__(256) k_reduce_parts(float* __restrict__ C, long ldc, int M, int N,
                                                       const float* __restrict__ P, int bnt, int tiles_n, int nk,
                                                       long W, int G, float scale, int lower) {
+    // block (x, t): tile t = blockIdx.y, rows [x * RB, x * RB + RB) of it
+    constexpr int RB = 16;
+    const int t = blockIdx.y;
+    const int bm = t / tiles_n, bn = t - bm * tiles_n;
+    const long ut0 = (long)t * nk, ut1 = ut0 + nk;
+    const int glo = (int)(((ut0 + 1) * G - 1) / W), ghi = (int)((ut1 * G - 1) / W);
+    if (glo == ghi && unit_begin(glo, W, G) <= ut0 && unit_begin(glo + 1, W, G) >= ut1) return;  // one CTA's piece
+    // slot of contributor glo: 2 glo + 1 when its range starts before the
+    // tile, else 2 glo; every later contributor starts inside the tile (2g)
+    const int slot_lo = 2 * glo + (unit_begin(glo, W, G) < ut0 ? 1 : 0);
+    const int ncon = ghi - glo + 1;
+    const int nq = bnt >> 2;  // float4 groups in a tile row
     pdl_wait();
-    const int nq = (N + 3) >> 2;  // groups of four columns
-    const long total = (long)M * nq;
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
-        const int i = (int)(e / nq), j = (int)(e - (long)i * nq) * 4;
-        if (lower && i < j) continue;
-        const int t = (i / BM) * tiles_n + j / bnt;
-        const long ut0 = (long)t * nk, ut1 = ut0 + nk;
-        const int glo = (int)(((ut0 + 1) * G - 1) / W), ghi = (int)((ut1 * G - 1) / W);
-        if (glo == ghi && unit_begin(glo, W, G) <= ut0 && unit_begin(glo + 1, W, G) >= ut1)
-            continue;  // the whole tile was one CTA's piece: already applied
-        const int r = i % BM, c = j % bnt;
-        float acc[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int gg = glo; gg <= ghi; ++gg) {
-            const int slot = 2 * gg + (unit_begin(gg, W, G) / nk == t ? 0 : 1);
-            const float4 pv = __ldcg(reinterpret_cast<const float4*>(P + ((long)slot * BM + r) * bnt + c));
-            acc[0] += pv.x;
-            acc[1] += pv.y;
-            acc[2] += pv.z;
-            acc[3] += pv.w;
+    for (int e = threadIdx.x; e < RB * nq; e += blockDim.x) {
+        const int r = blockIdx.x * RB + e / nq, c = (e % nq) * 4;
+        const int i = bm * BM + r, j = bn * bnt + c;
+        if (r >= BM || i >= M || j >= N || (lower && i < j)) continue;
+        const float* pr = P + (long)r * bnt + c;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        // contributors in K order; loads issued eight at a time, added in order
+        for (int k0 = 0; k0 < ncon; k0 += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = k0 + q;
+                const int slot = k == 0 ? slot_lo : 2 * (glo + k);
+                v[q] = k < ncon ? __ldcg(reinterpret_cast<const float4*>(pr + (long)slot * BM * bnt))
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (k0 + q < ncon) {
+                    acc.x += v[q].x;
+                    acc.y += v[q].y;
+                    acc.z += v[q].z;
+                    acc.w += v[q].w;
+                }
         }
         float* cp = C + (long)i * ldc + j;
+        const float a4[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
         for (int q = 0; q < 4; ++q)
-            if (j + q < N && !(lower && i < j + q)) cp[q] -= scale * acc[q];
+            if (j + q < N && !(lower && i < j + q)) cp[q] -= scale * a4[q];
     }
 }
 
@@ -597,13 +616,21 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
     if ((splits < 0 || splits == 0) && sb && sb->part && !(lower && tiles_n > 1)) {
         const int sms = splits < 0 ? -splits : g->sms;
         const int slots = (bnt == 128 && g->kind == 5 ? 2 : 1) * sms;
-        const int Gs = (int)std::min<long>(slots, W);
+        int Gs = (int)std::min<long>(slots, W);
         const double tk = nseg * (bnt == 256 ? 0.40 : 0.25);  // us per K tile (all segments)
         const double dp = (double)((T + slots - 1) / slots) * nk * tk;
-        const double sk = (double)((W + Gs - 1) / Gs) * tk + 10.0;
-        // splits = 0: stream-K whenever it gives more CTAs than tiles
-        const bool want = splits == 0 ? Gs > T : sk < 0.9 * dp;
-        if (want && (size_t)2 * Gs * BM * bnt <= sb->part_cap) G = Gs;
+        // stream-K over Gc CTAs: the longest range, plus the fix-up: a launch
+        // (~4 us) and its partial slots read at ~3 TB/s
+        auto sk_us = [&](int Gc) {
+            return (double)((W + Gc - 1) / Gc) * tk + 4.0 + 2.0 * Gc * BM * bnt * 4.0 / 3e6;
+        };
+        int best = Gs;
+        for (int d = 2; d <= 16; d *= 2)
+            if (Gs / d > T && sk_us(Gs / d) < sk_us(best)) best = Gs / d;
+        // splits = 0: stream-K over all slots whenever it gives more CTAs than tiles
+        const bool want = splits == 0 ? Gs > T : sk_us(best) < 0.9 * dp;
+        if (splits != 0) Gs = best;
+        if (want && Gs != T && (size_t)2 * Gs * BM * bnt <= sb->part_cap) G = Gs;
     }
     // stream-K (G != T: more or fewer CTAs than tiles) always writes partials
     float* part = (G != T) ? sb->part : nullptr;
@@ -616,8 +643,7 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
                          W, part, st);
     if (part) {
         cudaLaunchConfig_t cfg = {};
-        const long work = (long)M * ((N + 3) / 4);
-        cfg.gridDim = dim3((unsigned)std::max<long>(1, std::min<long>((work + 255) / 256, 4L * g->sms)));
+        cfg.gridDim = dim3(BM / 16, (unsigned)T);  // 16 rows of one tile per block
         cfg.blockDim = dim3(256);
         cfg.stream = s;
         cudaLaunchAttribute at[1];
