@@ -254,23 +254,9 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
 
     if (warp == 0) {
         if (lane == 0) {  // TMA producer
-            // operand tiles of the K tile PF ahead go to L2 first, so that
-            // the loads below meet L2 latency rather than HBM latency
-            constexpr int PF = 8;
-            auto prefetch = [&](int kin, int bm, int bn) {
-                for (int q = 0; q < nseg; ++q) {
-                    const int za = (segs >> (4 * q)) & 3, zb = (segs >> (4 * q + 2)) & 3;
-                    if (q == 0 || za != ((segs >> (4 * (q - 1))) & 3))
-                        tc::tma_prefetch_3d(&mapA, k0 + kin * BK, a_row0 + bm * BM, za);
-                    if (q == 0 || zb != ((segs >> (4 * (q - 1) + 2)) & 3))
-                        tc::tma_prefetch_3d(&mapB, k0 + kin * BK, b_row0 + bn * BNT, zb);
-                }
-            };
             int kt = 0;
             SPD_FOR_PIECES {
-                for (int kin = kb; kin < min(ke, kb + PF); ++kin) prefetch(kin, bm, bn);
-                for (int kin = kb; kin < ke && ok; ++kin) {
-                    if (kin + PF < ke) prefetch(kin + PF, bm, bn);
+                for (int kin = kb; kin < ke && ok; ++kin)
                     for (int q = 0; q < nseg; ++q, ++kt) {
                         const int s = kt % STAGES;
                         const uint32_t ph = (kt / STAGES) & 1u;
@@ -283,7 +269,6 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
                         tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
                         tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + kin * BK, b_row0 + bn * BNT, zb, &full[s]);
                     }
-                }
                 if (!ok) break;
             }
         }
