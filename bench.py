@@ -177,17 +177,79 @@ def job_rate(units_per_rank, world, seconds_max):
 # ---------------------------------------------------------------------------
 # workload
 # ---------------------------------------------------------------------------
-def make_systems(n, m, kappas, dev):
+def make_systems(n, m, kappas, dev, spectra=None):
+    """(kappa, A, B) on the device per kappa; with a list `spectra`, also
+    (lam, V, B on the host) of each system, for its exact solution."""
     import numpy as np
     import torch
     import workloads as W
     systems = []
     for i, kappa in enumerate(kappas):
         A, lam, V = W.householder_spectrum(n, kappa, k=32, seed=i, device=dev)
-        B = torch.from_numpy(np.ascontiguousarray(W.gaussian_rhs(n, m, 100 + i).T)).to(dev).t()
+        Bh = W.gaussian_rhs(n, m, 100 + i)
+        B = torch.from_numpy(np.ascontiguousarray(Bh.T)).to(dev).t()
         systems.append((kappa, A, B))
+        if spectra is not None:
+            spectra.append((lam, V, Bh))
     torch.cuda.synchronize()
     return systems
+
+
+def forward_errors(A_dev, X_gpu, lam, V, B, lapack=True):
+    """Normwise forward errors max_c ||x_c - x*_c||_inf / ||x*_c||_inf of the
+    GPU solution and (lapack) of LAPACK's float64 Cholesky solve of the same
+    assembled matrix on the host, both against the exact solution x* of the
+    prescribed spectrum (Q^T B by reflections, divided by lam, Q by
+    reflections: accurate to roundoff whatever kappa is)."""
+    import numpy as np
+    import oracle
+    Xs = oracle.spectral_solve(V, lam, B)
+    den = np.max(np.abs(Xs), axis=0)
+    fe = lambda X: float(np.max(np.max(np.abs(X - Xs), axis=0) / den))
+    out = {"fwd_err": fe(X_gpu)}
+    if lapack:
+        import scipy.linalg as sl
+        t0 = time.perf_counter()
+        Ah = A_dev.cpu().numpy()
+        Xl = sl.cho_solve(sl.cho_factor(Ah, lower=True, check_finite=False), B, check_finite=False)
+        out["fwd_err_lapack"] = fe(Xl)
+        out["lapack_s"] = time.perf_counter() - t0
+    return out
+
+
+def timed_repeats(fn, reps, nvml, stream):
+    """One untimed call, then `reps` calls each bracketed by CUDA events on
+    `stream`, inside one NVML energy window: (median ms, J per call)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    times = []
+    e0 = nvml.energy_mj() if nvml.ok else None
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(b))
+    e1 = nvml.energy_mj() if nvml.ok else None
+    j = (e1 - e0) / 1e3 / reps if e0 is not None and e1 is not None else None
+    return statistics.median(times), j, sum(times) / 1e3
+
+
+def idle_power(nvml, seconds=1.0):
+    """Mean GPU power with nothing running (NVML), the baseline of net energy."""
+    if not nvml.ok:
+        return None
+    vals = []
+    t_end = time.perf_counter() + seconds
+    while time.perf_counter() < t_end:
+        v = nvml.power_w()
+        if v is not None:
+            vals.append(v)
+        time.sleep(0.05)
+    return statistics.mean(vals) if vals else None
 
 
 def solve_one(spd, h, A, B, X, prec, opts, kappa):
@@ -282,8 +344,9 @@ def cpu_oracle_sample(n_full, m, seconds_hint=20.0):
     assert np.isfinite(X).all()
     scale = (n_full / ns) ** 3
     return {"value": 1.0 / (t * scale), "unit": UNIT, "cores": oracle.cpu_threads(), "kind": "oracle",
-            "sample": f"one float64 oracle solve (Cholesky + substitution) at n={ns}, m={m}, kappa=1e2: "
-                      f"{t:.2f} s, scaled by (n/{ns})^3 to n={n_full}"}
+            "extrapolated": True,
+            "sample": f"extrapolated: one float64 oracle solve (Cholesky + substitution) at n={ns}, m={m}, "
+                      f"kappa=1e2 took {t:.2f} s; scaled by (n/{ns})^3 to n={n_full}"}
 
 
 # FP32 instruction issue rate of the part: 152 SMs x 128 lanes x 2.07 GHz
@@ -296,37 +359,36 @@ DF32_OPS_PER_MADD = 12
 # DRAM bytes (read + write, ncu) of a phase's launches, measured on a smaller
 # case of the same kernels.  "solve": one forward + backward sweep pair at
 # n = 8192, m = 16 read 137.10 + 136.97 MB and wrote 0.22 + 3.12 MB; the
-# sweeps stream the factor once each, so the bytes scale with n^2.
-# "trailing_x3": the ratio of DRAM bytes to algorithmic bytes over every
-# update (and split-K reduction) of one n = 8192 FP32 factorisation; a
-# launch's traffic is that ratio times its algorithmic bytes.
+# sweeps stream the factor once each, so the bytes scale with n^2.  A phase
+# in MEASURED_TRAFFIC_RATIO reports that ratio of DRAM bytes to algorithmic
+# bytes (over a capture of its kernels) times its algorithmic bytes per launch.
 MEASURED_TRAFFIC = {
     "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2,
               "ncu DRAM bytes of one forward + backward sweep pair at n = 8192, m = 16, scaled by n^2"),
 }
-MEASURED_TRAFFIC_RATIO = {
-    "trailing_x3": (5595882752 / 5.012324e9, "ncu DRAM bytes / algorithmic bytes over one n = 8192 FP32 "
-                    "factorisation's updates, times this phase's algorithmic bytes per launch"),
-}
+MEASURED_TRAFFIC_RATIO = {}
 
 
-def roofline(phases, per_kappa, n=None):
-    """Roofline of the phase (kernel family) that took the most device time
-    in the timed region; achieved = its algorithmic work / its event time."""
+def phase_roofline(dom, ph, per_kappa, n=None):
+    """Roofline of one phase (kernel family): achieved = its algorithmic work
+    / its summed event time, against the peak of the unit that bounds it."""
     peaks, src = load_peaks()
     bf16 = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
-    dom = max(phases, key=lambda p: phases[p]["ms"])
-    ph = phases[dom]
+    bf16_burst = peaks["bf16_tflops"]
     sec = ph["ms"] * 1e-3
     low = sorted({k["prec_used"] for k in per_kappa} & set(TENSOR_RATIO))
     if dom == "trailing" and low:
         ratio = min(TENSOR_RATIO[p] for p in low)
-        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": bf16 * ratio,
-             "peak_source": f"{src} bf16 sustained x nominal {'/'.join(low)} ratio {ratio}"}
-    elif dom == "trailing_x3":
-        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12,
-             "peak": bf16 / 6,
-             "peak_source": f"{src} bf16 sustained / 6 bf16 slice products per float32 product"}
+        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": bf16_burst * ratio,
+             "peak_source": f"{src} bf16 burst x nominal {'/'.join(low)} ratio {ratio} (kernels timed alone)",
+             "frac_of_sustained": ph["flops"] / sec / 1e12 / (bf16 * ratio)}
+    elif dom in ("trailing_x3", "trailing_last") and ph["flops"]:
+        x3 = dom == "trailing_x3" or (low and low == ["fp32"])
+        div = 6 if x3 else 1
+        r = {"bound": "tensor", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": bf16_burst / div,
+             "peak_source": f"{src} bf16 burst" + (" / 6 bf16 slice products per float32 product" if x3 else "")
+                            + " (kernels timed alone)",
+             "frac_of_sustained": ph["flops"] / sec / 1e12 / (bf16 / div)}
     elif dom == "resid":
         r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP64_PEAK_TFLOPS,
              "peak_source": "nominal FP64 1.25 TFLOP/s of the part"}
@@ -356,6 +418,16 @@ def roofline(phases, per_kappa, n=None):
               "algorithmic_per_launch": work / max(ph["launches"], 1)})
     return r
 
+
+def roofline(phases, per_kappa, n=None):
+    """Roofline of the phase that took the most device time, and of every
+    phase that took at least 1 % of it (key "phases")."""
+    dom = max(phases, key=lambda p: phases[p]["ms"])
+    r = phase_roofline(dom, phases[dom], per_kappa, n)
+    r["phases"] = {p: {k: v for k, v in phase_roofline(p, ph, per_kappa, n).items()
+                       if k in ("bound", "unit", "achieved", "peak", "frac", "launches", "avg_launch_ms")}
+                   for p, ph in phases.items() if ph["ms"] >= 0.01 * phases[dom]["ms"] and ph["launches"]}
+    return r
 
 
 def reference_arm(args):
@@ -660,6 +732,9 @@ def case_leg(args):
     return 0
 
 
+FP64_REPS = 3
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,6 +748,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-fwd", action="store_true", help="skip the forward errors against the exact solution")
+    ap.add_argument("--no-lapack", action="store_true", help="forward errors without LAPACK's host solve")
     ap.add_argument("--lanes", type=int, default=3,
                     help="systems solved concurrently (one handle, stream and host thread each)")
     ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc"],
@@ -713,7 +790,8 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     h = spd.spd_create(stream)
-    systems = make_systems(args.n, args.m, args.kappas, dev)
+    spectra = []
+    systems = make_systems(args.n, args.m, args.kappas, dev, spectra)
     X = torch.zeros(args.m, args.n, dtype=torch.float64, device=dev).t()
     opts = {"tol": 1e-14, "crit": "berr", "resid": args.resid}
 
@@ -734,6 +812,8 @@ def main():
 
     smi = SmiSampler(torch.cuda.current_device())
     nvml = Nvml(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    idle_w = idle_power(nvml)
     for hh in handles:
         spd.spd_profile_enable(hh, True)
     launches0 = sum(spd.spd_launch_count(hh) for hh in handles)
@@ -776,15 +856,27 @@ def main():
         # come from one more step of the same workload with every kernel
         # running alone: one lane, the factor's serial schedule (CUDA events on
         # the launching stream).
+        # The same pass gives each system's solution (bit-identical to the
+        # timed region's: the serial schedule computes the same factor) for
+        # its forward error, computed on the host after the pass.
         spd.spd_profile_enable(h, True)
+        sols = []
         for (k, A, B), p in zip(systems, precs):
             st, F, _ = spd.spd_factor(h, A, p, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SERIAL)
             if st != spd.SPD_OK:
                 raise RuntimeError("roofline pass: " + spd.spd_last_error_string(h))
             st, _ = spd.spd_solve_ir(h, F, A, B, X, opts)
             spd.spd_factor_destroy(F)
+            sols.append(X.cpu().numpy())
         roof_phases = {p: spd.spd_profile_read(h, p) for p in spd.PHASES}
         spd.spd_profile_enable(h, False)
+        if not args.no_fwd:
+            for pk, (k, A, B), Xg, (lam, V, Bh) in zip(per_kappa, systems, sols, spectra):
+                fe = forward_errors(A, Xg, lam, V, Bh, lapack=not args.no_lapack)
+                fe["bound"] = 10.0 * k * 1e-16
+                if "fwd_err_lapack" in fe:
+                    fe["within_bound_of_lapack"] = fe["fwd_err"] <= fe["fwd_err_lapack"] + fe["bound"]
+                pk.update(fe)
         roof_note = ("phases of one extra step of the same workload with every kernel alone (one lane, serial "
                      "factor schedule); the timed region ran concurrent lanes and the look-ahead")
     roof = roofline(roof_phases, per_kappa, args.n)
@@ -792,8 +884,11 @@ def main():
     energy = None
     if e0 is not None and e1 is not None:
         j = (e1 - e0) / 1e3
-        energy = {"j_per_solve": j / (len(systems) * args.steps), "avg_power_w": j / (ms / 1e3),
+        nsol = len(systems) * args.steps
+        energy = {"j_per_solve": j / nsol, "avg_power_w": j / (ms / 1e3),
                   "source": "NVML total-energy counter, gross"}
+        if idle_w is not None:
+            energy.update({"idle_w": idle_w, "j_per_solve_net": (j - idle_w * ms / 1e3) / nsol})
     elif clocks:
         j = clocks["avg_power_w"] * ms / 1e3
         energy = {"j_per_solve": j / (len(systems) * args.steps), "avg_power_w": clocks["avg_power_w"],
@@ -859,21 +954,36 @@ def main():
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None
     if not args.no_fp64:
+        # float64 Cholesky of the first system (kappa = 1e2; the float64
+        # factor's cost does not depend on kappa): ours (blocked, CUDA cores,
+        # then refinement with float64 residuals) and cuSOLVER's through
+        # torch; one untimed solve, then FP64_REPS solves in one NVML window
         kappa, A, B = systems[0]
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        (fr, r), = run_step(spd, h, [systems[0]], ["fp64"], X, dict(opts, resid="fp64"))
-        torch.cuda.synchronize()
-        t_ours = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        Lc = torch.linalg.cholesky(A)
-        Xc = torch.cholesky_solve(B.contiguous(), Lc)
-        torch.cuda.synchronize()
-        t_cusolver = time.perf_counter() - t0
-        del Lc, Xc
-        best = min(t_ours, t_cusolver)
-        fp64 = {"ms_per_solve_ours": 1e3 * t_ours, "ms_per_solve_cusolver": 1e3 * t_cusolver,
-                "berr_ours": r.berr, "speedup_vs_faster": best / (ms / 1e3 / (len(systems) * args.steps))}
+        rep_out = []
+        t_ours, j_ours, s_ours = timed_repeats(
+            lambda: rep_out.append(run_step(spd, h, [systems[0]], ["fp64"], X, dict(opts, resid="fp64"))[0]),
+            FP64_REPS, nvml, stream)
+        fr, r = rep_out[-1]
+
+        def cusolver():
+            Lc = torch.linalg.cholesky(A)
+            torch.cholesky_solve(B.contiguous(), Lc)
+
+        t_cus, j_cus, s_cus = timed_repeats(cusolver, FP64_REPS, nvml, stream)
+        ms_mixed = ms / (len(systems) * args.steps)
+        fast_t = min(t_ours, t_cus)
+        fp64 = {"reps": FP64_REPS, "ms_per_solve_ours": t_ours, "ms_per_solve_cusolver": t_cus,
+                "timing": "median of the repeats, CUDA events; one untimed solve first",
+                "berr_ours": r.berr, "speedup_time_vs_faster": fast_t / ms_mixed}
+        if j_ours is not None and j_cus is not None:
+            fp64.update({"j_per_solve_ours": j_ours, "j_per_solve_cusolver": j_cus,
+                         "energy_window_s": [s_ours, s_cus]})
+            if energy is not None:
+                fp64["speedup_energy_vs_lower"] = min(j_ours, j_cus) / energy["j_per_solve"]
+                if idle_w is not None:
+                    net = lambda j, sec: j - idle_w * sec / FP64_REPS
+                    fp64["speedup_energy_net_vs_lower"] = (min(net(j_ours, s_ours), net(j_cus, s_cus))
+                                                           / energy["j_per_solve_net"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
