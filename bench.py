@@ -366,7 +366,15 @@ MEASURED_TRAFFIC = {
     "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2,
               "ncu DRAM bytes of one forward + backward sweep pair at n = 8192, m = 16, scaled by n^2"),
 }
-MEASURED_TRAFFIC_RATIO = {}
+MEASURED_TRAFFIC_RATIO = {
+    # one stream-K bulk update of an n = 8192 FP32 factorisation (block
+    # columns 32-33: M = 4096, N = 256, K = 3968, 152 CTAs): 99.76 MB read +
+    # 3.28 MB written against 105.6 MB algorithmic (C read and written once,
+    # three bf16 slices of each operand row once)
+    "trailing_x3": ((99757568 + 3281152) / (8.0 * (256 * 4096 - 0.5 * 256 * 255) + 6.0 * 3968 * 4096),
+                    "ncu DRAM bytes / algorithmic bytes of one stream-K FP32 bulk update at n = 8192, times this "
+                    "phase's algorithmic bytes per launch"),
+}
 
 
 def phase_roofline(dom, ph, per_kappa, n=None):
@@ -792,6 +800,12 @@ def main():
     h = spd.spd_create(stream)
     spectra = []
     systems = make_systems(args.n, args.m, args.kappas, dev, spectra)
+    # idle baseline of the energy figures: after the input generation has
+    # drained and a short pause, before any solver work
+    nvml = Nvml(torch.cuda.current_device())
+    torch.cuda.synchronize()
+    time.sleep(1.0)
+    idle_w = idle_power(nvml, 2.0)
     X = torch.zeros(args.m, args.n, dtype=torch.float64, device=dev).t()
     opts = {"tol": 1e-14, "crit": "berr", "resid": args.resid}
 
@@ -811,9 +825,6 @@ def main():
     torch.cuda.synchronize()
 
     smi = SmiSampler(torch.cuda.current_device())
-    nvml = Nvml(torch.cuda.current_device())
-    torch.cuda.synchronize()
-    idle_w = idle_power(nvml)
     for hh in handles:
         spd.spd_profile_enable(hh, True)
     launches0 = sum(spd.spd_launch_count(hh) for hh in handles)
