@@ -195,6 +195,20 @@ def make_systems(n, m, kappas, dev, spectra=None):
     return systems
 
 
+def make_cov_systems(n, m, count, dev):
+    """The covariance workload: A_ij = exp(-|p_i - p_j|_2 / 0.1) + 1e-3 delta_ij
+    over n points uniform in the unit cube (seed 0), m N(0,1) right-hand
+    sides (seed 100); `count` copies of (None, A, B) sharing A, one per
+    precision compared."""
+    import numpy as np
+    import torch
+    import workloads as W
+    A, _ = W.exp_kernel_cov(n, ell=0.1, nugget=1e-3, seed=0, dim=3, device=dev)
+    B = torch.from_numpy(np.ascontiguousarray(W.gaussian_rhs(n, m, 100).T)).to(dev).t()
+    torch.cuda.synchronize()
+    return [(None, A, B) for _ in range(count)]
+
+
 def forward_errors(A_dev, X_gpu, lam, V, B, lapack=True):
     """Normwise forward errors max_c ||x_c - x*_c||_inf / ||x*_c||_inf of the
     GPU solution and (lapack) of LAPACK's float64 Cholesky solve of the same
@@ -752,6 +766,9 @@ def main():
     ap.add_argument("--n", type=int, default=16384)
     ap.add_argument("--m", type=int, default=16)
     ap.add_argument("--kappas", default="1e2,1e4,1e6")
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "cov"],
+                    help="sweep: prescribed-spectrum matrices, one per kappa; cov: the exponential-kernel "
+                         "covariance matrix, one solve per precision in --precs")
     ap.add_argument("--precs", default="auto")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -777,7 +794,7 @@ def main():
     args = ap.parse_args()
     args.kappas = [float(k) for k in args.kappas.split(",")]
     precs = args.precs.split(",")
-    if len(precs) == 1:
+    if len(precs) == 1 and args.workload == "sweep":
         precs = precs * len(args.kappas)
     if args.impl == "reference":
         return reference_arm(args)
@@ -799,7 +816,11 @@ def main():
     stream = torch.cuda.current_stream()
     h = spd.spd_create(stream)
     spectra = []
-    systems = make_systems(args.n, args.m, args.kappas, dev, spectra)
+    if args.workload == "cov":
+        systems = make_cov_systems(args.n, args.m, len(precs), dev)
+        args.no_fwd = True  # no known exact solution for this matrix
+    else:
+        systems = make_systems(args.n, args.m, args.kappas, dev, spectra)
     # idle baseline of the energy figures: after the input generation has
     # drained and a short pause, before any solver work
     nvml = Nvml(torch.cuda.current_device())
@@ -859,7 +880,8 @@ def main():
     # dominant phase and its roofline
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
                   "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
-                  "fell_back": r.fell_back, "berr": r.berr} for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
+                  "iters_low": r.iters_low, "fell_back": r.fell_back, "berr": r.berr}
+                 for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
     roof_phases, roof_note = phases, "phases of the timed region"
     if True:
         # A launch's event time under concurrency (the lanes, and the factor's
@@ -1005,9 +1027,13 @@ def main():
                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "mixed: " + "/".join(sorted(set(precs))) + " factor, f64 refinement",
                "data": "synthetic",
-               "config": {"workload": f"precision sweep n={args.n} m={args.m} kappa in {args.kappas}",
-                          "n": args.n, "m": args.m, "kappas": args.kappas, "factor_prec": precs,
-                          "l2": "inputs larger than L2 (3 x 8 n^2 bytes resident)", "tol_berr": 1e-14,
+               "config": {"workload": (f"precision sweep n={args.n} m={args.m} kappa in {args.kappas}"
+                                       if args.workload == "sweep" else
+                                       f"covariance n={args.n} m={args.m}: exp(-|p_i-p_j|/0.1) + 1e-3 I, "
+                                       f"points U[0,1]^3, one solve per precision {precs}"),
+                          "n": args.n, "m": args.m, "factor_prec": precs,
+                          **({"kappas": args.kappas} if args.workload == "sweep" else {}),
+                          "l2": f"inputs larger than L2 ({len(systems)} x 8 n^2 bytes resident)", "tol_berr": 1e-14,
                           "lanes": args.lanes,
                           "residual": {"fp64": "float64 throughout",
                                        "df32": "float32 pairs while berr > 2^-36, float64 to finish "

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import DEV, check, dev_cols, dev_sym, dev_zeros, factor_L, host  # noqa: E402
 
 SIZES = [1, 2, 3, 31, 33, 127, 128, 129, 300, 513, 1000]
-PRECS = ["fp64", "fp32", "tf32", "bf16", "fp16"]
+PRECS = ["fp64", "fp32", "tf32", "bf16", "fp16", "fp8"]
 
 
 @pytest.fixture(scope="module")
@@ -53,7 +53,7 @@ def test_factor_matches_oracle(h, n, prec):
 
 
 @pytest.mark.parametrize("n", [129, 700, 2100])
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16", "fp16", "fp8"])
 def test_left_looking_and_recursive_schedules_agree(h, n, prec):
     """The default block-column (left-looking) schedule, its serial form and
     the recursive one compute the same factor up to rounding: all meet the
@@ -121,7 +121,7 @@ def test_residual_matches_oracle(h, n, m):
     np.testing.assert_allclose(cn[:, 2], np.abs(X).max(axis=0), rtol=0)
 
 
-@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("prec", [p for p in PRECS if p != "fp8"])
 @pytest.mark.parametrize("n,m", [(1, 1), (2, 2), (129, 3), (300, 1), (1024, 1), (777, 16), (400, 33)])
 def test_solve_ir_matches_oracle(h, prec, n, m):
     """Algorithm 1: low-precision factor, float64 refinement to backward error
@@ -314,3 +314,57 @@ def test_tensor_core_and_cuda_core_factors_agree(h, prec, n):
         spd.spd_factor_destroy(F2)
     kappa = np.linalg.cond(L2) ** 2
     assert np.max(np.abs(L1 - L2)) <= 64 * kappa * n * 2.0 ** -24
+
+
+@pytest.mark.parametrize("n,m", [(129, 3), (700, 1), (1100, 8), (2049, 2)])
+def test_fp8_update_factor_refines_where_iterref_holds(h, n, m):
+    """FP8 (e4m3) trailing-update operands put errors of about u = 2^-4 into
+    the factor: eq. (iterref) holds for a well-conditioned matrix (kappa ~ 1.6
+    here), so Algorithm 1 reaches backward error 1e-14 with no fallback; the
+    sweeps needed are more than for FP16 operands but bounded."""
+    A = np.eye(n) + 0.3 * W.gram_shifted(n, seed=n, shift=0.0)
+    x_true = W.gaussian_rhs(n, m, 2)
+    B = A @ x_true
+    Ad = dev_sym(A)
+    sweeps = {}
+    for prec in ("fp8", "fp16"):
+        st, F, _ = spd.spd_factor(h, Ad, prec)
+        check(h, st)
+        X = dev_zeros(n, m)
+        try:
+            st, rep = spd.spd_solve_ir(h, F, Ad, dev_cols(B), X, {"fallback": 0})
+            check(h, st)
+        finally:
+            spd.spd_factor_destroy(F)
+        Xg = host(X)
+        assert oracle.berr(A, B, Xg) <= 1e-14 and rep.fell_back == 0, prec
+        Xo = oracle.solve(A, B)
+        kappa = np.linalg.cond(A)
+        fw = np.max(np.abs(Xg - Xo), axis=0) / np.max(np.abs(Xo), axis=0)
+        assert np.all(fw <= 10 * kappa * 1e-16 * max(1.0, np.sqrt(n) / 8)), (prec, fw)
+        sweeps[prec] = rep.iters_high
+    assert sweeps["fp16"] <= sweeps["fp8"] <= 30, sweeps
+
+
+@pytest.mark.parametrize("n", [700, 2049])
+def test_fp8_update_factor_falls_back_where_iterref_fails(h, n):
+    """kappa ~ 41 (G G^T / n + 0.1 I): kappa u_fp8 is above one, eq. (iterref)
+    gives no guarantee and plain refinement with the FP8-update factor
+    stagnates (two sweeps in a row shrink the error by less than half); the
+    fallback (float64 CG preconditioned by the same factor, Section 3.1: any
+    inner solver that contracts will do) takes over and still reaches
+    backward error 1e-14."""
+    A = W.gram_shifted(n, seed=3, shift=0.1)
+    x_true = W.gaussian_rhs(n, 2, 4)
+    B = A @ x_true
+    Ad = dev_sym(A)
+    st, F, _ = spd.spd_factor(h, Ad, "fp8")
+    check(h, st)
+    X = dev_zeros(n, 2)
+    try:
+        st, rep = spd.spd_solve_ir(h, F, Ad, dev_cols(B), X)
+        check(h, st)
+    finally:
+        spd.spd_factor_destroy(F)
+    assert rep.fell_back == 1
+    assert oracle.berr(A, B, host(X)) <= 1e-14
