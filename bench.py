@@ -266,8 +266,12 @@ def idle_power(nvml, seconds=1.0):
     return statistics.mean(vals) if vals else None
 
 
+FACTOR_FLAGS = {"flags": None}  # spd_factor flags of every benchmark solve (set from --shift)
+
+
 def solve_one(spd, h, A, B, X, prec, opts, kappa):
-    st, F, frep = spd.spd_factor(h, A, prec)
+    flags = FACTOR_FLAGS["flags"] if FACTOR_FLAGS["flags"] is not None else spd.SPD_SCALE_DIAG
+    st, F, frep = spd.spd_factor(h, A, prec, flags)
     if st != spd.SPD_OK:
         raise RuntimeError(f"spd_factor({prec}, kappa={kappa}): {spd.spd_last_error_string(h)}")
     st, rep = spd.spd_solve_ir(h, F, A, B, X, opts)
@@ -774,6 +778,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-fwd", action="store_true", help="skip the forward errors against the exact solution")
+    ap.add_argument("--shift", action="store_true",
+                    help="factor with SPD_FACTOR_SHIFT (a shifted factor when the plain one breaks down)")
     ap.add_argument("--no-lapack", action="store_true", help="forward errors without LAPACK's host solve")
     ap.add_argument("--lanes", type=int, default=3,
                     help="systems solved concurrently (one handle, stream and host thread each)")
@@ -811,6 +817,8 @@ def main():
     import torch
     import paper_1405_4644_gb300 as spd
 
+    if args.shift:
+        FACTOR_FLAGS["flags"] = spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SHIFT
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -880,7 +888,7 @@ def main():
     # dominant phase and its roofline
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
                   "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
-                  "iters_low": r.iters_low, "fell_back": r.fell_back, "berr": r.berr}
+                  "iters_low": r.iters_low, "fell_back": r.fell_back, "berr": r.berr, "shift": fr.shift}
                  for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
     roof_phases, roof_note = phases, "phases of the timed region"
     if True:

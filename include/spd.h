@@ -123,6 +123,18 @@ typedef enum spd_resid {
                                     (large updates, many small panels) instead
                                     of the default left-looking 128-column
                                     schedule                                */
+#define SPD_FACTOR_SHIFT 16u     /* if the factorisation breaks down, factor
+                                    the scaled matrix plus sigma I instead,
+                                    sigma = 2 u (u the unit roundoff of the
+                                    update operands: the size of the updates'
+                                    rounding relative to the unit diagonal),
+                                    raised fourfold until it succeeds (at
+                                    most sigma = 1); refinement then sees a
+                                    perturbation of norm <= sigma and, when it
+                                    stagnates, hands over to the factor-
+                                    preconditioned CG fallback (Section 3.1,
+                                    eq. (iterref): the inner solver only has
+                                    to contract).  report.shift gives sigma */
 #define SPD_FACTOR_SERIAL 8u     /* left-looking schedule without its
                                     look-ahead: every kernel on the handle's
                                     stream in order (kernels then run alone,
@@ -157,6 +169,8 @@ typedef struct spd_report {
                         number of the scaled matrix (Hager's estimator);
                         -1 when the FP16 factor broke down before it could
                         be estimated; 0 for the other precisions           */
+    double shift;    /* spd_factor with SPD_FACTOR_SHIFT: the sigma of the
+                        factor actually kept (0 = no shift was needed)      */
 } spd_report;
 
 typedef struct spd_handle spd_handle;

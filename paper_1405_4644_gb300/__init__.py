@@ -43,6 +43,7 @@ SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
 SPD_FACTOR_RECURSIVE = 4
 SPD_FACTOR_SERIAL = 8
+SPD_FACTOR_SHIFT = 16
 
 # every symbol include/spd.h declares
 EXPORTED = [
@@ -64,7 +65,7 @@ class SpdOpts(C.Structure):
 class SpdReport(C.Structure):
     _fields_ = [("status", C.c_int), ("info", C.c_int), ("iters_low", C.c_int), ("iters_high", C.c_int),
                 ("prec_used", C.c_int), ("fell_back", C.c_int), ("berr", C.c_double), ("rel_resid", C.c_double),
-                ("time_ms", C.c_double), ("cond_est", C.c_double)]
+                ("time_ms", C.c_double), ("cond_est", C.c_double), ("shift", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

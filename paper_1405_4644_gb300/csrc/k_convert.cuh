@@ -98,6 +98,13 @@ static __global__ void k_scale_convert(const double* __restrict__ A, long lda, i
     }
 }
 
+// W[i][i] += sigma: the shifted factorisation of SPD_FACTOR_SHIFT.
+template <typename T>
+static __global__ void k_add_diag(T* __restrict__ W, long ldw, int n, double sigma) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) W[(long)i * ldw + i] += (T)sigma;
+}
+
 // Full low-precision copy A~ = fl(A) for the CG matrix-vector product:
 // row-major n x lda_out (A is symmetric, so this is also its column-major
 // copy).  T is float or __nv_bfloat16.

@@ -275,7 +275,7 @@ size_t mirror_elem(int kind) { return kind == 5 ? 6 : kind == 1 ? 4 : kind == 4 
 
 // One factorisation attempt in a fixed precision.
 spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
-                       spd_factor_t** out, spd_report* rep) {
+                       spd_factor_t** out, spd_report* rep, double shift = 0.0) {
     spd_factor_t* F = new spd_factor_t();
     F->h = h;
     F->n = n;
@@ -321,6 +321,12 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
             ++(h)->launches, k_scale_convert<double><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W64, F->ldw, h->dst);
         else
             ++(h)->launches, k_scale_convert<float><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W, F->ldw, h->dst);
+        if (shift > 0.0) {  // SPD_FACTOR_SHIFT: factor the scaled matrix plus shift I
+            if (prec == SPD_PREC_FP64)
+                ++(h)->launches, k_add_diag<double><<<ceil_div(n, 256), 256, 0, s>>>(F->W64, F->ldw, n, shift);
+            else
+                ++(h)->launches, k_add_diag<float><<<ceil_div(n, 256), 256, 0, s>>>(F->W, F->ldw, n, shift);
+        }
         delete pconv;
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(h, SPD_ERR_CUDA, "convert launch failed"));
         spd_status st = check_dev_status(h, rep, "spd_factor");
@@ -500,6 +506,18 @@ extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda,
     } else {
         st = factor_once(h, n, A, lda, prec, flags, F, rep);
     }
+    double sigma = 0.0;
+    if (st == SPD_ERR_NOT_SPD && (flags & SPD_FACTOR_SHIFT) && prec != SPD_PREC_AUTO && prec != SPD_PREC_FP64) {
+        // shifted retries: sigma = 2 u of the update operands (the updates'
+        // rounding relative to the unit diagonal of the scaled matrix),
+        // raised fourfold, at most 1
+        const double u = prec == SPD_PREC_FP32 ? 0x1p-24 : prec == SPD_PREC_BF16 ? 0x1p-8
+                         : prec == SPD_PREC_FP8 ? 0x1p-4 : 0x1p-11;
+        for (sigma = 2.0 * u; st == SPD_ERR_NOT_SPD && sigma <= 1.0; sigma *= 4.0)
+            st = factor_once(h, n, A, lda, prec, flags, F, rep, sigma);
+        sigma /= 4.0;  // the sigma of the last attempt
+        if (st != SPD_OK) sigma = 0.0;
+    }
     CUDA_TRY(h, cudaEventRecord(h->e1, h->stream));
     CUDA_TRY(h, cudaEventSynchronize(h->e1));
     if (rep) {
@@ -509,6 +527,8 @@ extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda,
         rep->status = st;
         rep->prec_used = used;
         rep->cond_est = kappa;
+        rep->shift = sigma;
+        if (st == SPD_OK) rep->info = 0;  // a failed attempt before the kept factor leaves no trace
     }
     return st;
 }
