@@ -346,17 +346,16 @@ def test_fp8_update_factor_refines_where_iterref_holds(h, n, m):
     assert sweeps["fp16"] <= sweeps["fp8"] <= 30, sweeps
 
 
-@pytest.mark.parametrize("n", [700, 2049])
-def test_fp8_update_factor_falls_back_where_iterref_fails(h, n):
-    """kappa ~ 41 (G G^T / n + 0.1 I): kappa u_fp8 is above one, eq. (iterref)
-    gives no guarantee and plain refinement with the FP8-update factor
-    stagnates (two sweeps in a row shrink the error by less than half); the
-    fallback (float64 CG preconditioned by the same factor, Section 3.1: any
-    inner solver that contracts will do) takes over and still reaches
-    backward error 1e-14."""
-    A = W.gram_shifted(n, seed=3, shift=0.1)
-    x_true = W.gaussian_rhs(n, 2, 4)
-    B = A @ x_true
+def test_fp8_update_factor_falls_back_where_iterref_fails(h):
+    """The exponential-kernel covariance matrix (n = 4096 points in the unit
+    cube, ell = 0.1, nugget 1e-3): the FP8-update factor does not break down,
+    but refinement with it stagnates (two sweeps in a row shrink the error by
+    less than half: eq. (iterref) fails in practice); the fallback -- float64
+    CG preconditioned by the same factor, Section 3.1: any inner solver that
+    contracts will do -- takes over and reaches backward error 1e-14."""
+    n = 4096
+    A, _ = W.exp_kernel_cov(n, ell=0.1, nugget=1e-3, seed=0)
+    B = W.gaussian_rhs(n, 2, 4)
     Ad = dev_sym(A)
     st, F, _ = spd.spd_factor(h, Ad, "fp8")
     check(h, st)
@@ -367,4 +366,34 @@ def test_fp8_update_factor_falls_back_where_iterref_fails(h, n):
     finally:
         spd.spd_factor_destroy(F)
     assert rep.fell_back == 1
+    assert oracle.berr(A, B, host(X)) <= 1e-14
+
+
+@pytest.mark.parametrize("prec,kappa", [("fp8", 1e4), ("fp16", 1e6), ("bf16", 1e6)])
+def test_shifted_factor_after_breakdown(h, prec, kappa):
+    """A low-precision factor of a prescribed-spectrum matrix that breaks down
+    (a non-positive pivot: the updates' rounding exceeds what is left of a
+    pivot).  With SPD_FACTOR_SHIFT the factorisation is retried on the scaled
+    matrix plus sigma I (sigma = 2u, 8u, 32u, ... of the update operands); the
+    shifted factor drives the factor-preconditioned CG fallback to backward
+    error 1e-14."""
+    n = 1024
+    A, lam, V = W.householder_spectrum(n, kappa, k=32, seed=1)
+    B = W.gaussian_rhs(n, 2, 4)
+    Ad = dev_sym(A)
+    st, F, rep = spd.spd_factor(h, Ad, prec)
+    check(h, st, spd.SPD_ERR_NOT_SPD)
+    assert F is None and rep.info > 0
+    st, F, rep = spd.spd_factor(h, Ad, prec, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SHIFT)
+    check(h, st)
+    u = UNIT_ROUNDOFF[prec]
+    k = np.log2(rep.shift / (2 * u)) / 2  # sigma = 2u 4^k
+    assert 0 < rep.shift <= 1 and k == round(k) and rep.info == 0
+    X = dev_zeros(n, 2)
+    try:
+        st, srep = spd.spd_solve_ir(h, F, Ad, dev_cols(B), X)
+        check(h, st)
+    finally:
+        spd.spd_factor_destroy(F)
+    assert srep.fell_back == 1
     assert oracle.berr(A, B, host(X)) <= 1e-14
