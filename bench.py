@@ -903,7 +903,8 @@ def main():
         spd.spd_profile_enable(h, True)
         sols = []
         for (k, A, B), p in zip(systems, precs):
-            st, F, _ = spd.spd_factor(h, A, p, spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SERIAL)
+            base = FACTOR_FLAGS["flags"] if FACTOR_FLAGS["flags"] is not None else spd.SPD_SCALE_DIAG
+            st, F, _ = spd.spd_factor(h, A, p, base | spd.SPD_FACTOR_SERIAL)
             if st != spd.SPD_OK:
                 raise RuntimeError("roofline pass: " + spd.spd_last_error_string(h))
             st, _ = spd.spd_solve_ir(h, F, A, B, X, opts)
