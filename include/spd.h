@@ -37,6 +37,8 @@
 #ifndef SPD_H
 #define SPD_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -446,6 +448,25 @@ spd_status spd_batch_destroy(spd_batch *plan);
 #define SPD_GEMM_STREAM_K 2
 spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,
                            const float *B, int ldb, float *C, int ldc, int flags);
+
+/* ---- resource limits and failure checks -------------------------------------
+ * (No passage of the paper: the library's own failure handling.)
+ * spd_set_wait_limit bounds every spin-wait of h's kernels on a flag that
+ * another CTA sets (the triangular sweeps' block flags and slot table;
+ * default 1 s, allowed (0, 60] s).  A wait that runs out raises
+ * SPD_ERR_TIMEOUT from the call, which winds down without fault; the handle
+ * and the CUDA context stay usable.
+ * spd_set_memory_cap caps the device memory one call on h may request
+ * (a factor's arrays, the workspace, spd_solve_ir_host's device copies);
+ * a larger request returns SPD_ERR_OOM before anything is allocated.
+ * 0 (the default) means no cap.
+ * spd_wait_probe launches one kernel that waits, with h's wait limit, on a
+ * device flag that nothing sets: it returns SPD_ERR_TIMEOUT after that
+ * limit, through the same device status word and error mapping as a real
+ * expired wait.  For callers that test their handling of SPD_ERR_TIMEOUT. */
+spd_status spd_set_wait_limit(spd_handle *h, double seconds);
+spd_status spd_set_memory_cap(spd_handle *h, size_t bytes);
+spd_status spd_wait_probe(spd_handle *h);
 
 /* ---- phase timing ---------------------------------------------------------
  * Code-phase markers in the spirit of the paper's instrumentation library

@@ -28,6 +28,7 @@ __all__ = [
     "spd_batch_create", "spd_batch_solve", "spd_batch_info", "spd_batch_destroy",
     "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params", "spd_learned_features", "spd_mlp_loss_grad",
     "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply", "spd_lowrank_destroy", "spd_solve_learned",
+    "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
@@ -52,7 +53,7 @@ EXPORTED = [
     "spd_profile_read", "spd_launch_count", "spd_gemm_update", "spd_residual_static", "spd_batch_create", "spd_batch_solve",
     "spd_batch_info", "spd_batch_destroy", "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params",
     "spd_learned_features", "spd_mlp_loss_grad", "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply",
-    "spd_lowrank_destroy", "spd_solve_learned",
+    "spd_lowrank_destroy", "spd_solve_learned", "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe",
 ]
 
 
@@ -130,6 +131,9 @@ def lib():
         "spd_solve_learned": (I, [P, P, I, I, P, I, P, I, P, I, O, R]),
         "spd_profile_read": (I, [P, I, C.POINTER(C.c_int), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double)]),
+        "spd_set_wait_limit": (I, [P, D]),
+        "spd_set_memory_cap": (I, [P, C.c_size_t]),
+        "spd_wait_probe": (I, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -547,3 +551,18 @@ def spd_solve_learned(h, P, A, B, X, opts=None):
     rep = SpdReport()
     st = lib().spd_solve_learned(h, P, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), C.byref(rep))
     return st, rep
+
+
+def spd_set_wait_limit(h, seconds):
+    """Bound of every spin-wait of h's kernels on another CTA's flag."""
+    return lib().spd_set_wait_limit(h, float(seconds))
+
+
+def spd_set_memory_cap(h, nbytes):
+    """Cap on the device memory one call on h may request (0: none)."""
+    return lib().spd_set_memory_cap(h, int(nbytes))
+
+
+def spd_wait_probe(h):
+    """One bounded wait on a flag nothing sets: SPD_ERR_TIMEOUT after the limit."""
+    return lib().spd_wait_probe(h)

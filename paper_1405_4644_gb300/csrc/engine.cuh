@@ -38,7 +38,12 @@ struct spd_handle {
     std::vector<cudaEvent_t> sync_ev;  // timing-free events for stream joins
     void* stage = nullptr;      // grow-only device copies of spd_solve_ir_host's A, B, X
     size_t stage_bytes = 0;
+    unsigned long long wait_ns = 1000000000ull;  // bound of a spin-wait on another CTA's flag
+    size_t mem_cap = 0;         // largest device request of one call (0 = no cap): spd_set_memory_cap
 };
+
+// SPD_ERR_OOM when one call's device request exceeds the handle's cap.
+static inline bool over_cap(const spd_handle* h, size_t bytes) { return h->mem_cap && bytes > h->mem_cap; }
 
 struct spd_factor_t {
     spd_handle* h = nullptr;
@@ -98,6 +103,9 @@ struct WsPlan {
 
 static inline spd_status ws_reserve(spd_handle* h, size_t bytes) {
     if (bytes <= h->ws_bytes) return SPD_OK;
+    if (over_cap(h, bytes))
+        return set_err(h, SPD_ERR_OOM, "workspace of %zu bytes exceeds the handle's memory cap of %zu bytes", bytes,
+                       h->mem_cap);
     if (h->ws) {
         CUDA_TRY(h, cudaStreamSynchronize(h->stream));
         CUDA_TRY(h, cudaFree(h->ws));

@@ -46,6 +46,7 @@ struct TrsvArgs {
     int epoch;           // value that marks a block finished in this sweep
     DevStatus* st;
     unsigned long long* slots;  // one per CTA: (epoch << 32) | SM id of the CTA in this sweep
+    unsigned long long wait_ns; // bound of every wait on another CTA's flag or slot
 };
 
 // largest grid of the sweeps (CTAs), the size of the slot table
@@ -144,7 +145,7 @@ __device__ __forceinline__ bool tv_wait(const TrsvArgs& a, int K, int* s_abort) 
         if (ld_acquire(a.ready + K) != a.epoch) {
             const uint64_t t0 = tv_globaltimer();
             while (ld_acquire(a.ready + K) != a.epoch) {
-                if (tv_globaltimer() - t0 > 1000000000ull) {
+                if (tv_globaltimer() - t0 > a.wait_ns) {
                     *s_abort = 1;
                     atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
                     break;
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
             if ((unsigned)(v >> 32) != (unsigned)a.epoch) {
                 const uint64_t t0 = tv_globaltimer();
                 while ((unsigned)((v = ld_acquire64(a.slots + b)) >> 32) != (unsigned)a.epoch) {
-                    if (tv_globaltimer() - t0 > 1000000000ull) {
+                    if (tv_globaltimer() - t0 > a.wait_ns) {
                         s_abort = 1;
                         atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
                         break;

@@ -290,6 +290,16 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         free_factor(F);
         return s;
     };
+    {  // the factor's whole device request against the handle's cap
+        const size_t nb = (size_t)std::max(F->nblk128, 1);
+        size_t req = sizeof(double) * std::max(n, 1);
+        if (prec == SPD_PREC_FP64) req += sizeof(double) * (std::max<size_t>(nW, 1) + 4096 * nb);
+        else req += sizeof(float) * (std::max<size_t>(nW, 1) + (1 + 4 + 0.25) * 16384 * nb) +
+                    (kind ? mirror_elem(kind) * std::max<size_t>(nW, 1) : 0);
+        if (over_cap(h, req))
+            return fail(set_err(h, SPD_ERR_OOM, "factor of order %d needs %zu bytes, above the handle's memory cap "
+                                "of %zu bytes", n, req, h->mem_cap));
+    }
     cudaError_t e = cudaSuccess;
     cudaStream_t as = h->stream;  // stream-ordered allocations (see free_factor)
     e = cudaMallocAsync(&F->d, sizeof(double) * std::max(n, 1), as);

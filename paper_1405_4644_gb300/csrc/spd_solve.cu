@@ -403,7 +403,7 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
     unsigned long long* slots = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->ready) +
                                                                       round_up((long)sizeof(int) * h->ready_n, 256));
     for (int dir = 0; dir < 2; ++dir) {
-        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst, slots};
+        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst, slots, h->wait_ns};
         void* args[] = {&a};
         const int grid = std::min({NB, occ.per_sm[dir] * h->sms, TV_SLOTS});
         ++h->launches;
@@ -1014,6 +1014,9 @@ extern "C" spd_status spd_solve_ir_host(spd_handle* h, int n, int m, const doubl
     const size_t bytesA = (size_t)round_up((long)(sizeof(double) * (size_t)n * n), 256);
     const size_t bytesB = (size_t)round_up((long)(sizeof(double) * (size_t)n * m), 256);
     if (h->stage_bytes < bytesA + 2 * bytesB) {  // grow (the previous call ended synchronised)
+        if (over_cap(h, bytesA + 2 * bytesB))
+            return set_err(h, SPD_ERR_OOM, "spd_solve_ir_host: device copies of %zu bytes exceed the handle's "
+                           "memory cap of %zu bytes", bytesA + 2 * bytesB, h->mem_cap);
         CUDA_TRY(h, cudaStreamSynchronize(s));
         cudaFree(h->stage);
         h->stage = nullptr;
