@@ -382,6 +382,17 @@ spd_status spd_lowrank_build(spd_mlp *net, int n, const double *A, int lda, cons
 /* Z = M R for m columns (float64, column-major). */
 spd_status spd_lowrank_apply(spd_lowrank *P, int m, const double *R, int ldr, double *Z, int ldz);
 spd_status spd_lowrank_destroy(spd_lowrank *P);
+/* Checkpoint of a network (the survey's "weights and training-data
+ * manifest" item; no passage of the paper): spd_learned_save writes
+ * <path>.json (format, features, hidden width, outputs, bf16, parameter
+ * count, Adam step), <path>.bin (the float32 parameters, little endian, in
+ * the order W1 b1 W2 b2 W3 b3) and <path>.adam.bin (the two Adam moments);
+ * spd_learned_load creates a network on h from them (Adam state restored
+ * when <path>.adam.bin is present), so that training resumes or inference
+ * runs in another process.  A manifest that does not match this library's
+ * feature and output counts, or a short file, gives SPD_ERR_ARG. */
+spd_status spd_learned_save(spd_mlp *net, const char *path);
+spd_status spd_learned_load(spd_handle *h, const char *path, spd_mlp **net);
 /* PCG on A in float64 with the learned M (spd_cg with SPD_PC_LOWRANK, at
  * most opts->maxit_inner steps); if it misses the tolerance, float32
  * Cholesky with iterative refinement takes over (report.fell_back = 1). */
@@ -419,6 +430,22 @@ spd_status spd_batch_create(spd_handle *h, int count, const int *n, const double
                             spd_batch **plan);
 spd_status spd_batch_solve(spd_batch *plan, int method, int prec, const spd_opts *opts,
                            spd_report *summary, int *status, double *berr, int *iters);
+/* The solve of spd_batch_solve as a CUDA graph the caller launches: after
+ * spd_batch_graph (which tunes the CTA size on first use and captures a
+ * counter reset plus the one persistent launch), *graph_exec is a
+ * cudaGraphExec_t owned by the plan -- valid until spd_batch_destroy or the
+ * next spd_batch_graph/spd_batch_solve of the same method and precision with
+ * other opts; launch it on any stream with spd_graph_launch (or
+ * cudaGraphLaunch), as often as wanted; launches of one plan must not
+ * overlap.  spd_batch_results reads the last launch's per-system results
+ * (as spd_batch_solve returns them; time_ms 0) after the caller has
+ * synchronised the launching stream; it also drains the handle's stream. */
+spd_status spd_batch_graph(spd_batch *plan, int method, int prec, const spd_opts *opts,
+                           void **graph_exec);
+spd_status spd_batch_results(spd_batch *plan, int method, int prec, spd_report *summary, int *status,
+                             double *berr, int *iters);
+/* cudaGraphLaunch(graph_exec, stream) through this library's CUDA runtime. */
+spd_status spd_graph_launch(void *graph_exec, void *stream);
 /* Tuned CTA size (0 before the first solve), CTA count and the timed
  * candidates (ms for 256 and 512 threads; tune_ms may be NULL). */
 spd_status spd_batch_info(const spd_batch *plan, int method, int *threads_per_cta, int *ctas,

@@ -28,7 +28,8 @@ __all__ = [
     "spd_batch_create", "spd_batch_solve", "spd_batch_info", "spd_batch_destroy",
     "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params", "spd_learned_features", "spd_mlp_loss_grad",
     "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply", "spd_lowrank_destroy", "spd_solve_learned",
-    "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe",
+    "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe", "spd_batch_graph", "spd_batch_results",
+    "spd_graph_launch", "spd_learned_save", "spd_learned_load",
 ]
 
 SPD_OK, SPD_ERR_ARG, SPD_ERR_NOT_SPD, SPD_ERR_NO_CONVERGENCE = 0, 1, 2, 3
@@ -134,6 +135,11 @@ def lib():
         "spd_set_wait_limit": (I, [P, D]),
         "spd_set_memory_cap": (I, [P, C.c_size_t]),
         "spd_wait_probe": (I, [P]),
+        "spd_batch_graph": (I, [P, I, I, O, PP]),
+        "spd_batch_results": (I, [P, I, I, R, P, P, P]),
+        "spd_graph_launch": (I, [P, P]),
+        "spd_learned_save": (I, [P, C.c_char_p]),
+        "spd_learned_load": (I, [P, C.c_char_p, PP]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -566,3 +572,40 @@ def spd_set_memory_cap(h, nbytes):
 def spd_wait_probe(h):
     """One bounded wait on a flag nothing sets: SPD_ERR_TIMEOUT after the limit."""
     return lib().spd_wait_probe(h)
+
+
+def spd_batch_graph(plan, method="chol_ir", prec="fp32", opts=None):
+    """(status, graph exec handle owned by the plan) of the batched solve."""
+    m = BATCH[method] if isinstance(method, str) else int(method)
+    gx = C.c_void_p()
+    st = lib().spd_batch_graph(plan, m, _prec(prec), _opts(opts), C.byref(gx))
+    return st, (gx if st == SPD_OK else None)
+
+
+def spd_batch_results(plan, method="chol_ir", prec="fp32", count=0):
+    """Per-system results of the plan's last launch (after the caller synchronised)."""
+    import numpy as np
+    m = BATCH[method] if isinstance(method, str) else int(method)
+    rep = SpdReport()
+    cnt = int(count)
+    sts = np.zeros(max(cnt, 1), dtype=np.int32)
+    be = np.zeros(max(cnt, 1))
+    it = np.zeros(max(cnt, 1), dtype=np.int32)
+    args = (sts.ctypes.data, be.ctypes.data, it.ctypes.data) if cnt else (None, None, None)
+    st = lib().spd_batch_results(plan, m, _prec(prec), C.byref(rep), *args)
+    return st, rep, sts[:cnt], be[:cnt], it[:cnt]
+
+
+def spd_graph_launch(graph_exec, stream=None):
+    return lib().spd_graph_launch(graph_exec, _stream_ptr(stream))
+
+
+def spd_learned_save(net, path):
+    return lib().spd_learned_save(net, str(path).encode())
+
+
+def spd_learned_load(h, path):
+    """(status, network or None)."""
+    net = C.c_void_p()
+    st = lib().spd_learned_load(h, str(path).encode(), C.byref(net))
+    return st, (net if st == SPD_OK else None)

@@ -118,19 +118,19 @@ extern "C" spd_status spd_batch_destroy(spd_batch* b) {
     return SPD_OK;
 }
 
-extern "C" spd_status spd_batch_solve(spd_batch* b, int method, int prec, const spd_opts* opts_in, spd_report* summary,
-                                      int* status, double* berr, int* iters) {
-    if (!b) return SPD_ERR_ARG;
+namespace {
+
+// The graph of (method, prec, opts): tune the CTA size on first use, then
+// capture (or reuse) counter reset + one persistent launch.
+spd_status batch_graph(spd_batch* b, int method, int prec, const spd_opts* opts_in, cudaGraphExec_t* out) {
     spd_handle* h = b->h;
     spd_opts o;
     spd_opts_default(&o);
     if (opts_in) o = *opts_in;
-    if (summary) memset(summary, 0, sizeof(*summary));
     if (method != SPD_BATCH_CHOL_IR && method != SPD_BATCH_PCG_JACOBI)
-        return set_err(h, SPD_ERR_ARG, "spd_batch_solve: unknown method %d", method);
+        return set_err(h, SPD_ERR_ARG, "spd_batch: unknown method %d", method);
     if (method == SPD_BATCH_CHOL_IR && prec != SPD_PREC_FP32 && prec != SPD_PREC_BF16 && prec != SPD_PREC_FP16)
-        return set_err(h, SPD_ERR_UNSUPPORTED, "spd_batch_solve: Cholesky-IR precision must be FP32, BF16 or FP16");
-    if (b->count == 0) return SPD_OK;
+        return set_err(h, SPD_ERR_UNSUPPORTED, "spd_batch: Cholesky-IR precision must be FP32, BF16 or FP16");
     const int mi = method == SPD_BATCH_CHOL_IR ? 0 : 1;
     const int pi = method == SPD_BATCH_CHOL_IR ? prec : 0;
     BatchArgs a{b->sys, b->order, b->count, b->next, b->scratch, b->rep, prec, o.tol,
@@ -181,25 +181,24 @@ extern "C" spd_status spd_batch_solve(spd_batch* b, int method, int prec, const 
         cudaStreamDestroy(cs);
         if (e != cudaSuccess) {
             gx = nullptr;
-            return set_err(h, SPD_ERR_CUDA, "spd_batch_solve: graph capture failed: %s", cudaGetErrorString(e));
+            return set_err(h, SPD_ERR_CUDA, "spd_batch: graph capture failed: %s", cudaGetErrorString(e));
         }
         b->graph_nt[mi][pi] = nt;
         b->graph_tol[mi][pi] = o.tol;
         b->graph_maxit[mi][pi] = a.maxit;
         b->graph_polish[mi][pi] = a.polish;
     }
-    CUDA_TRY(h, cudaEventRecord(h->e0, s));
-    {
-        ProfScope ps(h, method == SPD_BATCH_CHOL_IR ? SPD_PHASE_BATCH : SPD_PHASE_BATCH, 0.0, 0.0);
-        ++h->launches;
-        CUDA_TRY(h, cudaGraphLaunch(gx, s));
-    }
-    CUDA_TRY(h, cudaEventRecord(h->e1, s));
+    *out = gx;
+    return SPD_OK;
+}
+
+// Per-system results of the last launch (the handle's stream is drained first).
+spd_status batch_results(spd_batch* b, int method, int prec, float ms, spd_report* summary, int* status,
+                         double* berr, int* iters) {
+    spd_handle* h = b->h;
     std::vector<BatchRep> hr(b->count);
-    CUDA_TRY(h, cudaMemcpyAsync(hr.data(), b->rep, sizeof(BatchRep) * b->count, cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(h, cudaStreamSynchronize(s));
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    CUDA_TRY(h, cudaMemcpyAsync(hr.data(), b->rep, sizeof(BatchRep) * b->count, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     int bad = 0, maxit = 0, notspd = 0;
     double maxb = 0.0;
     for (int i = 0; i < b->count; ++i) {
@@ -212,9 +211,10 @@ extern "C" spd_status spd_batch_solve(spd_batch* b, int method, int prec, const 
         maxb = std::max(maxb, hr[i].berr);
     }
     spd_status result = SPD_OK;
-    if (notspd) result = set_err(h, SPD_ERR_NOT_SPD, "spd_batch_solve: %d systems broke down", notspd);
-    else if (bad) result = set_err(h, SPD_ERR_NO_CONVERGENCE, "spd_batch_solve: %d systems did not converge", bad);
+    if (notspd) result = set_err(h, SPD_ERR_NOT_SPD, "spd_batch: %d systems broke down", notspd);
+    else if (bad) result = set_err(h, SPD_ERR_NO_CONVERGENCE, "spd_batch: %d systems did not converge", bad);
     if (summary) {
+        memset(summary, 0, sizeof(*summary));
         summary->status = result;
         summary->info = bad;
         summary->iters_low = maxit;
@@ -224,6 +224,55 @@ extern "C" spd_status spd_batch_solve(spd_batch* b, int method, int prec, const 
         summary->time_ms = ms;
     }
     return result;
+}
+
+}  // namespace
+
+extern "C" spd_status spd_batch_solve(spd_batch* b, int method, int prec, const spd_opts* opts_in, spd_report* summary,
+                                      int* status, double* berr, int* iters) {
+    if (!b) return SPD_ERR_ARG;
+    spd_handle* h = b->h;
+    if (summary) memset(summary, 0, sizeof(*summary));
+    if (b->count == 0) return SPD_OK;
+    cudaGraphExec_t gx = nullptr;
+    spd_status st = batch_graph(b, method, prec, opts_in, &gx);
+    if (st != SPD_OK) return st;
+    cudaStream_t s = h->stream;
+    CUDA_TRY(h, cudaEventRecord(h->e0, s));
+    {
+        ProfScope ps(h, SPD_PHASE_BATCH, 0.0, 0.0);
+        ++h->launches;
+        CUDA_TRY(h, cudaGraphLaunch(gx, s));
+    }
+    CUDA_TRY(h, cudaEventRecord(h->e1, s));
+    CUDA_TRY(h, cudaEventSynchronize(h->e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    return batch_results(b, method, prec, ms, summary, status, berr, iters);
+}
+
+extern "C" spd_status spd_batch_graph(spd_batch* b, int method, int prec, const spd_opts* opts, void** graph_exec) {
+    if (!b || !graph_exec) return SPD_ERR_ARG;
+    *graph_exec = nullptr;
+    if (b->count == 0) return set_err(b->h, SPD_ERR_ARG, "spd_batch_graph: empty plan");
+    cudaGraphExec_t gx = nullptr;
+    spd_status st = batch_graph(b, method, prec, opts, &gx);
+    if (st == SPD_OK) *graph_exec = gx;
+    return st;
+}
+
+extern "C" spd_status spd_batch_results(spd_batch* b, int method, int prec, spd_report* summary, int* status,
+                                        double* berr, int* iters) {
+    if (!b) return SPD_ERR_ARG;
+    if (b->count == 0) return SPD_OK;
+    return batch_results(b, method, prec, 0.f, summary, status, berr, iters);
+}
+
+extern "C" spd_status spd_graph_launch(void* graph_exec, void* stream) {
+    if (!graph_exec) return SPD_ERR_ARG;
+    return cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? SPD_OK
+               : SPD_ERR_CUDA;
 }
 
 extern "C" spd_status spd_batch_info(const spd_batch* b, int method, int* threads_per_cta, int* ctas,

@@ -3,6 +3,7 @@
 // gradient, preconditioner build/apply, and the PCG solve with the
 // Cholesky-IR fallback.
 #include <random>
+#include <string>
 #include "engine.cuh"
 #include "k_learned.cuh"
 
@@ -321,6 +322,109 @@ extern "C" spd_status spd_mlp_params(spd_mlp* m, float* out, const float* in, fl
     if (in) CUDA_TRY(h, cudaMemcpy(m->p, in, sizeof(float) * m->count, cudaMemcpyDefault));
     if (out) CUDA_TRY(h, cudaMemcpy(out, m->p, sizeof(float) * m->count, cudaMemcpyDefault));
     if (grad_out) CUDA_TRY(h, cudaMemcpy(grad_out, m->g, sizeof(float) * m->count, cudaMemcpyDefault));
+    return SPD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint: <path>.json (manifest) + <path>.bin (float32 parameters, little
+// endian, in layout order W1 b1 W2 b2 W3 b3) + <path>.adam.bin (the two Adam
+// moments, 2 count float32), so that training can resume where it stopped
+// ---------------------------------------------------------------------------
+namespace {
+
+bool write_file(const std::string& path, const void* data, size_t bytes) {
+    FILE* f = fopen(path.c_str(), "wb");
+    if (!f) return false;
+    const bool ok = fwrite(data, 1, bytes, f) == bytes;
+    return fclose(f) == 0 && ok;
+}
+
+bool read_file(const std::string& path, void* data, size_t bytes) {
+    FILE* f = fopen(path.c_str(), "rb");
+    if (!f) return false;
+    const bool ok = fread(data, 1, bytes, f) == bytes && fgetc(f) == EOF;
+    fclose(f);
+    return ok;
+}
+
+// value of "key": <integer> in the manifest text (false if absent)
+bool json_long(const std::string& text, const char* key, long* out) {
+    const std::string k = std::string("\"") + key + "\":";
+    const size_t pos = text.find(k);
+    if (pos == std::string::npos) return false;
+    return sscanf(text.c_str() + pos + k.size(), " %ld", out) == 1;
+}
+
+}  // namespace
+
+extern "C" spd_status spd_learned_save(spd_mlp* m, const char* path) {
+    if (!m || !path || !*path) return SPD_ERR_ARG;
+    spd_handle* h = m->h;
+    std::vector<float> p(m->count), mom(2 * m->count);
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    CUDA_TRY(h, cudaMemcpy(p.data(), m->p, sizeof(float) * m->count, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(mom.data(), m->m1, sizeof(float) * m->count, cudaMemcpyDeviceToHost));
+    CUDA_TRY(h, cudaMemcpy(mom.data() + m->count, m->m2, sizeof(float) * m->count, cudaMemcpyDeviceToHost));
+    char js[512];
+    snprintf(js, sizeof(js),
+             "{\"format\": \"spd-mlp\", \"version\": 1, \"features\": %d, \"hidden\": %d, \"outputs\": %d, "
+             "\"bf16\": %d, \"count\": %ld, \"adam_step\": %ld, \"dtype\": \"float32\", "
+             "\"layout\": \"W1 b1 W2 b2 W3 b3\"}\n",
+             m->F, m->H, m->O, m->bf16, m->count, m->step);
+    const std::string base(path);
+    if (!write_file(base + ".bin", p.data(), sizeof(float) * p.size()) ||
+        !write_file(base + ".adam.bin", mom.data(), sizeof(float) * mom.size()) ||
+        !write_file(base + ".json", js, strlen(js)))
+        return set_err(h, SPD_ERR_ARG, "spd_learned_save: cannot write %s.{json,bin,adam.bin}", path);
+    return SPD_OK;
+}
+
+extern "C" spd_status spd_learned_load(spd_handle* h, const char* path, spd_mlp** out) {
+    if (!h) return SPD_ERR_ARG;
+    if (!path || !*path || !out) return set_err(h, SPD_ERR_ARG, "spd_learned_load: bad arguments");
+    *out = nullptr;
+    const std::string base(path);
+    std::string text;
+    {
+        FILE* f = fopen((base + ".json").c_str(), "rb");
+        if (!f) return set_err(h, SPD_ERR_ARG, "spd_learned_load: cannot open %s.json", path);
+        char buf[1024];
+        const size_t k = fread(buf, 1, sizeof(buf) - 1, f);
+        fclose(f);
+        text.assign(buf, k);
+    }
+    long F = 0, H = 0, O = 0, bf16 = 0, count = 0, step = 0;
+    if (text.find("\"spd-mlp\"") == std::string::npos || !json_long(text, "features", &F) ||
+        !json_long(text, "hidden", &H) || !json_long(text, "outputs", &O) || !json_long(text, "bf16", &bf16) ||
+        !json_long(text, "count", &count) || !json_long(text, "adam_step", &step))
+        return set_err(h, SPD_ERR_ARG, "spd_learned_load: %s.json is not an spd-mlp manifest", path);
+    if (F != LR_FEAT || O != 1 + LR_RANK)
+        return set_err(h, SPD_ERR_ARG, "spd_learned_load: %ld features / %ld outputs, this library has %d / %d", F,
+                       O, LR_FEAT, 1 + LR_RANK);
+    spd_mlp* m = nullptr;
+    spd_status st = spd_mlp_create(h, (int)H, 0, (int)bf16, &m);
+    if (st != SPD_OK) return st;
+    if (m->count != count) {
+        spd_mlp_destroy(m);
+        return set_err(h, SPD_ERR_ARG, "spd_learned_load: manifest count %ld, layout of hidden %ld has %ld", count, H,
+                       m->count);
+    }
+    std::vector<float> p(count), mom(2 * count);
+    if (!read_file(base + ".bin", p.data(), sizeof(float) * count)) {
+        spd_mlp_destroy(m);
+        return set_err(h, SPD_ERR_ARG, "spd_learned_load: %s.bin does not hold %ld float32 values", path, count);
+    }
+    const bool adam = read_file(base + ".adam.bin", mom.data(), sizeof(float) * mom.size());
+    cudaError_t e = cudaMemcpy(m->p, p.data(), sizeof(float) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && adam) e = cudaMemcpy(m->m1, mom.data(), sizeof(float) * count, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && adam)
+        e = cudaMemcpy(m->m2, mom.data() + count, sizeof(float) * count, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        spd_mlp_destroy(m);
+        return set_err(h, SPD_ERR_CUDA, "spd_learned_load: %s", cudaGetErrorString(e));
+    }
+    m->step = adam ? step : 0;
+    *out = m;
     return SPD_OK;
 }
 

@@ -87,3 +87,43 @@ def test_batched_rejects_oversize(h):
     b = torch.ones(513, dtype=torch.float64, device="cuda")
     st, plan = spd.spd_batch_create(h, [A], [b], [b.clone()])
     assert st == spd.SPD_ERR_ARG and plan is None
+
+
+def test_batched_graph_launched_by_the_caller(h):
+    """spd_batch_graph hands out the captured graph; launched twice on the
+    caller's own stream (the second time after the right-hand sides changed)
+    it gives the same solutions as spd_batch_solve, bit for bit, and every
+    system meets the tolerance against the oracle."""
+    sizes = SIZES[:14]
+    As, bs, Ad, bd, xd = make_batch(sizes, seed_base=2000)
+    st, plan = spd.spd_batch_create(h, Ad, bd, xd)
+    assert st == spd.SPD_OK
+    try:
+        st, rep, sts, be, it = spd.spd_batch_solve(plan, "chol_ir", "fp32", count=len(sizes))
+        assert st == spd.SPD_OK
+        ref = [x.cpu().numpy().copy() for x in xd]
+        st, gx = spd.spd_batch_graph(plan, "chol_ir", "fp32")
+        assert st == spd.SPD_OK and gx
+        s = torch.cuda.Stream()
+        for x in xd:
+            x.zero_()
+        torch.cuda.synchronize()
+        assert spd.spd_graph_launch(gx, s) == spd.SPD_OK
+        s.synchronize()
+        st, rep2, sts2, be2, it2 = spd.spd_batch_results(plan, "chol_ir", "fp32", count=len(sizes))
+        assert st == spd.SPD_OK and np.all(sts2 == 0)
+        for x, r in zip(xd, ref):
+            assert np.array_equal(x.cpu().numpy(), r)
+        # new right-hand sides in the same buffers, the same graph
+        bs2 = [b * 2.0 - 1.0 for b in bs]
+        for b, b2 in zip(bd, bs2):
+            b.copy_(torch.from_numpy(b2))
+        torch.cuda.synchronize()
+        assert spd.spd_graph_launch(gx, s) == spd.SPD_OK
+        s.synchronize()
+        st, rep3, sts3, _, _ = spd.spd_batch_results(plan, "chol_ir", "fp32", count=len(sizes))
+        assert st == spd.SPD_OK and rep3.berr <= 1e-14
+        for A, b2, x in zip(As, bs2, xd):
+            assert oracle.berr(A, b2[:, None], x.cpu().numpy()[:, None]) <= 1e-14
+    finally:
+        spd.spd_batch_destroy(plan)

@@ -166,3 +166,46 @@ def test_learned_solve_falls_back_to_cholesky_ir(h):
         spd.spd_mlp_destroy(net)
     assert st == 0 and rep.fell_back == 1
     assert oracle.berr(A, b, X.cpu().numpy()) <= 1e-14
+
+
+def test_checkpoint_round_trip_resumes_training(h, tmp_path):
+    """spd_learned_save / spd_learned_load: parameters and Adam state come
+    back bit for bit, the loss of the reloaded network equals the original's,
+    and one more Adam step from either gives identical parameters."""
+    n, H, p = 96, 32, 4
+    A, pts, ell, nug = system(n, 11)
+    Ad = torch.from_numpy(A).cuda()
+    Fg = torch.from_numpy(LO.features(A, pts, ell, nug).astype(np.float32)).cuda()
+    Zd = torch.from_numpy(np.ascontiguousarray(W.gaussian_rhs(n, p, 3).T)).cuda().t()
+    net = _net(h, H, seed=4)
+    net2 = None
+    try:
+        for _ in range(3):
+            st, _ = spd.spd_mlp_loss_grad(net, Ad, Fg, Zd)
+            assert st == 0 and spd.spd_mlp_adam(net, 1e-3) == 0
+        path = tmp_path / "net"
+        assert spd.spd_learned_save(net, path) == 0
+        assert (tmp_path / "net.json").exists() and (tmp_path / "net.bin").exists()
+        st, net2 = spd.spd_learned_load(h, path)
+        assert st == 0
+        cnt = spd.spd_mlp_params(net)
+        a, b = np.zeros(cnt, np.float32), np.zeros(cnt, np.float32)
+        spd.spd_mlp_params(net, out=a)
+        spd.spd_mlp_params(net2, out=b)
+        assert np.array_equal(a, b)
+        st, l1 = spd.spd_mlp_loss_grad(net, Ad, Fg, Zd)
+        st2, l2 = spd.spd_mlp_loss_grad(net2, Ad, Fg, Zd)
+        assert st == 0 and st2 == 0 and l1 == l2
+        assert spd.spd_mlp_adam(net, 1e-3) == 0 and spd.spd_mlp_adam(net2, 1e-3) == 0
+        spd.spd_mlp_params(net, out=a)
+        spd.spd_mlp_params(net2, out=b)
+        assert np.array_equal(a, b)
+        # a truncated parameter file is refused
+        raw = (tmp_path / "net.bin").read_bytes()
+        (tmp_path / "net.bin").write_bytes(raw[:-4])
+        st, bad = spd.spd_learned_load(h, path)
+        assert st == spd.SPD_ERR_ARG and bad is None
+    finally:
+        spd.spd_mlp_destroy(net)
+        if net2 is not None:
+            spd.spd_mlp_destroy(net2)
