@@ -55,6 +55,7 @@ EXPORTED = [
     "spd_batch_info", "spd_batch_destroy", "spd_mlp_create", "spd_mlp_destroy", "spd_mlp_params",
     "spd_learned_features", "spd_mlp_loss_grad", "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply",
     "spd_lowrank_destroy", "spd_solve_learned", "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe",
+    "spd_batch_graph", "spd_batch_results", "spd_graph_launch", "spd_learned_save", "spd_learned_load",
 ]
 
 
