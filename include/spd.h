@@ -245,6 +245,41 @@ spd_status spd_solve_ir(spd_handle *h, const spd_factor_t *F, int n, int m,
                         const double *A, int lda, const double *B, int ldb,
                         double *X, int ldx, const spd_opts *opts, spd_report *rep);
 
+/* Algorithm 1 with the loop's stop decision on the device, for CUDA graph
+ * capture (no passage of the paper beyond Alg. 1 itself).  The call only
+ * enqueues work on h's stream and returns: line 2, the first residual, then
+ * opts->maxit refinement sweeps whose triangular solves and residuals
+ * return at once on the device once every column meets opts->crit/tol
+ * (each such sweep then costs a few microseconds of launches), and finally
+ * a kernel that writes *rep (DEVICE memory).  The residual is
+ * SPD_RESID_TC when opts->resid asks for it, else float64 (SPD_RESID_DF32
+ * is taken as float64: its switch needs host decisions); there is no
+ * stagnation fallback (rep->stagnated counts the columns that stalled:
+ * solve those with spd_solve_ir).  FP64 factors are not accepted.
+ * Capture: make one call with the same n, m and opts outside any capture
+ * first (it sizes h's workspace and allocates the device epoch counter);
+ * later calls allocate nothing and contain no host synchronisation.  The
+ * sweeps' block flags take their epochs from a device counter the solve
+ * itself advances, so a captured graph may be replayed any number of
+ * times; replays must not overlap each other or other cooperative work of
+ * the process (the sweeps are cooperative launches).
+ * A, B, X, F, *rep stay owned by the caller and must stay valid until the
+ * work has run. */
+typedef struct spd_report_dev {
+    int status;       /* SPD_OK if every column met the rule, SPD_ERR_NO_CONVERGENCE
+                         if not, SPD_ERR_TIMEOUT / SPD_ERR_CUDA on a device error */
+    int active;       /* columns above the tolerance at the end                     */
+    int sweeps;       /* refinement sweeps applied (max over columns)               */
+    int stagnated;    /* columns whose error stopped shrinking                      */
+    int dev_flags;    /* the handle's device status word at the end                 */
+    int pad;
+    double berr;      /* max-over-columns normwise backward error                   */
+    double rel_resid; /* max-over-columns ||r||_2 / ||b||_2                         */
+} spd_report_dev;
+spd_status spd_solve_ir_async(spd_handle *h, const spd_factor_t *F, int n, int m,
+                              const double *A, int lda, const double *B, int ldb,
+                              double *X, int ldx, const spd_opts *opts, spd_report_dev *rep);
+
 /* Factor and refine in one call on HOST buffers: copies A and B to the
  * device, runs spd_factor + spd_solve_ir, copies X back (column-major,
  * lda/ldb/ldx >= n).  The device copies of A, B and X are the handle's: they

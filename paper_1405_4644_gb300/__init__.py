@@ -56,6 +56,7 @@ EXPORTED = [
     "spd_learned_features", "spd_mlp_loss_grad", "spd_mlp_adam", "spd_lowrank_build", "spd_lowrank_apply",
     "spd_lowrank_destroy", "spd_solve_learned", "spd_set_wait_limit", "spd_set_memory_cap", "spd_wait_probe",
     "spd_batch_graph", "spd_batch_results", "spd_graph_launch", "spd_learned_save", "spd_learned_load",
+    "spd_solve_ir_async",
 ]
 
 
@@ -74,6 +75,12 @@ class SpdReport(C.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["prec_used"] = PREC_NAME.get(d["prec_used"], d["prec_used"])
         return d
+
+
+class SpdReportDev(C.Structure):
+    """Host view of the device-side report of spd_solve_ir_async."""
+    _fields_ = [("status", C.c_int), ("active", C.c_int), ("sweeps", C.c_int), ("stagnated", C.c_int),
+                ("dev_flags", C.c_int), ("pad", C.c_int), ("berr", C.c_double), ("rel_resid", C.c_double)]
 
 
 class SpdError(RuntimeError):
@@ -141,6 +148,7 @@ def lib():
         "spd_graph_launch": (I, [P, P]),
         "spd_learned_save": (I, [P, C.c_char_p]),
         "spd_learned_load": (I, [P, C.c_char_p, PP]),
+        "spd_solve_ir_async": (I, [P, P, I, I, P, I, P, I, P, I, O, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -610,3 +618,27 @@ def spd_learned_load(h, path):
     net = C.c_void_p()
     st = lib().spd_learned_load(h, str(path).encode(), C.byref(net))
     return st, (net if st == SPD_OK else None)
+
+
+def spd_report_dev_buffer(device="cuda"):
+    """A device buffer for spd_solve_ir_async's report (torch uint8 tensor)."""
+    import torch
+    return torch.zeros(C.sizeof(SpdReportDev), dtype=torch.uint8, device=device)
+
+
+def spd_report_dev_read(buf):
+    """Copy a device report to the host (synchronises with the device)."""
+    raw = bytes(buf.cpu().numpy().tobytes())
+    return SpdReportDev.from_buffer_copy(raw)
+
+
+def spd_solve_ir_async(h, F, A, B, X, rep_buf, opts=None):
+    """Enqueue Algorithm 1 with its stop decision on the device (capturable);
+    rep_buf from spd_report_dev_buffer()."""
+    pA, lda, n = _sym(A)
+    pB, ldb, _, m = _cols(B, "B", n)
+    pX, ldx, _, _ = _cols(X, "X", n, m)
+    _need_dev(rep_buf, "rep_buf", "uint8")
+    if rep_buf.numel() < C.sizeof(SpdReportDev):
+        raise ValueError("rep_buf is too small for spd_report_dev")
+    return lib().spd_solve_ir_async(h, F, n, m, pA, lda, pB, ldb, pX, ldx, _opts(opts), rep_buf.data_ptr())

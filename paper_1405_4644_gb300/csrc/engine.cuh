@@ -39,6 +39,14 @@ struct spd_handle {
     void* stage = nullptr;      // grow-only device copies of spd_solve_ir_host's A, B, X
     size_t stage_bytes = 0;
     unsigned long long wait_ns = 1000000000ull;  // bound of a spin-wait on another CTA's flag
+    // a capturable solve in progress (spd_solve_ir_async): its kernels return
+    // at once while *async_gate == 0, and its sweeps take their flag epochs
+    // from the device counter async_epoch_dev (advanced by the solve itself),
+    // never from values fixed when the launches were issued
+    bool async_on = false;
+    const int* async_gate = nullptr;
+    int* async_epoch_dev = nullptr;
+    int async_rel = 0, async_total = 0;
     size_t mem_cap = 0;         // largest device request of one call (0 = no cap): spd_set_memory_cap
 };
 

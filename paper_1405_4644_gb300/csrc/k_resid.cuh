@@ -22,8 +22,10 @@ template <int MT>
 static __global__ void __launch_bounds__(RESID_ROWS) k_resid_partial(const double* __restrict__ A, long lda, int n,
                                                               const double* __restrict__ X, long ldx, int c0,
                                                               int mc, int jchunk, int mtot,
-                                                              double* __restrict__ P, float* __restrict__ rowabs) {
+                                                              double* __restrict__ P, float* __restrict__ rowabs,
+                                                              const int* __restrict__ gate = nullptr) {
     __shared__ __align__(16) double xs[RESID_JT][MT];
+    if (gate && *gate == 0) return;  // refinement over: nothing to do (capturable solves)
     const int tid = threadIdx.x;
     const int i = blockIdx.x * RESID_ROWS + tid;
     const int s = blockIdx.y;
@@ -77,8 +79,10 @@ static __global__ void __launch_bounds__(256) k_resid_final(const double* __rest
                                                      const double* __restrict__ P, int S,
                                                      double* __restrict__ R, long ldr,
                                                      const double* __restrict__ X, long ldx,
-                                                     double* __restrict__ NP, int mode) {
+                                                     double* __restrict__ NP, int mode,
+                                                     const int* __restrict__ gate = nullptr) {
     __shared__ double red[3][8];
+    if (gate && *gate == 0) return;
     const int c = blockIdx.y;
     const int i = blockIdx.x * 256 + threadIdx.x;
     double rmax = 0.0, r2 = 0.0, xmax = 0.0;

@@ -47,6 +47,8 @@ struct TrsvArgs {
     DevStatus* st;
     unsigned long long* slots;  // one per CTA: (epoch << 32) | SM id of the CTA in this sweep
     unsigned long long wait_ns; // bound of every wait on another CTA's flag or slot
+    const int* gate;            // (may be NULL) return at once when *gate == 0
+    const int* epoch_base;      // (may be NULL) epoch = 2^30 + *epoch_base + epoch
 };
 
 // largest grid of the sweeps (CTAs), the size of the slot table
@@ -276,6 +278,11 @@ __global__ void __launch_bounds__(256, 1) k_trsv32(TrsvArgs a) {
     const int tq = tid >> 3, ts = tid & 7;            // tile products: row quad, reduction slice
     const int i = tid >> 1, half = tid & 1;           // diagonal step: row, column half
     const int cbase = (MC >= 2) ? half * CPT : 0;
+    // a capturable solve: nothing to do once its refinement is over, and the
+    // epoch comes from the device counter the solve advanced (every CTA reads
+    // the same values: both were written by earlier kernels in the stream)
+    if (a.gate && *a.gate == 0) return;
+    if (a.epoch_base) a.epoch += (1 << 30) + *a.epoch_base;
     if (tid == 0) {
         s_abort = 0;
         s_rank = 0;

@@ -277,8 +277,10 @@ __global__ void __launch_bounds__(256) k_tcr_digits_a(const double* __restrict__
 // one CTA per column of X: its exponent, then ten digit planes (row c of
 // plane q holds the digits of column c)
 __global__ void __launch_bounds__(256) k_tcr_digits_x(const double* __restrict__ X, long ldx, int n, int m,
-                                                      int* __restrict__ xe, uint16_t* __restrict__ Xd, long ldp) {
+                                                      int* __restrict__ xe, uint16_t* __restrict__ Xd, long ldp,
+                                                      const int* __restrict__ gate) {
     __shared__ unsigned long long red[8];
+    if (gate && *gate == 0) return;  // refinement over (capturable solves)
     const int c = blockIdx.x;
     const double* x = X + (long)c * ldx;
     unsigned long long mx = 0ull;
@@ -326,7 +328,8 @@ __global__ void __launch_bounds__(256) k_tcr_digits_x(const double* __restrict__
 constexpr int TCR_FLUSH = 256;
 __global__ void __launch_bounds__(TCR_THREADS, 1)
     k_tcr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapX, int n, int RB,
-              int Nkc, long T, unsigned long long* __restrict__ part, DevStatus* st) {
+              int Nkc, long T, unsigned long long* __restrict__ part, DevStatus* st, const int* __restrict__ gate) {
+    if (gate && *gate == 0) return;  // before any barrier or tensor memory
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
@@ -523,8 +526,10 @@ __global__ void __launch_bounds__(256) k_tcr_final(const unsigned long long* __r
                                                    const unsigned long long* __restrict__ part, int n, int m, int RB,
                                                    const double* __restrict__ B, long ldb,
                                                    const double* __restrict__ X, long ldx, double* __restrict__ R,
-                                                   long ldr, double* __restrict__ NP, int mode) {
+                                                   long ldr, double* __restrict__ NP, int mode,
+                                                   const int* __restrict__ gate) {
     __shared__ double red[3][8];
+    if (gate && *gate == 0) return;
     const int c = blockIdx.y;
     const int i = blockIdx.x * 256 + threadIdx.x;
     double rmax = 0.0, r2 = 0.0, xmax = 0.0;
@@ -709,7 +714,7 @@ spd_status tc_resid_prepare(spd_handle* h, TcResidWs* w, const double* A, long l
 }
 
 spd_status tc_resid_run(spd_handle* h, const TcResidWs* w, const double* B, long ldb, const double* X, long ldx,
-                        double* R, long ldr, double* NP, int mode) {
+                        double* R, long ldr, double* NP, int mode, const int* gate) {
     static const bool attr = [] {  // once per process, thread-safe
         cudaFuncSetAttribute(k_tcr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCR_SMEM);
         return true;
@@ -717,15 +722,15 @@ spd_status tc_resid_run(spd_handle* h, const TcResidWs* w, const double* B, long
     (void)attr;
     cudaStream_t s = h->stream;
     const int n = w->n, m = w->m;
-    ++(h)->launches, k_tcr_digits_x<<<m, 256, 0, s>>>(X, ldx, n, m, w->xe, w->Xd, w->ldp);
+    ++(h)->launches, k_tcr_digits_x<<<m, 256, 0, s>>>(X, ldx, n, m, w->xe, w->Xd, w->ldp, gate);
     LAUNCH_CHECK(h);
     CUDA_TRY(h, cudaMemsetAsync(w->part, 0, sizeof(unsigned long long) * (size_t)w->CB * w->RB * TCR_NG * 16 * 128, s));
     ++(h)->launches, k_tcr_mma<<<w->G, TCR_THREADS, TCR_SMEM, s>>>(w->mapA, w->mapX, n, w->RB, w->Nkc, w->T, w->part,
-                                                                   h->dst);
+                                                                   h->dst, gate);
     LAUNCH_CHECK(h);
     ++(h)->launches, k_tcr_final<<<dim3(ceil_div(n, 256), m), 256, 0, s>>>(
         w->rowmax, w->xe, w->part, n, m, w->RB, mode == 0 ? B : nullptr, ldb, X, ldx, R,
-        ldr, NP, mode);
+        ldr, NP, mode, gate);
     LAUNCH_CHECK(h);
     return SPD_OK;
 }

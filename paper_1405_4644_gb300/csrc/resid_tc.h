@@ -40,5 +40,7 @@ spd_status tc_resid_bind(spd_handle* h, TcResidWs* w, int n, int m, const size_t
 spd_status tc_resid_prepare(spd_handle* h, TcResidWs* w, const double* A, long lda);
 // R = B - A X (mode 0) or R = A X (mode 1) for the A of the last prepare;
 // block partial norms into NP (256-row blocks, as k_resid_final).
+// gate (device int, may be NULL): every kernel returns at once when it is 0
+// (the refinement of a capturable solve is over)
 spd_status tc_resid_run(spd_handle* h, const TcResidWs* w, const double* B, long ldb, const double* X, long ldx,
-                        double* R, long ldr, double* NP, int mode);
+                        double* R, long ldr, double* NP, int mode, const int* gate = nullptr);

@@ -78,6 +78,7 @@ extern "C" spd_status spd_destroy(spd_handle* h) {
     cudaEventDestroy(h->e1);
     cudaFree(h->ready);
     cudaFree(h->stage);
+    cudaFree(h->async_epoch_dev);
     if (h->aux) cudaStreamDestroy(h->aux);
     for (auto e : h->sync_ev) cudaEventDestroy(e);
     for (auto& r : h->prof) {
@@ -254,7 +255,7 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
         if (!w.tc || w.tc->n != n || w.tc->m != m) return set_err(h, SPD_ERR_ARG, "tensor-core residual not prepared");
         // algorithmic work: 55 digit products of 2 n^2 m; bytes: the ten digit planes
         ProfScope ps(h, SPD_PHASE_RESID_TC, 110.0 * n * (double)n * m, 20.0 * n * (double)n + 24.0 * n * (double)m);
-        spd_status st = tc_resid_run(h, w.tc, B, ldb, X, ldx, R, ldr, w.NP, mode);
+        spd_status st = tc_resid_run(h, w.tc, B, ldb, X, ldx, R, ldr, w.NP, mode, h->async_on ? h->async_gate : nullptr);
         if (st != SPD_OK) return st;
         const int G = ceil_div(n, 256);
         if (colnorms) {
@@ -269,6 +270,7 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
     }
     ProfScope ps(h, kind == SPD_RESID_DF32 ? SPD_PHASE_RESID_DF32 : SPD_PHASE_RESID, 2.0 * n * (double)n * m,
                  8.0 * n * (double)n + 24.0 * n * (double)m);
+    const int* gate = h->async_on ? h->async_gate : nullptr;
     const int S = kind == SPD_RESID_DF32 ? w.Sdf : w.S;
     const int jchunk = (int)round_up(ceil_div(n, S), RESID_JT);
     dim3 grid(ceil_div(n, RESID_ROWS), S);
@@ -280,19 +282,19 @@ spd_status resid_run(spd_handle* h, const ResidWs& w, int n, int m, const double
         int mc = std::min(16, m - c0);
         float* ra = (anorm && c0 == 0) ? w.rowabs : nullptr;
         if (mc == 1)
-            ++(h)->launches, k_resid_partial<1><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+            ++(h)->launches, k_resid_partial<1><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra, gate);
         else if (mc == 2)
-            ++(h)->launches, k_resid_partial<2><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+            ++(h)->launches, k_resid_partial<2><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra, gate);
         else if (mc <= 4)
-            ++(h)->launches, k_resid_partial<4><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+            ++(h)->launches, k_resid_partial<4><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra, gate);
         else if (mc <= 8)
-            ++(h)->launches, k_resid_partial<8><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+            ++(h)->launches, k_resid_partial<8><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra, gate);
         else
-            ++(h)->launches, k_resid_partial<16><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra);
+            ++(h)->launches, k_resid_partial<16><<<grid, RESID_ROWS, 0, s>>>(A, lda, n, X, ldx, c0, mc, jchunk, m, w.P, ra, gate);
         LAUNCH_CHECK(h);
     }
     const int G = ceil_div(n, 256);
-    ++(h)->launches, k_resid_final<<<dim3(G, m), 256, 0, s>>>(B, ldb, n, m, w.P, S, R, ldr, X, ldx, w.NP, mode);
+    ++(h)->launches, k_resid_final<<<dim3(G, m), 256, 0, s>>>(B, ldb, n, m, w.P, S, R, ldr, X, ldx, w.NP, mode, gate);
     LAUNCH_CHECK(h);
     if (colnorms) {
         ++(h)->launches, k_colnorms<<<m, 256, 0, s>>>(w.NP, G, m, colnorms);
@@ -358,6 +360,13 @@ CoopGate& coop_gate() {
     return g;
 }
 cudaError_t coop_launch(const void* fn, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+    // while s is being captured into a graph, the order against other
+    // streams' cooperative launches cannot be recorded (an event from outside
+    // the capture): the graph's launches are issued as they are, and the
+    // caller must not replay it concurrently with other cooperative work
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusActive)
+        return cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s);
     CoopGate& g = coop_gate();
     std::lock_guard<std::mutex> lock(g.mu);
     cudaError_t e = cudaSuccess;
@@ -403,7 +412,13 @@ spd_status trsv32_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, in
     unsigned long long* slots = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(h->ready) +
                                                                       round_up((long)sizeof(int) * h->ready_n, 256));
     for (int dir = 0; dir < 2; ++dir) {
-        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ++h->epoch, h->dst, slots, h->wait_ns};
+        // epochs: the host counter, or (capturable solves) an offset from
+        // the device counter, which the solve advanced by async_total at its
+        // start: 2^30 + base - total + 1 .. 2^30 + base, never a value of the
+        // host counter (< 2^30) or of an earlier capturable solve
+        const int ep = h->async_on ? (++h->async_rel - h->async_total) : ++h->epoch;
+        TrsvArgs a{F->W, F->ldw, n, NB, F->LinvT, F->Cpl, Y, c0, mc, h->ready, ep, h->dst, slots, h->wait_ns,
+                   h->async_on ? h->async_gate : nullptr, h->async_on ? h->async_epoch_dev : nullptr};
         void* args[] = {&a};
         const int grid = std::min({NB, occ.per_sm[dir] * h->sms, TV_SLOTS});
         ++h->launches;
@@ -894,6 +909,109 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
         rep->time_ms = ms;
     }
     return result;
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1, capturable: the loop's stop decision stays on the device
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_epoch_advance(int* e, int by) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *e += by;
+}
+
+// The report of a capturable solve, from the refinement state on the device.
+__global__ void k_async_report(const IrSummary* __restrict__ sum, const IrCol* __restrict__ cols, int m,
+                               const DevStatus* __restrict__ st, spd_report_dev* __restrict__ out) {
+    __shared__ int s_sweeps;
+    if (threadIdx.x == 0) s_sweeps = 0;
+    __syncthreads();
+    for (int c = threadIdx.x; c < m; c += blockDim.x) atomicMax(&s_sweeps, cols[c].iters);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out->status = st->flags ? (st->flags & SPD_DEV_TIMEOUT ? SPD_ERR_TIMEOUT : SPD_ERR_CUDA)
+                                : (sum->active == 0 ? SPD_OK : SPD_ERR_NO_CONVERGENCE);
+        out->active = sum->active;
+        out->sweeps = s_sweeps;
+        out->stagnated = sum->stagnated;
+        out->dev_flags = st->flags;
+        out->berr = sum->max_berr;
+        out->rel_resid = sum->max_rel;
+    }
+}
+
+// Clears h's capturable-solve state on every way out.
+struct AsyncScope {
+    spd_handle* h;
+    ~AsyncScope() {
+        h->async_on = false;
+        h->async_gate = nullptr;
+    }
+};
+
+}  // namespace
+
+extern "C" spd_status spd_solve_ir_async(spd_handle* h, const spd_factor_t* F, int n, int m, const double* A, int lda,
+                                         const double* B, int ldb, double* X, int ldx, const spd_opts* opts_in,
+                                         spd_report_dev* rep) {
+    if (!h) return SPD_ERR_ARG;
+    spd_opts o;
+    spd_opts_default(&o);
+    if (opts_in) o = *opts_in;
+    if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || !rep || o.maxit < 0 || !(o.tol >= 0.0) ||
+        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_TC || F->prec == SPD_PREC_FP64)
+        return set_err(h, SPD_ERR_ARG, "spd_solve_ir_async: bad arguments");
+    if (n == 0 || m == 0) return SPD_OK;
+    const int kind = o.resid == SPD_RESID_TC ? SPD_RESID_TC : SPD_RESID_FP64;  // no hybrid: no host decision
+    cudaStream_t s = h->stream;
+    WsPlan p;
+    size_t o_[22];
+    int S, G2;
+    cg_plan(p, h, n, m, o_, &S, &G2);
+    TcSetup tcs;
+    tc_plan_if(p, h, n, m, kind, tcs);
+    spd_status st = ws_reserve(h, p.bytes);
+    if (st != SPD_OK) return st;
+    if (!h->async_epoch_dev) {  // first capturable solve of this handle
+        CUDA_TRY(h, cudaMalloc(&h->async_epoch_dev, 256));
+        CUDA_TRY(h, cudaMemsetAsync(h->async_epoch_dev, 0, 256, s));
+    }
+    CgWs w = cg_bind(h, n, o_, S, G2);
+    st = tc_bind_prepare(h, tcs, n, m, A, lda, w.rw);
+    if (st != SPD_OK) return st;
+    AsyncScope scope{h};
+    h->async_on = true;
+    h->async_gate = nullptr;  // line 2 and the first residual always run
+    h->async_rel = 0;
+    h->async_total = 2 * ceil_div(m, 16) * (1 + o.maxit);  // sweep launches of this solve
+    ++h->launches, k_epoch_advance<<<1, 32, 0, s>>>(h->async_epoch_dev, h->async_total);
+    ++(h)->launches, k_ircols_init<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, std::max(0, o.polish));
+    ++(h)->launches, k_col_nrm2<<<m, 256, 0, s>>>(B, ldb, n, w.b2);
+    LAUNCH_CHECK(h);
+    st = lp_apply(h, F, n, m, B, ldb, w.Yz, X, ldx, nullptr, 0);  // line 2
+    if (st != SPD_OK) return st;
+    st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, w.anorm, 0, kind);  // line 3
+    if (st != SPD_OK) return st;
+    ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 0,
+                                                  std::max(0, o.polish), 1);
+    LAUNCH_CHECK(h);
+    // maxit sweeps; the solves and residuals of each return at once when no
+    // column is left (sum->active == 0); the frozen-column update and the
+    // check leave a converged state as it is
+    h->async_gate = &w.sum->active;
+    for (int it = 0; it < o.maxit; ++it) {
+        ++(h)->launches, k_frozen_from_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.cols, m, w.frozen);
+        st = lp_apply(h, F, n, m, w.R, n, w.Yz, X, ldx, w.frozen, 1);  // lines 5-6
+        if (st != SPD_OK) return st;
+        st = resid_run(h, w.rw, n, m, A, lda, B, ldb, X, ldx, w.R, n, w.colnorms, nullptr, 0, kind);  // line 7
+        if (st != SPD_OK) return st;
+        ++(h)->launches, k_ir_check<<<1, 256, 0, s>>>(w.colnorms, w.anorm, w.b2, m, o.crit, o.tol, w.cols, w.sum, 1,
+                                                      std::max(0, o.polish), 1);
+        LAUNCH_CHECK(h);
+    }
+    ++h->launches, k_async_report<<<1, 256, 0, s>>>(w.sum, w.cols, m, h->dst, rep);
+    LAUNCH_CHECK(h);
+    return SPD_OK;
 }
 
 // ---------------------------------------------------------------------------
