@@ -17,6 +17,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import math
 import ctypes
 import json
 import os
@@ -624,6 +625,139 @@ def cg_leg(args):
     return 0
 
 
+class PowerSampler:
+    """NVML power samples (every 20 ms) on a background thread: the mean and
+    its standard error over a measured window, as Table 1 reports them."""
+
+    def __init__(self, nvml):
+        self.nvml = nvml
+        self.vals = []
+        self.stop_flag = False
+        self.th = None
+
+    def __enter__(self):
+        import threading
+        self.vals, self.stop_flag = [], False
+
+        def run():
+            while not self.stop_flag:
+                v = self.nvml.power_w() if self.nvml.ok else None
+                if v is not None:
+                    self.vals.append(v)
+                time.sleep(0.02)
+
+        self.th = threading.Thread(target=run, daemon=True)
+        self.th.start()
+        return self
+
+    def __exit__(self, *exc):
+        self.stop_flag = True
+        self.th.join()
+
+    def stats(self):
+        if len(self.vals) < 2:
+            return None, None
+        mean = statistics.mean(self.vals)
+        return mean, statistics.stdev(self.vals) / math.sqrt(len(self.vals))
+
+
+def table1_leg(args):
+    """The paper's Table 1 (Section 4.1) on this GPU: the model covariance
+    matrix of Section 4 (A(i,j) = 1/|i-j|^d off the diagonal, 1 + sqrt(i) on
+    it, i 1-based), n = args.n_cg (70000 in the paper), d in {1, 2, 4};
+    right-hand sides U[0,1] (seed 0), stop at ||r||_2 < 1e-5 as printed.
+    Rows: Cholesky-IR with 32 right-hand sides (float32 factor, float64
+    residual), CG with 1 and 32 (float32 products, float64 outer residual),
+    and CG whose inner products use the banded matrix (bandwidth 33).  Per
+    row: low/high iterations, seconds (device time of the library calls,
+    repeated to fill at least one second), average power and its standard
+    error (NVML samples), energy, and the paper's GFlops convention (CG:
+    2 n^2 (low + high) m; banded: high iterations at 2 n^2, low ones at
+    2 * 33 * n, per right-hand side; Cholesky: n^3 / 3) and GFlops/W.  The
+    paper's numbers (IBM PS702, two POWER7) are printed beside each row."""
+    import numpy as np
+    import torch
+    import paper_1405_4644_gb300 as spd
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    h = spd.spd_create(torch.cuda.current_stream())
+    n = args.n_cg
+    nvml = Nvml(torch.cuda.current_device())
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                                       "table1_n70000.json")))
+    paper = {(r[0], r[1], r[2]): dict(zip(gold["columns"], r)) for r in gold["rows"]}
+    idx = torch.arange(n, dtype=torch.float64, device=dev)
+    A = torch.empty((n, n), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    idle_w = idle_power(nvml, 2.0)
+    crit = {"tol": 1e-5, "crit": "abs2"}
+    rows = []
+    for d in (1, 2, 4):
+        for r0 in range(0, n, 4096):  # assembled in row blocks on the device (untimed, as in the paper)
+            blk = A[r0:r0 + 4096]
+            torch.sub(idx[r0:r0 + 4096, None], idx[None, :], out=blk)
+            blk.abs_().clamp_min_(1.0).pow_(d).reciprocal_()
+        A.diagonal().copy_(1.0 + torch.sqrt(idx + 1.0))
+        for method, m in (("cholesky", 32), ("cg", 1), ("cg", 32), ("banded_cg", 1), ("banded_cg", 32)):
+            B = torch.from_numpy(np.ascontiguousarray(W.uniform_rhs(n, m, 0).T)).to(dev).t()
+            X = torch.zeros(m, n, dtype=torch.float64, device=dev).t()
+
+            def run():
+                if method == "cholesky":
+                    st, F, fr = spd.spd_factor(h, A, "fp32")
+                    if st != spd.SPD_OK:
+                        raise RuntimeError(f"table1 factor d={d}: {spd.spd_last_error_string(h)}")
+                    st, r = spd.spd_solve_ir(h, F, A, B, X, dict(crit, resid="fp64"))
+                    spd.spd_factor_destroy(F)
+                    ms = fr.time_ms + r.time_ms
+                else:
+                    opts = dict(crit, eta=0.0, maxit_inner=20000, **({"band": 16} if method == "banded_cg" else {}))
+                    st, r = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
+                    ms = r.time_ms
+                if st != spd.SPD_OK:
+                    raise RuntimeError(f"table1 {method} d={d} m={m}: {spd.spd_last_error_string(h)}")
+                return ms, r
+
+            run()  # warm-up (workspace, conversions)
+            torch.cuda.synchronize()
+            times, last = [], None
+            e0 = nvml.energy_mj() if nvml.ok else None
+            with PowerSampler(nvml) as ps:
+                while not times or (sum(times) < 1000.0 and len(times) < 50):
+                    X.zero_()
+                    t, last = run()
+                    times.append(t)
+                torch.cuda.synchronize()
+            e1 = nvml.energy_mj() if nvml.ok else None
+            sec = statistics.median(times) / 1e3
+            low, high = last.iters_low, last.iters_high
+            if method == "cholesky":
+                flops = n ** 3 / 3.0
+            elif method == "cg":
+                flops = 2.0 * n * n * (low + high) * m
+            else:
+                flops = (2.0 * n * n * high + 2.0 * 33 * n * low) * m
+            pw, se = ps.stats()
+            j = (e1 - e0) / 1e3 / len(times) if e0 is not None and e1 is not None else None
+            row = {"method": method, "d": d, "rhs": m, "iters_low": low, "iters_high": high, "time_s": sec,
+                   "avg_power_w": pw, "power_std_err_w": se, "energy_j": j,
+                   "energy_j_net": (j - idle_w * sec) if (j is not None and idle_w is not None) else None,
+                   "gflops": flops / sec / 1e9, "gflops_per_w": (flops / sec / 1e9 / pw) if pw else None,
+                   "rel_resid_max": last.rel_resid, "repeats": len(times),
+                   "paper": {k: paper[(method, d, m)][k] for k in ("iters_low", "iters_high", "time_s",
+                                                                    "avg_power_w", "energy_kj", "gflops",
+                                                                    "gflops_per_w")}}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            del B, X
+    spd.spd_destroy(h)
+    out = {"leg": "table1", "metric": "Table 1 (Section 4.1): time, power and energy per row on one GB300",
+           "config": {"workload": f"model covariance (Section 4), n={n}, d in (1, 2, 4), right-hand sides U[0,1], "
+                                  "||r||_2 < 1e-5", "n": n, "idle_w": idle_w}, "rows": rows}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def learned_leg(args):
     """Learned preconditioner on the Matern-3/2 family (n points uniform in the
     unit square, ell ~ U[0.02, 0.5], nugget ~ logU[1e-4, 1e-1]): train on
@@ -786,7 +920,7 @@ def main():
     ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc"],
                     help="refinement residual: float64; float32 pairs until berr < 2^-36 then float64; "
                          "or exact bf16 digit products on the tensor cores")
-    ap.add_argument("--leg", default="main", choices=["main", "batched", "learned", "cg"])
+    ap.add_argument("--leg", default="main", choices=["main", "batched", "learned", "cg", "table1"])
     ap.add_argument("--n-cg", type=int, default=16384)
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n-learned", type=int, default=4096)
@@ -810,6 +944,8 @@ def main():
         return batched_leg(args)
     if args.leg == "cg":
         return cg_leg(args)
+    if args.leg == "table1":
+        return table1_leg(args)
     if args.leg == "learned":
         return learned_leg(args)
 
