@@ -707,7 +707,8 @@ def table1_leg(args):
                     st, F, fr = spd.spd_factor(h, A, "fp32")
                     if st != spd.SPD_OK:
                         raise RuntimeError(f"table1 factor d={d}: {spd.spd_last_error_string(h)}")
-                    st, r = spd.spd_solve_ir(h, F, A, B, X, dict(crit, resid="fp64"))
+                    # the paper's rule: stop as soon as the tolerance holds (no polish sweep)
+                    st, r = spd.spd_solve_ir(h, F, A, B, X, dict(crit, resid="fp64", polish=0))
                     spd.spd_factor_destroy(F)
                     ms = fr.time_ms + r.time_ms
                 else:
