@@ -128,6 +128,32 @@ class Nvml:
             return None
         return v.value / 1000.0
 
+    def local_cpus(self):
+        """The CPUs NVML lists as closest to the device (its CPU affinity
+        mask), or None."""
+        words = (os.cpu_count() or 64) // 64 + 1
+        mask = (ctypes.c_ulong * words)()
+        if self.lib.nvmlDeviceGetCpuAffinity(self.dev, words, mask) != 0:
+            return None
+        cpus = {64 * w + b for w in range(words) for b in range(64) if mask[w] >> b & 1}
+        return cpus or None
+
+
+def bind_near_gpu(nvml):
+    """Run this process (and the threads it starts later) on the CPUs next
+    to the GPU, so that pinned host buffers, first touched here, sit in the
+    GPU's local memory node: the host-to-device copies of the end-to-end
+    measurement then cross one link, not the link between CPU sockets.  Only
+    this process's CPU affinity changes.  Returns a description."""
+    cpus = nvml.local_cpus() if nvml.ok else None
+    if not cpus or not hasattr(os, "sched_setaffinity"):
+        return {"bound": False}
+    cpus &= os.sched_getaffinity(0)
+    if not cpus:
+        return {"bound": False}
+    os.sched_setaffinity(0, cpus)
+    return {"bound": True, "cpus": len(cpus)}
+
 
 # ---------------------------------------------------------------------------
 # distributed plumbing (replicas only: no collective on the data path)
@@ -564,8 +590,11 @@ def cg_leg(args):
     1-based), d in {1, 2, 4}; 1 and 32 right-hand sides U[0, 1] (seed 0);
     stop at ||r||_2 <= 1e-5 as in Table 1; float32 matrix products, float64
     outer residual.  Per case: solves/s (library device time), the low and
-    high iteration counts, and the matrix products' HBM rate (4 n^2 bytes of
-    the float32 copy per product) against the measured copy bandwidth."""
+    high iteration counts, and the matrix products' HBM rate (the bytes of
+    A~ one product reads: 4 n^2 for the float32 copy on the CUDA cores, 6 n^2
+    for its three bf16 slice planes on the tensor cores, which the library
+    takes for m >= 8 unless --mv-cores says otherwise) against the measured
+    copy bandwidth."""
     import numpy as np
     import torch
     import paper_1405_4644_gb300 as spd
@@ -576,7 +605,7 @@ def cg_leg(args):
     peaks, src = load_peaks()
     idx = torch.arange(n, dtype=torch.float64, device=dev)
     A = torch.empty((n, n), dtype=torch.float64, device=dev)
-    base = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000}
+    base = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000, "matvec_cores": args.mv_cores}
     nvml = Nvml(torch.cuda.current_device())
     out = {"leg": "cg", "metric": "CG solves/s (Algorithm 2, float32 products, float64 outer residual)",
            "unit": "solves/s", "config": {"workload": f"model covariance (Section 4), n={n}, d in (1, 2, 4), "
@@ -712,7 +741,8 @@ def table1_leg(args):
                     spd.spd_factor_destroy(F)
                     ms = fr.time_ms + r.time_ms
                 else:
-                    opts = dict(crit, eta=0.0, maxit_inner=20000, **({"band": 16} if method == "banded_cg" else {}))
+                    opts = dict(crit, eta=0.0, maxit_inner=20000, matvec_cores=args.mv_cores,
+                                **({"band": 16} if method == "banded_cg" else {}))
                     st, r = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
                     ms = r.time_ms
                 if st != spd.SPD_OK:
@@ -875,8 +905,9 @@ def case_leg(args):
                 ok(st)
                 print(f"factor {prec} n={n}: {rep.time_ms:.3f} ms")
                 spd.spd_factor_destroy(F)
-        if args.case == "sweeps":
-            st, F, _ = spd.spd_factor(h, A, "fp16")
+        if args.case in ("sweeps", "sweeps_sb"):
+            flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_SB_SWEEPS if args.case == "sweeps_sb" else 0)
+            st, F, _ = spd.spd_factor(h, A, "fp16", flags)
             ok(st)
             for _ in range(args.reps):
                 ok(spd.spd_factor_solve(h, F, B, R))
@@ -923,12 +954,15 @@ def main():
                          "or exact bf16 digit products on the tensor cores")
     ap.add_argument("--leg", default="main", choices=["main", "batched", "learned", "cg", "table1"])
     ap.add_argument("--n-cg", type=int, default=16384)
+    ap.add_argument("--mv-cores", default="auto", choices=["auto", "cuda", "tensor"],
+                    help="cg and table1 legs: where the float32 products run (auto: tensor cores for m >= 8)")
     ap.add_argument("--count", type=int, default=4096)
     ap.add_argument("--n-learned", type=int, default=4096)
     ap.add_argument("--train-systems", type=int, default=1000)
     ap.add_argument("--test-systems", type=int, default=32)
     ap.add_argument("--case", default=None,
-                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "convert", "factor", "factor_serial"],
+                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "sweeps_sb", "convert", "factor",
+                             "factor_serial"],
                     help="run one kernel family on a fixed case (for profilers) and exit")
     ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
     ap.add_argument("--phases", action="store_true", help="--case: print the library's phase records")
@@ -958,6 +992,7 @@ def main():
         FACTOR_FLAGS["flags"] = spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SHIFT
     rank, world, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local)
+    affinity = bind_near_gpu(Nvml(local))
     stream = torch.cuda.current_stream()
     h = spd.spd_create(stream)
     spectra = []
@@ -1128,7 +1163,7 @@ def main():
         e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
                "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
-               "h2d_gbs_one_copy": h2d_gbs}
+               "h2d_gbs_one_copy": h2d_gbs, "cpu_affinity": affinity}
 
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None

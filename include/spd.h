@@ -137,6 +137,12 @@ typedef enum spd_resid {
                                     preconditioned CG fallback (Section 3.1,
                                     eq. (iterref): the inner solver only has
                                     to contract).  report.shift gives sigma */
+#define SPD_FACTOR_SB_SWEEPS 32u /* float32 factors of at least 16 128-row
+                                    blocks: also form the inverses of the
+                                    diagonal super-blocks (8 blocks each) and
+                                    apply the factor with the super-block
+                                    sweeps instead of the default sweeps over
+                                    128-row blocks */
 #define SPD_FACTOR_SERIAL 8u     /* left-looking schedule without its
                                     look-ahead: every kernel on the handle's
                                     stream in order (kernels then run alone,
@@ -155,7 +161,21 @@ typedef struct spd_opts {
     int polish;      /* spd_solve_ir: extra sweeps after a column first meets
                         the rule, to bring its forward error to the float64
                         floor (default 1)                                     */
+    int matvec_cores;/* spd_cg with FP32 products (step C1): spd_mv_cores
+                        (default SPD_MV_AUTO)                                 */
 } spd_opts;
+
+/* Where spd_cg computes its FP32 products z = A~ p (Section 3.2, step C1).
+ * On the tensor cores, A~ (float32) and p (float32) enter as three bf16
+ * slices each and the six slice products of order <= 2 accumulate in float32
+ * tensor memory, so the product keeps the float32 product's accuracy; A~ is
+ * then held as three bf16 planes (6 n^2 bytes) instead of one float32 copy
+ * (4 n^2 bytes).  On the CUDA cores, float32 fused multiply-adds. */
+typedef enum spd_mv_cores {
+    SPD_MV_AUTO = 0,    /* tensor cores when m >= 8, else CUDA cores */
+    SPD_MV_CUDA = 1,    /* CUDA cores for every m                    */
+    SPD_MV_TENSOR = 2   /* tensor cores for every m                  */
+} spd_mv_cores;
 
 typedef struct spd_report {
     int status;      /* spd_status of the call                               */
@@ -508,6 +528,11 @@ spd_status spd_batch_destroy(spd_batch *plan);
  * result does not depend on timing).  Device pointers; synchronous. */
 #define SPD_GEMM_LOWER 1
 #define SPD_GEMM_STREAM_K 2
+#define SPD_GEMM_NARROW 4  /* SPD_PREC_FP32 only, not with LOWER: tiles of
+                              128 x 32 (N <= 32) or 128 x 64 whose pipeline
+                              stages hold all three slices of both operand
+                              tiles -- the skinny products of spd_cg with
+                              several right-hand sides (Section 3.2) */
 spd_status spd_gemm_update(spd_handle *h, int prec, int M, int N, int K, const float *A, int lda,
                            const float *B, int ldb, float *C, int ldc, int flags);
 

@@ -46,6 +46,8 @@ SPD_FACTOR_CUDA_CORES = 2
 SPD_FACTOR_RECURSIVE = 4
 SPD_FACTOR_SERIAL = 8
 SPD_FACTOR_SHIFT = 16
+SPD_FACTOR_SB_SWEEPS = 32
+MV_CORES = {"auto": 0, "cuda": 1, "tensor": 2}
 
 # every symbol include/spd.h declares
 EXPORTED = [
@@ -63,7 +65,7 @@ EXPORTED = [
 class SpdOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("crit", C.c_int), ("maxit", C.c_int), ("maxit_inner", C.c_int),
                 ("eta", C.c_double), ("band", C.c_int), ("fallback", C.c_int), ("resid", C.c_int),
-                ("polish", C.c_int)]
+                ("polish", C.c_int), ("matvec_cores", C.c_int)]
 
 
 class SpdReport(C.Structure):
@@ -241,6 +243,8 @@ def _opts(opts):
             v = CRIT[v]
         if k == "resid" and isinstance(v, str):
             v = RESID[v]
+        if k == "matvec_cores" and isinstance(v, str):
+            v = MV_CORES[v]
         setattr(o, k, v)
     return C.byref(o)
 
@@ -409,10 +413,10 @@ def spd_launch_count(h):
     return c.value
 
 
-SPD_GEMM_LOWER, SPD_GEMM_STREAM_K = 1, 2
+SPD_GEMM_LOWER, SPD_GEMM_STREAM_K, SPD_GEMM_NARROW = 1, 2, 4
 
 
-def spd_gemm_update(h, prec, A, B, C, lower=False, stream_k=False):
+def spd_gemm_update(h, prec, A, B, C, lower=False, stream_k=False, narrow=False):
     """C -= round(A) round(B)^T on the tensor cores; float32 row-major device
     tensors A (M, K), B (N, K), C (M, N)."""
     for t, nm in ((A, "A"), (B, "B"), (C, "C")):
@@ -425,7 +429,8 @@ def spd_gemm_update(h, prec, A, B, C, lower=False, stream_k=False):
         raise ValueError(f"shapes A {tuple(A.shape)}, B {tuple(B.shape)}, C {tuple(C.shape)} do not match")
     return lib().spd_gemm_update(h, _prec(prec), M, N, K, A.data_ptr(), A.stride(0), B.data_ptr(), B.stride(0),
                                  C.data_ptr(), C.stride(0),
-                                 (SPD_GEMM_LOWER if lower else 0) | (SPD_GEMM_STREAM_K if stream_k else 0))
+                                 (SPD_GEMM_LOWER if lower else 0) | (SPD_GEMM_STREAM_K if stream_k else 0) |
+                                 (SPD_GEMM_NARROW if narrow else 0))
 
 
 def spd_residual_static(stream, A, B, X, R, colnorms=None):

@@ -10,6 +10,7 @@
 #define SPD_SUB 32     // order of the warp-level sub-blocks inside a leaf
 #define SPD_MAXM 4096  // largest right-hand-side count per call
 #define SPD_FP8_SCALE 256.0f  // operand scale of the e4m3 mirror (products carry 2^16)
+#define SPD_SB_BLOCKS 8       // 128-blocks per diagonal super-block of the super-block sweeps
 
 // Device-side error word: bit flags raised by kernels, read by the host.
 enum : int {

@@ -47,6 +47,8 @@ struct spd_handle {
     const int* async_gate = nullptr;
     int* async_epoch_dev = nullptr;
     int async_rel = 0, async_total = 0;
+    void* sb_buf = nullptr;     // super-block sweeps: partial tiles, then two barrier words
+    size_t sb_bytes = 0;
     size_t mem_cap = 0;         // largest device request of one call (0 = no cap): spd_set_memory_cap
 };
 
@@ -68,6 +70,8 @@ struct spd_factor_t {
     float* Cpl = nullptr;      // float32 factor: sweep couplings M_J, N_J, P_J, Q_J (4 x nblk128 blocks)
     float* Dinv32 = nullptr;   // float32 factor: inverses of the 32x32 diagonal sub-blocks
     int nblk128 = 0;
+    float* Xsb = nullptr;      // float32 factor: inverses of the diagonal super-blocks (sbb 128-blocks each)
+    int sbb = 0, nsb = 0;      // 128-blocks per super-block, super-blocks (0: 128-block sweeps)
 };
 
 static spd_status set_err(spd_handle* h, spd_status s, const char* fmt, ...) {

@@ -44,9 +44,18 @@ constexpr int A_STAGE = BM * 128;  // bytes: 128 rows x 128 B
 // with ST pipeline stages: 4 stages and one CTA per SM, or (128-wide tf32
 // tiles, whose six-segment float32 updates are long) 3 stages of 32 KB and
 // two CTAs per SM, so that one CTA's epilogue overlaps the other's main loop.
+// Narrow tiles (BNT = 32 or 64, the skinny products A~ P of CG with m
+// right-hand sides) take all three slices of an A tile and of a B tile in one
+// stage (SL = 3 slices per stage, one TMA load each with a box three planes
+// deep), so that each slice tile crosses from L2 to shared memory once per K
+// tile and the six slice products are issued from the same stage.
 template <int BNT> __host__ __device__ constexpr int b_stage() { return BNT * 128; }
-template <int BNT> __host__ __device__ constexpr int stage_bytes() { return A_STAGE + b_stage<BNT>(); }
-template <int BNT, int ST> constexpr size_t smem_bytes() { return (size_t)ST * stage_bytes<BNT>() + 1024 + 256; }
+template <int BNT, int SL = 1> __host__ __device__ constexpr int stage_bytes() {
+    return SL * (A_STAGE + b_stage<BNT>());
+}
+template <int BNT, int ST, int SL = 1> constexpr size_t smem_bytes() {
+    return (size_t)ST * stage_bytes<BNT, SL>() + 1024 + 256;
+}
 constexpr uint64_t WAIT_NS = 2000000000ull;  // 2 s per wait
 
 template <int KIND> struct KindTraits;
@@ -182,17 +191,18 @@ __device__ __forceinline__ long unit_begin(int g, long W, int G) { return (long)
 // accumulator (accsel >> q) & 1.  With one accumulator per tile (NACC = 1)
 // the tensor memory holds two, so the epilogue of one piece overlaps the
 // main loop of the next.
-template <int KIND, int BNT, int ST, int NACC>
-__global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
+template <int KIND, int BNT, int ST, int NACC, int SL = 1>
+__global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
               const __grid_constant__ CUtensorMap mapC, int use_map_c, float* __restrict__ C, long ldc, int cx0,
               int cy0, int M, int N, int a_row0, int b_row0, int k0, int lower, uint32_t idesc, float scale, int nseg,
               uint32_t segs, uint32_t accsel, int tiles_n, int nk, long W, int G, float* __restrict__ Cpart,
               DevStatus* st) {
     constexpr int BK = KindTraits<KIND>::BK;
-    constexpr int B_STAGE = b_stage<BNT>();
+    constexpr int B_STAGE = b_stage<BNT>();      // one slice of a B tile
     constexpr int STAGES = ST;
-    constexpr int STAGE_BYTES = stage_bytes<BNT>();
+    constexpr int STAGE_BYTES = stage_bytes<BNT, SL>();
+    constexpr int A_ST = SL * A_STAGE, B_ST = SL * B_STAGE;  // a stage's A and B parts
     constexpr int NBUF = NACC == 1 ? 2 : 1;
     constexpr uint32_t ACC_COLS = BNT * NACC;  // one tile's accumulator(s)
     constexpr uint32_t TMEM_COLS = ACC_COLS * NBUF;
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                            ~static_cast<uintptr_t>(1023));
     unsigned char* sA = base;
-    unsigned char* sB = base + STAGES * A_STAGE;
+    unsigned char* sB = base + STAGES * A_ST;
     uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
     uint64_t* accfull = empty + STAGES;  // [NBUF] MMA -> epilogue
@@ -256,6 +266,21 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
         if (lane == 0) {  // TMA producer
             int kt = 0;
             SPD_FOR_PIECES {
+                if constexpr (SL == 3) {  // one stage per K tile: every slice of both tiles
+                    for (int kin = kb; kin < ke; ++kin, ++kt) {
+                        const int s = kt % STAGES;
+                        const uint32_t ph = (kt / STAGES) & 1u;
+                        if (kt >= STAGES && !tc::mbar_wait(&empty[s], ph ^ 1u, abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        tc::tma_load_3d(sA + s * A_ST, &mapA, k0 + kin * BK, a_row0 + bm * BM, 0, &full[s]);
+                        tc::tma_load_3d(sB + s * B_ST, &mapB, k0 + kin * BK, b_row0 + bn * BNT, 0, &full[s]);
+                    }
+                    if (!ok) break;
+                    continue;
+                }
                 for (int kin = kb; kin < ke && ok; ++kin)
                     for (int q = 0; q < nseg; ++q, ++kt) {
                         const int s = kt % STAGES;
@@ -266,8 +291,8 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
                             break;
                         }
                         tc::mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                        tc::tma_load_3d(sA + s * A_STAGE, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
-                        tc::tma_load_3d(sB + s * B_STAGE, &mapB, k0 + kin * BK, b_row0 + bn * BNT, zb, &full[s]);
+                        tc::tma_load_3d(sA + s * A_ST, &mapA, k0 + kin * BK, a_row0 + bm * BM, za, &full[s]);
+                        tc::tma_load_3d(sB + s * B_ST, &mapB, k0 + kin * BK, b_row0 + bn * BNT, zb, &full[s]);
                     }
                 if (!ok) break;
             }
@@ -288,6 +313,33 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
                     }
                     tc::fence_after_sync();
                 }
+                if constexpr (SL == 3) {
+                    for (int kin = kb; kin < ke; ++kin, ++kt) {
+                        const int s = kt % STAGES;
+                        const uint32_t ph = (kt / STAGES) & 1u;
+                        if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::fence_after_sync();
+                        for (int q = 0; q < nseg; ++q) {
+                            const int za = (segs >> (4 * q)) & 3, zb = (segs >> (4 * q + 2)) & 3;
+                            const int a = (accsel >> q) & 1;
+                            const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_ST + za * A_STAGE));
+                            const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_ST + zb * B_STAGE));
+                            const uint32_t d = tmem + (uint32_t)(buf * ACC_COLS + a * BNT);
+                            const bool fresh = kin == kb && q == first[a];
+#pragma unroll
+                            for (int k = 0; k < MMA_PER_STAGE; ++k)
+                                tc::mma<KIND>(d, ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
+                        }
+                        tc::mma_commit(&empty[s]);
+                    }
+                    if (!ok) break;
+                    tc::mma_commit(&accfull[buf]);
+                    ++p;
+                    continue;
+                }
                 for (int kin = kb; kin < ke && ok; ++kin)
                     for (int q = 0; q < nseg; ++q, ++kt) {
                         const int s = kt % STAGES;
@@ -298,8 +350,8 @@ __global__ void __launch_bounds__(192, ST == 3 ? 2 : 1)
                             break;
                         }
                         tc::fence_after_sync();
-                        const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_STAGE));
-                        const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_STAGE));
+                        const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_ST));
+                        const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_ST));
                         const uint32_t d = tmem + (uint32_t)(buf * ACC_COLS + a * BNT);
                         const bool fresh = kin == kb && q == first[a];
 #pragma unroll
@@ -391,9 +443,11 @@ int elem_bytes(int kind) { return kind == 1 ? 4 : kind == 4 ? 1 : 2; }
 int slices_of(int kind) { return kind == 5 ? 3 : 1; }
 
 // 3-D map over `planes` row-major (rows x cols, ld elements) operand planes
-// (plane stride rows*ld) with a box of (128 bytes of K) x box_rows x 1,
-// 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols, long ld, int box_rows) {
+// (plane stride rows*ld) with a box of (128 bytes of K) x box_rows x box_z
+// (box_z = 1: one slice; 3: every slice of a float32 operand), 128-byte
+// swizzle, zero fill outside.
+bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols, long ld, int box_rows,
+              int box_z = 1) {
     auto enc = get_encode();
     if (!enc) return false;
     CUtensorMapDataType dt = kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -403,7 +457,7 @@ bool make_map(CUtensorMap* map, const void* base, int kind, long rows, long cols
     const int es = elem_bytes(kind);
     cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)slices_of(kind)};
     cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)(rows * ld * es)};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, (cuuint32_t)box_z};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -436,10 +490,10 @@ uint32_t idesc_for(int kind, int bn) {
     }
 }
 
-template <int KIND, int BNT, int ST, int NACC>
+template <int KIND, int BNT, int ST, int NACC, int SL = 1>
 void set_smem() {
-    cudaFuncSetAttribute(k_gemm_tc<KIND, BNT, ST, NACC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem_bytes<BNT, ST>());
+    cudaFuncSetAttribute(k_gemm_tc<KIND, BNT, ST, NACC, SL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem_bytes<BNT, ST, SL>());
 }
 
 void set_attrs() {
@@ -453,6 +507,8 @@ void set_attrs() {
         set_smem<1, 128, 4, 1>();
         set_smem<2, 128, 4, 1>();
         set_smem<0, 128, 3, 2>();
+        set_smem<0, 32, 3, 2, 3>();
+        set_smem<0, 64, 3, 2, 3>();
         return true;
     }();
     (void)done;
@@ -520,6 +576,7 @@ struct TcGemm {
     CUtensorMap mapA, mapB, mapB128;  // box heights 128 (A), 256 and 128 (B)
     CUtensorMap mapC;                 // C in 32 x 32 boxes (when has_map_c)
     bool has_map_c;
+    int narrow;                       // 32 or 64: narrow fused-slice tiles (maps three planes deep), else 0
     float* C;
     long ldc;
     int kind;
@@ -554,6 +611,31 @@ spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a
     return SPD_OK;
 }
 
+spd_status tc_gemm_create_narrow(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
+                                 long b_ld, long cols, float* C, long c_rows, long c_cols, long ldc, int bnt) {
+    *out = nullptr;
+    if (bnt != 32 && bnt != 64) return SPD_ERR_ARG;
+    TcGemm* g = new TcGemm();
+    memset(g, 0, sizeof(*g));
+    if (!make_map(&g->mapA, Ah, 5, a_rows, cols, a_ld, BM, 3) || !make_map(&g->mapB, Bh, 5, b_rows, cols, b_ld, bnt, 3)) {
+        delete g;
+        return SPD_ERR_UNSUPPORTED;
+    }
+    g->has_map_c = (ldc % 4 == 0) && (reinterpret_cast<uintptr_t>(C) % 16 == 0) &&
+                   make_map_c(&g->mapC, C, c_rows, c_cols, ldc);
+    g->C = C;
+    g->ldc = ldc;
+    g->kind = 5;
+    g->narrow = bnt;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        g->sms = 148;
+    set_attrs();
+    *out = g;
+    return SPD_OK;
+}
+
 spd_status tc_gemm_create(TcGemm** out, float* W, long ldw, void* Wh, long ldh, int kind, int n) {
     return tc_gemm_create_maps(out, Wh, n, ldh, Wh, n, ldh, n, W, n, n, ldw, kind);
 }
@@ -564,21 +646,25 @@ template <int BNT>
 void launch_kind(TcGemm* g, cudaStream_t s, int G, int cx0, int cy0, int M, int N, int a_row0, int b_row0, int k0,
                  int lower, float scale, int nseg, uint32_t segs, uint32_t accsel, int tiles_n, int nk, long W,
                  float* Cpart, DevStatus* st) {
-    const CUtensorMap& mb = BNT == 128 ? g->mapB128 : g->mapB;
+    const CUtensorMap& mb = (BNT == 128 && !g->narrow) ? g->mapB128 : g->mapB;
     const uint32_t idesc = idesc_for(g->kind, BNT);
     float* Cb = g->C + (long)cy0 * g->ldc + cx0;  // the block's origin (epilogue without a tensor map)
 #define SPD_GEMM_ARGS                                                                                            \
     g->mapA, mb, g->mapC, g->has_map_c ? 1 : 0, Cb, g->ldc, cx0, cy0, M, N, a_row0, b_row0, k0, lower, idesc, \
         scale, nseg, segs, accsel, tiles_n, nk, W, G, Cpart, st
-    switch (g->kind) {
-        case 1: k_gemm_tc<1, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
-        case 5: {  // float32 as bf16 slices: two accumulators; two CTAs per SM on 128-wide tiles
-            constexpr int ST = BNT == 128 ? 3 : 4;
-            k_gemm_tc<0, BNT, ST, 2><<<G, 192, smem_bytes<BNT, ST>(), s>>>(SPD_GEMM_ARGS);
-            break;
+    if constexpr (BNT <= 64) {  // narrow tiles: float32 as bf16 slices, all slices in one stage
+        k_gemm_tc<0, BNT, 3, 2, 3><<<G, 192, smem_bytes<BNT, 3, 3>(), s>>>(SPD_GEMM_ARGS);
+    } else {
+        switch (g->kind) {
+            case 1: k_gemm_tc<1, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+            case 5: {  // float32 as bf16 slices: two accumulators; two CTAs per SM on 128-wide tiles
+                constexpr int ST = BNT == 128 ? 3 : 4;
+                k_gemm_tc<0, BNT, ST, 2><<<G, 192, smem_bytes<BNT, ST>(), s>>>(SPD_GEMM_ARGS);
+                break;
+            }
+            case 4: k_gemm_tc<2, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
+            default: k_gemm_tc<0, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS);
         }
-        case 4: k_gemm_tc<2, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS); break;
-        default: k_gemm_tc<0, BNT, 4, 1><<<G, 192, smem_bytes<BNT, 4>(), s>>>(SPD_GEMM_ARGS);
     }
 #undef SPD_GEMM_ARGS
 }
@@ -603,7 +689,7 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
         accsel = 1u << 5;
     }
     const int nk = K / bk;
-    const int bnt = (N <= 128) ? 128 : 256;
+    const int bnt = g->narrow ? g->narrow : (N <= 128) ? 128 : 256;
     const int tiles_n = (N + bnt - 1) / bnt, tiles_m = (M + BM - 1) / BM;
     const int T = tiles_n * tiles_m;
     const long W = (long)T * nk;
@@ -617,7 +703,9 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
         const int sms = splits < 0 ? -splits : g->sms;
         const int slots = (bnt == 128 && g->kind == 5 ? 2 : 1) * sms;
         int Gs = (int)std::min<long>(slots, W);
-        const double tk = nseg * (bnt == 256 ? 0.40 : 0.25);  // us per K tile (all segments)
+        // us per K tile (all segments); a narrow tile streams 48 KB of A
+        // slices per K tile at about an SM's share of HBM bandwidth
+        const double tk = g->narrow ? 1.0 : nseg * (bnt == 256 ? 0.40 : 0.25);
         const double dp = (double)((T + slots - 1) / slots) * nk * tk;
         // stream-K over Gc CTAs: the longest range, plus the fix-up: a launch
         // (~4 us) and its partial slots read at ~3 TB/s
@@ -635,7 +723,13 @@ spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, in
     // stream-K (G != T: more or fewer CTAs than tiles) always writes partials
     float* part = (G != T) ? sb->part : nullptr;
     if (G != T && !part) return SPD_ERR_ARG;
-    if (bnt == 128)
+    if (bnt == 32)
+        launch_kind<32>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
+                        W, part, st);
+    else if (bnt == 64)
+        launch_kind<64>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
+                        W, part, st);
+    else if (bnt == 128)
         launch_kind<128>(g, s, G, cx0, cy0, M, N, a_row0, b_row0, k0, lower, scale, nseg, segs, accsel, tiles_n, nk,
                          W, part, st);
     else

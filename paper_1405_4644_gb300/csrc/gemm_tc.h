@@ -32,6 +32,13 @@ void tc_gemm_destroy(TcGemm* g);
 // C (c_rows x c_cols, ldc floats, row-major).
 spd_status tc_gemm_create_maps(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
                                long b_ld, long cols, float* C, long c_rows, long c_cols, long ldc, int kind);
+// Narrow form for skinny products (B with few rows: the right-hand sides of
+// CG): float32 operands as three bf16 slices (kind 5 mirrors), tiles of
+// 128 x bnt (bnt = 32 or 64) whose pipeline stages hold all three slices of
+// both operand tiles; b_rows a multiple of bnt, c_cols and ldc multiples of
+// 32 for the epilogue's 32 x 32 boxes of C.
+spd_status tc_gemm_create_narrow(TcGemm** out, const void* Ah, long a_rows, long a_ld, const void* Bh, long b_rows,
+                                 long b_ld, long cols, float* C, long c_rows, long c_cols, long ldc, int bnt);
 // C[cy0 + i][cx0 + j] -= sum_k A[a_row0 + i][k0 + k] B[b_row0 + j][k0 + k]
 // for i < M, j < N (cx0 a multiple of 4).
 spd_status tc_gemm_launch(TcGemm* g, cudaStream_t s, int cy0, int cx0, int M, int N, int K, int a_row0, int b_row0,

@@ -70,6 +70,62 @@ static __global__ void __launch_bounds__(256) k_matvec_lp(const T* __restrict__ 
     }
 }
 
+// The tensor-core product of C1 for m > 1 right-hand sides: A~ and the
+// float32 P enter the tensor cores as three bf16 slices each (x = s0 + s1 +
+// s2, the float32 value to within a last rounding below 2^-24 |x|), and the
+// six slice products of order <= 2 accumulate in float32, so the product
+// carries the float32 product's accuracy.  The narrow GEMM computes
+// C -= A~ P^T on a zeroed float32 C (n x ldc, row-major); Q = -C.
+//
+// Slice planes of A~ (plane stride `plane`): row j, column i = the slices of
+// fl32(A(i, j)) (A symmetric), zero in the padding columns n <= i < Kp.
+static __global__ void k_convert_x3(const double* __restrict__ A, long lda, int n, int Kp,
+                                    __nv_bfloat16* __restrict__ M, long ldo, long plane, DevStatus* st) {
+    const long total = (long)n * Kp;
+    bool bad = false;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long j = e / Kp, i = e - j * Kp;  // column j of A = row j of the planes: coalesced both ways
+        float v = 0.f;
+        if (i < n) {
+            const double a = A[j * lda + i];
+            if (!isfinite(a)) bad = true;
+            v = (float)a;
+        }
+        __nv_bfloat16 s0, s1, s2;
+        split_bf16x3(v, s0, s1, s2);
+        __nv_bfloat16* q = M + j * ldo + i;
+        q[0] = s0;
+        q[plane] = s1;
+        q[2 * plane] = s2;
+    }
+    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+}
+
+// Rows c < m of P^T's slice planes: row c, column k = the slices of Pf[c n + k]
+// (padding rows and columns stay zero from the setup).
+static __global__ void k_p_x3(const float* __restrict__ Pf, int n, int m, __nv_bfloat16* __restrict__ Pm, long ldo,
+                              long plane) {
+    const long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long c = e / n, k = e - c * n;
+        __nv_bfloat16 s0, s1, s2;
+        split_bf16x3(Pf[e], s0, s1, s2);
+        __nv_bfloat16* q = Pm + c * ldo + k;
+        q[0] = s0;
+        q[plane] = s1;
+        q[2 * plane] = s2;
+    }
+}
+
+// Q[c n + i] = -C[i ldc + c] (float64, column-major) from the narrow GEMM's C
+static __global__ void k_cf_to_q(const float* __restrict__ Cf, long ldc, int n, int m, double* __restrict__ Q) {
+    const long total = (long)n * m;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total; e += (long)gridDim.x * blockDim.x) {
+        const long c = e / n, i = e - c * n;
+        Q[e] = -(double)Cf[i * ldc + c];
+    }
+}
+
 // Banded product with the diagonal-major band Ab[(o+band)*n + i] = A~(i, i+o).
 static __global__ void k_matvec_band(const float* __restrict__ Ab, int n, int band, const float* __restrict__ Pf,
                               int m, double* __restrict__ Q) {
@@ -86,38 +142,39 @@ static __global__ void k_matvec_band(const float* __restrict__ Ab, int n, int ba
     }
 }
 
-// Per-CTA partial dots: part[(blk*m + c)*2 + {0,1}] = sum a1.b1, sum a2.b2
-// over the CTA's rows (a2/b2 may be NULL).
+// Per-block partial dots: block (x, c) sums rows [x r, (x + 1) r) of column
+// c (r = ceil(n / gridDim.x)): part[(x m + c) 2 + {0, 1}] = sum a1.b1,
+// sum a2.b2 (a2/b2 may be NULL).  Every column reduces at once; the row
+// chunks per column shrink as m grows, so that the consumers' fixed-order
+// sums over gridDim.x partials stay short.
 static __global__ void __launch_bounds__(256) k_dot2(const double* __restrict__ a1, const double* __restrict__ b1,
                                               const double* __restrict__ a2, const double* __restrict__ b2,
                                               int n, int m, double* __restrict__ part) {
     __shared__ double red[2][8];
+    const int c = blockIdx.y;
     const int rows_per = (n + gridDim.x - 1) / gridDim.x;
     const int i0 = blockIdx.x * rows_per, i1 = min(n, i0 + rows_per);
-    for (int c = 0; c < m; ++c) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int i = i0 + threadIdx.x; i < i1; i += 256) {
-            long k = (long)c * n + i;
-            s1 += a1[k] * b1[k];
-            if (a2) s2 += a2[k] * b2[k];
+    double s1 = 0.0, s2 = 0.0;
+    for (int i = i0 + threadIdx.x; i < i1; i += 256) {
+        const long k = (long)c * n + i;
+        s1 += a1[k] * b1[k];
+        if (a2) s2 += a2[k] * b2[k];
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s1;
+        red[1][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            t1 += red[0][k];
+            t2 += red[1][k];
         }
-        s1 = warp_sum(s1);
-        s2 = warp_sum(s2);
-        if ((threadIdx.x & 31) == 0) {
-            red[0][threadIdx.x >> 5] = s1;
-            red[1][threadIdx.x >> 5] = s2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t1 = 0.0, t2 = 0.0;
-            for (int k = 0; k < 8; ++k) {
-                t1 += red[0][k];
-                t2 += red[1][k];
-            }
-            part[((long)blockIdx.x * m + c) * 2 + 0] = t1;
-            part[((long)blockIdx.x * m + c) * 2 + 1] = t2;
-        }
-        __syncthreads();
+        part[((long)blockIdx.x * m + c) * 2 + 0] = t1;
+        part[((long)blockIdx.x * m + c) * 2 + 1] = t2;
     }
 }
 

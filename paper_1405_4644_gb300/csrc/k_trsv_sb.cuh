@@ -1,0 +1,397 @@
+// k_trsv_sb.cuh -- step A4 (Algorithm 1, lines 2 and 5) over diagonal
+// super-blocks: the float32 sweeps y = L^{-1} y and z = L^{-T} z with the
+// explicit inverses X_I = L_II^{-1} of the diagonal super-blocks (SBB
+// 128-blocks each, S = 128 SBB rows), formed once per factor.
+//
+// Forward, super-block by super-block (I = 0, 1, ...):
+//   y_I = X_I r_I,   then   r_J -= L_JI y_I  for every 128-row block J below,
+// backward (I = last, ..., 0):
+//   z_I = X_I^T y_I, then   y_K -= L_IK^T z_I  for every 128-row block K above,
+// i.e. block substitution with the diagonal solve replaced by a product with
+// the inverse.  One persistent cooperative kernel per sweep runs three
+// grid-wide phases per super-block, separated by bounded grid barriers:
+//   F   the SBB (SBB + 1) / 2 tile products X_I[b][c] r_I[c] (c <= b; for the
+//       backward sweep X_I[c][b]^T r_I[c], c >= b) into partial tiles, and
+//       the fix-up of the previous panel update's split rows (below);
+//   A2  y_I[b] = the sum of row block b's partial tiles in a fixed order,
+//       written over r_I;
+//   B   the panel update: units (J, c) = the tile L_{J, I c} (backward
+//       L_{I c, J}^T) times y_I[c], J-major over every remaining 128-row block
+//       J, in equal contiguous ranges over all CTAs ("stream-K"), so the
+//       panel of L streams through every SM.  A CTA whose range covers a
+//       whole block row subtracts its sum from r_J; the pieces of a row shared
+//       by several CTAs go to partial slots (2g for CTA g's first piece, 2g+1
+//       for its last), which the next phase F adds in CTA order (= c order):
+//       folded into the staged rows of the next super-block's tile products,
+//       subtracted from r_J for every other row.
+// Every result is formed in an order fixed by the launch's grid, not by
+// timing.  The chain of the 128-block sweeps (one cross-SM hand-over per 128
+// rows) becomes three barriers per S rows.  The product of a 128x128 tile
+// with a 128 x MC block uses the register tiles of k_trsv32.cuh.
+#pragma once
+#include "k_trsv32.cuh"
+
+struct SbArgs {
+    const float* W;       // factor rows (row-major, lower), ldw
+    long ldw;
+    int n, NB;            // order and number of 128-blocks
+    const float* X;       // super-block inverses: NS blocks of S x S floats, row-major
+    int S, SBB, NS;       // super-block order (= 128 SBB), 128-blocks per super-block, super-blocks
+    float* Y;             // n x m, column-major (ld n), in place
+    int c0, mc;           // columns [c0, c0 + mc) in this pass
+    float* P;             // partial tiles of phase F: SBB (SBB + 1) / 2 x 128 x MC floats
+    float* P2;            // partial slots of phase B: 2 gridDim.x x 128 x MC floats
+    int* bar;             // [0] barrier arrivals, [1] abort (both zero at launch)
+    unsigned long long wait_ns;
+    DevStatus* st;
+    const int* gate;      // (may be NULL) return at once when *gate == 0
+};
+
+// Grid-wide barrier: the k-th barrier of a launch waits for k * gridDim.x
+// arrivals (bounded; a CTA that gives up raises SPD_DEV_TIMEOUT and the abort
+// flag, which releases the others).  Every write before it is visible after.
+__device__ __forceinline__ bool sb_barrier(const SbArgs& a, int k, int* s_abort) {
+    __syncthreads();
+    if (threadIdx.x == 0 && !*s_abort) {
+        __threadfence();
+        atomicAdd(a.bar, 1);
+        const int target = k * (int)gridDim.x;
+        if (ld_acquire(a.bar) < target) {
+            const uint64_t t0 = tv_globaltimer();
+            while (ld_acquire(a.bar) < target) {
+                if (ld_acquire(a.bar + 1)) {
+                    *s_abort = 1;
+                    break;
+                }
+                if (tv_globaltimer() - t0 > a.wait_ns) {
+                    *s_abort = 1;
+                    atomicOr(&a.st->flags, SPD_DEV_TIMEOUT);
+                    atomicExch(a.bar + 1, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return !*s_abort;
+}
+
+// Geometry of one panel update (phase B): units u = (J - J0) nb + c for
+// J0 <= J < J0 + rows, c < nb; CTA g < geff takes [g W / geff, (g+1) W / geff).
+struct SbPanel {
+    int J0, nb, geff;
+    long W;
+};
+__device__ __forceinline__ long sb_ub(int g, long W, int G) { return (long)g * W / G; }
+
+// The partial slots of block row J of panel pn in CTA order (= c order):
+// returns their count (0: one CTA covered the row, nothing pending); slots
+// are slot_lo, 2 (glo + 1), ..., 2 ghi.
+__device__ __forceinline__ int sb_row_slots(const SbPanel& pn, int J, int& slot_lo, int& glo) {
+    const long ut0 = (long)(J - pn.J0) * pn.nb, ut1 = ut0 + pn.nb;
+    glo = (int)(((ut0 + 1) * pn.geff - 1) / pn.W);  // owner of the row's first unit
+    const int ghi = (int)((ut1 * pn.geff - 1) / pn.W);
+    if (glo == ghi) return 0;
+    slot_lo = 2 * glo + (sb_ub(glo, pn.W, pn.geff) < ut0 ? 1 : 0);
+    return ghi - glo + 1;
+}
+
+// Element (l, cc) of block row J's pending sum: the row's partial slots
+// added in CTA order.
+template <int MC>
+__device__ __forceinline__ float sb_pending(const SbArgs& a, int ns, int slot_lo, int glo, int l, int cc) {
+    float s = 0.f;
+    for (int k = 0; k < ns; ++k) {
+        const int slot = k == 0 ? slot_lo : 2 * (glo + k);
+        s += __ldcg(a.P2 + ((long)slot * 128 + l) * MC + cc);
+    }
+    return s;
+}
+
+// Yk[l][c] = Y[r0 + l, c0 + c] (zero past n or past mc), minus the block
+// row's pending partial sum when ns > 0
+template <int MC>
+__device__ __forceinline__ void sb_stage(float* Yk, const SbArgs& a, long r0, int ns = 0, int slot_lo = 0,
+                                         int glo = 0) {
+    constexpr int PER = (128 * MC + 255) / 256;
+    float v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+        const long r = r0 + l;
+        v[u] = (e < 128 * MC && c < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + c) * a.n + r) : 0.f;
+    }
+    if (ns > 0) {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+            if (e < 128 * MC && c < a.mc && r0 + l < a.n) v[u] -= sb_pending<MC>(a, ns, slot_lo, glo, l, c);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+        const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+        if (e < 128 * MC) Yk[l * tv_ys<MC>() + c] = v[u];
+    }
+}
+
+template <int MC>
+constexpr size_t trsv_sb_smem() {
+    return (size_t)(128 * tv_ys<MC>()) * sizeof(float);
+}
+
+// tile index of the pair (p, q), q <= p, in the order (0,0), (1,0), (1,1), ...
+__device__ __forceinline__ int sb_tri(int p, int q) { return p * (p + 1) / 2 + q; }
+
+template <int MC, bool FWD>
+__global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* Yk = reinterpret_cast<float*>(smem_raw);  // [128][tv_ys] one staged 128 x MC block
+    __shared__ int s_abort;
+    if (a.gate && *a.gate == 0) return;  // refinement over (capturable solves)
+    const int tid = threadIdx.x;
+    const int tq = tid >> 3, ts = tid & 7;
+    const int G = gridDim.x, g = blockIdx.x;
+    if (tid == 0) s_abort = 0;
+    __syncthreads();
+    int nbar = 0;
+    float ra[64], rb[64];
+    SbPanel prev{0, 1, 1, 0};  // the previous step's panel update (W = 0: none)
+    for (int t = 0; t < a.NS; ++t) {
+        const int I = FWD ? t : a.NS - 1 - t;
+        const int jb0 = I * a.SBB;                    // first 128-block of the super-block
+        const int nb = min(a.SBB, a.NB - jb0);        // its 128-blocks
+        const float* XI = a.X + (long)I * a.S * a.S;  // its inverse, S x S row-major
+        // F: partial tiles, and the previous panel's split rows outside this
+        // super-block (forward: below it; backward: above it)
+        const int ntile = nb * (nb + 1) / 2;
+        const int nfix = prev.W == 0 ? 0 : (FWD ? a.NB - (jb0 + nb) : jb0);
+        for (int task = g; task < ntile + nfix; task += G) {
+            if (task >= ntile) {
+                const int J = FWD ? jb0 + nb + (task - ntile) : task - ntile;
+                int slot_lo, glo;
+                const int ns = sb_row_slots(prev, J, slot_lo, glo);
+                if (ns == 0) continue;  // block-uniform
+                for (int e = tid; e < 128 * MC; e += 256) {
+                    const int l = e / MC, cc = e - l * MC;
+                    const long row = (long)J * 128 + l;
+                    if (cc < a.mc && row < a.n) {
+                        float* y = a.Y + (long)(a.c0 + cc) * a.n + row;
+                        *y = __ldcg(y) - sb_pending<MC>(a, ns, slot_lo, glo, l, cc);
+                    }
+                }
+                continue;
+            }
+            int p = 0;
+            while (sb_tri(p + 1, 0) <= task) ++p;
+            const int q = task - sb_tri(p, 0);  // q <= p
+            // forward: X[b][c] with b = p, c = q; backward: X[c][b]^T with b = q, c = p
+            const int b = FWD ? p : q, c = FWD ? q : p;
+            tv_tile<FWD>(ra, XI, a.S, a.S, b, c, tq, ts);
+            int slot_lo = 0, glo = 0;
+            const int ns = prev.W == 0 ? 0 : sb_row_slots(prev, jb0 + c, slot_lo, glo);
+            sb_stage<MC>(Yk, a, (long)(jb0 + c) * 128, ns, slot_lo, glo);
+            __syncthreads();
+            float acc[4][MC];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int cc = 0; cc < MC; ++cc) acc[j][cc] = 0.f;
+            tv_dot<MC>(acc, ra, Yk, ts);
+            tv_reduce8<MC>(acc);
+            if (ts == 0) {
+                float* pt = a.P + (long)task * 128 * MC;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int cc = 0; cc < MC; ++cc) pt[(4 * tq + j) * MC + cc] = acc[j][cc];
+            }
+            __syncthreads();
+        }
+        if (!sb_barrier(a, ++nbar, &s_abort)) return;
+        // A2: y_I[b] = its partials in order (forward c = 0..b, backward c = b..nb-1)
+        for (int b = g; b < nb; b += G) {
+            for (int e = tid; e < 128 * MC; e += 256) {
+                const int r = e / MC, cc = e - r * MC;
+                float s = 0.f;
+                if (FWD) {
+                    for (int c = 0; c <= b; ++c) s += __ldcg(a.P + ((long)sb_tri(b, c) * 128 + r) * MC + cc);
+                } else {
+                    for (int c = b; c < nb; ++c) s += __ldcg(a.P + ((long)sb_tri(c, b) * 128 + r) * MC + cc);
+                }
+                const long row = (long)(jb0 + b) * 128 + r;
+                if (cc < a.mc && row < a.n) a.Y[(long)(a.c0 + cc) * a.n + row] = s;
+            }
+        }
+        if (t + 1 == a.NS) break;  // no rows left to update
+        if (!sb_barrier(a, ++nbar, &s_abort)) return;
+        // B: units (J, c) of every remaining 128-row block J (forward: below
+        // the super-block, backward: above it), in equal ranges over the CTAs
+        SbPanel pn;
+        pn.J0 = FWD ? jb0 + nb : 0;
+        pn.nb = nb;
+        pn.W = (long)((FWD ? a.NB : jb0) - pn.J0) * nb;
+        pn.geff = (int)min((long)G, pn.W);
+        if (g < pn.geff) {
+            const long u0 = sb_ub(g, pn.W, pn.geff), u1 = sb_ub(g + 1, pn.W, pn.geff);
+            for (long u = u0; u < u1;) {
+                const int J = pn.J0 + (int)(u / nb), ca = (int)(u % nb);
+                const int ce = (int)min((long)nb, ca + (u1 - u));
+                float acc[4][MC];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int cc = 0; cc < MC; ++cc) acc[j][cc] = 0.f;
+                // tiles L_{J, jb0 + c} (forward) or L_{jb0 + c, J}^T (backward),
+                // two per trip so that the register buffers alternate
+                tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, jb0 + ca, tq, ts);
+                for (int c = ca; c < ce; c += 2) {
+                    sb_stage<MC>(Yk, a, (long)(jb0 + c) * 128);
+                    __syncthreads();
+                    if (c + 1 < ce) tv_tile<FWD>(rb, a.W, a.ldw, a.n, J, jb0 + c + 1, tq, ts);
+                    tv_dot<MC>(acc, ra, Yk, ts);
+                    __syncthreads();
+                    if (c + 1 >= ce) break;
+                    sb_stage<MC>(Yk, a, (long)(jb0 + c + 1) * 128);
+                    __syncthreads();
+                    if (c + 2 < ce) tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, jb0 + c + 2, tq, ts);
+                    tv_dot<MC>(acc, rb, Yk, ts);
+                    __syncthreads();
+                }
+                tv_reduce8<MC>(acc);
+                if (ts == 0) {
+                    if (ca == 0 && ce == nb) {  // the whole row: subtract in place
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const long row = (long)J * 128 + 4 * tq + j;
+#pragma unroll
+                            for (int cc = 0; cc < MC; ++cc)
+                                if (cc < a.mc && row < a.n) {
+                                    float* y = a.Y + (long)(a.c0 + cc) * a.n + row;
+                                    *y = __ldcg(y) - acc[j][cc];
+                                }
+                        }
+                    } else {  // a piece of a shared row: partial slot
+                        float* pt = a.P2 + (long)(2 * g + (u == u0 ? 0 : 1)) * 128 * MC;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int cc = 0; cc < MC; ++cc) pt[(4 * tq + j) * MC + cc] = acc[j][cc];
+                    }
+                }
+                u += ce - ca;
+            }
+        }
+        prev = pn;
+        if (!sb_barrier(a, ++nbar, &s_abort)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// the super-block inverses, once per factor
+// ---------------------------------------------------------------------------
+// CTA (c, I) forms block column c of X_I = L_II^{-1} by block forward
+// substitution: X_cc = L_cc^{-1} (the transpose of LinvT's block), then for
+// b = c+1 .. nb-1, X_bc = -L_bb^{-1} (sum_{k=c}^{b-1} L_bk X_kc).  Rows of L
+// past n are zero and LinvT's rows past n are the identity; those rows of X
+// meet only right-hand-side rows past n, which the sweeps hold at zero.
+// Products are 128x128x128 in float32 through shared memory, thread (ty, tx)
+// = (tid / 16, tid % 16) owning an 8 x 8 block of the result.
+constexpr size_t sb_inverse_smem() { return (size_t)(128 * 33 + 32 * 132 + 128 * 132) * sizeof(float); }
+
+static __global__ void __launch_bounds__(256) k_sb_inverse(const float* __restrict__ W, long ldw, int n, int NB,
+                                                           const float* __restrict__ LinvT, int SBB,
+                                                           float* __restrict__ X) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* As = reinterpret_cast<float*>(smem_raw);  // [128][33] a 128 x 32 slice of the left factor
+    float* Bs = As + 128 * 33;                       // [32][132] a 32 x 128 slice of the right factor
+    float* Ts = Bs + 32 * 132;                       // [128][132] T = sum_k L_bk X_kc
+    const int c = blockIdx.x, I = blockIdx.y, tid = threadIdx.x;
+    const int S = SBB * 128;
+    const int jb0 = I * SBB, nb = min(SBB, NB - jb0);
+    if (c >= nb) return;
+    float* XI = X + (long)I * S * S;
+    const int ty = tid >> 4, tx = tid & 15;
+    // X_cc = (LinvT block)^T
+    {
+        const float* lt = LinvT + (long)(jb0 + c) * 16384;
+        for (int e = tid; e < 16384; e += 256) {
+            const int r = e >> 7, col = e & 127;
+            XI[(long)(c * 128 + r) * S + c * 128 + col] = lt[col * 128 + r];
+        }
+    }
+    __syncthreads();
+    float acc[8][8];
+    for (int b = c + 1; b < nb; ++b) {
+        // T = sum_{k=c}^{b-1} L_bk X_kc
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int k = c; k < b; ++k) {
+            for (int kk = 0; kk < 128; kk += 32) {
+                for (int e = tid; e < 128 * 32; e += 256) {  // As[r][q] = L[row r of block b][col kk+q of block k]
+                    const int r = e >> 5, q = e & 31;
+                    const long gr = (long)(jb0 + b) * 128 + r;
+                    As[r * 33 + q] = gr < n ? W[gr * ldw + (long)(jb0 + k) * 128 + kk + q] : 0.f;
+                }
+                for (int e = tid; e < 32 * 128; e += 256) {  // Bs[q][col] = X_kc[kk + q][col]
+                    const int q = e >> 7, col = e & 127;
+                    Bs[q * 132 + col] = __ldcg(XI + (long)(k * 128 + kk + q) * S + c * 128 + col);
+                }
+                __syncthreads();
+#pragma unroll 4
+                for (int q = 0; q < 32; ++q) {
+                    float av[8], bv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) av[i] = As[(ty * 8 + i) * 33 + q];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) bv[j] = Bs[q * 132 + tx * 8 + j];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                }
+                __syncthreads();
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) Ts[(ty * 8 + i) * 132 + tx * 8 + j] = acc[i][j];
+        __syncthreads();
+        // X_bc = -L_bb^{-1} T, L_bb^{-1}[r][q] = LinvT_b[q][r]
+        const float* lt = LinvT + (long)(jb0 + b) * 16384;
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int kk = 0; kk < 128; kk += 32) {
+            for (int e = tid; e < 128 * 32; e += 256) {  // As[r][q] = L_bb^{-1}[r][kk + q]
+                const int r = e >> 5, q = e & 31;
+                As[r * 33 + q] = lt[(kk + q) * 128 + r];
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int q = 0; q < 32; ++q) {
+                float av[8], bv[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) av[i] = As[(ty * 8 + i) * 33 + q];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) bv[j] = Ts[(kk + q) * 132 + tx * 8 + j];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                XI[(long)(b * 128 + ty * 8 + i) * S + c * 128 + tx * 8 + j] = -acc[i][j];
+        __syncthreads();  // X_bc is read (through L2) by the next b
+    }
+}

@@ -20,6 +20,7 @@
 #include "k_leaf.cuh"
 #include "k_leaf32.cuh"
 #include "k_gemm_simt.cuh"
+#include "k_trsv_sb.cuh"
 #include "gemm_tc.h"
 
 namespace {
@@ -256,7 +257,7 @@ void free_factor(spd_factor_t* F) {
     // other handles' streams keep running
     cudaStream_t s = F->h ? F->h->stream : nullptr;
     for (void* p : {(void*)F->W, (void*)F->W64, F->Wh, (void*)F->d, (void*)F->LinvT, (void*)F->Cpl, (void*)F->Dinv32,
-                    (void*)F->Dinv64})
+                    (void*)F->Dinv64, (void*)F->Xsb})
         if (p) cudaFreeAsync(p, s);
     delete F;
 }
@@ -295,7 +296,11 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         size_t req = sizeof(double) * std::max(n, 1);
         if (prec == SPD_PREC_FP64) req += sizeof(double) * (std::max<size_t>(nW, 1) + 4096 * nb);
         else req += sizeof(float) * (std::max<size_t>(nW, 1) + (1 + 4 + 0.25) * 16384 * nb) +
-                    (kind ? mirror_elem(kind) * std::max<size_t>(nW, 1) : 0);
+                    (kind ? mirror_elem(kind) * std::max<size_t>(nW, 1) : 0) +
+                    (nb >= 2 * SPD_SB_BLOCKS && (flags & SPD_FACTOR_SB_SWEEPS)
+                         ? sizeof(float) * (size_t)ceil_div((long)nb, SPD_SB_BLOCKS) * SPD_SB_BLOCKS * 128 *
+                               SPD_SB_BLOCKS * 128
+                         : 0);
         if (over_cap(h, req))
             return fail(set_err(h, SPD_ERR_OOM, "factor of order %d needs %zu bytes, above the handle's memory cap "
                                 "of %zu bytes", n, req, h->mem_cap));
@@ -379,6 +384,29 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
             if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "block inverse launch failed");
         }
         if (st == SPD_OK && prec != SPD_PREC_FP64) st = factor_couplings(h, F);
+        if (st == SPD_OK && prec != SPD_PREC_FP64 && (flags & SPD_FACTOR_SB_SWEEPS) &&
+            F->nblk128 >= 2 * SPD_SB_BLOCKS) {
+            // inverses of the diagonal super-blocks for the super-block sweeps
+            F->sbb = SPD_SB_BLOCKS;
+            F->nsb = ceil_div(F->nblk128, F->sbb);
+            const size_t S = (size_t)F->sbb * 128;
+            if (cudaMallocAsync(&F->Xsb, sizeof(float) * S * S * F->nsb, s) != cudaSuccess) {
+                cudaGetLastError();
+                F->Xsb = nullptr;  // the 128-block sweeps serve instead
+                F->sbb = F->nsb = 0;
+            } else {
+                static const bool attr = [] {
+                    cudaFuncSetAttribute(k_sb_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sb_inverse_smem());
+                    return true;
+                }();
+                (void)attr;
+                ProfScope pinv(h, SPD_PHASE_LEAF, (double)F->nsb * S * S * S / 3.0, 4.0 * F->nsb * S * S);
+                ++h->launches, k_sb_inverse<<<dim3(F->sbb, F->nsb), 256, sb_inverse_smem(), s>>>(
+                    F->W, F->ldw, n, F->nblk128, F->LinvT, F->sbb, F->Xsb);
+                if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "super-block inverse launch failed");
+            }
+        }
         if (st == SPD_OK) st = check_dev_status(h, rep, "spd_factor");
         if (tc) tc_gemm_destroy(tc);
         if (st != SPD_OK) return fail(st);

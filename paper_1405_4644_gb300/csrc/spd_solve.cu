@@ -7,9 +7,11 @@
 #include "k_convert.cuh"
 #include "k_solve.cuh"
 #include "k_trsv32.cuh"
+#include "k_trsv_sb.cuh"
 #include "k_resid.cuh"
 #include "k_cg.cuh"
 #include "resid_tc.h"
+#include "gemm_tc.h"
 
 // ---------------------------------------------------------------------------
 // handle
@@ -25,6 +27,7 @@ extern "C" void spd_opts_default(spd_opts* o) {
     o->fallback = 1;
     o->resid = SPD_RESID_FP64;
     o->polish = 1;
+    o->matvec_cores = SPD_MV_AUTO;
 }
 
 extern "C" spd_status spd_create(spd_handle** out, void* stream) {
@@ -79,6 +82,7 @@ extern "C" spd_status spd_destroy(spd_handle* h) {
     cudaFree(h->ready);
     cudaFree(h->stage);
     cudaFree(h->async_epoch_dev);
+    cudaFree(h->sb_buf);
     if (h->aux) cudaStreamDestroy(h->aux);
     for (auto e : h->sync_ev) cudaEventDestroy(e);
     for (auto& r : h->prof) {
@@ -451,10 +455,68 @@ spd_status factor_couplings(spd_handle* h, spd_factor_t* F) {
 
 namespace {
 
+// One forward and one backward super-block sweep of columns [c0, c0 + mc)
+// (k_trsv_sb.cuh): the barrier words are cleared before each launch (a
+// stream-ordered memset, so that a captured graph clears them on replay).
+// The scratch (partial tiles, partial slots, barrier words) is sized once
+// per handle; the first call on a handle must not be captured.
+template <int MC>
+spd_status trsv_sb_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, int c0, int mc) {
+    const size_t smem = trsv_sb_smem<MC>();
+    auto fwd = k_trsv_sb<MC, true>;
+    auto bwd = k_trsv_sb<MC, false>;
+    static const int per_sm = [&] {  // once per instantiation, thread-safe
+        cudaFuncSetAttribute(fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int a = 0, b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, fwd, 256, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bwd, 256, smem);
+        return std::max(1, std::min(a, b));
+    }();
+    const size_t ntile = (size_t)F->sbb * (F->sbb + 1) / 2;
+    // every SM streams the panel updates: one CTA per resident slot
+    const int G = std::min(per_sm * h->sms, TV_SLOTS);
+    const size_t pbytes = (size_t)round_up((long)(sizeof(float) * ntile * 128 * 16), 256);
+    const size_t p2bytes = (size_t)round_up((long)(sizeof(float) * 2 * (size_t)G * 128 * 16), 256);
+    if (h->sb_bytes < pbytes + p2bytes + 256) {
+        if (h->sb_buf) {
+            CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+            CUDA_TRY(h, cudaFree(h->sb_buf));
+        }
+        h->sb_buf = nullptr;
+        h->sb_bytes = 0;
+        CUDA_TRY(h, cudaMalloc(&h->sb_buf, pbytes + p2bytes + 256));
+        h->sb_bytes = pbytes + p2bytes + 256;
+    }
+    float* P = static_cast<float*>(h->sb_buf);
+    float* P2 = reinterpret_cast<float*>(static_cast<char*>(h->sb_buf) + pbytes);
+    int* bar = reinterpret_cast<int*>(static_cast<char*>(h->sb_buf) + pbytes + p2bytes);
+    for (int dir = 0; dir < 2; ++dir) {
+        SbArgs a{F->W, F->ldw, n, F->nblk128, F->Xsb, F->sbb * 128, F->sbb, F->nsb, Y, c0, mc, P, P2, bar,
+                 h->wait_ns, h->dst, h->async_on ? h->async_gate : nullptr};
+        void* args[] = {&a};
+        CUDA_TRY(h, cudaMemsetAsync(bar, 0, 2 * sizeof(int), h->stream));
+        ++h->launches;
+        CUDA_TRY(h, coop_launch(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(G), dim3(256), args, smem,
+                                h->stream));
+    }
+    return SPD_OK;
+}
+
 // Y <- (L L^T)^{-1} Y for a float32 factor (n x m, ld n).
 spd_status lp_sweeps32(spd_handle* h, const spd_factor_t* F, int n, int m, float* Y) {
     ProfScope ps(h, SPD_PHASE_SOLVE, 2.0 * n * (double)n * m, 4.0 * n * (double)n);
-    for (int c0 = 0; c0 < m; c0 += 16) {
+    for (int c0 = 0; c0 < m && F->Xsb; c0 += 16) {  // super-block sweeps
+        const int mc = std::min(16, m - c0);
+        spd_status st;
+        if (mc == 1) st = trsv_sb_pass<1>(h, F, Y, n, c0, mc);
+        else if (mc <= 2) st = trsv_sb_pass<2>(h, F, Y, n, c0, mc);
+        else if (mc <= 4) st = trsv_sb_pass<4>(h, F, Y, n, c0, mc);
+        else if (mc <= 8) st = trsv_sb_pass<8>(h, F, Y, n, c0, mc);
+        else st = trsv_sb_pass<16>(h, F, Y, n, c0, mc);
+        if (st != SPD_OK) return st;
+    }
+    for (int c0 = 0; c0 < m && !F->Xsb; c0 += 16) {
         const int mc = std::min(16, m - c0);
         spd_status st;
         if (mc == 1) st = trsv32_pass<1>(h, F, Y, n, c0, mc);
@@ -590,7 +652,7 @@ extern "C" spd_status spd_factor_solve(spd_handle* h, const spd_factor_t* F, int
 // ---------------------------------------------------------------------------
 namespace {
 
-enum MatvecKind { MV_FP64 = 0, MV_FP32 = 1, MV_BF16 = 2, MV_BAND = 3 };
+enum MatvecKind { MV_FP64 = 0, MV_FP32 = 1, MV_BF16 = 2, MV_BAND = 3, MV_TC = 4 };
 
 struct CgSetup {
     int matvec = MV_FP64;
@@ -601,7 +663,29 @@ struct CgSetup {
     const spd_factor_t* F = nullptr;
     const spd_lowrank* LR = nullptr;
     const double* dinv = nullptr;
+    // MV_TC: A~ and P^T as bf16 slice planes, the narrow GEMM's C and its
+    // stream-K partial slots
+    TcGemm* tg = nullptr;
+    __nv_bfloat16* Pm = nullptr;
+    float* Cf = nullptr;
+    long ldo = 0, ldc = 0, plane_p = 0;
+    int Kp = 0;
+    TcSplit sk{nullptr, 0};
 };
+
+// Q = A~ P on the tensor cores (float32 operands as three bf16 slices each)
+spd_status mv_tc(spd_handle* h, const CgSetup& cs, int n, int m, const float* Pf, double* Q) {
+    ProfScope ps(h, SPD_PHASE_MATVEC, 2.0 * n * (double)n * m, 6.0 * n * (double)cs.Kp);
+    cudaStream_t s = h->stream;
+    const int gv = grid_for((long)n * m, 256, 8 * h->sms);
+    ++h->launches, k_p_x3<<<gv, 256, 0, s>>>(Pf, n, m, cs.Pm, cs.ldo, cs.plane_p);
+    CUDA_TRY(h, cudaMemsetAsync(cs.Cf, 0, sizeof(float) * n * cs.ldc, s));
+    ++h->launches;
+    const spd_status st = tc_gemm_launch(cs.tg, s, 0, 0, n, m, cs.Kp, 0, 0, 0, 0, h->dst, -h->sms, &cs.sk);
+    if (st != SPD_OK) return set_err(h, st, "spd_cg: tensor-core product launch failed");
+    ++h->launches, k_cf_to_q<<<gv, 256, 0, s>>>(cs.Cf, cs.ldc, n, m, Q);
+    return SPD_OK;
+}
 
 template <typename T, int MC>
 void mv_launch(spd_handle* h, const CgSetup& cs, int n, int m, const float* Pf, double* Q) {
@@ -635,7 +719,9 @@ struct CgWs {
 
 size_t cg_plan(WsPlan& p, spd_handle* h, int n, int m, size_t* o, int* S, int* G2) {
     *S = (int)resid_plan(p, h, n, m, o);
-    *G2 = std::max(1, std::min(2 * h->sms, ceil_div(n, 256)));
+    // row chunks per column of the dot products: about 2 blocks per SM over
+    // all m columns, at least 256 rows each
+    *G2 = std::max(1, std::min(2 * h->sms, ceil_div(n, 256)) / std::max(m, 1));
     size_t nm = (size_t)n * m;
     o[4] = p.add<double>(nm);       // R
     o[5] = p.add<double>(3 * m);    // colnorms
@@ -747,13 +833,17 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             if (st != SPD_OK) return st;
             ++(h)->launches, k_copy_p<<<gv, 256, 0, s>>>(n, m, w.Z, w.P, w.Pf);
         }
-        ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
+        ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
         ++(h)->launches, k_cg_init_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.part, w.G2, m, w.cg, w.frozen, o.eta, w.target);
         LAUNCH_CHECK(h);
         for (int t = 0; t < o.maxit_inner; ++t) {
             const int par = t & 1;
             switch (cs.matvec) {
                 case MV_FP32: mv_dispatch<float>(h, cs, n, m, w.Pf, w.Q); break;
+                case MV_TC:
+                    st = mv_tc(h, cs, n, m, w.Pf, w.Q);
+                    if (st != SPD_OK) return st;
+                    break;
                 case MV_BF16: mv_dispatch<__nv_bfloat16>(h, cs, n, m, w.Pf, w.Q); break;
                 case MV_BAND: {  // (2b + 1) n float32 entries of the band per product
                     ProfScope ps(h, SPD_PHASE_MATVEC, 2.0 * (2.0 * cs.band + 1.0) * n * m,
@@ -767,7 +857,7 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                     if (st != SPD_OK) return st;
             }
             LAUNCH_CHECK(h);
-            ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.P, w.Q, nullptr, nullptr, n, m, w.part);
+            ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.P, w.Q, nullptr, nullptr, n, m, w.part);
             ++(h)->launches, k_cg_update<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.E, w.Rr, w.P, w.Q,
                                            cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, w.Z);
             LAUNCH_CHECK(h);
@@ -776,7 +866,7 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                          : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
                 if (st != SPD_OK) return st;
             }
-            ++(h)->launches, k_dot2<<<w.G2, 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
+            ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
             ++(h)->launches, k_cg_pupdate<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.active, w.P, w.Pf, Zr);
             LAUNCH_CHECK(h);
             if ((t + 1) % 8 == 0 || t + 1 == o.maxit_inner) {
@@ -1048,12 +1138,28 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     cs.pc = pc;
     if (pc == SPD_PC_FACTOR) cs.F = static_cast<const spd_factor_t*>(pc_data);
     if (pc == SPD_PC_LOWRANK) cs.LR = static_cast<const spd_lowrank*>(pc_data);
-    size_t o_at = 0, o_dinv = 0;
+    size_t o_at = 0, o_dinv = 0, o_pm = 0, o_cf = 0, o_sk = 0;
     long ldt = round_up(n, 64);
+    // float32 products with several right-hand sides go to the tensor cores
+    const bool tc_mv = o.band < 0 && matvec_prec == SPD_PREC_FP32 &&
+                       (o.matvec_cores == SPD_MV_TENSOR || (o.matvec_cores == SPD_MV_AUTO && m >= 8));
+    const int bnt = m <= 32 ? 32 : 64;
     if (o.band >= 0) {
         cs.matvec = MV_BAND;
         cs.band = o.band;
         o_at = p.add<float>((size_t)(2 * o.band + 1) * n);
+    } else if (tc_mv) {
+        cs.matvec = MV_TC;
+        cs.Kp = (int)round_up(n, 128);
+        cs.ldo = cs.Kp;
+        const long prow = round_up(m, bnt);
+        cs.plane_p = prow * cs.ldo;
+        cs.ldc = round_up(m, 32);
+        o_at = p.add<__nv_bfloat16>((size_t)3 * n * cs.ldo);
+        o_pm = p.add<__nv_bfloat16>((size_t)3 * cs.plane_p);
+        o_cf = p.add<float>((size_t)n * cs.ldc);
+        cs.sk.part_cap = (size_t)2 * std::max(h->sms, 1) * 128 * bnt;
+        o_sk = p.add<float>(cs.sk.part_cap);
     } else if (matvec_prec == SPD_PREC_FP32) {
         cs.matvec = MV_FP32;
         o_at = p.add<float>((size_t)n * ldt);
@@ -1071,7 +1177,24 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     st = tc_bind_prepare(h, tcs, n, m, A, lda, w.rw);
     if (st != SPD_OK) return st;
     const int gbig = grid_for((long)n * n, 256, 16 * h->sms);
-    if (cs.matvec == MV_BAND) {
+    struct TgGuard {  // the narrow GEMM's maps live for this call
+        TcGemm*& g;
+        ~TgGuard() {
+            if (g) tc_gemm_destroy(g);
+        }
+    } tg_guard{cs.tg};
+    if (cs.matvec == MV_TC) {
+        __nv_bfloat16* Am = ws_at<__nv_bfloat16>(h, o_at);
+        cs.Pm = ws_at<__nv_bfloat16>(h, o_pm);
+        cs.Cf = ws_at<float>(h, o_cf);
+        cs.sk.part = ws_at<float>(h, o_sk);
+        ++(h)->launches, k_convert_x3<<<gbig, 256, 0, s>>>(A, lda, n, cs.Kp, Am, cs.ldo, (long)n * cs.ldo, h->dst);
+        CUDA_TRY(h, cudaMemsetAsync(cs.Pm, 0, sizeof(__nv_bfloat16) * 3 * cs.plane_p, s));
+        st = tc_gemm_create_narrow(&cs.tg, Am, n, cs.ldo, cs.Pm, cs.plane_p / cs.ldo, cs.ldo, cs.Kp, cs.Cf, n,
+                                   cs.ldc, cs.ldc, bnt);
+        if (st != SPD_OK) return set_err(h, st, "spd_cg: tensor maps of the product failed");
+        cs.At = Am;
+    } else if (cs.matvec == MV_BAND) {
         float* Ab = ws_at<float>(h, o_at);
         ++(h)->launches, k_convert_band<<<grid_for((long)(2 * o.band + 1) * n, 256, 16 * h->sms), 256, 0, s>>>(A, lda, n, o.band, Ab,
                                                                                             h->dst);
