@@ -139,6 +139,18 @@ class Nvml:
         return cpus or None
 
 
+def host_numa_info():
+    """The memory nodes this process may allocate from (for the record of the
+    end-to-end host copies)."""
+    try:
+        for line in open("/proc/self/status"):
+            if line.startswith("Mems_allowed_list"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
 def bind_near_gpu(nvml):
     """Run this process (and the threads it starts later) on the CPUs next
     to the GPU, so that pinned host buffers, first touched here, sit in the
@@ -695,9 +707,14 @@ def table1_leg(args):
     matrix of Section 4 (A(i,j) = 1/|i-j|^d off the diagonal, 1 + sqrt(i) on
     it, i 1-based), n = args.n_cg (70000 in the paper), d in {1, 2, 4};
     right-hand sides U[0,1] (seed 0), stop at ||r||_2 < 1e-5 as printed.
-    Rows: Cholesky-IR with 32 right-hand sides (float32 factor, float64
-    residual), CG with 1 and 32 (float32 products, float64 outer residual),
-    and CG whose inner products use the banded matrix (bandwidth 33).  Per
+    Rows: Cholesky-IR with 32 right-hand sides (float32 factor, float64-
+    accurate residual), CG with 1 and 32 (float32 products, float64-accurate
+    outer residual), and CG whose inner products use the banded matrix
+    (bandwidth 33).  The residual arithmetic is --resid when given, else
+    the library's automatic choice: float64 fused multiply-adds for one
+    right-hand side, exact products of bf16 digits on the tensor cores for
+    32 (float64 fused multiply-adds are then bound by the FP64 rate).
+    Per
     row: low/high iterations, seconds (device time of the library calls,
     repeated to fill at least one second), average power and its standard
     error (NVML samples), energy, and the paper's GFlops convention (CG:
@@ -720,6 +737,9 @@ def table1_leg(args):
     torch.cuda.synchronize()
     idle_w = idle_power(nvml, 2.0)
     crit = {"tol": 1e-5, "crit": "abs2"}
+    # the leg's residual: the run's --resid when given, else float64 for one
+    # right-hand side and the tensor-core residual for 32
+    resid = args.resid if args.resid_given else "auto"
     rows = []
     for d in (1, 2, 4):
         for r0 in range(0, n, 4096):  # assembled in row blocks on the device (untimed, as in the paper)
@@ -737,11 +757,11 @@ def table1_leg(args):
                     if st != spd.SPD_OK:
                         raise RuntimeError(f"table1 factor d={d}: {spd.spd_last_error_string(h)}")
                     # the paper's rule: stop as soon as the tolerance holds (no polish sweep)
-                    st, r = spd.spd_solve_ir(h, F, A, B, X, dict(crit, resid="fp64", polish=0))
+                    st, r = spd.spd_solve_ir(h, F, A, B, X, dict(crit, resid=resid, polish=0))
                     spd.spd_factor_destroy(F)
                     ms = fr.time_ms + r.time_ms
                 else:
-                    opts = dict(crit, eta=0.0, maxit_inner=20000, matvec_cores=args.mv_cores,
+                    opts = dict(crit, eta=0.0, maxit_inner=20000, matvec_cores=args.mv_cores, resid=resid,
                                 **({"band": 16} if method == "banded_cg" else {}))
                     st, r = spd.spd_cg(h, A, B, X, "fp32", opts=opts)
                     ms = r.time_ms
@@ -905,8 +925,8 @@ def case_leg(args):
                 ok(st)
                 print(f"factor {prec} n={n}: {rep.time_ms:.3f} ms")
                 spd.spd_factor_destroy(F)
-        if args.case in ("sweeps", "sweeps_sb"):
-            flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_SB_SWEEPS if args.case == "sweeps_sb" else 0)
+        if args.case in ("sweeps", "sweeps_block"):
+            flags = spd.SPD_SCALE_DIAG | (spd.SPD_FACTOR_BLOCK_SWEEPS if args.case == "sweeps_block" else 0)
             st, F, _ = spd.spd_factor(h, A, "fp16", flags)
             ok(st)
             for _ in range(args.reps):
@@ -949,9 +969,10 @@ def main():
     ap.add_argument("--no-lapack", action="store_true", help="forward errors without LAPACK's host solve")
     ap.add_argument("--lanes", type=int, default=3,
                     help="systems solved concurrently (one handle, stream and host thread each)")
-    ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc"],
+    ap.add_argument("--resid", default="tc", choices=["fp64", "df32", "tc", "auto"],
                     help="refinement residual: float64; float32 pairs until berr < 2^-36 then float64; "
-                         "or exact bf16 digit products on the tensor cores")
+                         "exact bf16 digit products on the tensor cores; or auto (float64 for one right-hand "
+                         "side, tensor cores for more; the table1 leg's default)")
     ap.add_argument("--leg", default="main", choices=["main", "batched", "learned", "cg", "table1"])
     ap.add_argument("--n-cg", type=int, default=16384)
     ap.add_argument("--mv-cores", default="auto", choices=["auto", "cuda", "tensor"],
@@ -961,12 +982,13 @@ def main():
     ap.add_argument("--train-systems", type=int, default=1000)
     ap.add_argument("--test-systems", type=int, default=32)
     ap.add_argument("--case", default=None,
-                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "sweeps_sb", "convert", "factor",
+                    choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "sweeps_block", "convert", "factor",
                              "factor_serial"],
                     help="run one kernel family on a fixed case (for profilers) and exit")
     ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
     ap.add_argument("--phases", action="store_true", help="--case: print the library's phase records")
     args = ap.parse_args()
+    args.resid_given = any(a == "--resid" or a.startswith("--resid=") for a in sys.argv[1:])
     args.kappas = [float(k) for k in args.kappas.split(",")]
     precs = args.precs.split(",")
     if len(precs) == 1 and args.workload == "sweep":
@@ -1163,7 +1185,7 @@ def main():
         e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
                "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
-               "h2d_gbs_one_copy": h2d_gbs, "cpu_affinity": affinity}
+               "h2d_gbs_one_copy": h2d_gbs, "cpu_affinity": affinity, "mems_allowed": host_numa_info()}
 
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None

@@ -106,12 +106,16 @@ typedef enum spd_resid {
                            rule and its guarantee are those of SPD_RESID_FP64.
                            The float64 products of the CG fallback use
                            spd_residual_df32's arithmetic throughout.        */
-    SPD_RESID_TC = 2    /* every residual (and every float64 product of the
+    SPD_RESID_TC = 2,   /* every residual (and every float64 product of the
                            CG fallback) from spd_residual_tc: exact products
                            of bf16 digits on the tensor cores; columns may be
                            accepted on it.  The digit planes of A (20 bytes
                            per entry of A) are formed once per solve and stay
                            in the handle's workspace.                        */
+    SPD_RESID_AUTO = 3  /* SPD_RESID_FP64 for one right-hand side (8 bytes
+                           per entry of A, bound by HBM), SPD_RESID_TC for
+                           m >= 2 (float64 fused multiply-adds are then bound
+                           by the FP64 rate)                                  */
 } spd_resid;
 
 /* Flags of spd_factor. */
@@ -137,12 +141,13 @@ typedef enum spd_resid {
                                     preconditioned CG fallback (Section 3.1,
                                     eq. (iterref): the inner solver only has
                                     to contract).  report.shift gives sigma */
-#define SPD_FACTOR_SB_SWEEPS 32u /* float32 factors of at least 16 128-row
-                                    blocks: also form the inverses of the
-                                    diagonal super-blocks (8 blocks each) and
-                                    apply the factor with the super-block
-                                    sweeps instead of the default sweeps over
-                                    128-row blocks */
+#define SPD_FACTOR_BLOCK_SWEEPS 32u /* float32 factors: apply the factor
+                                    with the sweeps over 128-row blocks.  By
+                                    default a factor of at least 16 blocks
+                                    also holds the inverses of its diagonal
+                                    super-blocks (8 blocks each, formed once,
+                                    4 (1024)^2 bytes each) and is applied with
+                                    the super-block sweeps */
 #define SPD_FACTOR_SERIAL 8u     /* left-looking schedule without its
                                     look-ahead: every kernel on the handle's
                                     stream in order (kernels then run alone,

@@ -39,14 +39,14 @@ PREC = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "fp16": 4, "fp8": 5, "auto":
 PREC_NAME = {v: k for k, v in PREC.items()}
 CRIT = {"berr": 0, "rel2": 1, "abs2": 2}
 PC = {"none": 0, "jacobi": 1, "factor": 2, "lowrank": 3}
-RESID = {"fp64": 0, "df32": 1, "tc": 2}
+RESID = {"fp64": 0, "df32": 1, "tc": 2, "auto": 3}
 BATCH = {"chol_ir": 0, "pcg_jacobi": 1}
 SPD_SCALE_DIAG = 1
 SPD_FACTOR_CUDA_CORES = 2
 SPD_FACTOR_RECURSIVE = 4
 SPD_FACTOR_SERIAL = 8
 SPD_FACTOR_SHIFT = 16
-SPD_FACTOR_SB_SWEEPS = 32
+SPD_FACTOR_BLOCK_SWEEPS = 32
 MV_CORES = {"auto": 0, "cuda": 1, "tensor": 2}
 
 # every symbol include/spd.h declares

@@ -109,7 +109,8 @@ __device__ __forceinline__ void load_acc(uint32_t tacc, int ch, float* v) {
     }
 }
 
-// C -= scale * acc for one warp's 32 rows through shared memory (the idle
+// C -= scale * acc (get(ch, v) gives 32 columns of this thread's row of the
+// accumulator) for one warp's 32 rows through shared memory (the idle
 // stage buffers, once the CTA's main loop is over): the rows as 32 x 32 boxes
 // (4 KB each, 128-byte swizzle: 16-byte chunk q of box row r sits at chunk
 // q ^ (r & 7), so a thread's row is read without bank conflicts), loaded by
@@ -117,9 +118,9 @@ __device__ __forceinline__ void load_acc(uint32_t tacc, int ch, float* v) {
 // entries above the diagonal keep their value: the boxes may reach past the
 // update's block and every box entry is written back.  Returns false if the
 // loads did not land in time.
-template <int NACC, int BNT>
+template <int BNT, typename Get>
 __device__ __forceinline__ bool epilogue_tma(unsigned char* base, uint64_t* cbar, volatile int* abort_flag,
-                                             const CUtensorMap* mapC, uint32_t tacc, int cx0, int cy0, int M, int N,
+                                             const CUtensorMap* mapC, Get get, int cx0, int cy0, int M, int N,
                                              int bm, int bn, int qd, int lane, int lower, float scale) {
     float* slab = reinterpret_cast<float*>(base) + qd * 32 * BNT;
     const int row_w = bm * BM + qd * 32, row = row_w + lane;
@@ -141,10 +142,12 @@ __device__ __forceinline__ bool epilogue_tma(unsigned char* base, uint64_t* cbar
     bool landed = tc::mbar_wait(&cbar[qd], 0, abort_flag, WAIT_NS);
     if (!__all_sync(0xffffffffu, landed)) return false;
     const int lim = row < M ? (lower ? min(N - 1, row) : N - 1) : -1;  // last column to update
-    for (int ch = 0; ch < nbox; ++ch) {
+#pragma unroll
+    for (int ch = 0; ch < BNT / 32; ++ch) {
+        if (ch >= nbox) break;
         if (!(need >> ch & 1u)) continue;  // warp-uniform
         float v[32];
-        load_acc<NACC, BNT>(tacc, ch, v);
+        get(ch, v);
         float4* rp = reinterpret_cast<float4*>(slab + ch * 1024 + lane * 32);
         const int col0 = bn * BNT + ch * 32;
 #pragma unroll
@@ -203,7 +206,10 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
     constexpr int STAGES = ST;
     constexpr int STAGE_BYTES = stage_bytes<BNT, SL>();
     constexpr int A_ST = SL * A_STAGE, B_ST = SL * B_STAGE;  // a stage's A and B parts
-    constexpr int NBUF = NACC == 1 ? 2 : 1;
+    // accumulator buffers: two per tile with one accumulator (the epilogue of
+    // one piece overlaps the next); narrow tiles (SL = 3) promote every K
+    // tile's sums to float32 registers, alternating two buffers
+    constexpr int NBUF = (SL == 3 || NACC == 1) ? 2 : 1;
     constexpr uint32_t ACC_COLS = BNT * NACC;  // one tile's accumulator(s)
     constexpr uint32_t TMEM_COLS = ACC_COLS * NBUF;
     constexpr int MMA_PER_STAGE = BK / KindTraits<KIND>::KMMA;  // 32 bytes of K each
@@ -303,7 +309,7 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
             // first segment (in issue order) of each accumulator starts it from zero
             int first[2] = {-1, -1};
             for (int q = nseg - 1; q >= 0; --q) first[(accsel >> q) & 1] = q;
-            int kt = 0, p = 0;
+            int kt = 0, p = 0, pk = 0;
             SPD_FOR_PIECES {
                 const int buf = p % NBUF;
                 if (p >= NBUF) {  // the epilogue has drained this accumulator
@@ -314,7 +320,17 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
                     tc::fence_after_sync();
                 }
                 if constexpr (SL == 3) {
-                    for (int kin = kb; kin < ke; ++kin, ++kt) {
+                    // each K tile into a fresh accumulator pair (buffer pk & 1),
+                    // which the epilogue adds to its float32 registers
+                    for (int kin = kb; kin < ke; ++kin, ++kt, ++pk) {
+                        const int b2 = pk & 1;
+                        if (pk >= 2) {
+                            if (!tc::mbar_wait(&accempty[b2], ((pk >> 1) - 1) & 1, abort_flag, WAIT_NS)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::fence_after_sync();
+                        }
                         const int s = kt % STAGES;
                         const uint32_t ph = (kt / STAGES) & 1u;
                         if (!tc::mbar_wait(&full[s], ph, abort_flag, WAIT_NS)) {
@@ -327,17 +343,16 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
                             const int a = (accsel >> q) & 1;
                             const uint64_t ad = tc::sdesc_kmajor_sw128(tc::smem_u32(sA + s * A_ST + za * A_STAGE));
                             const uint64_t bd = tc::sdesc_kmajor_sw128(tc::smem_u32(sB + s * B_ST + zb * B_STAGE));
-                            const uint32_t d = tmem + (uint32_t)(buf * ACC_COLS + a * BNT);
-                            const bool fresh = kin == kb && q == first[a];
+                            const uint32_t d = tmem + (uint32_t)(b2 * ACC_COLS + a * BNT);
+                            const bool fresh = q == first[a];
 #pragma unroll
                             for (int k = 0; k < MMA_PER_STAGE; ++k)
                                 tc::mma<KIND>(d, ad + 2 * k, bd + 2 * k, idesc, (fresh && k == 0) ? 0u : 1u);
                         }
                         tc::mma_commit(&empty[s]);
+                        tc::mma_commit(&accfull[b2]);
                     }
                     if (!ok) break;
-                    tc::mma_commit(&accfull[buf]);
-                    ++p;
                     continue;
                 }
                 for (int kin = kb; kin < ke && ok; ++kin)
@@ -367,16 +382,58 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
         __syncwarp();
     } else {  // epilogue warps
         const int qd = warp & 3;  // TMEM lane quadrant = rows 32 qd .. 32 qd + 31 of the tile
-        int p = 0;
+        int p = 0, pk = 0;
+        // narrow tiles: the piece's sums, promoted K tile by K tile into
+        // float32 registers (round to nearest) -- the tensor cores' own
+        // float32 accumulation rounds toward zero, a bias that grows with K
+        constexpr int NR = SL == 3 ? BNT : 1;
+        float S0[NR], S1[NR];
         SPD_FOR_PIECES {
             const int buf = p % NBUF;
-            ok = tc::mbar_wait(&accfull[buf], (p / NBUF) & 1, abort_flag, WAIT_NS);
-            ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
-            if (!ok) break;
-            tc::fence_after_sync();
+            uint32_t tacc = 0;
+            if constexpr (SL == 3) {
+#pragma unroll
+                for (int j = 0; j < NR; ++j) S0[j] = S1[j] = 0.f;
+                for (int kin = kb; kin < ke; ++kin, ++pk) {
+                    const int b2 = pk & 1;
+                    ok = tc::mbar_wait(&accfull[b2], (pk >> 1) & 1, abort_flag, WAIT_NS);
+                    ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+                    if (!ok) break;
+                    tc::fence_after_sync();
+                    const uint32_t ta = tmem + (static_cast<uint32_t>(qd * 32) << 16) + (uint32_t)(b2 * ACC_COLS);
+#pragma unroll
+                    for (int ch = 0; ch < BNT / 32; ++ch) {
+                        float v[32];
+                        tc::tmem_ld_32x32b_x32(ta + ch * 32, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) S0[ch * 32 + j] += v[j];
+                        tc::tmem_ld_32x32b_x32(ta + BNT + ch * 32, v);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) S1[ch * 32 + j] += v[j];
+                    }
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&accempty[b2]);
+                }
+                if (!ok) break;
+            } else {
+                ok = tc::mbar_wait(&accfull[buf], (p / NBUF) & 1, abort_flag, WAIT_NS);
+                ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
+                if (!ok) break;
+                tc::fence_after_sync();
+                tacc = tmem + (static_cast<uint32_t>(qd * 32) << 16) + (uint32_t)(buf * ACC_COLS);
+            }
+            // 32 columns (chunk ch) of this thread's row of the piece's sum
+            auto get = [&](int ch, float* v) {
+                if constexpr (SL == 3) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = S0[ch * 32 + j] + S1[ch * 32 + j];  // small + s0*t0
+                } else {
+                    load_acc<NACC, BNT>(tacc, ch, v);
+                }
+            };
             const bool last = un >= u1;
             if (last && warp == 2 && lane == 0) pdl_trigger();  // a dependent kernel may be scheduled
-            const uint32_t tacc = tmem + (static_cast<uint32_t>(qd * 32) << 16) + (uint32_t)(buf * ACC_COLS);
             const int row_w = bm * BM + qd * 32;  // first row of this warp's slab (local, warp-uniform)
             const int row = row_w + lane;
             if (!(kb == 0 && ke == nk) && !Cpart) {
@@ -386,10 +443,11 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
                 // CTA's first piece) or 2g + 1 (its last)
                 const int slot = 2 * g + (u == u0 ? 0 : 1);
                 float* prow = Cpart + ((long)slot * BM + qd * 32 + lane) * BNT;
+#pragma unroll
                 for (int ch = 0; ch < BNT / 32; ++ch) {
                     if (bn * BNT + ch * 32 >= N) break;  // warp-uniform
                     float v[32];
-                    load_acc<NACC, BNT>(tacc, ch, v);
+                    get(ch, v);
                     if (row < M) {
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
@@ -398,23 +456,26 @@ __global__ void __launch_bounds__(192, (ST == 3 && SL == 1) ? 2 : 1)
                     }
                 }
             } else if (last && use_map_c) {
-                if (row_w < M && !epilogue_tma<NACC, BNT>(base, cbar, abort_flag, &mapC, tacc, cx0, cy0, M, N, bm,
-                                                            bn, qd, lane, lower, scale))
+                if (row_w < M && !epilogue_tma<BNT>(base, cbar, abort_flag, &mapC, get, cx0, cy0, M, N, bm, bn, qd,
+                                                    lane, lower, scale))
                     ok = false;
             } else {
+#pragma unroll
                 for (int ch = 0; ch < BNT / 32; ++ch) {
                     const int col0 = bn * BNT + ch * 32;
                     if (col0 >= N) break;                      // warp-uniform
                     if (lower && row_w + 31 < col0) continue;  // warp-uniform: chunk above the diagonal
                     float v[32];
-                    load_acc<NACC, BNT>(tacc, ch, v);
+                    get(ch, v);
                     if (row < M) apply_chunk(C + (long)row * ldc + col0, v, row, col0, N, lower, scale);
                 }
             }
             ok = __all_sync(0xffffffffu, ok);
-            tc::fence_before_sync();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&accempty[buf]);
+            if constexpr (SL != 3) {
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&accempty[buf]);
+            }
             if (!ok) break;
             ++p;
         }

@@ -178,10 +178,14 @@ static __global__ void __launch_bounds__(256) k_dot2(const double* __restrict__ 
     }
 }
 
-__device__ __forceinline__ double sum_parts(const double* part, int G, int m, int c, int which) {
+// The G partials of column c (which = 0 or 1) summed by one warp: lane l adds
+// partials l, l + 32, ... in order, then a fixed shuffle tree; every lane
+// returns lane 0's total, so every CTA that sums them gets the same value.
+__device__ __forceinline__ double warp_sum_parts(const double* part, int G, int m, int c, int which, int lane) {
     double s = 0.0;
-    for (int g = 0; g < G; ++g) s += part[((long)g * m + c) * 2 + which];
-    return s;
+    for (int g = lane; g < G; g += 32) s += part[((long)g * m + c) * 2 + which];
+    s = warp_sum(s);
+    return __shfl_sync(0xffffffffu, s, 0);
 }
 
 // Per-column CG state (inner loop of Algorithm 2).
@@ -204,13 +208,16 @@ static __global__ void __launch_bounds__(256) k_cg_update(const double* __restri
                                                    const double* __restrict__ P, const double* __restrict__ Qv,
                                                    const double* __restrict__ dinv, double* __restrict__ Z) {
     __shared__ double s_alpha[64];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int cb = 0; cb < m; cb += 64) {
         const int cn = min(64, m - cb);
         __syncthreads();
-        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
-            const CgCol& st = cols[cb + c];
-            double pq = sum_parts(part, G, m, cb + c, 0);
-            s_alpha[c] = st.done ? 0.0 : st.rho[parity] / pq;
+        for (int c = warp; c < cn; c += blockDim.x >> 5) {  // one warp per column
+            const double pq = warp_sum_parts(part, G, m, cb + c, 0, lane);
+            if (lane == 0) {
+                const CgCol& st = cols[cb + c];
+                s_alpha[c] = st.done ? 0.0 : st.rho[parity] / pq;
+            }
         }
         __syncthreads();
         long total = (long)n * cn;
@@ -238,14 +245,16 @@ static __global__ void __launch_bounds__(256) k_cg_pupdate(const double* __restr
     __shared__ double s_beta[64];
     __shared__ int s_done[64];
     __shared__ int s_active;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_active = 0;
     for (int cb = 0; cb < m; cb += 64) {
         const int cn = min(64, m - cb);
         __syncthreads();
-        for (int c = threadIdx.x; c < cn; c += blockDim.x) {
+        for (int c = warp; c < cn; c += blockDim.x >> 5) {  // one warp per column
+            const double rz = warp_sum_parts(part, G, m, cb + c, 0, lane);
+            const double rr = warp_sum_parts(part, G, m, cb + c, 1, lane);
+            if (lane != 0) continue;
             CgCol st = cols[cb + c];
-            double rz = sum_parts(part, G, m, cb + c, 0);
-            double rr = sum_parts(part, G, m, cb + c, 1);
             bool was_done = st.done;
             bool stop = was_done || (sqrt(rr) <= st.stop);
             s_beta[c] = stop ? 0.0 : rz / st.rho[parity];
@@ -310,10 +319,12 @@ static __global__ void k_copy_p(int n, int m, const double* __restrict__ Z, doub
 // rho[0] = (r^T z), rr = r^T r, stop = max(eta * ||r||_2, target_c).
 static __global__ void k_cg_init_cols(const double* __restrict__ part, int G, int m, CgCol* __restrict__ cols,
                                const int* __restrict__ frozen, double eta, const double* __restrict__ target) {
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m; c += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int c = blockIdx.x * wpb + (threadIdx.x >> 5); c < m; c += gridDim.x * wpb) {  // one warp per column
+        const double rz = warp_sum_parts(part, G, m, c, 0, lane);
+        const double rr = warp_sum_parts(part, G, m, c, 1, lane);
+        if (lane != 0) continue;
         CgCol st = cols[c];
-        double rz = sum_parts(part, G, m, c, 0);
-        double rr = sum_parts(part, G, m, c, 1);
         st.rho[0] = rz;
         st.rho[1] = rz;
         st.rr = rr;

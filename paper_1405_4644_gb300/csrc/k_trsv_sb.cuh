@@ -97,16 +97,21 @@ __device__ __forceinline__ int sb_row_slots(const SbPanel& pn, int J, int& slot_
     return ghi - glo + 1;
 }
 
-// Element (l, cc) of block row J's pending sum: the row's partial slots
-// added in CTA order.
-template <int MC>
-__device__ __forceinline__ float sb_pending(const SbArgs& a, int ns, int slot_lo, int glo, int l, int cc) {
-    float s = 0.f;
+// Block row J's pending partial sum, for this thread's elements e = tid +
+// 256 u (row l = e & 127, column c = e >> 7): the row's slots added in CTA
+// order, each slot's loads issued together.
+template <int MC, int PER>
+__device__ __forceinline__ void sb_pending(const SbArgs& a, int ns, int slot_lo, int glo, float (&pend)[PER]) {
+#pragma unroll
+    for (int u = 0; u < PER; ++u) pend[u] = 0.f;
     for (int k = 0; k < ns; ++k) {
-        const int slot = k == 0 ? slot_lo : 2 * (glo + k);
-        s += __ldcg(a.P2 + ((long)slot * 128 + l) * MC + cc);
+        const float* ps = a.P2 + (long)(k == 0 ? slot_lo : 2 * (glo + k)) * 128 * MC;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
+            if (e < 128 * MC) pend[u] += __ldcg(ps + l * MC + c);
+        }
     }
-    return s;
 }
 
 // Yk[l][c] = Y[r0 + l, c0 + c] (zero past n or past mc), minus the block
@@ -123,10 +128,12 @@ __device__ __forceinline__ void sb_stage(float* Yk, const SbArgs& a, long r0, in
         v[u] = (e < 128 * MC && c < a.mc && r < a.n) ? __ldcg(a.Y + (long)(a.c0 + c) * a.n + r) : 0.f;
     }
     if (ns > 0) {
+        float pend[PER];
+        sb_pending<MC>(a, ns, slot_lo, glo, pend);
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int e = threadIdx.x + u * 256, l = e & 127, c = e >> 7;
-            if (e < 128 * MC && c < a.mc && r0 + l < a.n) v[u] -= sb_pending<MC>(a, ns, slot_lo, glo, l, c);
+            if (e < 128 * MC && c < a.mc && r0 + l < a.n) v[u] -= pend[u];
         }
     }
 #pragma unroll
@@ -136,9 +143,63 @@ __device__ __forceinline__ void sb_stage(float* Yk, const SbArgs& a, long r0, in
     }
 }
 
+// Blocks [cs0, cs1) of y_I into YI (block c at YI + c 128 tv_ys), loads
+// issued eight per thread at a time
+template <int MC>
+__device__ __forceinline__ void sb_stage_range(float* YI, const SbArgs& a, int jb0, int cs0, int cs1) {
+    constexpr int BATCH = 8;
+    const int total = (cs1 - cs0) * 128 * MC;
+    for (int base = threadIdx.x; base < total; base += 256 * BATCH) {
+        float v[BATCH];
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int e = base + k * 256;
+            v[k] = 0.f;
+            if (e < total) {
+                const int blk = cs0 + e / (128 * MC), rem = e - (blk - cs0) * 128 * MC;
+                const int l = rem & 127, c = rem >> 7;
+                const long row = (long)(jb0 + blk) * 128 + l;
+                if (c < a.mc && row < a.n) v[k] = __ldcg(a.Y + (long)(a.c0 + c) * a.n + row);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < BATCH; ++k) {
+            const int e = base + k * 256;
+            if (e < total) {
+                const int blk = cs0 + e / (128 * MC), rem = e - (blk - cs0) * 128 * MC;
+                YI[(blk * 128 + (rem & 127)) * tv_ys<MC>() + (rem >> 7)] = v[k];
+            }
+        }
+    }
+}
+
+// Prefetch into L2 the 128 x 128 tile at rows r0.., columns k0.. of a
+// row-major float matrix (ld floats, rows < nrows): 512 lines of 128 bytes,
+// two per thread.  Nothing waits for it; the later loads find the lines in L2.
+__device__ __forceinline__ void sb_prefetch_tile(const float* M, long ld, long nrows, long r0, long k0) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int line = threadIdx.x + k * 256, r = line >> 2, part = line & 3;
+        if (r0 + r < nrows) {
+            const float* ptr = M + (r0 + r) * ld + k0 + part * 32;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+        }
+    }
+}
+
+// The tile of unit u of panel pn (forward L_{J, jb0 + c}, backward
+// L_{jb0 + c, J}), prefetched
+template <bool FWD>
+__device__ __forceinline__ void sb_prefetch_unit(const SbArgs& a, const SbPanel& pn, int jb0, long u) {
+    const int J = pn.J0 + (int)(u / pn.nb), K = jb0 + (int)(u % pn.nb);
+    if (FWD) sb_prefetch_tile(a.W, a.ldw, a.n, (long)J * 128, (long)K * 128);
+    else sb_prefetch_tile(a.W, a.ldw, a.n, (long)K * 128, (long)J * 128);
+}
+
+// shared memory: y_I of one super-block (SPD_SB_BLOCKS staged 128 x MC blocks)
 template <int MC>
 constexpr size_t trsv_sb_smem() {
-    return (size_t)(128 * tv_ys<MC>()) * sizeof(float);
+    return (size_t)SPD_SB_BLOCKS * 128 * tv_ys<MC>() * sizeof(float);
 }
 
 // tile index of the pair (p, q), q <= p, in the order (0,0), (1,0), (1,1), ...
@@ -147,7 +208,8 @@ __device__ __forceinline__ int sb_tri(int p, int q) { return p * (p + 1) / 2 + q
 template <int MC, bool FWD>
 __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float* Yk = reinterpret_cast<float*>(smem_raw);  // [128][tv_ys] one staged 128 x MC block
+    float* YI = reinterpret_cast<float*>(smem_raw);  // [SBB][128][tv_ys] staged blocks of y_I (F: one)
+    constexpr int YB = 128 * tv_ys<MC>();           // floats per staged block
     __shared__ int s_abort;
     if (a.gate && *a.gate == 0) return;  // refinement over (capturable solves)
     const int tid = threadIdx.x;
@@ -173,12 +235,16 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
                 int slot_lo, glo;
                 const int ns = sb_row_slots(prev, J, slot_lo, glo);
                 if (ns == 0) continue;  // block-uniform
-                for (int e = tid; e < 128 * MC; e += 256) {
-                    const int l = e / MC, cc = e - l * MC;
+                constexpr int PER = (128 * MC + 255) / 256;
+                float pend[PER];
+                sb_pending<MC>(a, ns, slot_lo, glo, pend);
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    const int e = tid + u * 256, l = e & 127, cc = e >> 7;
                     const long row = (long)J * 128 + l;
-                    if (cc < a.mc && row < a.n) {
+                    if (e < 128 * MC && cc < a.mc && row < a.n) {
                         float* y = a.Y + (long)(a.c0 + cc) * a.n + row;
-                        *y = __ldcg(y) - sb_pending<MC>(a, ns, slot_lo, glo, l, cc);
+                        *y = __ldcg(y) - pend[u];
                     }
                 }
                 continue;
@@ -191,14 +257,14 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
             tv_tile<FWD>(ra, XI, a.S, a.S, b, c, tq, ts);
             int slot_lo = 0, glo = 0;
             const int ns = prev.W == 0 ? 0 : sb_row_slots(prev, jb0 + c, slot_lo, glo);
-            sb_stage<MC>(Yk, a, (long)(jb0 + c) * 128, ns, slot_lo, glo);
+            sb_stage<MC>(YI, a, (long)(jb0 + c) * 128, ns, slot_lo, glo);
             __syncthreads();
             float acc[4][MC];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int cc = 0; cc < MC; ++cc) acc[j][cc] = 0.f;
-            tv_dot<MC>(acc, ra, Yk, ts);
+            tv_dot<MC>(acc, ra, YI, ts);
             tv_reduce8<MC>(acc);
             if (ts == 0) {
                 float* pt = a.P + (long)task * 128 * MC;
@@ -210,19 +276,24 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
             __syncthreads();
         }
         if (!sb_barrier(a, ++nbar, &s_abort)) return;
-        // A2: y_I[b] = its partials in order (forward c = 0..b, backward c = b..nb-1)
-        for (int b = g; b < nb; b += G) {
-            for (int e = tid; e < 128 * MC; e += 256) {
-                const int r = e / MC, cc = e - r * MC;
-                float s = 0.f;
-                if (FWD) {
-                    for (int c = 0; c <= b; ++c) s += __ldcg(a.P + ((long)sb_tri(b, c) * 128 + r) * MC + cc);
-                } else {
-                    for (int c = b; c < nb; ++c) s += __ldcg(a.P + ((long)sb_tri(c, b) * 128 + r) * MC + cc);
-                }
-                const long row = (long)(jb0 + b) * 128 + r;
-                if (cc < a.mc && row < a.n) a.Y[(long)(a.c0 + cc) * a.n + row] = s;
+        // A2: y_I[b] = its partials in order (forward c = 0..b, backward c =
+        // b..nb-1), the elements spread over every CTA, each one's loads
+        // issued together
+        for (int e = g * 256 + tid; e < nb * 128 * MC; e += G * 256) {
+            const int b = e / (128 * MC), rem = e - b * 128 * MC, r = rem / MC, cc = rem - r * MC;
+            float t[SPD_SB_BLOCKS];
+#pragma unroll
+            for (int k = 0; k < SPD_SB_BLOCKS; ++k) {
+                const int c = FWD ? k : b + k;
+                const bool in = FWD ? k <= b : c < nb;
+                t[k] = in ? __ldcg(a.P + ((long)(FWD ? sb_tri(b, c) : sb_tri(c, b)) * 128 + r) * MC + cc) : 0.f;
             }
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < SPD_SB_BLOCKS; ++k)
+                if (FWD ? k <= b : b + k < nb) s += t[k];
+            const long row = (long)(jb0 + b) * 128 + r;
+            if (cc < a.mc && row < a.n) a.Y[(long)(a.c0 + cc) * a.n + row] = s;
         }
         if (t + 1 == a.NS) break;  // no rows left to update
         if (!sb_barrier(a, ++nbar, &s_abort)) return;
@@ -235,6 +306,12 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
         pn.geff = (int)min((long)G, pn.W);
         if (g < pn.geff) {
             const long u0 = sb_ub(g, pn.W, pn.geff), u1 = sb_ub(g + 1, pn.W, pn.geff);
+            // the blocks of y_I this CTA's units multiply, staged once
+            const bool all = (u1 - u0 >= nb) || (u0 / nb != (u1 - 1) / nb);
+            const int cs0 = all ? 0 : (int)(u0 % nb), cs1 = all ? nb : (int)((u1 - 1) % nb) + 1;
+            for (long v = u0; v < min(u1, u0 + 2); ++v) sb_prefetch_unit<FWD>(a, pn, jb0, v);
+            sb_stage_range<MC>(YI, a, jb0, cs0, cs1);
+            __syncthreads();
             for (long u = u0; u < u1;) {
                 const int J = pn.J0 + (int)(u / nb), ca = (int)(u % nb);
                 const int ce = (int)min((long)nb, ca + (u1 - u));
@@ -244,20 +321,19 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
 #pragma unroll
                     for (int cc = 0; cc < MC; ++cc) acc[j][cc] = 0.f;
                 // tiles L_{J, jb0 + c} (forward) or L_{jb0 + c, J}^T (backward),
-                // two per trip so that the register buffers alternate
+                // two per trip so that the register buffers alternate: the
+                // next tile's loads are in flight during this tile's products
+                // (tiles two units ahead, across pieces, are prefetched into L2)
                 tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, jb0 + ca, tq, ts);
                 for (int c = ca; c < ce; c += 2) {
-                    sb_stage<MC>(Yk, a, (long)(jb0 + c) * 128);
-                    __syncthreads();
+                    const long uc = u + (c - ca);
+                    if (uc + 2 < u1) sb_prefetch_unit<FWD>(a, pn, jb0, uc + 2);
                     if (c + 1 < ce) tv_tile<FWD>(rb, a.W, a.ldw, a.n, J, jb0 + c + 1, tq, ts);
-                    tv_dot<MC>(acc, ra, Yk, ts);
-                    __syncthreads();
+                    tv_dot<MC>(acc, ra, YI + c * YB, ts);
                     if (c + 1 >= ce) break;
-                    sb_stage<MC>(Yk, a, (long)(jb0 + c + 1) * 128);
-                    __syncthreads();
+                    if (uc + 3 < u1) sb_prefetch_unit<FWD>(a, pn, jb0, uc + 3);
                     if (c + 2 < ce) tv_tile<FWD>(ra, a.W, a.ldw, a.n, J, jb0 + c + 2, tq, ts);
-                    tv_dot<MC>(acc, rb, Yk, ts);
-                    __syncthreads();
+                    tv_dot<MC>(acc, rb, YI + (c + 1) * YB, ts);
                 }
                 tv_reduce8<MC>(acc);
                 if (ts == 0) {
@@ -283,6 +359,19 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
                 u += ce - ca;
             }
         }
+        {   // the next super-block's inverse tiles this CTA will multiply in phase F
+            const int In = FWD ? I + 1 : I - 1;
+            const int nbn = min(a.SBB, a.NB - In * a.SBB), ntn = nbn * (nbn + 1) / 2;
+            for (int task = g; task < ntn; task += G) {
+                int p = 0;
+                while (sb_tri(p + 1, 0) <= task) ++p;
+                const int q = task - sb_tri(p, 0);
+                const int b = FWD ? p : q, c = FWD ? q : p;
+                const float* XN = a.X + (long)In * a.S * a.S;
+                if (FWD) sb_prefetch_tile(XN, a.S, a.S, (long)b * 128, (long)c * 128);
+                else sb_prefetch_tile(XN, a.S, a.S, (long)c * 128, (long)b * 128);
+            }
+        }
         prev = pn;
         if (!sb_barrier(a, ++nbar, &s_abort)) return;
     }
@@ -291,107 +380,131 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
 // ---------------------------------------------------------------------------
 // the super-block inverses, once per factor
 // ---------------------------------------------------------------------------
-// CTA (c, I) forms block column c of X_I = L_II^{-1} by block forward
-// substitution: X_cc = L_cc^{-1} (the transpose of LinvT's block), then for
-// b = c+1 .. nb-1, X_bc = -L_bb^{-1} (sum_{k=c}^{b-1} L_bk X_kc).  Rows of L
+// X_I = L_II^{-1} by block forward substitution: X_cc = L_cc^{-1} (the
+// transpose of LinvT's block), then for b = c+1 .. nb-1,
+// X_bc = -L_bb^{-1} (sum_{k=c}^{b-1} L_bk X_kc).  A strip of 32 columns of
+// block column c only needs the same strip of the blocks above it, so CTA
+// (4 c + s, I) forms strip s of block column c of X_I on its own.  Rows of L
 // past n are zero and LinvT's rows past n are the identity; those rows of X
 // meet only right-hand-side rows past n, which the sweeps hold at zero.
-// Products are 128x128x128 in float32 through shared memory, thread (ty, tx)
-// = (tid / 16, tid % 16) owning an 8 x 8 block of the result.
-constexpr size_t sb_inverse_smem() { return (size_t)(128 * 33 + 32 * 132 + 128 * 132) * sizeof(float); }
+// Products are 128 x 128 x 32 in float32 through shared memory, thread
+// (ty, tx) = (tid / 8, tid % 8) owning a 4 x 4 block of the result.
+constexpr int SB_STRIPS = 4;  // 32-column strips per block column
+constexpr size_t sb_inverse_smem() { return (size_t)(128 * 33 + 32 * 36 + 128 * 36) * sizeof(float); }
 
 static __global__ void __launch_bounds__(256) k_sb_inverse(const float* __restrict__ W, long ldw, int n, int NB,
                                                            const float* __restrict__ LinvT, int SBB,
                                                            float* __restrict__ X) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* As = reinterpret_cast<float*>(smem_raw);  // [128][33] a 128 x 32 slice of the left factor
-    float* Bs = As + 128 * 33;                       // [32][132] a 32 x 128 slice of the right factor
-    float* Ts = Bs + 32 * 132;                       // [128][132] T = sum_k L_bk X_kc
-    const int c = blockIdx.x, I = blockIdx.y, tid = threadIdx.x;
+    float* Bs = As + 128 * 33;                       // [32][36]  a 32 x 32 slice of the right factor
+    float* Ts = Bs + 32 * 36;                        // [128][36] T = sum_k L_bk X_kc (this strip)
+    const int c = blockIdx.x / SB_STRIPS, strip = blockIdx.x % SB_STRIPS;
+    const int I = blockIdx.y, tid = threadIdx.x;
     const int S = SBB * 128;
     const int jb0 = I * SBB, nb = min(SBB, NB - jb0);
     if (c >= nb) return;
     float* XI = X + (long)I * S * S;
-    const int ty = tid >> 4, tx = tid & 15;
-    // X_cc = (LinvT block)^T
+    const int x0 = c * 128 + strip * 32;  // first column of the strip in X_I
+    const int ty = tid >> 3, tx = tid & 7;
+    // X_cc (this strip) = (LinvT block)^T
     {
         const float* lt = LinvT + (long)(jb0 + c) * 16384;
-        for (int e = tid; e < 16384; e += 256) {
-            const int r = e >> 7, col = e & 127;
-            XI[(long)(c * 128 + r) * S + c * 128 + col] = lt[col * 128 + r];
+        for (int e = tid; e < 128 * 32; e += 256) {
+            const int r = e >> 5, col = e & 31;
+            XI[(long)(c * 128 + r) * S + x0 + col] = lt[(strip * 32 + col) * 128 + r];
         }
     }
     __syncthreads();
-    float acc[8][8];
+    float acc[4][4];
+    // chunk q of T's K loop: block k = c + q / 4, columns kk = 32 (q % 4);
+    // the next chunk's entries wait in registers while this one is used
+    float an[16], bn[4];
+    auto load_chunk = [&](int b, int q) {
+        const int k = c + (q >> 2), kk = (q & 3) * 32;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {  // As[r][q'] = L[row r of block b][col kk + q' of block k]
+            const int e = tid + i * 256, r = e >> 5, qq = e & 31;
+            const long gr = (long)(jb0 + b) * 128 + r;
+            an[i] = gr < n ? W[gr * ldw + (long)(jb0 + k) * 128 + kk + qq] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {  // Bs[q'][col] = X_kc[kk + q'][strip col]
+            const int e = tid + i * 256, qq = e >> 5, col = e & 31;
+            bn[i] = __ldcg(XI + (long)(k * 128 + kk + qq) * S + x0 + col);
+        }
+    };
     for (int b = c + 1; b < nb; ++b) {
         // T = sum_{k=c}^{b-1} L_bk X_kc
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
-        for (int k = c; k < b; ++k) {
-            for (int kk = 0; kk < 128; kk += 32) {
-                for (int e = tid; e < 128 * 32; e += 256) {  // As[r][q] = L[row r of block b][col kk+q of block k]
-                    const int r = e >> 5, q = e & 31;
-                    const long gr = (long)(jb0 + b) * 128 + r;
-                    As[r * 33 + q] = gr < n ? W[gr * ldw + (long)(jb0 + k) * 128 + kk + q] : 0.f;
-                }
-                for (int e = tid; e < 32 * 128; e += 256) {  // Bs[q][col] = X_kc[kk + q][col]
-                    const int q = e >> 7, col = e & 127;
-                    Bs[q * 132 + col] = __ldcg(XI + (long)(k * 128 + kk + q) * S + c * 128 + col);
-                }
-                __syncthreads();
-#pragma unroll 4
-                for (int q = 0; q < 32; ++q) {
-                    float av[8], bv[8];
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        const int nq = (b - c) * 4;
+        load_chunk(b, 0);
+        for (int q = 0; q < nq; ++q) {
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) av[i] = As[(ty * 8 + i) * 33 + q];
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) bv[j] = Bs[q * 132 + tx * 8 + j];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i)
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-                }
-                __syncthreads();
+            for (int i = 0; i < 16; ++i) {
+                const int e = tid + i * 256;
+                As[(e >> 5) * 33 + (e & 31)] = an[i];
             }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int e = tid + i * 256;
+                Bs[(e >> 5) * 36 + (e & 31)] = bn[i];
+            }
+            __syncthreads();
+            if (q + 1 < nq) load_chunk(b, q + 1);
+#pragma unroll 8
+            for (int qq = 0; qq < 32; ++qq) {
+                float av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = As[(ty * 4 + i) * 33 + qq];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[qq * 36 + tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+            __syncthreads();
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) Ts[(ty * 8 + i) * 132 + tx * 8 + j] = acc[i][j];
+            for (int j = 0; j < 4; ++j) Ts[(ty * 4 + i) * 36 + tx * 4 + j] = acc[i][j];
         __syncthreads();
         // X_bc = -L_bb^{-1} T, L_bb^{-1}[r][q] = LinvT_b[q][r]
         const float* lt = LinvT + (long)(jb0 + b) * 16384;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
         for (int kk = 0; kk < 128; kk += 32) {
             for (int e = tid; e < 128 * 32; e += 256) {  // As[r][q] = L_bb^{-1}[r][kk + q]
                 const int r = e >> 5, q = e & 31;
                 As[r * 33 + q] = lt[(kk + q) * 128 + r];
             }
             __syncthreads();
-#pragma unroll 4
+#pragma unroll 8
             for (int q = 0; q < 32; ++q) {
-                float av[8], bv[8];
+                float av[4], bv[4];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) av[i] = As[(ty * 8 + i) * 33 + q];
+                for (int i = 0; i < 4; ++i) av[i] = As[(ty * 4 + i) * 33 + q];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) bv[j] = Ts[(kk + q) * 132 + tx * 8 + j];
+                for (int j = 0; j < 4; ++j) bv[j] = Ts[(kk + q) * 36 + tx * 4 + j];
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
             }
             __syncthreads();
         }
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                XI[(long)(b * 128 + ty * 8 + i) * S + c * 128 + tx * 8 + j] = -acc[i][j];
+            for (int j = 0; j < 4; ++j)
+                XI[(long)(b * 128 + ty * 4 + i) * S + x0 + tx * 4 + j] = -acc[i][j];
         __syncthreads();  // X_bc is read (through L2) by the next b
     }
 }

@@ -297,7 +297,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (prec == SPD_PREC_FP64) req += sizeof(double) * (std::max<size_t>(nW, 1) + 4096 * nb);
         else req += sizeof(float) * (std::max<size_t>(nW, 1) + (1 + 4 + 0.25) * 16384 * nb) +
                     (kind ? mirror_elem(kind) * std::max<size_t>(nW, 1) : 0) +
-                    (nb >= 2 * SPD_SB_BLOCKS && (flags & SPD_FACTOR_SB_SWEEPS)
+                    (nb >= 2 * SPD_SB_BLOCKS && !(flags & SPD_FACTOR_BLOCK_SWEEPS)
                          ? sizeof(float) * (size_t)ceil_div((long)nb, SPD_SB_BLOCKS) * SPD_SB_BLOCKS * 128 *
                                SPD_SB_BLOCKS * 128
                          : 0);
@@ -384,7 +384,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
             if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "block inverse launch failed");
         }
         if (st == SPD_OK && prec != SPD_PREC_FP64) st = factor_couplings(h, F);
-        if (st == SPD_OK && prec != SPD_PREC_FP64 && (flags & SPD_FACTOR_SB_SWEEPS) &&
+        if (st == SPD_OK && prec != SPD_PREC_FP64 && !(flags & SPD_FACTOR_BLOCK_SWEEPS) &&
             F->nblk128 >= 2 * SPD_SB_BLOCKS) {
             // inverses of the diagonal super-blocks for the super-block sweeps
             F->sbb = SPD_SB_BLOCKS;
@@ -402,7 +402,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                 }();
                 (void)attr;
                 ProfScope pinv(h, SPD_PHASE_LEAF, (double)F->nsb * S * S * S / 3.0, 4.0 * F->nsb * S * S);
-                ++h->launches, k_sb_inverse<<<dim3(F->sbb, F->nsb), 256, sb_inverse_smem(), s>>>(
+                ++h->launches, k_sb_inverse<<<dim3(F->sbb * SB_STRIPS, F->nsb), 256, sb_inverse_smem(), s>>>(
                     F->W, F->ldw, n, F->nblk128, F->LinvT, F->sbb, F->Xsb);
                 if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "super-block inverse launch failed");
             }

@@ -16,6 +16,14 @@
 // ---------------------------------------------------------------------------
 // handle
 // ---------------------------------------------------------------------------
+// SPD_RESID_AUTO: float64 fused multiply-adds for one right-hand side (8
+// bytes per entry of A, against 20 for the digit planes and their one-time
+// formation), the tensor-core residual from m = 2 on, where the FP64 rate
+// bounds the float64 residual (2 m flops per 8 bytes).
+static int resolve_resid(int resid, int m) {
+    return resid == SPD_RESID_AUTO ? (m >= 2 ? SPD_RESID_TC : SPD_RESID_FP64) : resid;
+}
+
 extern "C" void spd_opts_default(spd_opts* o) {
     if (!o) return;
     o->tol = 1e-14;
@@ -653,6 +661,7 @@ extern "C" spd_status spd_factor_solve(spd_handle* h, const spd_factor_t* F, int
 namespace {
 
 enum MatvecKind { MV_FP64 = 0, MV_FP32 = 1, MV_BF16 = 2, MV_BAND = 3, MV_TC = 4 };
+constexpr int CG_GRAPH_STEPS = 8;  // inner steps per captured graph (= the host's check interval)
 
 struct CgSetup {
     int matvec = MV_FP64;
@@ -809,6 +818,18 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
     }
     CUDA_TRY(h, cudaMemsetAsync(w.cg, 0, sizeof(CgCol) * m, s));
     const double* Zr = (cs.pc == SPD_PC_NONE) ? w.Rr : w.Z;
+    // inner steps whose launches do not change from one step to the next
+    // (dense or banded float32/bf16 products, no preconditioner or Jacobi)
+    // replay as a CUDA graph of CG_GRAPH_STEPS steps, captured once per call;
+    // not while profiling (the phase records would be captured once)
+    struct CgGraph {
+        cudaGraphExec_t exec = nullptr;
+        long kernels = 0;
+        ~CgGraph() {
+            if (exec) cudaGraphExecDestroy(exec);
+        }
+    } cg_graph;
+    bool graph_ok = !h->prof_on && cs.matvec != MV_FP64 && (cs.pc == SPD_PC_NONE || cs.pc == SPD_PC_JACOBI);
     int outer = 0;
     IrSummary sm{};
     for (;;) {
@@ -834,17 +855,19 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             ++(h)->launches, k_copy_p<<<gv, 256, 0, s>>>(n, m, w.Z, w.P, w.Pf);
         }
         ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
-        ++(h)->launches, k_cg_init_cols<<<ceil_div(m, 128), 128, 0, s>>>(w.part, w.G2, m, w.cg, w.frozen, o.eta, w.target);
+        ++(h)->launches, k_cg_init_cols<<<ceil_div(m, 4), 128, 0, s>>>(w.part, w.G2, m, w.cg, w.frozen, o.eta, w.target);
         LAUNCH_CHECK(h);
-        for (int t = 0; t < o.maxit_inner; ++t) {
+        // one inner step (products, dots, updates) at iteration t
+        auto step = [&](int t) -> spd_status {
             const int par = t & 1;
+            spd_status sst = SPD_OK;
             switch (cs.matvec) {
                 case MV_FP32: mv_dispatch<float>(h, cs, n, m, w.Pf, w.Q); break;
-                case MV_TC:
-                    st = mv_tc(h, cs, n, m, w.Pf, w.Q);
-                    if (st != SPD_OK) return st;
-                    break;
                 case MV_BF16: mv_dispatch<__nv_bfloat16>(h, cs, n, m, w.Pf, w.Q); break;
+                case MV_TC:
+                    sst = mv_tc(h, cs, n, m, w.Pf, w.Q);
+                    if (sst != SPD_OK) return sst;
+                    break;
                 case MV_BAND: {  // (2b + 1) n float32 entries of the band per product
                     ProfScope ps(h, SPD_PHASE_MATVEC, 2.0 * (2.0 * cs.band + 1.0) * n * m,
                                  4.0 * (2.0 * cs.band + 1.0) * n, s);
@@ -853,8 +876,8 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                     break;
                 }
                 default:
-                    st = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1, o.resid);
-                    if (st != SPD_OK) return st;
+                    sst = resid_run(h, w.rw, n, m, A, lda, nullptr, 0, w.P, n, w.Q, n, nullptr, nullptr, 1, o.resid);
+                    if (sst != SPD_OK) return sst;
             }
             LAUNCH_CHECK(h);
             ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.P, w.Q, nullptr, nullptr, n, m, w.part);
@@ -862,14 +885,49 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
                                            cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, w.Z);
             LAUNCH_CHECK(h);
             if (fac || lowrank) {
-                st = fac ? lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0)
-                         : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
-                if (st != SPD_OK) return st;
+                sst = fac ? lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0)
+                          : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
+                if (sst != SPD_OK) return sst;
             }
             ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);
             ++(h)->launches, k_cg_pupdate<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.active, w.P, w.Pf, Zr);
             LAUNCH_CHECK(h);
-            if ((t + 1) % 8 == 0 || t + 1 == o.maxit_inner) {
+            return SPD_OK;
+        };
+        for (int t = 0; t < o.maxit_inner;) {
+            if (graph_ok && (t & 1) == 0 && t + CG_GRAPH_STEPS <= o.maxit_inner) {
+                if (!cg_graph.exec) {
+                    // capture CG_GRAPH_STEPS steps (the launches are the same
+                    // for every group starting at an even step); on any
+                    // failure run the steps directly
+                    const long l0 = h->launches;
+                    cudaGraph_t graph = nullptr;
+                    spd_status cst = SPD_OK;
+                    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                        for (int k = 0; k < CG_GRAPH_STEPS && cst == SPD_OK; ++k) cst = step(t + k);
+                        const cudaError_t e = cudaStreamEndCapture(s, &graph);
+                        if (cst == SPD_OK && e == cudaSuccess &&
+                            cudaGraphInstantiate(&cg_graph.exec, graph, 0) != cudaSuccess)
+                            cg_graph.exec = nullptr;
+                    }
+                    if (graph) cudaGraphDestroy(graph);
+                    cudaGetLastError();
+                    cg_graph.kernels = h->launches - l0;
+                    h->launches = l0;
+                    if (!cg_graph.exec) {
+                        graph_ok = false;
+                        continue;
+                    }
+                }
+                CUDA_TRY(h, cudaGraphLaunch(cg_graph.exec, s));
+                h->launches += cg_graph.kernels;
+                t += CG_GRAPH_STEPS;
+            } else {
+                st = step(t);
+                if (st != SPD_OK) return st;
+                ++t;
+            }
+            if (t % 8 == 0 || t == o.maxit_inner) {
                 int act = 0;
                 st = read_int(h, w.active, &act);
                 if (st != SPD_OK) return st;
@@ -911,7 +969,7 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     if (opts_in) o = *opts_in;
     if (rep) memset(rep, 0, sizeof(*rep));
     if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_TC)
+        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_AUTO)
         return set_err(h, SPD_ERR_ARG, "spd_solve_ir: bad arguments");
     if (n == 0 || m == 0) return SPD_OK;
     cudaStream_t s = h->stream;
@@ -920,6 +978,7 @@ extern "C" spd_status spd_solve_ir(spd_handle* h, const spd_factor_t* F, int n, 
     int S, G2;
     cg_plan(p, h, n, m, o_, &S, &G2);
     TcSetup tcs;
+    o.resid = resolve_resid(o.resid, m);
     tc_plan_if(p, h, n, m, o.resid, tcs);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;
@@ -1049,9 +1108,10 @@ extern "C" spd_status spd_solve_ir_async(spd_handle* h, const spd_factor_t* F, i
     spd_opts_default(&o);
     if (opts_in) o = *opts_in;
     if (!F || F->n != n || bad_args(n, m, A, lda, B, ldb, X, ldx) || !rep || o.maxit < 0 || !(o.tol >= 0.0) ||
-        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_TC || F->prec == SPD_PREC_FP64)
+        o.crit < 0 || o.crit > 2 || o.resid < SPD_RESID_FP64 || o.resid > SPD_RESID_AUTO || F->prec == SPD_PREC_FP64)
         return set_err(h, SPD_ERR_ARG, "spd_solve_ir_async: bad arguments");
     if (n == 0 || m == 0) return SPD_OK;
+    o.resid = resolve_resid(o.resid, m);
     const int kind = o.resid == SPD_RESID_TC ? SPD_RESID_TC : SPD_RESID_FP64;  // no hybrid: no host decision
     cudaStream_t s = h->stream;
     WsPlan p;
@@ -1117,7 +1177,7 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     if (rep) memset(rep, 0, sizeof(*rep));
     if (bad_args(n, m, A, lda, B, ldb, X, ldx) || o.maxit < 0 || o.maxit_inner < 1 || !(o.tol >= 0.0) ||
         o.crit < 0 || o.crit > 2 || pc < SPD_PC_NONE || pc > SPD_PC_LOWRANK || o.resid < SPD_RESID_FP64 ||
-        o.resid > SPD_RESID_TC ||
+        o.resid > SPD_RESID_AUTO ||
         ((pc == SPD_PC_FACTOR || pc == SPD_PC_LOWRANK) && !pc_data))
         return set_err(h, SPD_ERR_ARG, "spd_cg: bad arguments");
     if (matvec_prec != SPD_PREC_FP64 && matvec_prec != SPD_PREC_FP32 && matvec_prec != SPD_PREC_BF16)
@@ -1169,6 +1229,7 @@ extern "C" spd_status spd_cg(spd_handle* h, int n, int m, const double* A, int l
     }
     if (pc == SPD_PC_JACOBI) o_dinv = p.add<double>(n);
     TcSetup tcs;
+    o.resid = resolve_resid(o.resid, m);
     tc_plan_if(p, h, n, m, o.resid, tcs);
     spd_status st = ws_reserve(h, p.bytes);
     if (st != SPD_OK) return st;

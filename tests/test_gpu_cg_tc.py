@@ -1,8 +1,9 @@
 """GPU parity of the tensor-core product of CG with several right-hand sides
 (step C1 of Algorithm 2): the narrow fused-slice GEMM against the rounded
-float32 product (and bit for bit against the 128-wide tiles, which issue the
-same slice products in the same order), and Algorithm 2 with its products on
-the tensor cores against the CUDA-core products and the float64 oracle."""
+float32 product, without the bias of the tensor cores' own float32
+accumulation (each K tile's sums are promoted to float32 registers), and
+Algorithm 2 with its products on the tensor cores against the CUDA-core
+products and the float64 oracle."""
 import numpy as np
 import pytest
 import torch
@@ -50,11 +51,24 @@ def test_narrow_gemm_matches_rounded_product(h, M, N, K, stream_k):
     bound = (K + 8) * 2.0 ** -24 * (np.abs(f32(A)) @ np.abs(f32(B)).T) + 2.0 ** -24 * np.abs(C0)
     err = np.abs(got - ref)
     assert np.all(err <= bound), float((err / bound).max())
-    if not stream_k:
-        # same slice products in the same order per entry as the 128-wide tiles
-        assert np.array_equal(got, gemm(h, A, B, C0))
-    else:
-        assert np.array_equal(got, gemm(h, A, B, C0, narrow=True, stream_k=True))  # deterministic
+    assert np.array_equal(got, gemm(h, A, B, C0, narrow=True, stream_k=stream_k))  # deterministic
+
+
+def test_narrow_gemm_has_no_accumulation_bias(h):
+    """Positive operands, K = 16384: a float32 sum that rounds toward zero at
+    every step loses about K 2^-24 / 3 of the result (about 1e-4 here); with
+    each 64-long K tile promoted to float32 registers (round to nearest) the
+    mean relative error stays at the level of one K tile's sum."""
+    M, N, K = 512, 32, 16384
+    g = np.random.default_rng(7)
+    A = g.uniform(0, 1, (M, K))
+    B = g.uniform(0, 1, (N, K))
+    C0 = np.zeros((M, N))
+    exact = f32(A) @ f32(B).T
+    got = -gemm(h, A, B, C0, narrow=True, stream_k=True)
+    rel = (got - exact) / exact
+    assert abs(rel.mean()) <= 2e-6, rel.mean()
+    assert np.abs(rel).max() <= (K + 8) * 2.0 ** -24
 
 
 def test_narrow_gemm_rejects_other_precisions_and_lower(h):
@@ -116,3 +130,54 @@ def test_cg_paper_rule_many_rhs_on_tensor_cores(h):
     assert ok
     assert abs(rep.iters_low - int(lo.max())) <= max(3, 0.1 * lo.max())
     assert abs(rep.iters_high - int(hi.max())) <= 1
+
+
+@pytest.mark.parametrize("m", [1, 3])
+def test_auto_residual_in_both_algorithms(h, m):
+    """SPD_RESID_AUTO (float64 fused multiply-adds for one right-hand side,
+    the tensor-core residual for more) reaches the float64 target in
+    Algorithm 1 and Algorithm 2; an unknown residual code is refused."""
+    n = 700
+    A = W.gram_shifted(n, seed=50 + m, shift=0.1)
+    B = W.gaussian_rhs(n, m, 4)
+    Ad, Bd = dev_sym(A), dev_cols(B)
+    X = dev_zeros(n, m)
+    st, rep = spd.spd_cg(h, Ad, Bd, X, "fp32", opts={"tol": 1e-14, "crit": "berr", "resid": "auto"})
+    check(h, st)
+    assert oracle.berr(A, B, host(X)) <= 1e-14
+    st, F, _ = spd.spd_factor(h, Ad, "fp16")
+    check(h, st)
+    try:
+        X2 = dev_zeros(n, m)
+        st, rep = spd.spd_solve_ir(h, F, Ad, Bd, X2, {"resid": "auto"})
+        check(h, st)
+        assert oracle.berr(A, B, host(X2)) <= 1e-14
+        st, _ = spd.spd_solve_ir(h, F, Ad, Bd, X2, {"resid": 4})
+        assert st == spd.SPD_ERR_ARG
+    finally:
+        spd.spd_factor_destroy(F)
+
+
+@pytest.mark.parametrize("mv,m,band", [("fp32", 1, -1), ("fp32", 16, -1), ("bf16", 3, -1), ("fp32", 2, 16)])
+def test_cg_inner_steps_as_a_graph_match_direct_launches(mv, m, band):
+    """Groups of inner steps replayed from a captured CUDA graph give the
+    same iterates, bit for bit, as the same kernels launched one by one
+    (profiling on: the library then launches directly)."""
+    n = 1200
+    A = W.model_covariance(n, 2)
+    B = W.uniform_rhs(n, m, 5)
+    Ad, Bd = dev_sym(A), dev_cols(B)
+    opts = {"tol": 1e-5, "crit": "abs2", "eta": 0.0, "maxit_inner": 5000, "band": band}
+    out = []
+    for prof in (False, True):
+        h = spd.spd_create(torch.cuda.current_stream())
+        try:
+            spd.spd_profile_enable(h, prof)
+            X = dev_zeros(n, m)
+            st, rep = spd.spd_cg(h, Ad, Bd, X, mv, opts=opts)
+            check(h, st)
+            out.append((host(X), rep.iters_low, rep.iters_high))
+        finally:
+            spd.spd_destroy(h)
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1:] == out[1][1:]

@@ -175,7 +175,8 @@ def test_resid_option_out_of_range_is_rejected(h):
     st, F, _ = spd.spd_factor(h, A, "fp32")
     check(h, st)
     try:
-        st, _ = spd.spd_solve_ir(h, F, A, dev_cols(np.ones((n, 1))), dev_zeros(n, 1), {"resid": 3})
-        assert st == spd.SPD_ERR_ARG
+        for code in (4, -1):  # 0-3 are the residual kinds (3: automatic)
+            st, _ = spd.spd_solve_ir(h, F, A, dev_cols(np.ones((n, 1))), dev_zeros(n, 1), {"resid": code})
+            assert st == spd.SPD_ERR_ARG
     finally:
         spd.spd_factor_destroy(F)

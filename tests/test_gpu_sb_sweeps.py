@@ -1,8 +1,8 @@
 """GPU parity of the super-block triangular sweeps (step A4 of Algorithm 1
-with explicit inverses of the diagonal super-blocks, SPD_FACTOR_SB_SWEEPS,
-taken once a float32 factor has at least two super-blocks of eight 128-row
-blocks): against the float64 oracle applying the GPU's own factor, against
-the default 128-row block sweeps on the same factor, at ragged orders (a last
+with explicit inverses of the diagonal super-blocks, the default once a
+float32 factor has at least two super-blocks of eight 128-row blocks):
+against the float64 oracle applying the GPU's own factor, against the
+128-row block sweeps (SPD_FACTOR_BLOCK_SWEEPS) on the same factor, at ragged orders (a last
 super-block of one block, a last block of one row) and right-hand-side counts
 that span several column passes; and inside Algorithm 1, synchronous,
 device-gated and replayed from a CUDA graph."""
@@ -19,7 +19,8 @@ pytestmark = pytest.mark.gpu
 from tests.gpu_util import check, dev_cols, dev_sym, dev_zeros, factor_L, host  # noqa: E402
 
 U32 = 2.0 ** -24
-SB = spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_SB_SWEEPS
+SB = spd.SPD_SCALE_DIAG
+BLK = spd.SPD_SCALE_DIAG | spd.SPD_FACTOR_BLOCK_SWEEPS
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +70,7 @@ def test_superblock_and_block_sweeps_agree(h, n, m, prec):
     A = W.gram_shifted(n, seed=3 * n, shift=0.5)
     Rh = W.gaussian_rhs(n, m, 12)
     out = []
-    for flags in [SB, spd.SPD_SCALE_DIAG]:
+    for flags in [SB, BLK]:
         st, F, _ = spd.spd_factor(h, dev_sym(A), prec, flags)
         check(h, st)
         try:
@@ -89,7 +90,7 @@ def test_small_orders_keep_the_block_sweeps(h):
     A = W.gram_shifted(n, seed=5, shift=0.5)
     Rh = W.gaussian_rhs(n, m, 6)
     Z = []
-    for flags in [SB, spd.SPD_SCALE_DIAG]:
+    for flags in [SB, BLK]:
         st, F, _ = spd.spd_factor(h, dev_sym(A), "fp32", flags)
         check(h, st)
         try:
