@@ -881,9 +881,12 @@ def case_leg(args):
       resid_fp64  float64 residual, n x n, m right-hand sides
       resid_tc    tensor-core residual (digit planes and products)
       sweeps      triangular sweeps of an FP16 factor, m right-hand sides
+                  (super-block sweeps; sweeps_block: the 128-block sweeps)
       convert     scale + convert and the whole FP32 factorisation
       factor      the factorisation in --precs (look-ahead schedule)
-      factor_serial  the same on one stream (every kernel alone, for phase rates)"""
+      factor_serial  the same on one stream (every kernel alone, for phase rates)
+      cg          one Algorithm 2 solve on the model covariance (d = 2), m
+                  right-hand sides, Table 1's rule (tensor-core products for m >= 8)"""
     import torch
     import paper_1405_4644_gb300 as spd
     import workloads as W
@@ -904,7 +907,7 @@ def case_leg(args):
         C = torch.zeros(n, n, device=dev)
         for _ in range(args.reps):
             ok(spd.spd_gemm_update(h, "bf16", A, A, C))
-    else:
+    elif args.case != "cg":
         if args.case == "resid_fp64":
             A = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
             A = A + A.T
@@ -932,6 +935,17 @@ def case_leg(args):
             for _ in range(args.reps):
                 ok(spd.spd_factor_solve(h, F, B, R))
             spd.spd_factor_destroy(F)
+    if args.case == "cg":  # Algorithm 2 on the model covariance (d = 2), m right-hand sides, one solve
+        idx = torch.arange(n, dtype=torch.float64, device=dev)
+        Ac = (idx[:, None] - idx[None, :]).abs_().clamp_min_(1.0).pow_(2).reciprocal_()
+        Ac.diagonal().copy_(1.0 + torch.sqrt(idx + 1.0))
+        Bc = torch.rand(m, n, dtype=torch.float64, device=dev, generator=g).t()
+        Xc = torch.zeros(m, n, dtype=torch.float64, device=dev).t()
+        st, rep = spd.spd_cg(h, Ac, Bc, Xc, "fp32", opts={"tol": 1e-5, "crit": "abs2", "eta": 0.0,
+                                                          "maxit_inner": 5000, "resid": "auto"})
+        ok(st)
+        print(f"cg n={n} m={m}: {rep.time_ms:.3f} ms, {rep.iters_low}/{rep.iters_high}")
+        del Ac
     torch.cuda.synchronize()
     if args.phases:
         for p in spd.PHASES:
@@ -983,7 +997,7 @@ def main():
     ap.add_argument("--test-systems", type=int, default=32)
     ap.add_argument("--case", default=None,
                     choices=["gemm", "resid_fp64", "resid_tc", "sweeps", "sweeps_block", "convert", "factor",
-                             "factor_serial"],
+                             "factor_serial", "cg"],
                     help="run one kernel family on a fixed case (for profilers) and exit")
     ap.add_argument("--reps", type=int, default=2, help="--case: repetitions")
     ap.add_argument("--phases", action="store_true", help="--case: print the library's phase records")

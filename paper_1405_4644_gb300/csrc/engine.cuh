@@ -204,3 +204,4 @@ struct spd_lowrank;
 int lowrank_order(const spd_lowrank* P);
 spd_status lowrank_apply_cg(spd_handle* h, const spd_lowrank* P, int n, int m, const double* R, long ldr, double* Z,
                             long ldz);
+spd_status lowrank_reserve(spd_handle* h, const spd_lowrank* P, int n, int m);

@@ -171,9 +171,12 @@ static __global__ void k_out_to_dU(const float* __restrict__ O, int n, double* _
 
 // Cc = I + Uh^T Dh^{-1} Uh (32 x 32, float64), then its Cholesky factor Lc
 // (lower, row-major) -- one CTA of 1024 threads: thread (a, b) sums over n.
+// Writes Lc (the core's Cholesky factor, row-major) and, after it, Ci = the
+// core's inverse Lc^{-T} Lc^{-1} (the Woodbury apply multiplies by it).
 static __global__ void __launch_bounds__(1024) k_core_chol(const double* __restrict__ dh, const double* __restrict__ Uh,
                                                            int n, double* __restrict__ Lc, int* __restrict__ bad) {
     __shared__ double Cs[LR_RANK][LR_RANK + 1];
+    __shared__ double Li[LR_RANK][LR_RANK + 1];
     const int a = threadIdx.x / LR_RANK, b = threadIdx.x % LR_RANK;
     double s = (a == b) ? 1.0 : 0.0;
     for (int i = 0; i < n; ++i) s += Uh[(long)i * LR_RANK + a] * Uh[(long)i * LR_RANK + b] / dh[i];
@@ -202,64 +205,62 @@ static __global__ void __launch_bounds__(1024) k_core_chol(const double* __restr
     }
     __syncthreads();
     Lc[a * LR_RANK + b] = (b <= a) ? Cs[a][b] : 0.0;
+    if (threadIdx.x < 32) {  // lane b: column b of Lc^{-1} by forward substitution
+        const int bb = threadIdx.x;
+        for (int r = 0; r < LR_RANK; ++r) {
+            double v = (r == bb) ? 1.0 : 0.0;
+            for (int k = bb; k < r; ++k) v -= Cs[r][k] * Li[k][bb];
+            Li[r][bb] = (r >= bb) ? v / Cs[r][r] : 0.0;
+        }
+    }
+    __syncthreads();
+    double ci = 0.0;
+    for (int k = max(a, b); k < LR_RANK; ++k) ci += Li[k][a] * Li[k][b];
+    Lc[LR_RANK * LR_RANK + a * LR_RANK + b] = ci;
 }
 
 // Woodbury apply, p columns (float64, n x p, ld n):
 // out = s .* (q - Dh^{-1} Uh Cc^{-1} Uh^T q),  q = Dh^{-1} (s .* r)
-// step 1 (k_wb_proj): w[c][k] = sum_i Uh_ik q_i  (one CTA per column c, fixed order)
+// step 1 (k_wb_proj): partial projections, block (x, c) over rows
+// [256 x, 256 x + 256): wpart[(x p + c) R + k] = sum_i Uh_ik q_i
 static __global__ void __launch_bounds__(256) k_wb_proj(const double* __restrict__ R, long ldr, const double* __restrict__ sdg,
                                                         const double* __restrict__ dh, const double* __restrict__ Uh, int n,
-                                                        double* __restrict__ w) {
+                                                        int p, double* __restrict__ wpart) {
     __shared__ double red[8][LR_RANK];
-    const int c = blockIdx.x;
-    double acc[LR_RANK];
-#pragma unroll
-    for (int k = 0; k < LR_RANK; ++k) acc[k] = 0.0;
-    for (int i = threadIdx.x; i < n; i += 256) {
-        const double q = sdg[i] * R[(long)c * ldr + i] / dh[i];
-#pragma unroll
-        for (int k = 0; k < LR_RANK; ++k) acc[k] = fma(Uh[(long)i * LR_RANK + k], q, acc[k]);
-    }
+    const int c = blockIdx.y, i = blockIdx.x * 256 + threadIdx.x;
+    const double q = i < n ? sdg[i] * R[(long)c * ldr + i] / dh[i] : 0.0;
 #pragma unroll
     for (int k = 0; k < LR_RANK; ++k) {
-        double v = warp_sum(acc[k]);
+        double v = warp_sum(i < n ? Uh[(long)i * LR_RANK + k] * q : 0.0);
         if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
     }
     __syncthreads();
     if (threadIdx.x < LR_RANK) {
         double s = 0.0;
         for (int wv = 0; wv < 8; ++wv) s += red[wv][threadIdx.x];
-        // solve Cc y = w with Lc (forward, backward) by thread 0 below
-        red[0][threadIdx.x] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        // w holds the projection; the solve happens in k_wb_apply's prologue
-        for (int k = 0; k < LR_RANK; ++k) w[(long)c * LR_RANK + k] = red[0][k];
+        wpart[((long)blockIdx.x * p + c) * LR_RANK + threadIdx.x] = s;
     }
 }
 
-// step 2: y = Cc^{-1} w (per column, 32x32 triangular solves), then
-// out_i = s_i (q_i - (Uh_i . y) / dh_i)
+// step 2: w = the G partials in order, y = Ci w (Ci = Cc^{-1}, after Lc),
+// then out_i = s_i (q_i - (Uh_i . y) / dh_i)
 static __global__ void __launch_bounds__(256) k_wb_apply(const double* __restrict__ R, long ldr, const double* __restrict__ sdg,
                                                          const double* __restrict__ dh, const double* __restrict__ Uh,
-                                                         const double* __restrict__ Lc, const double* __restrict__ w,
-                                                         int n, int p, double* __restrict__ out, long ldo) {
-    __shared__ double ys[LR_RANK];
+                                                         const double* __restrict__ Lc, const double* __restrict__ wpart,
+                                                         int G, int n, int p, double* __restrict__ out, long ldo) {
+    __shared__ double ws[LR_RANK], ys[LR_RANK];
     const int c = blockIdx.y;
-    if (threadIdx.x == 0) {
-        double y[LR_RANK];
-        for (int k = 0; k < LR_RANK; ++k) {
-            double v = w[(long)c * LR_RANK + k];
-            for (int l = 0; l < k; ++l) v -= Lc[k * LR_RANK + l] * y[l];
-            y[k] = v / Lc[k * LR_RANK + k];
-        }
-        for (int k = LR_RANK - 1; k >= 0; --k) {
-            double v = y[k];
-            for (int l = k + 1; l < LR_RANK; ++l) v -= Lc[l * LR_RANK + k] * y[l];
-            y[k] = v / Lc[k * LR_RANK + k];
-        }
-        for (int k = 0; k < LR_RANK; ++k) ys[k] = y[k];
+    if (threadIdx.x < LR_RANK) {
+        double s = 0.0;
+        for (int x = 0; x < G; ++x) s += wpart[((long)x * p + c) * LR_RANK + threadIdx.x];
+        ws[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < LR_RANK) {
+        const double* ci = Lc + LR_RANK * LR_RANK + threadIdx.x * LR_RANK;
+        double y = 0.0;
+        for (int k = 0; k < LR_RANK; ++k) y = fma(ci[k], ws[k], y);
+        ys[threadIdx.x] = y;
     }
     __syncthreads();
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {

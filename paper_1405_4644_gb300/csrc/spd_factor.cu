@@ -383,7 +383,6 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                                                                                         F->LinvT);
             if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "block inverse launch failed");
         }
-        if (st == SPD_OK && prec != SPD_PREC_FP64) st = factor_couplings(h, F);
         if (st == SPD_OK && prec != SPD_PREC_FP64 && !(flags & SPD_FACTOR_BLOCK_SWEEPS) &&
             F->nblk128 >= 2 * SPD_SB_BLOCKS) {
             // inverses of the diagonal super-blocks for the super-block sweeps
@@ -407,6 +406,8 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                 if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "super-block inverse launch failed");
             }
         }
+        // the 128-block sweeps' couplings, only where they will run
+        if (st == SPD_OK && prec != SPD_PREC_FP64 && !F->Xsb) st = factor_couplings(h, F);
         if (st == SPD_OK) st = check_dev_status(h, rep, "spd_factor");
         if (tc) tc_gemm_destroy(tc);
         if (st != SPD_OK) return fail(st);

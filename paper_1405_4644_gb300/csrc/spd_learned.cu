@@ -210,12 +210,15 @@ __global__ void k_unscale(const double* __restrict__ V, const double* __restrict
         Vh[e] = V[e] / s[e % n];
 }
 
+// row chunks of the Woodbury projection (256 rows each)
+int wb_chunks(int n) { return std::max(1, ceil_div(n, 256)); }
+
 spd_status lowrank_alloc(spd_handle* h, spd_lowrank* P, int n) {
     P->h = h;
     P->n = n;
     CUDA_TRY(h, cudaMalloc(&P->dh, sizeof(double) * n));
     CUDA_TRY(h, cudaMalloc(&P->Uh, sizeof(double) * (size_t)n * LR_RANK));
-    CUDA_TRY(h, cudaMalloc(&P->Lc, sizeof(double) * LR_RANK * LR_RANK));
+    CUDA_TRY(h, cudaMalloc(&P->Lc, sizeof(double) * 2 * LR_RANK * LR_RANK));  // Lc, then the core's inverse
     CUDA_TRY(h, cudaMalloc(&P->sdg, sizeof(double) * n));
     return SPD_OK;
 }
@@ -246,26 +249,36 @@ spd_status build_core(spd_mlp* m, spd_lowrank* P, int n, int* dbad) {
 spd_status lowrank_apply_internal(spd_handle* h, const spd_lowrank* P, int n, int m, const double* R, long ldr,
                                   double* Z, long ldz, double* wbuf) {
     ProfScope ps(h, SPD_PHASE_VECTOR, 4.0 * LR_RANK * n * (double)m, 8.0 * (LR_RANK + 4) * n * (double)m);
-    ++h->launches, k_wb_proj<<<m, 256, 0, h->stream>>>(R, ldr, P->sdg, P->dh, P->Uh, n, wbuf);
+    const int G = wb_chunks(n);
+    ++h->launches, k_wb_proj<<<dim3(G, m), 256, 0, h->stream>>>(R, ldr, P->sdg, P->dh, P->Uh, n, m, wbuf);
     dim3 g(grid_for(n, 256, 2 * h->sms), m);
-    ++h->launches, k_wb_apply<<<g, 256, 0, h->stream>>>(R, ldr, P->sdg, P->dh, P->Uh, P->Lc, wbuf, n, m, Z, ldz);
+    ++h->launches, k_wb_apply<<<g, 256, 0, h->stream>>>(R, ldr, P->sdg, P->dh, P->Uh, P->Lc, wbuf, G, n, m, Z, ldz);
     LAUNCH_CHECK(h);
     return SPD_OK;
 }
 
 int lowrank_order(const spd_lowrank* P) { return P ? P->n : -1; }
 
-// Woodbury apply for the CG loop: grows the projection buffer on demand.
-spd_status lowrank_apply_cg(spd_handle* h, const spd_lowrank* Pc, int n, int m, const double* R, long ldr, double* Z,
-                            long ldz) {
+// The projection buffer of the Woodbury apply for m columns (grown on
+// demand; spd_cg sizes it before its inner steps, which may be captured).
+spd_status lowrank_reserve(spd_handle* h, const spd_lowrank* Pc, int n, int m) {
     spd_lowrank* P = const_cast<spd_lowrank*>(Pc);
-    if (P->wcap < m) {
+    const int need = wb_chunks(n) * LR_RANK * m;  // partial projections
+    if (P->wcap < need) {
         cudaFree(P->w);
         P->w = nullptr;
-        CUDA_TRY(h, cudaMalloc(&P->w, sizeof(double) * LR_RANK * m));
-        P->wcap = m;
+        CUDA_TRY(h, cudaMalloc(&P->w, sizeof(double) * need));
+        P->wcap = need;
     }
-    return lowrank_apply_internal(h, P, n, m, R, ldr, Z, ldz, P->w);
+    return SPD_OK;
+}
+
+// Woodbury apply for the CG loop.
+spd_status lowrank_apply_cg(spd_handle* h, const spd_lowrank* Pc, int n, int m, const double* R, long ldr, double* Z,
+                            long ldz) {
+    const spd_status st = lowrank_reserve(h, Pc, n, m);
+    if (st != SPD_OK) return st;
+    return lowrank_apply_internal(h, Pc, n, m, R, ldr, Z, ldz, Pc->w);
 }
 
 extern "C" spd_status spd_mlp_create(spd_handle* h, int hidden, unsigned long long seed, int bf16, spd_mlp** out) {
@@ -459,9 +472,11 @@ extern "C" spd_status spd_mlp_loss_grad(spd_mlp* m, int n, const double* A, int 
     WsPlan pl;
     size_t o_sd = pl.add<double>(n), o_Y = pl.add<double>(np), o_Q = pl.add<double>(np), o_E = pl.add<double>(np),
            o_G = pl.add<double>(np), o_Wv = pl.add<double>(np), o_Yh = pl.add<double>(np), o_Wh = pl.add<double>(np),
-           o_PY = pl.add<double>(LR_RANK * p), o_PW = pl.add<double>(LR_RANK * p), o_w = pl.add<double>(LR_RANK * p),
+           o_PY = pl.add<double>(LR_RANK * p), o_PW = pl.add<double>(LR_RANK * p),
+           o_w = pl.add<double>((size_t)wb_chunks(n) * LR_RANK * p),
            o_sums = pl.add<double>(2 * p + 2), o_coef = pl.add<double>(p), o_dh = pl.add<double>(n),
-           o_Uh = pl.add<double>((size_t)n * LR_RANK), o_Lc = pl.add<double>(LR_RANK * LR_RANK), o_bad = pl.add<int>(1);
+           o_Uh = pl.add<double>((size_t)n * LR_RANK), o_Lc = pl.add<double>(2 * LR_RANK * LR_RANK),
+           o_bad = pl.add<int>(1);
     if ((st = ws_reserve(h, pl.bytes)) != SPD_OK) return st;
     double *sd = ws_at<double>(h, o_sd), *Y = ws_at<double>(h, o_Y), *Q = ws_at<double>(h, o_Q),
            *E = ws_at<double>(h, o_E), *G = ws_at<double>(h, o_G), *Wv = ws_at<double>(h, o_Wv),

@@ -819,9 +819,11 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
     CUDA_TRY(h, cudaMemsetAsync(w.cg, 0, sizeof(CgCol) * m, s));
     const double* Zr = (cs.pc == SPD_PC_NONE) ? w.Rr : w.Z;
     // inner steps whose launches do not change from one step to the next
-    // (dense or banded float32/bf16 products, no preconditioner or Jacobi)
-    // replay as a CUDA graph of CG_GRAPH_STEPS steps, captured once per call;
-    // not while profiling (the phase records would be captured once)
+    // (every product; no preconditioner, Jacobi or the learned low-rank one;
+    // not the factor preconditioner, whose sweeps number their epochs, nor
+    // the float32-pair residual, which the host switches) replay as a CUDA
+    // graph of CG_GRAPH_STEPS steps, captured once per call; not while
+    // profiling (the phase records would be captured once)
     struct CgGraph {
         cudaGraphExec_t exec = nullptr;
         long kernels = 0;
@@ -829,7 +831,11 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             if (exec) cudaGraphExecDestroy(exec);
         }
     } cg_graph;
-    bool graph_ok = !h->prof_on && cs.matvec != MV_FP64 && (cs.pc == SPD_PC_NONE || cs.pc == SPD_PC_JACOBI);
+    bool graph_ok = !h->prof_on && cs.pc != SPD_PC_FACTOR && o.resid != SPD_RESID_DF32;
+    if (cs.pc == SPD_PC_LOWRANK) {
+        st = lowrank_reserve(h, cs.LR, n, m);
+        if (st != SPD_OK) return st;
+    }
     int outer = 0;
     IrSummary sm{};
     for (;;) {

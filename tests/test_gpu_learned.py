@@ -81,8 +81,9 @@ def test_loss_and_gradient_match_oracle_finite_differences(h):
     np.testing.assert_allclose(an, fd, rtol=2e-3, atol=1e-5 * np.abs(fd).max())
 
 
-def test_woodbury_apply_matches_dense_inverse(h):
-    n, H = 96, 32
+@pytest.mark.parametrize("n", [96, 700])  # one projection chunk; three, the last ragged
+def test_woodbury_apply_matches_dense_inverse(h, n):
+    H = 32
     A, pts, ell, nug = system(n, 8)
     net = _net(h, H, seed=4)
     try:
