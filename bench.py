@@ -414,15 +414,19 @@ DF32_OPS_PER_MADD = 12
 
 
 # DRAM bytes (read + write, ncu) of a phase's launches, measured on a smaller
-# case of the same kernels.  "solve": one forward + backward sweep pair at
-# n = 8192, m = 16 read 137.10 + 136.97 MB and wrote 0.22 + 3.12 MB; the
-# sweeps stream the factor once each, so the bytes scale with n^2.  A phase
-# in MEASURED_TRAFFIC_RATIO reports that ratio of DRAM bytes to algorithmic
-# bytes (over a capture of its kernels) times its algorithmic bytes per launch.
+# case of the same kernels.  "solve": one forward + backward pair of the
+# super-block sweeps at n = 8192, m = 16 moved 655 GB/s x 215 us + 586 GB/s x
+# 240 us (DRAM throughput x duration of each launch); the sweeps stream the
+# factor once each, so the bytes scale with n^2.  A phase in
+# MEASURED_TRAFFIC_RATIO reports that ratio of DRAM bytes to algorithmic bytes
+# (over a capture of its kernels) times its algorithmic bytes per launch.
 MEASURED_TRAFFIC = {
-    "solve": ((137097728 + 217344 + 136969472 + 3122944) / 8192 ** 2,
-              "ncu DRAM bytes of one forward + backward sweep pair at n = 8192, m = 16, scaled by n^2"),
+    "solve": ((655e9 * 215.17e-6 + 586e9 * 240.16e-6) / 8192 ** 2,
+              "ncu DRAM throughput x duration of one forward + backward super-block sweep pair at n = 8192, "
+              "m = 16, scaled by n^2"),
 }
+# FP32 rate of one SM: a one-CTA kernel's ceiling
+FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.07e9 / 1e12
 MEASURED_TRAFFIC_RATIO = {
     # one stream-K bulk update of an n = 8192 FP32 factorisation (block
     # columns 32-33: M = 4096, N = 256, K = 3968, 152 CTAs): 99.76 MB read +
@@ -464,7 +468,12 @@ def phase_roofline(dom, ph, per_kappa, n=None):
     elif dom == "resid_tc":
         r = {"bound": "hbm", "unit": "GB/s", "achieved": ph["bytes"] / sec / 1e9, "peak": peaks["hbm_gbs"],
              "peak_source": f"{src} copy bandwidth (the digit planes stream from HBM)"}
-    elif dom in ("trailing", "leaf", "panel"):
+    elif dom == "leaf":  # one CTA per 128 x 128 diagonal block, on the critical path
+        r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP32_SM_PEAK_TFLOPS,
+             "peak_source": "one SM's 128 FP32 lanes x 2 x 2.07 GHz (each leaf is one CTA on one SM by design; "
+                            "the concurrent lanes' work fills the other SMs)",
+             "frac_of_gpu": ph["flops"] / sec / 1e12 / FP32_SIMT_PEAK_TFLOPS}
+    elif dom in ("trailing", "panel", "inverses"):
         r = {"bound": "alu", "unit": "TFLOP/s", "achieved": ph["flops"] / sec / 1e12, "peak": FP32_SIMT_PEAK_TFLOPS,
              "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     else:

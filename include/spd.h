@@ -584,7 +584,10 @@ typedef enum spd_phase {
                                      factorisation's critical path (the
                                      last update of each block column before
                                      its diagonal block is factored)        */
-    SPD_PHASE_COUNT = 13
+    SPD_PHASE_INVERSES = 13,      /* once per factor: inverses of the diagonal
+                                     blocks and super-blocks, and the
+                                     128-block sweeps' couplings (A4)        */
+    SPD_PHASE_COUNT = 14
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

@@ -387,7 +387,7 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
 
 
 PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch", "trailing_x3",
-          "resid_df32", "resid_tc", "trailing_last"]
+          "resid_df32", "resid_tc", "trailing_last", "inverses"]
 
 
 def spd_profile_enable(h, on=True):

@@ -34,6 +34,7 @@ static __global__ void __launch_bounds__(RESID_ROWS) k_resid_partial(const doubl
     double acc[MT];
 #pragma unroll
     for (int c = 0; c < MT; ++c) acc[c] = 0.0;
+    double q0 = 0.0, q1 = 0.0, q2 = 0.0, q3 = 0.0;  // MT == 1: the interleaved accumulators
     float asum = 0.f;
     const double* Ai = A + (i < n ? i : 0);
     for (int jb = j0; jb < j1; jb += RESID_JT) {
@@ -46,7 +47,20 @@ static __global__ void __launch_bounds__(RESID_ROWS) k_resid_partial(const doubl
         __syncthreads();
         if (i < n) {
             const double* ap = Ai + (long)jb * lda;
-            if (jn == RESID_JT) {
+            if (MT == 1 && jn == RESID_JT && !rowabs) {
+                // one column: four interleaved accumulators (column jj into
+                // accumulator jj % 4) and sixteen loads in flight per thread,
+                // added in a fixed order below
+#pragma unroll 4
+                for (int jj = 0; jj < RESID_JT; jj += 4) {
+                    const double a0 = __ldg(ap + (long)jj * lda), a1 = __ldg(ap + (long)(jj + 1) * lda);
+                    const double a2 = __ldg(ap + (long)(jj + 2) * lda), a3 = __ldg(ap + (long)(jj + 3) * lda);
+                    q0 = fma(a0, xs[jj][0], q0);
+                    q1 = fma(a1, xs[jj + 1][0], q1);
+                    q2 = fma(a2, xs[jj + 2][0], q2);
+                    q3 = fma(a3, xs[jj + 3][0], q3);
+                }
+            } else if (jn == RESID_JT) {
 #pragma unroll 4
                 for (int jj = 0; jj < RESID_JT; ++jj) {
                     double a = __ldg(ap + (long)jj * lda);
@@ -65,6 +79,7 @@ static __global__ void __launch_bounds__(RESID_ROWS) k_resid_partial(const doubl
         }
     }
     if (i < n) {
+        if (MT == 1) acc[0] += (q0 + q1) + (q2 + q3);
 #pragma unroll
         for (int c = 0; c < MT; ++c)
             if (c < mc) P[((long)s * mtot + c0 + c) * n + i] = acc[c];

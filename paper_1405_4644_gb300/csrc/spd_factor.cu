@@ -377,7 +377,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (st == SPD_OK && prec != SPD_PREC_FP64) {
             // per-block inverses and sweep couplings: off the factorisation's
             // critical path, all blocks at once
-            ProfScope pinv(h, SPD_PHASE_LEAF, (double)F->nblk128 * 128.0 * 128.0 * 128.0 / 3.0,
+            ProfScope pinv(h, SPD_PHASE_INVERSES, (double)F->nblk128 * 128.0 * 128.0 * 128.0 / 3.0,
                            (double)F->nblk128 * (8.0 * 16384.0 + 16384.0));
             ++h->launches, k_block_inverse<<<F->nblk128, 256, block_inverse_smem(), s>>>(F->W, F->ldw, n, F->Dinv32,
                                                                                         F->LinvT);
@@ -400,7 +400,7 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
                     return true;
                 }();
                 (void)attr;
-                ProfScope pinv(h, SPD_PHASE_LEAF, (double)F->nsb * S * S * S / 3.0, 4.0 * F->nsb * S * S);
+                ProfScope pinv(h, SPD_PHASE_INVERSES, (double)F->nsb * S * S * S / 3.0, 4.0 * F->nsb * S * S);
                 ++h->launches, k_sb_inverse<<<dim3(F->sbb * SB_STRIPS, F->nsb), 256, sb_inverse_smem(), s>>>(
                     F->W, F->ldw, n, F->nblk128, F->LinvT, F->sbb, F->Xsb);
                 if (cudaGetLastError() != cudaSuccess) st = set_err(h, SPD_ERR_CUDA, "super-block inverse launch failed");

@@ -144,6 +144,8 @@ spd_status tc_bind_prepare(spd_handle* h, TcSetup& t, int n, int m, const double
     return SPD_OK;
 }
 
+// Column splits of the float64 residual: about four CTAs per SM, each split
+// at least four column tiles long
 int resid_splits(spd_handle* h, int n) {
     int rowblk = ceil_div(n, RESID_ROWS);
     int want = std::max(1, (4 * h->sms + rowblk - 1) / rowblk);
@@ -454,7 +456,7 @@ spd_status factor_couplings(spd_handle* h, spd_factor_t* F) {
     (void)attr;
     // distance 1 (NB - 1 per direction) and distance 2 (NB - 2 per direction)
     const int ncp = (NB - 1) + std::max(NB - 2, 0);
-    ProfScope ps(h, SPD_PHASE_LEAF, 2.0 * 2.0 * ncp * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * ncp * 16384.0);
+    ProfScope ps(h, SPD_PHASE_INVERSES, 2.0 * 2.0 * ncp * 128.0 * 128.0 * 128.0, 3.0 * 4.0 * 2.0 * ncp * 16384.0);
     ++h->launches, k_trsv_couplings<<<dim3(NB - 1, NB >= 3 ? 4 : 2), 256, trsv_couplings_smem(), h->stream>>>(
         F->W, F->ldw, F->n, NB, F->LinvT, F->Cpl);
     LAUNCH_CHECK(h);

@@ -84,3 +84,15 @@ def test_tensor_core_residual_is_hbm_bound():
     r = bench.roofline(ph, [{"prec_used": "fp16"}], 16384)
     assert r["bound"] == "hbm" and r["peak"] == peaks["hbm_gbs"]
     assert r["achieved"] == pytest.approx(by / 3.3e-3 / 1e9)
+
+
+def test_leaf_dominant_is_measured_against_one_sm():
+    """The leaves are one CTA each by design: their ceiling is one SM's FP32
+    rate; the fraction of the whole GPU is reported beside it."""
+    ph = phases(leaf=(650, 26.0, 650 * 128 ** 3 / 3.0, 650 * 128 * 128 * 4.0), solve=(23, 22.0, 0.0, 23 * 4.0 * 16384 ** 2))
+    r = bench.roofline(ph, [{"prec_used": "fp16"}], 16384)
+    assert r["kernel_phase"] == "leaf" and r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(bench.FP32_SM_PEAK_TFLOPS)
+    assert r["achieved"] == pytest.approx(650 * 128 ** 3 / 3.0 / 26e-3 / 1e12)
+    assert r["frac_of_gpu"] == pytest.approx(r["achieved"] / bench.FP32_SIMT_PEAK_TFLOPS)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
