@@ -44,9 +44,12 @@ struct BatchArgs {
     int polish;
 };
 
+// The panel's rows transposed: PnT[l * BLDP + i] = L[i][k0 + l] (rounded to the
+// update type), rows contiguous so that four rows are one 16-byte load.
+#define BLDP 516
 constexpr size_t batch_smem_bytes() {
     return (size_t)(BMAX / 32) * 32 * 33 * sizeof(float)  // Inv
-           + (size_t)BMAX * 33 * sizeof(float)            // panel
+           + (size_t)BMAX * 33 * sizeof(float)            // panel (PnT: 32 x BLDP floats fit in it)
            + (size_t)4 * BMAX * sizeof(double)            // x, r, d, rowabs
            + (size_t)2 * BMAX * sizeof(float);            // y, z
 }
@@ -112,11 +115,12 @@ __device__ void batch_lsolve(const float* W, const float* Inv, float* y, int n) 
             if (k0 + lane < n) y[k0 + lane] = s;
         }
         __syncthreads();
-        for (int i = tid; i < k0; i += NT) {  // y_i -= sum_c L[k0+c][i] z[k0+c]
-            float s = 0.f;
-            const float* col = W + (long)i * BLD + k0;
-            for (int c = 0; c < 32 && k0 + c < n; ++c) s += col[c] * y[k0 + c];
-            y[i] -= s;
+        // y_i -= sum_c L[k0+c][i] z[k0+c]: one warp per row i, lane c reading
+        // L[k0+c][i] (32 contiguous floats of W's column i), a fixed shuffle sum
+        for (int i = warp; i < k0; i += NT / 32) {
+            const float v = (k0 + lane < n) ? W[(long)i * BLD + k0 + lane] * y[k0 + lane] : 0.f;
+            const float s = warp_sum(v);
+            if (lane == 0) y[i] -= s;
         }
         __syncthreads();
     }
@@ -129,12 +133,30 @@ __device__ double batch_residual(const BatchSys& S, const double* x, double* r, 
     const int n = S.n;
     double rmax = 0.0, amax = 0.0, xmax = 0.0;
     for (int i = threadIdx.x; i < n; i += NT) {
-        double s = S.B[i], a = 0.0;
-        for (int j = 0; j < n; ++j) {
-            const double v = S.A[i + (long)j * S.lda];
-            s = fma(-v, x[j], s);
-            if (want_anorm) a += fabs(v);
+        // four interleaved accumulators (column j into j % 4), eight loads in
+        // flight, added in a fixed order
+        double q[4] = {0.0, 0.0, 0.0, 0.0}, a = 0.0;
+        const double* Ai = S.A + i;
+        int j = 0;
+        for (; j + 8 <= n; j += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = Ai[(long)(j + u) * S.lda];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                q[u & 3] = fma(v[u], x[j + u], q[u & 3]);
+                if (want_anorm) a += fabs(v[u]);
+            }
         }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {  // the last n % 8 columns (j is a multiple of 8 here)
+            if (j + u < n) {
+                const double v = Ai[(long)(j + u) * S.lda];
+                q[u & 3] = fma(v, x[j + u], q[u & 3]);
+                if (want_anorm) a += fabs(v);
+            }
+        }
+        const double s = S.B[i] - ((q[0] + q[1]) + (q[2] + q[3]));
         r[i] = s;
         rmax = fmax(rmax, fabs(s));
         xmax = fmax(xmax, fabs(x[i]));
@@ -182,9 +204,21 @@ __global__ void __launch_bounds__(NT, 1) k_batch_chol_ir(BatchArgs a) {
         }
         if (tid == 0) s_bad = 0;
         __syncthreads();
-        for (int j = 0; j < n; ++j)
-            for (int i = j + tid; i < n; i += NT)
-                W[i + (long)j * BLD] = (float)(ds[i] * S.A[i + (long)j * S.lda] * ds[j]);
+        // (every entry of the n x n block, four per thread at a time; only
+        // the lower triangle is kept)
+        for (int e0 = tid; e0 < n * n; e0 += 4 * NT) {
+            double v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * NT, j = e / n, i = e - j * n;
+                v[u] = (e < n * n && i >= j) ? S.A[i + (long)j * S.lda] : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u * NT, j = e / n, i = e - j * n;
+                if (e < n * n && i >= j) W[i + (long)j * BLD] = (float)(ds[i] * v[u] * ds[j]);
+            }
+        }
         __syncthreads();
         // factor (A1-A3) by 32-column panels
         const int nb = (n + 31) / 32;
@@ -255,35 +289,51 @@ __global__ void __launch_bounds__(NT, 1) k_batch_chol_ir(BatchArgs a) {
                     for (int l = 0; l < 32; ++l)
                         if (l <= c) s = fmaf(b[l], I[c * 33 + l], s);
                     W[(k0 + 32 + i) + (long)(k0 + c) * BLD] = s;
-                    Pn[i * 33 + c] = round_op(s, a.prec);
+                    Pn[c * BLDP + i] = round_op(s, a.prec);
                 }
             }
+            for (int e = tid; e < 32 * 4; e += NT) Pn[(e >> 2) * BLDP + R + (e & 3)] = 0.f;  // rows R.. of the last group
             __syncthreads();
-            // trailing update of the lower part, 4x4 register blocks
+            // trailing update of the lower part, 4x4 register blocks: consecutive
+            // threads take consecutive row groups bi of one column group bj, so
+            // that the panel reads are 16-byte broadcasts or contiguous and the
+            // updates of W are contiguous rows of a column
             const int Rb = (R + 3) / 4;
             for (int e = tid; e < Rb * Rb; e += NT) {
-                const int bi = e / Rb, bj = e - bi * Rb;
+                const int bj = e / Rb, bi = e - bj * Rb;
                 if (bj > bi) continue;
                 float acc[4][4] = {};
+#pragma unroll 8
                 for (int l = 0; l < 32; ++l) {
-                    float pi[4], pj[4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        pi[q] = (4 * bi + q < R) ? Pn[(4 * bi + q) * 33 + l] : 0.f;
-                        pj[q] = (4 * bj + q < R) ? Pn[(4 * bj + q) * 33 + l] : 0.f;
-                    }
+                    const float4 pi = *reinterpret_cast<const float4*>(Pn + l * BLDP + 4 * bi);
+                    const float4 pj = *reinterpret_cast<const float4*>(Pn + l * BLDP + 4 * bj);
+                    const float ip[4] = {pi.x, pi.y, pi.z, pi.w}, jq[4] = {pj.x, pj.y, pj.z, pj.w};
 #pragma unroll
                     for (int p = 0; p < 4; ++p)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(pi[p], pj[q], acc[p][q]);
+                        for (int q = 0; q < 4; ++q) acc[p][q] = fmaf(ip[p], jq[q], acc[p][q]);
                 }
+                const bool full = (bi > bj) && (4 * bi + 3 < R);  // four rows inside, below the diagonal block
 #pragma unroll
-                for (int p = 0; p < 4; ++p)
+                for (int q = 0; q < 4; ++q) {
+                    const int j = 4 * bj + q;
+                    if (j >= R) break;
+                    float* w = W + (k0 + 32 + 4 * bi) + (long)(k0 + 32 + j) * BLD;
+                    if (full) {
+                        float4 v = *reinterpret_cast<float4*>(w);
+                        v.x -= acc[0][q];
+                        v.y -= acc[1][q];
+                        v.z -= acc[2][q];
+                        v.w -= acc[3][q];
+                        *reinterpret_cast<float4*>(w) = v;
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int i = 4 * bi + p, j = 4 * bj + q;
-                        if (i < R && j <= i) W[(k0 + 32 + i) + (long)(k0 + 32 + j) * BLD] -= acc[p][q];
+                        for (int p = 0; p < 4; ++p) {
+                            const int i = 4 * bi + p;
+                            if (i < R && j <= i) w[p] -= acc[p][q];
+                        }
                     }
+                }
             }
             __syncthreads();
         }
