@@ -342,18 +342,30 @@ class Lanes:
         self.X = [torch.zeros(m, n, dtype=torch.float64, device=dev).t() for _ in range(count)]
 
     def run(self, systems, precs, opts, steps):
-        """steps x len(systems) solves; system i goes to lane i mod count.
-        Returns the reports of the last step, in system order."""
+        """steps x len(systems) solves, taken from one shared queue (solve q
+        is system q mod len(systems)): a lane that finishes takes the next
+        solve, so cheap systems do not leave a lane idle while an expensive
+        one runs.  Returns the report of each system's last solve."""
         import threading
         out = [None] * len(systems)
         err = []
+        total = steps * len(systems)
+        self.last_lane = [None] * len(systems)  # the lane (and X buffer) of each system's last solve
+        nxt = [0]
+        lock = threading.Lock()
 
         def work(lane):
             try:
-                for _ in range(steps):
-                    for i in range(lane, len(systems), len(self.handles)):
-                        k, A, B = systems[i]
-                        out[i] = solve_one(self.spd, self.handles[lane], A, B, self.X[lane], precs[i], opts, k)
+                while True:
+                    with lock:
+                        q = nxt[0]
+                        nxt[0] += 1
+                    if q >= total or err:
+                        return
+                    i = q % len(systems)
+                    k, A, B = systems[i]
+                    out[i] = solve_one(self.spd, self.handles[lane], A, B, self.X[lane], precs[i], opts, k)
+                    self.last_lane[i] = lane
             except Exception as e:  # noqa: BLE001 -- re-raised on the main thread
                 err.append(e)
 
@@ -1071,8 +1083,8 @@ def main():
     torch.cuda.synchronize()
 
     smi = SmiSampler(torch.cuda.current_device())
-    for hh in handles:
-        spd.spd_profile_enable(hh, True)
+    # no profiling in the timed region: its events would sit between the
+    # programmatically dependent launches and serialise them
     launches0 = sum(spd.spd_launch_count(hh) for hh in handles)
     barrier(world)
     torch.cuda.synchronize()
@@ -1093,21 +1105,14 @@ def main():
     clocks = smi.stop()
     ms = ev0.elapsed_time(ev1)
     launches = sum(spd.spd_launch_count(hh) for hh in handles) - launches0
-    phases = {}
-    for p in spd.PHASES:
-        recs = [spd.spd_profile_read(hh, p) for hh in handles]
-        phases[p] = {k: sum(r[k] for r in recs) for k in recs[0]}
-    for hh in handles:
-        spd.spd_profile_enable(hh, False)
     ms_max = max_over_ranks(ms, world)
     value = job_rate(len(systems) * args.steps, world, ms_max / 1e3)
 
     # dominant phase and its roofline
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
-                  "cond_est": fr.cond_est, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
+                  "cond_est": fr.cond_est, "cond_lower": fr.cond_lower, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
                   "iters_low": r.iters_low, "fell_back": r.fell_back, "berr": r.berr, "shift": fr.shift}
                  for (k, _, _), p, (fr, r) in zip(systems, precs, reps)]
-    roof_phases, roof_note = phases, "phases of the timed region"
     if True:
         # A launch's event time under concurrency (the lanes, and the factor's
         # look-ahead stream) includes sharing the SMs, so the kernel rooflines
@@ -1268,7 +1273,8 @@ def main():
                                              "digits per entry, 55 digit products), every residual"}[args.resid]},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                "energy": energy, "fp64_baseline": fp64, "per_kappa": per_kappa,
-               "phases": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in phases.items()}}
+               "phases": {k: {"ms": v["ms"], "launches": v["launches"]} for k, v in roof_phases.items()},
+               "phases_measured_on": roof_note}
         print(json.dumps(out), flush=True)
     if lanes:
         lanes.destroy()

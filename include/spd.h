@@ -195,9 +195,19 @@ typedef struct spd_report {
     double cond_est; /* spd_factor with AUTO: estimated 1-norm condition
                         number of the scaled matrix (Hager's estimator);
                         -1 when the FP16 factor broke down before it could
-                        be estimated; 0 for the other precisions           */
+                        be estimated; 0 when no FP16 factor ran (the
+                        pre-check below ruled it out) and for the other
+                        precisions                                          */
     double shift;    /* spd_factor with SPD_FACTOR_SHIFT: the sigma of the
                         factor actually kept (0 = no shift was needed)      */
+    double cond_lower; /* spd_factor with AUTO and n >= 4096: a lower bound
+                        on the 2-norm condition number of the scaled matrix
+                        from at most 16 Lanczos steps before any factor
+                        (Ritz values lie inside the spectrum); above 512
+                        (kappa u_fp16 > 1/4, eq. (iterref)) no FP16 factor
+                        is attempted.  +inf when the float32 products do
+                        not resolve the smallest eigenvalue; 0 when not
+                        taken                                               */
 } spd_report;
 
 typedef struct spd_handle spd_handle;
@@ -587,7 +597,10 @@ typedef enum spd_phase {
     SPD_PHASE_INVERSES = 13,      /* once per factor: inverses of the diagonal
                                      blocks and super-blocks, and the
                                      128-block sweeps' couplings (A4)        */
-    SPD_PHASE_COUNT = 14
+    SPD_PHASE_ESTIMATE = 14,      /* AUTO: the Lanczos condition bound before
+                                     any factor (symmetric products of the
+                                     scaled float32 matrix)                 */
+    SPD_PHASE_COUNT = 15
 } spd_phase;
 
 spd_status spd_profile_enable(spd_handle *h, int on);

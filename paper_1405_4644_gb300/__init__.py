@@ -71,7 +71,8 @@ class SpdOpts(C.Structure):
 class SpdReport(C.Structure):
     _fields_ = [("status", C.c_int), ("info", C.c_int), ("iters_low", C.c_int), ("iters_high", C.c_int),
                 ("prec_used", C.c_int), ("fell_back", C.c_int), ("berr", C.c_double), ("rel_resid", C.c_double),
-                ("time_ms", C.c_double), ("cond_est", C.c_double), ("shift", C.c_double)]
+                ("time_ms", C.c_double), ("cond_est", C.c_double), ("shift", C.c_double),
+                ("cond_lower", C.c_double)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -387,7 +388,7 @@ def spd_cg(h, A, B, X, matvec_prec="fp32", pc="none", pc_data=None, opts=None):
 
 
 PHASES = ["convert", "leaf", "trailing", "solve", "resid", "matvec", "vector", "panel", "batch", "trailing_x3",
-          "resid_df32", "resid_tc", "trailing_last", "inverses"]
+          "resid_df32", "resid_tc", "trailing_last", "inverses", "estimate"]
 
 
 def spd_profile_enable(h, on=True):

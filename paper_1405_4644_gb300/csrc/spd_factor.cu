@@ -21,6 +21,7 @@
 #include "k_leaf32.cuh"
 #include "k_gemm_simt.cuh"
 #include "k_trsv_sb.cuh"
+#include "k_lanczos.cuh"
 #include "gemm_tc.h"
 
 namespace {
@@ -274,9 +275,134 @@ int mirror_kind(int prec) {
 }
 size_t mirror_elem(int kind) { return kind == 5 ? 6 : kind == 1 ? 4 : kind == 4 ? 1 : 2; }
 
+// Extreme eigenvalues of the symmetric tridiagonal T (diagonal a[0..k-1],
+// off-diagonal b[0..k-2]) by bisection on Sturm counts (the number of
+// negative pivots of T - x I is the number of eigenvalues below x).
+static int sturm_below(const double* a, const double* b, int k, double x) {
+    int cnt = 0;
+    double d = 1.0;
+    for (int i = 0; i < k; ++i) {
+        d = a[i] - x - (i > 0 ? b[i - 1] * b[i - 1] / d : 0.0);
+        if (d == 0.0) d = -1e-300;  // x on an eigenvalue of a leading block: count it below
+        cnt += d < 0.0;
+    }
+    return cnt;
+}
+
+static void tridiag_extremes(const double* a, const double* b, int k, double* lo_out, double* hi_out) {
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < k; ++i) {  // Gershgorin interval
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < k ? fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    double l = lo, u = hi;  // smallest: the first x with one eigenvalue below
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(fabs(l), fabs(u)); ++it) {
+        const double mid = 0.5 * (l + u);
+        if (sturm_below(a, b, k, mid) >= 1) u = mid; else l = mid;
+    }
+    *lo_out = u;
+    l = lo, u = hi;  // largest: the first x with all k below
+    for (int it = 0; it < 200 && u - l > 1e-15 * std::max(fabs(l), fabs(u)); ++it) {
+        const double mid = 0.5 * (l + u);
+        if (sturm_below(a, b, k, mid) >= k) u = mid; else l = mid;
+    }
+    *hi_out = u;
+}
+
+// Lanczos lower bound on kappa_2 of the scaled matrix in W (float32 lower
+// triangle, row-major): at most LZ_MAXK steps, checked every four from the
+// eighth; stops as soon as the bound exceeds `stop_above` (or the Krylov
+// space becomes invariant).  *bound = theta_max / theta_min of the last
+// check (+inf when theta_min <= 0: the float32 products do not resolve
+// lambda_min), 0 when the scratch could not be had (no bound).
+spd_status lanczos_lower(spd_handle* h, const float* W, long ldw, int n, double stop_above, double* bound,
+                         int* steps) {
+    *bound = 0.0;
+    *steps = 0;
+    const int nb = ceil_div(n, LZ_T);
+    const long ldq = round_up(n, 4);
+    const size_t bytesP = sizeof(float) * (size_t)nb * nb * LZ_T;
+    const size_t bytesQ = sizeof(float) * (size_t)(LZ_MAXK + 2) * ldq;  // Q_0..Q_K and y
+    const size_t bytesD = sizeof(double) * ((LZ_MAXK + 1) * LZ_CHUNKS + LZ_CHUNKS + 2 * LZ_MAXK);
+    if (over_cap(h, bytesP + bytesQ + bytesD)) return SPD_OK;
+    cudaStream_t s = h->stream;
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, bytesP + bytesQ + bytesD, s) != cudaSuccess) {
+        cudaGetLastError();
+        return SPD_OK;  // no bound: the caller proceeds as without one
+    }
+    float* P = static_cast<float*>(mem);
+    float* Q = reinterpret_cast<float*>(static_cast<char*>(mem) + bytesP);
+    float* y = Q + (size_t)(LZ_MAXK + 1) * ldq;
+    double* dpart = reinterpret_cast<double*>(static_cast<char*>(mem) + bytesP + bytesQ);
+    double* npart = dpart + (LZ_MAXK + 1) * LZ_CHUNKS;
+    double* alpha = npart + LZ_CHUNKS;
+    double* beta = alpha + LZ_MAXK;
+    ProfScope pl(h, SPD_PHASE_ESTIMATE, 0.0, 0.0);
+    const long tiles = (long)nb * (nb + 1) / 2;
+    ++h->launches, k_lz_start<<<ceil_div(n, 256), 256, 0, s>>>(y, n);
+    ++h->launches, k_lz_orth<<<LZ_CHUNKS, 256, 0, s>>>(Q, ldq, y, n, -1, dpart, npart, alpha);
+    ++h->launches, k_lz_normalize<<<LZ_CHUNKS, 256, 0, s>>>(y, Q, n, -1, npart, beta);
+    spd_status st = SPD_OK;
+    double ha[LZ_MAXK], hb[LZ_MAXK];
+    int j = 0;
+    for (; j < LZ_MAXK; ++j) {
+        ++h->launches, k_lz_symv_tiles<<<(unsigned)tiles, 256, 0, s>>>(W, ldw, n, nb, Q + (size_t)j * ldq, P);
+        ++h->launches, k_lz_symv_reduce<<<nb, dim3(LZ_T, 8), 0, s>>>(P, n, nb, y);
+        ++h->launches, k_lz_dots<<<dim3(LZ_CHUNKS, j + 1), 256, 0, s>>>(Q, ldq, y, n, dpart);
+        ++h->launches, k_lz_orth<<<LZ_CHUNKS, 256, 0, s>>>(Q, ldq, y, n, j, dpart, npart, alpha);
+        ++h->launches, k_lz_normalize<<<LZ_CHUNKS, 256, 0, s>>>(y, Q + (size_t)(j + 1) * ldq, n, j, npart, beta);
+        const int k = j + 1;
+        if (k < 8 || (k % 4 && k < LZ_MAXK)) continue;
+        if (cudaGetLastError() != cudaSuccess) {
+            st = set_err(h, SPD_ERR_CUDA, "condition bound: launch failed");
+            break;
+        }
+        cudaError_t e = cudaMemcpyAsync(ha, alpha, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hb, beta, sizeof(double) * k, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = set_err(h, SPD_ERR_CUDA, "condition bound: %s", cudaGetErrorString(e));
+            break;
+        }
+        // an invariant subspace ends the iteration: T_k's Ritz values are then
+        // eigenvalues of As; stop at the first vanishing beta
+        int kk = k;
+        for (int i = 0; i < k - 1; ++i)
+            if (!(hb[i] > 1e-7 * (fabs(ha[i]) + fabs(ha[i + 1])))) {
+                kk = i + 1;
+                break;
+            }
+        double lo = 0.0, hi = 0.0;
+        tridiag_extremes(ha, hb, kk, &lo, &hi);
+        *bound = lo > 0.0 ? hi / lo : INFINITY;
+        *steps = kk;
+        if (!(*bound <= stop_above) || kk < k || !(hb[k - 1] > 1e-7 * fabs(ha[k - 1]))) break;
+    }
+    // work of the symmetric products that ran: 2 n^2 flops, the lower
+    // triangle read once (4 n^2 / 2 bytes) and the tile partials written and read
+    const double ran = std::min(j + 1, LZ_MAXK);
+    pl.r.flops = ran * 2.0 * n * (double)n;
+    pl.r.bytes = ran * (2.0 * n * (double)n + 2.0 * bytesP);
+    cudaFreeAsync(mem, s);
+    return st;
+}
+
 // One factorisation attempt in a fixed precision.
+// The AUTO pre-check of one attempt: when `lz` is given and n >= LZ_MIN_N,
+// the Lanczos bound on the freshly scaled matrix runs before the factor, and
+// a bound above lz->stop_above ends the attempt (SPD_ERR_NOT_SPD, lz->skip).
+struct LzCheck {
+    double stop_above;
+    double bound;
+    int steps;
+    bool skip;
+};
+constexpr int LZ_MIN_N = 4096;
+
 spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec, unsigned flags,
-                       spd_factor_t** out, spd_report* rep, double shift = 0.0) {
+                       spd_factor_t** out, spd_report* rep, double shift = 0.0, LzCheck* lz = nullptr) {
     spd_factor_t* F = new spd_factor_t();
     F->h = h;
     F->n = n;
@@ -346,6 +472,14 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         if (cudaGetLastError() != cudaSuccess) return fail(set_err(h, SPD_ERR_CUDA, "convert launch failed"));
         spd_status st = check_dev_status(h, rep, "spd_factor");
         if (st != SPD_OK) return fail(st);
+        if (lz && n >= LZ_MIN_N && prec != SPD_PREC_FP64) {
+            st = lanczos_lower(h, F->W, F->ldw, n, lz->stop_above, &lz->bound, &lz->steps);
+            if (st != SPD_OK) return fail(st);
+            if (!(lz->bound <= lz->stop_above)) {
+                lz->skip = true;
+                return fail(SPD_ERR_NOT_SPD);
+            }
+        }
 
         FCtx c{h, F, Mirror{F->Wh, F->ldh, kind, (long)n * F->ldh}, nullptr};
         TcGemm* tc = nullptr;
@@ -514,16 +648,21 @@ extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda,
     CUDA_TRY(h, cudaEventRecord(h->e0, h->stream));
     spd_status st;
     int used = prec;
-    double kappa = 0.0;
+    double kappa = 0.0, cond_lower = 0.0;
     if (prec == SPD_PREC_AUTO) {
         // FP16 tensor-core factor first; keep it when the estimated
         // kappa u_fp16 <= 1/4 (eq. (iterref) with margin), else FP32, and
         // FP64 if FP32 breaks down too.  kappa_1 / sqrt(n) stands in for the
         // 2-norm condition number (kappa_1 / n <= kappa_2 <= kappa_1 for a
         // symmetric matrix).
+        // Before the FP16 factor (n >= LZ_MIN_N): a Lanczos lower bound on
+        // kappa_2 of the scaled matrix; above 2^11 / 4 the same test can
+        // only fail, so the FP16 attempt is skipped.
         used = SPD_PREC_FP16;
-        st = factor_once(h, n, A, lda, SPD_PREC_FP16, flags, F, rep);
-        if (st == SPD_ERR_NOT_SPD) kappa = -1.0;  // the FP16 factor broke down before any estimate
+        LzCheck lz{0x1p11 * 0.25, 0.0, 0, false};
+        st = factor_once(h, n, A, lda, SPD_PREC_FP16, flags, F, rep, 0.0, &lz);
+        cond_lower = lz.bound;
+        if (st == SPD_ERR_NOT_SPD && !lz.skip) kappa = -1.0;  // the FP16 factor broke down before any estimate
         if (st == SPD_OK && n > 0) {
             st = cond_estimate(h, *F, A, lda, &kappa);
             if (st != SPD_OK || !(kappa / sqrt((double)n) * 0x1p-11 <= 0.25)) {
@@ -566,6 +705,7 @@ extern "C" spd_status spd_factor(spd_handle* h, int n, const double* A, int lda,
         rep->status = st;
         rep->prec_used = used;
         rep->cond_est = kappa;
+        rep->cond_lower = cond_lower;
         rep->shift = sigma;
         if (st == SPD_OK) rep->info = 0;  // a failed attempt before the kept factor leaves no trace
     }

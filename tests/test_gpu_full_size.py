@@ -50,7 +50,7 @@ def test_benchmark_workload_three_lanes():
     try:
         reps = lanes.run(systems, ["auto"] * len(KAPPAS), {"tol": 1e-14, "crit": "berr", "resid": "tc"}, 1)
         torch.cuda.synchronize()
-        Xs = [lanes.X[i].cpu().numpy() for i in range(len(KAPPAS))]  # lane i solved system i
+        Xs = [lanes.X[lanes.last_lane[i]].cpu().numpy() for i in range(len(KAPPAS))]
     finally:
         lanes.destroy()
     g = np.random.default_rng(7)

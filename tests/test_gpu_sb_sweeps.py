@@ -84,6 +84,22 @@ def test_superblock_and_block_sweeps_agree(h, n, m, prec):
     assert err <= 32 * n * kappa_scaled(A) * U32, err
 
 
+@pytest.mark.parametrize("n,m", [(4097, 16), (9000, 40)])
+def test_superblock_sweeps_repeat_bit_for_bit(h, n, m):
+    """Every sum of the super-block sweeps is formed in an order fixed by the
+    launch's grid (stream-K pieces added in CTA order), not by timing:
+    repeated applications of one factor are identical."""
+    A = W.gram_shifted(n, seed=7 * n + m, shift=0.5)
+    Rh = W.gaussian_rhs(n, m, 13)
+    st, F, _ = spd.spd_factor(h, dev_sym(A), "fp32", SB)
+    check(h, st)
+    try:
+        Z = [apply_factor(h, F, Rh) for _ in range(3)]
+    finally:
+        spd.spd_factor_destroy(F)
+    assert np.array_equal(Z[0], Z[1]) and np.array_equal(Z[0], Z[2])
+
+
 def test_small_orders_keep_the_block_sweeps(h):
     """Below two super-blocks no inverses are formed: the flag changes nothing."""
     n, m = 1919, 4  # fifteen 128-row blocks
