@@ -877,7 +877,7 @@ def learned_leg(args):
     def summ(rows):
         a = np.array([r[:3] for r in rows], dtype=np.float64)
         return {"median_iters": float(np.median(a[:, 0])), "mean_ms": float(np.mean(a[:, 1])),
-                "max_berr": float(np.max(a[:, 2]))}
+                "median_ms": float(np.median(a[:, 1])), "max_berr": float(np.max(a[:, 2]))}
     out = {"leg": "learned", "metric": "PCG iterations and ms per FP64-accurate solve, learned vs Jacobi",
            "config": {"workload": f"Matern-3/2 family, n={n}, {args.train_systems} training systems, "
                                   f"{args.test_systems} held-out", "n": n},
@@ -886,7 +886,12 @@ def learned_leg(args):
            "jacobi_pcg": summ(res["jacobi"]), "learned_pcg": summ(res["learned"]),
            "learned_fallbacks": int(sum(r[3] for r in res["learned"])), "chol_ir_fp32": summ(res["chol_ir"]),
            "iteration_gain_median": float(np.median([j[0] / max(l[0], 1) for j, l in zip(res["jacobi"],
-                                                                                       res["learned"])]))}
+                                                                                       res["learned"])])),
+           # per held-out system: Jacobi-PCG time / learned PCG time (the learned
+           # time includes building M from the network's output)
+           "time_gain_median": float(np.median([j[1] / max(l[1], 1e-9) for j, l in zip(res["jacobi"],
+                                                                                    res["learned"])])),
+           "learned_faster_systems": int(sum(l[1] < j[1] for j, l in zip(res["jacobi"], res["learned"])))}
     print(json.dumps(out), flush=True)
     return 0
 

@@ -205,3 +205,14 @@ int lowrank_order(const spd_lowrank* P);
 spd_status lowrank_apply_cg(spd_handle* h, const spd_lowrank* P, int n, int m, const double* R, long ldr, double* Z,
                             long ldz);
 spd_status lowrank_reserve(spd_handle* h, const spd_lowrank* P, int n, int m);
+// The arrays of a built low-rank preconditioner, for the CG kernels that fuse
+// its Woodbury apply into the inner step (rank LOWRANK_RANK): G = 256-row
+// chunks, wpart = G x m x rank partial projections, dpart = G x m x 2 dot
+// partials (both inside the buffer lowrank_reserve sized for m columns).
+constexpr int LOWRANK_RANK = 32;
+struct LowrankView {
+    const double *sdg, *dh, *Uh, *Lc;
+    double *wpart, *dpart;
+    int G;
+};
+LowrankView lowrank_view(const spd_lowrank* P, int n, int m);

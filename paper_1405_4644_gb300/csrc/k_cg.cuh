@@ -365,3 +365,142 @@ static __global__ void k_jacobi_dinv(const double* __restrict__ A, long lda, int
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dinv[i] = 1.0 / A[(long)i * lda + i];
 }
+
+// ---- learned preconditioner (Woodbury form) fused into the inner step -------
+// M r = S (Dh^{-1} s - Dh^{-1} Uh Ci Uh^T Dh^{-1} s) with s = S r, Ci the
+// inverse of the 32 x 32 core, rows in 256-row chunks x.
+
+// The update of k_cg_update for block (x, c) = rows [256 x, 256 x + 256) of
+// column c (alpha from the partials of p^T q), then the chunk's partial
+// projection wpart[(x m + c) 32 + k] = sum_i Uh_ik q_i, q = sdg .* r ./ dh:
+// warp w takes rows 32 w .. 32 w + 31, lane k column k, the eight warps'
+// sums added in warp order.
+static __global__ void __launch_bounds__(256) k_cg_update_wb(const double* __restrict__ part, int G2, int n, int m,
+                                                      CgCol* __restrict__ cols, int parity, double* __restrict__ E,
+                                                      double* __restrict__ Rr, const double* __restrict__ P,
+                                                      const double* __restrict__ Qv, const double* __restrict__ sdg,
+                                                      const double* __restrict__ dh, const double* __restrict__ Uh,
+                                                      double* __restrict__ wpart) {
+    static_assert(LOWRANK_RANK == 32, "one lane per column of Uh");
+    __shared__ double s_alpha;
+    __shared__ double qs[256];
+    __shared__ double red[8][LOWRANK_RANK];
+    const int c = blockIdx.y, x = blockIdx.x, i0 = 256 * x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (w == 0) {
+        const double pq = warp_sum_parts(part, G2, m, c, 0, lane);
+        if (lane == 0) {
+            const CgCol& st = cols[c];
+            s_alpha = st.done ? 0.0 : st.rho[parity] / pq;
+        }
+    }
+    __syncthreads();
+    const double a = s_alpha;
+    {
+        const int i = i0 + threadIdx.x;
+        double q = 0.0;
+        if (i < n) {
+            const long k = (long)c * n + i;
+            double r = Rr[k];
+            if (a != 0.0) {
+                E[k] = fma(a, P[k], E[k]);
+                r = fma(-a, Qv[k], r);
+                Rr[k] = r;
+            }
+            q = sdg[i] * r / dh[i];
+        }
+        qs[threadIdx.x] = q;
+    }
+    __syncthreads();
+    double u[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int i = i0 + 32 * w + r;
+        u[r] = i < n ? Uh[(long)i * LOWRANK_RANK + lane] : 0.0;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc = fma(u[r], qs[32 * w + r], acc);
+    red[w][lane] = acc;
+    __syncthreads();
+    if (threadIdx.x < LOWRANK_RANK) {
+        double s = 0.0;
+#pragma unroll
+        for (int wv = 0; wv < 8; ++wv) s += red[wv][threadIdx.x];
+        wpart[((long)x * m + c) * LOWRANK_RANK + threadIdx.x] = s;
+    }
+    if (x == 0 && threadIdx.x == 0) cols[c].alpha = a;
+}
+
+// The apply for block (x, c): w = column c's G partial projections (chunk
+// order within eight groups, then group order), y = Ci w, z_i = s_i (q_i -
+// (Uh_i . y) / dh_i) for the chunk's rows, and the chunk's partials of r^T z
+// and r^T r into dpart[(x m + c) 2 + {0, 1}] (the layout k_cg_pupdate reads).
+static __global__ void __launch_bounds__(256) k_wb_apply_dot(const double* __restrict__ Rr, const double* __restrict__ sdg,
+                                                      const double* __restrict__ dh, const double* __restrict__ Uh,
+                                                      const double* __restrict__ Lc, const double* __restrict__ wpart,
+                                                      int G, int n, int m, double* __restrict__ Z,
+                                                      double* __restrict__ dpart) {
+    __shared__ double red[8][LOWRANK_RANK];
+    __shared__ double ws[LOWRANK_RANK], ys[LOWRANK_RANK];
+    __shared__ double rd[2][8];
+    const int c = blockIdx.y, x = blockIdx.x, k = threadIdx.x & 31, g = threadIdx.x >> 5;
+    {
+        double s = 0.0;
+        for (int xx = g; xx < G; xx += 8) s += wpart[((long)xx * m + c) * LOWRANK_RANK + k];
+        red[g][k] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < LOWRANK_RANK) {
+        double s = 0.0;
+#pragma unroll
+        for (int gv = 0; gv < 8; ++gv) s += red[gv][threadIdx.x];
+        ws[threadIdx.x] = s;
+    }
+    __syncthreads();
+    {   // y_k = sum_j Ci[k][j] w_j: group g takes j = 4 g .. 4 g + 3
+        const double* ci = Lc + LOWRANK_RANK * LOWRANK_RANK + k * LOWRANK_RANK + 4 * g;
+        double y = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y = fma(ci[j], ws[4 * g + j], y);
+        red[g][k] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x < LOWRANK_RANK) {
+        double y = 0.0;
+#pragma unroll
+        for (int gv = 0; gv < 8; ++gv) y += red[gv][threadIdx.x];
+        ys[threadIdx.x] = y;
+    }
+    __syncthreads();
+    const int i = 256 * x + threadIdx.x;
+    double s1 = 0.0, s2 = 0.0;
+    if (i < n) {
+        const long kk = (long)c * n + i;
+        const double r = Rr[kk];
+        const double q = sdg[i] * r / dh[i];
+        double u = 0.0;
+#pragma unroll
+        for (int j = 0; j < LOWRANK_RANK; ++j) u = fma(Uh[(long)i * LOWRANK_RANK + j], ys[j], u);
+        const double z = sdg[i] * (q - u / dh[i]);
+        Z[kk] = z;
+        s1 = r * z;
+        s2 = r * r;
+    }
+    s1 = warp_sum(s1);
+    s2 = warp_sum(s2);
+    if ((threadIdx.x & 31) == 0) {
+        rd[0][threadIdx.x >> 5] = s1;
+        rd[1][threadIdx.x >> 5] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            t1 += rd[0][q];
+            t2 += rd[1][q];
+        }
+        dpart[((long)x * m + c) * 2 + 0] = t1;
+        dpart[((long)x * m + c) * 2 + 1] = t2;
+    }
+}

@@ -222,44 +222,77 @@ static __global__ void __launch_bounds__(1024) k_core_chol(const double* __restr
 // Woodbury apply, p columns (float64, n x p, ld n):
 // out = s .* (q - Dh^{-1} Uh Cc^{-1} Uh^T q),  q = Dh^{-1} (s .* r)
 // step 1 (k_wb_proj): partial projections, block (x, c) over rows
-// [256 x, 256 x + 256): wpart[(x p + c) R + k] = sum_i Uh_ik q_i
+// [256 x, 256 x + 256): wpart[(x p + c) R + k] = sum_i Uh_ik q_i.  Warp w
+// takes rows 32 w .. 32 w + 31 of the chunk, lane k column k (each row of Uh
+// one coalesced 256-byte load across the warp); the eight warps' sums are
+// added in warp order.
 static __global__ void __launch_bounds__(256) k_wb_proj(const double* __restrict__ R, long ldr, const double* __restrict__ sdg,
                                                         const double* __restrict__ dh, const double* __restrict__ Uh, int n,
                                                         int p, double* __restrict__ wpart) {
+    static_assert(LR_RANK == 32, "one lane per column of Uh");
+    __shared__ double qs[256];
     __shared__ double red[8][LR_RANK];
-    const int c = blockIdx.y, i = blockIdx.x * 256 + threadIdx.x;
-    const double q = i < n ? sdg[i] * R[(long)c * ldr + i] / dh[i] : 0.0;
-#pragma unroll
-    for (int k = 0; k < LR_RANK; ++k) {
-        double v = warp_sum(i < n ? Uh[(long)i * LR_RANK + k] * q : 0.0);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+    const int c = blockIdx.y, i0 = blockIdx.x * 256, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    {
+        const int i = i0 + threadIdx.x;
+        qs[threadIdx.x] = i < n ? sdg[i] * R[(long)c * ldr + i] / dh[i] : 0.0;
     }
+    __syncthreads();
+    double u[32];
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const int i = i0 + 32 * w + r;
+        u[r] = i < n ? Uh[(long)i * LR_RANK + lane] : 0.0;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) acc = fma(u[r], qs[32 * w + r], acc);
+    red[w][lane] = acc;
     __syncthreads();
     if (threadIdx.x < LR_RANK) {
         double s = 0.0;
+#pragma unroll
         for (int wv = 0; wv < 8; ++wv) s += red[wv][threadIdx.x];
         wpart[((long)blockIdx.x * p + c) * LR_RANK + threadIdx.x] = s;
     }
 }
 
-// step 2: w = the G partials in order, y = Ci w (Ci = Cc^{-1}, after Lc),
-// then out_i = s_i (q_i - (Uh_i . y) / dh_i)
+// step 2: w = the G partials (in chunk order within each of eight groups,
+// then group order), y = Ci w (Ci = Cc^{-1}, after Lc), then
+// out_i = s_i (q_i - (Uh_i . y) / dh_i).  Every CTA forms w and y itself
+// with all 256 threads: thread (g, k) = (tid / 32, tid % 32).
 static __global__ void __launch_bounds__(256) k_wb_apply(const double* __restrict__ R, long ldr, const double* __restrict__ sdg,
                                                          const double* __restrict__ dh, const double* __restrict__ Uh,
                                                          const double* __restrict__ Lc, const double* __restrict__ wpart,
                                                          int G, int n, int p, double* __restrict__ out, long ldo) {
+    __shared__ double red[8][LR_RANK];
     __shared__ double ws[LR_RANK], ys[LR_RANK];
-    const int c = blockIdx.y;
-    if (threadIdx.x < LR_RANK) {
+    const int c = blockIdx.y, k = threadIdx.x & 31, g = threadIdx.x >> 5;
+    {
         double s = 0.0;
-        for (int x = 0; x < G; ++x) s += wpart[((long)x * p + c) * LR_RANK + threadIdx.x];
-        ws[threadIdx.x] = s;
+        for (int x = g; x < G; x += 8) s += wpart[((long)x * p + c) * LR_RANK + k];
+        red[g][k] = s;
     }
     __syncthreads();
     if (threadIdx.x < LR_RANK) {
-        const double* ci = Lc + LR_RANK * LR_RANK + threadIdx.x * LR_RANK;
+        double s = 0.0;
+#pragma unroll
+        for (int gv = 0; gv < 8; ++gv) s += red[gv][threadIdx.x];
+        ws[threadIdx.x] = s;
+    }
+    __syncthreads();
+    {   // y_k = sum_j Ci[k][j] w_j: group g takes j = 4 g .. 4 g + 3
+        const double* ci = Lc + LR_RANK * LR_RANK + k * LR_RANK + 4 * g;
         double y = 0.0;
-        for (int k = 0; k < LR_RANK; ++k) y = fma(ci[k], ws[k], y);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) y = fma(ci[j], ws[4 * g + j], y);
+        red[g][k] = y;
+    }
+    __syncthreads();
+    if (threadIdx.x < LR_RANK) {
+        double y = 0.0;
+#pragma unroll
+        for (int gv = 0; gv < 8; ++gv) y += red[gv][threadIdx.x];
         ys[threadIdx.x] = y;
     }
     __syncthreads();
@@ -267,7 +300,7 @@ static __global__ void __launch_bounds__(256) k_wb_apply(const double* __restric
         const double q = sdg[i] * R[(long)c * ldr + i] / dh[i];
         double u = 0.0;
 #pragma unroll
-        for (int k = 0; k < LR_RANK; ++k) u = fma(Uh[(long)i * LR_RANK + k], ys[k], u);
+        for (int kk = 0; kk < LR_RANK; ++kk) u = fma(Uh[(long)i * LR_RANK + kk], ys[kk], u);
         out[(long)c * ldo + i] = sdg[i] * (q - u / dh[i]);
     }
 }

@@ -259,11 +259,17 @@ spd_status lowrank_apply_internal(spd_handle* h, const spd_lowrank* P, int n, in
 
 int lowrank_order(const spd_lowrank* P) { return P ? P->n : -1; }
 
+LowrankView lowrank_view(const spd_lowrank* P, int n, int m) {
+    static_assert(LR_RANK == LOWRANK_RANK, "one rank for the kernels and the view");
+    const int G = wb_chunks(n);
+    return LowrankView{P->sdg, P->dh, P->Uh, P->Lc, P->w, P->w + (long)G * LR_RANK * m, G};
+}
+
 // The projection buffer of the Woodbury apply for m columns (grown on
 // demand; spd_cg sizes it before its inner steps, which may be captured).
 spd_status lowrank_reserve(spd_handle* h, const spd_lowrank* Pc, int n, int m) {
     spd_lowrank* P = const_cast<spd_lowrank*>(Pc);
-    const int need = wb_chunks(n) * LR_RANK * m;  // partial projections
+    const int need = wb_chunks(n) * (LR_RANK + 2) * m;  // partial projections, then dot partials
     if (P->wcap < need) {
         cudaFree(P->w);
         P->w = nullptr;

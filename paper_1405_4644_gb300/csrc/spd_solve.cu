@@ -889,12 +889,23 @@ spd_status cg_ir_core(spd_handle* h, CgWs& w, int n, int m, const double* A, lon
             }
             LAUNCH_CHECK(h);
             ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.P, w.Q, nullptr, nullptr, n, m, w.part);
+            if (lowrank) {
+                // the Woodbury apply fused into the update and the next dots:
+                // as many launches per step as Jacobi-PCG
+                const LowrankView v = lowrank_view(cs.LR, n, m);
+                ++(h)->launches, k_cg_update_wb<<<dim3(v.G, m), 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.E, w.Rr,
+                                                                            w.P, w.Q, v.sdg, v.dh, v.Uh, v.wpart);
+                ++(h)->launches, k_wb_apply_dot<<<dim3(v.G, m), 256, 0, s>>>(w.Rr, v.sdg, v.dh, v.Uh, v.Lc, v.wpart, v.G,
+                                                                            n, m, w.Z, v.dpart);
+                ++(h)->launches, k_cg_pupdate<<<gv, 256, 0, s>>>(v.dpart, v.G, n, m, w.cg, par, w.active, w.P, w.Pf, Zr);
+                LAUNCH_CHECK(h);
+                return SPD_OK;
+            }
             ++(h)->launches, k_cg_update<<<gv, 256, 0, s>>>(w.part, w.G2, n, m, w.cg, par, w.E, w.Rr, w.P, w.Q,
                                            cs.pc == SPD_PC_JACOBI ? cs.dinv : nullptr, w.Z);
             LAUNCH_CHECK(h);
-            if (fac || lowrank) {
-                sst = fac ? lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0)
-                          : lowrank_apply_cg(h, cs.LR, n, m, w.Rr, n, w.Z, n);
+            if (fac) {
+                sst = lp_apply(h, cs.F, n, m, w.Rr, n, w.Yz, w.Z, n, nullptr, 0);
                 if (sst != SPD_OK) return sst;
             }
             ++(h)->launches, k_dot2<<<dim3(w.G2, m), 256, 0, s>>>(w.Rr, Zr, w.Rr, w.Rr, n, m, w.part);

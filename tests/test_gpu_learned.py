@@ -106,6 +106,40 @@ def test_woodbury_apply_matches_dense_inverse(h, n):
     np.testing.assert_allclose(Zd.cpu().numpy(), M @ R, rtol=1e-5, atol=1e-7 * np.abs(M @ R).max())
 
 
+@pytest.mark.parametrize("n,m", [(700, 1), (700, 3), (1300, 2)])
+def test_learned_pcg_fused_step_graph_and_direct_agree(n, m):
+    """The learned PCG's inner step fuses the Woodbury apply into the CG
+    update (projection partials) and the next dots: it reaches the relative
+    target against the float64 solution, and the steps replayed from a CUDA
+    graph give the iterates of the same kernels launched one by one
+    (profiling on), bit for bit."""
+    A, pts, ell, nug = system(n, 9)
+    B = W.gaussian_rhs(n, m, 10)
+    out = []
+    for prof in (False, True):
+        hh = spd.spd_create(torch.cuda.current_stream())
+        net = _net(hh, 32, seed=6)
+        try:
+            spd.spd_profile_enable(hh, prof)
+            Ad = torch.from_numpy(A).cuda()
+            Fg = torch.from_numpy(LO.features(A, pts, ell, nug).astype(np.float32)).cuda()
+            st, P = spd.spd_lowrank_build(net, Ad, Fg)
+            assert st == 0
+            X = torch.zeros((m, n), dtype=torch.float64, device="cuda").t()
+            Bd = torch.from_numpy(np.ascontiguousarray(B.T)).cuda().t()
+            st, rep = spd.spd_cg(hh, Ad, Bd, X, "fp64", "lowrank", P,
+                                 opts={"tol": 1e-10, "crit": "rel2", "eta": 1e-12, "maxit_inner": 5000})
+            spd.spd_lowrank_destroy(P)
+            assert st == 0
+            out.append((X.cpu().numpy(), rep.iters_low))
+        finally:
+            spd.spd_mlp_destroy(net)
+            spd.spd_destroy(hh)
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
+    x_ref = np.linalg.solve(A, B)
+    assert np.max(np.abs(out[0][0] - x_ref)) <= 1e-7 * np.max(np.abs(x_ref))
+
+
 def _pcg_iters(h, A, b, pc, P=None):
     Ad = torch.from_numpy(A).cuda()
     X = torch.zeros((1, len(b)), dtype=torch.float64, device="cuda").t()
