@@ -1113,6 +1113,76 @@ def main():
     ms_max = max_over_ranks(ms, world)
     value = job_rate(len(systems) * args.steps, world, ms_max / 1e3)
 
+    # e2e right after the device-resident timing, before the extra roofline
+    # step and the host-side forward errors (LAPACK threads on every core)
+    e2e = None
+    if not args.no_e2e:
+        import numpy as np
+        hostA = [torch.empty((args.n, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
+        hostB = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
+        hostX = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in handles]
+        for (k, A, B), ha, hb in zip(systems, hostA, hostB):
+            ha.copy_(A)
+            hb.copy_(B.t())
+        torch.cuda.synchronize()
+        e2e_steps = max(1, args.steps)
+        import threading
+
+        def host_lane(j, errs, queue):
+            # solves from one shared queue, as in the device-resident timing
+            hh = handles[j]
+            try:
+                while True:
+                    with queue["lock"]:
+                        q = queue["next"]
+                        queue["next"] += 1
+                    if q >= queue["total"] or errs:
+                        return
+                    i = q % len(systems)
+                    st = spd.lib().spd_solve_ir_host(hh, args.n, args.m, hostA[i].data_ptr(), args.n,
+                                                     hostB[i].data_ptr(), args.n, hostX[j].data_ptr(), args.n,
+                                                     spd.PREC[precs[i]], spd._opts(opts),
+                                                     ctypes.byref(spd.SpdReport()))
+                    if st != spd.SPD_OK:
+                        raise RuntimeError("e2e: " + spd.spd_last_error_string(hh))
+            except Exception as e:  # noqa: BLE001 -- re-raised below
+                errs.append(e)
+
+        def host_steps(steps):
+            errs = []
+            queue = {"lock": threading.Lock(), "next": 0, "total": steps * len(systems)}
+            th = [threading.Thread(target=host_lane, args=(j, errs, queue)) for j in range(len(handles))]
+            for x in th:
+                x.start()
+            for x in th:
+                x.join()
+            if errs:
+                raise errs[0]
+
+        host_steps(1)  # untimed: the handles' device copies of A, B, X are allocated here
+        # the host link's rate for one pinned copy of each system's A, alone
+        # (untimed; context for the number)
+        tmp = torch.empty((args.n, args.n), dtype=torch.float64, device=dev)
+        h2d_each = []
+        for ha in hostA:
+            torch.cuda.synchronize()
+            c0 = time.perf_counter()
+            tmp.copy_(ha, non_blocking=True)
+            torch.cuda.synchronize()
+            h2d_each.append(8.0 * args.n * args.n / (time.perf_counter() - c0) / 1e9)
+        h2d_gbs = h2d_each[0]
+        del tmp
+        barrier(world)
+        t0 = time.perf_counter()
+        host_steps(e2e_steps)
+        t = time.perf_counter() - t0
+        t = max_over_ranks(t, world)
+        e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
+               "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
+               "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
+               "h2d_gbs_one_copy": h2d_gbs, "h2d_gbs_each_system": h2d_each, "cpu_affinity": affinity,
+               "mems_allowed": host_numa_info()}
+
     # dominant phase and its roofline
     per_kappa = [{"kappa": k, "prec": p, "prec_used": spd.PREC_NAME.get(fr.prec_used, fr.prec_used),
                   "cond_est": fr.cond_est, "cond_lower": fr.cond_lower, "factor_ms": fr.time_ms, "solve_ms": r.time_ms, "iters": r.iters_high,
@@ -1162,63 +1232,6 @@ def main():
         j = clocks["avg_power_w"] * ms / 1e3
         energy = {"j_per_solve": j / (len(systems) * args.steps), "avg_power_w": clocks["avg_power_w"],
                   "source": "nvidia-smi power.draw mean x time, gross"}
-
-    e2e = None
-    if not args.no_e2e:
-        import numpy as np
-        hostA = [torch.empty((args.n, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
-        hostB = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in systems]
-        hostX = [torch.empty((args.m, args.n), dtype=torch.float64, pin_memory=True) for _ in handles]
-        for (k, A, B), ha, hb in zip(systems, hostA, hostB):
-            ha.copy_(A)
-            hb.copy_(B.t())
-        torch.cuda.synchronize()
-        e2e_steps = max(1, min(args.steps, 2))
-
-        def host_lane(j, errs, steps):
-            hh = handles[j]
-            try:
-                for _ in range(steps):
-                    for i in range(j, len(systems), len(handles)):
-                        st = spd.lib().spd_solve_ir_host(hh, args.n, args.m, hostA[i].data_ptr(), args.n,
-                                                         hostB[i].data_ptr(), args.n, hostX[j].data_ptr(), args.n,
-                                                         spd.PREC[precs[i]], spd._opts(opts),
-                                                         ctypes.byref(spd.SpdReport()))
-                        if st != spd.SPD_OK:
-                            raise RuntimeError("e2e: " + spd.spd_last_error_string(hh))
-            except Exception as e:  # noqa: BLE001 -- re-raised below
-                errs.append(e)
-
-        import threading
-
-        def host_steps(steps):
-            errs = []
-            th = [threading.Thread(target=host_lane, args=(j, errs, steps)) for j in range(len(handles))]
-            for x in th:
-                x.start()
-            for x in th:
-                x.join()
-            if errs:
-                raise errs[0]
-
-        host_steps(1)  # untimed: the handles' device copies of A, B, X are allocated here
-        # the host link's rate for one pinned copy of A, alone (untimed; context for the number)
-        tmp = torch.empty((args.n, args.n), dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
-        c0 = time.perf_counter()
-        tmp.copy_(hostA[0], non_blocking=True)
-        torch.cuda.synchronize()
-        h2d_gbs = 8.0 * args.n * args.n / (time.perf_counter() - c0) / 1e9
-        del tmp
-        barrier(world)
-        t0 = time.perf_counter()
-        host_steps(e2e_steps)
-        t = time.perf_counter() - t0
-        t = max_over_ranks(t, world)
-        e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
-               "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
-               "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
-               "h2d_gbs_one_copy": h2d_gbs, "cpu_affinity": affinity, "mems_allowed": host_numa_info()}
 
     # float64 blocked Cholesky on the same GPU (the plain baseline), one system
     fp64 = None

@@ -173,13 +173,38 @@ static __global__ void k_out_to_dU(const float* __restrict__ O, int n, double* _
 // (lower, row-major) -- one CTA of 1024 threads: thread (a, b) sums over n.
 // Writes Lc (the core's Cholesky factor, row-major) and, after it, Ci = the
 // core's inverse Lc^{-T} Lc^{-1} (the Woodbury apply multiplies by it).
-static __global__ void __launch_bounds__(1024) k_core_chol(const double* __restrict__ dh, const double* __restrict__ Uh,
-                                                           int n, double* __restrict__ Lc, int* __restrict__ bad) {
+// The core's Gram term over row chunks: block x (1024 threads) stages rows
+// [CORE_ROWS x, CORE_ROWS (x + 1)) of Uh and 1/dh in shared memory; thread
+// (a, b) writes part[x][a][b] = sum over the chunk's rows, in row order, of
+// Uh_ia Uh_ib (1/dh_i).
+#define CORE_ROWS 128
+static __global__ void __launch_bounds__(1024) k_core_gram(const double* __restrict__ dh, const double* __restrict__ Uh,
+                                                           int n, double* __restrict__ part) {
+    __shared__ double Us[CORE_ROWS][LR_RANK];
+    __shared__ double rd[CORE_ROWS];
+    const int i0 = blockIdx.x * CORE_ROWS, rows = min(CORE_ROWS, n - i0);
+    for (int e = threadIdx.x; e < CORE_ROWS * LR_RANK; e += 1024) {
+        const int r = e / LR_RANK, k = e % LR_RANK;
+        Us[r][k] = r < rows ? Uh[(long)(i0 + r) * LR_RANK + k] : 0.0;
+    }
+    if (threadIdx.x < CORE_ROWS) rd[threadIdx.x] = threadIdx.x < rows ? 1.0 / dh[i0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    const int a = threadIdx.x / LR_RANK, b = threadIdx.x % LR_RANK;
+    double s = 0.0;
+#pragma unroll 8
+    for (int r = 0; r < CORE_ROWS; ++r) s = fma(Us[r][a] * Us[r][b], rd[r], s);
+    part[(long)blockIdx.x * LR_RANK * LR_RANK + threadIdx.x] = s;
+}
+
+// Cc = I + the G chunk partials (in chunk order), then its Cholesky factor Lc
+// and the inverse Ci = Lc^{-T} Lc^{-1}.
+static __global__ void __launch_bounds__(1024) k_core_chol(const double* __restrict__ part, int G,
+                                                           double* __restrict__ Lc, int* __restrict__ bad) {
     __shared__ double Cs[LR_RANK][LR_RANK + 1];
     __shared__ double Li[LR_RANK][LR_RANK + 1];
     const int a = threadIdx.x / LR_RANK, b = threadIdx.x % LR_RANK;
     double s = (a == b) ? 1.0 : 0.0;
-    for (int i = 0; i < n; ++i) s += Uh[(long)i * LR_RANK + a] * Uh[(long)i * LR_RANK + b] / dh[i];
+    for (int x = 0; x < G; ++x) s += part[(long)x * LR_RANK * LR_RANK + threadIdx.x];
     Cs[a][b] = s;
     __syncthreads();
     if (threadIdx.x < 32) {  // warp 0: Cholesky of Cs in place, lane = row

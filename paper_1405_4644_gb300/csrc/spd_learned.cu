@@ -238,7 +238,14 @@ spd_status build_core(spd_mlp* m, spd_lowrank* P, int n, int* dbad) {
     spd_handle* h = m->h;
     ++h->launches, k_out_to_dU<<<grid_for(n, 256, 4 * h->sms), 256, 0, h->stream>>>(m->Ob, n, P->dh, P->Uh);
     CUDA_TRY(h, cudaMemsetAsync(dbad, 0, sizeof(int), h->stream));
-    ++h->launches, k_core_chol<<<1, 1024, 0, h->stream>>>(P->dh, P->Uh, n, P->Lc, dbad);
+    // the Gram term over 128-row chunks on many SMs, then one CTA for the
+    // 32 x 32 core (one float64 division per row, not per row and entry)
+    const int G = ceil_div(n, CORE_ROWS);
+    double* part = nullptr;
+    CUDA_TRY(h, cudaMallocAsync(&part, sizeof(double) * (size_t)G * LR_RANK * LR_RANK, h->stream));
+    ++h->launches, k_core_gram<<<G, 1024, 0, h->stream>>>(P->dh, P->Uh, n, part);
+    ++h->launches, k_core_chol<<<1, 1024, 0, h->stream>>>(part, G, P->Lc, dbad);
+    cudaFreeAsync(part, h->stream);
     LAUNCH_CHECK(h);
     return SPD_OK;
 }
