@@ -1173,14 +1173,18 @@ def main():
         h2d_gbs = h2d_each[0]
         del tmp
         barrier(world)
+        smi_e2e = SmiSampler(torch.cuda.current_device())
+        smi_e2e.start()
         t0 = time.perf_counter()
         host_steps(e2e_steps)
         t = time.perf_counter() - t0
+        clocks_e2e = smi_e2e.stop()
         t = max_over_ranks(t, world)
         e2e = {"value": job_rate(len(systems) * e2e_steps, world, t), "unit": UNIT,
                "h2d_bytes_per_step": len(systems) * 8 * (args.n * args.n + args.n * args.m),
                "d2h_bytes_per_step": len(systems) * 8 * args.n * args.m,
-               "h2d_gbs_one_copy": h2d_gbs, "h2d_gbs_each_system": h2d_each, "cpu_affinity": affinity,
+               "h2d_gbs_one_copy": h2d_gbs, "h2d_gbs_each_system": h2d_each, "clocks": clocks_e2e,
+               "cpu_affinity": affinity,
                "mems_allowed": host_numa_info()}
 
     # dominant phase and its roofline
