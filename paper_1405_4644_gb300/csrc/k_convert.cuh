@@ -59,44 +59,6 @@ __device__ __forceinline__ float scaled_f32(double a, double di, double dj) {
     return (b >> 63) ? -v : v;
 }
 
-// W (row-major, ldw) lower triangle <- d_i A_ij d_j for i >= j, rounded to
-// T.  A is column-major (lda); element (i, j) lives at A[i + j*lda].  A
-// 32x32 tile is read along i (coalesced in A) and written along j
-// (coalesced in W) through shared memory.  Tiles strictly above the
-// diagonal are skipped.  Non-finite entries raise SPD_DEV_NONFINITE.  For
-// float32 W the scaling avoids float64 arithmetic (scaled_f32; d is positive
-// and normal).
-template <typename T>
-static __global__ void k_scale_convert(const double* __restrict__ A, long lda, int n,
-                                const double* __restrict__ d, T* __restrict__ W, long ldw,
-                                DevStatus* st) {
-    __shared__ T tile[32][33];
-    int bi = blockIdx.y, bj = blockIdx.x;  // tile row (i) and column (j)
-    if (bj > bi) return;
-    int i0 = bi * 32, j0 = bj * 32;
-    int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-    bool bad = false;
-    // read: columns j0+jj, rows i0+tx (contiguous in A)
-    for (int jj = ty; jj < 32; jj += 8) {
-        int i = i0 + tx, j = j0 + jj;
-        T v = T(0);
-        if (i < n && j < n && j <= i) {
-            const double a = A[(long)j * lda + i];
-            if (((unsigned long long)__double_as_longlong(a) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
-                bad = true;
-            if constexpr (sizeof(T) == 8) v = d[i] * a * d[j];
-            else v = scaled_f32(a, d[i], d[j]);
-        }
-        tile[tx][jj] = v;  // tile[i_local][j_local]
-    }
-    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
-    __syncthreads();
-    // write: rows i0+ii, columns j0+tx (contiguous in W)
-    for (int ii = ty; ii < 32; ii += 8) {
-        int i = i0 + ii, j = j0 + tx;
-        if (i < n && j < n && j <= i) W[(long)i * ldw + j] = tile[ii][tx];
-    }
-}
 
 // W[i][i] += sigma: the shifted factorisation of SPD_FACTOR_SHIFT.
 template <typename T>
@@ -144,4 +106,66 @@ static __global__ void k_convert_band(const double* __restrict__ A, long lda, in
         Ab[e] = v;
     }
     if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+}
+
+// W (row-major, ldw) lower triangle <- d_i A_ij d_j for i >= j, rounded to
+// T.  A is column-major (lda); element (i, j) lives at A[i + j*lda].  Only
+// the 64 x 64 tiles of the lower triangle are launched (a triangular grid:
+// block t -> tile (bi, bj), bj <= bi).  Thread (tx, ty) = (tid % 32, tid / 32)
+// reads rows i0 + tx and i0 + 32 + tx of the columns j0 + ty + 8 k (coalesced
+// in A), all sixteen loads in flight before any is converted; the tile goes
+// back along W's rows (coalesced in W) through shared memory.  Non-finite
+// entries raise SPD_DEV_NONFINITE.  For float32 W the scaling avoids float64
+// arithmetic (scaled_f32; d is positive and normal).
+template <typename T>
+static __global__ void __launch_bounds__(256) k_scale_convert(const double* __restrict__ A, long lda, int n,
+                                                                const double* __restrict__ d, T* __restrict__ W,
+                                                                long ldw, DevStatus* st) {
+    __shared__ T tile[64][65];  // tile[i_local][j_local]
+    const long t = blockIdx.x;
+    int bi = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((long)(bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while ((long)bi * (bi + 1) / 2 > t) --bi;
+    const int bj = (int)(t - (long)bi * (bi + 1) / 2);
+    const int i0 = bi * 64, j0 = bj * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double a[16];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + 32 * h + tx, j = j0 + ty + 8 * k;
+            a[2 * k + h] = (i < n && j < n && j <= i) ? A[(long)j * lda + i] : 0.0;
+        }
+    const double di0 = (i0 + tx < n) ? d[i0 + tx] : 0.0;
+    const double di1 = (i0 + 32 + tx < n) ? d[i0 + 32 + tx] : 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int j = j0 + ty + 8 * k;
+        const double dj = j < n ? d[j] : 0.0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + 32 * h + tx;
+            const double v = a[2 * k + h];
+            T w = T(0);
+            if (i < n && j < n && j <= i) {
+                if (((unsigned long long)__double_as_longlong(v) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull)
+                    bad = true;
+                const double di = h ? di1 : di0;
+                if constexpr (sizeof(T) == 8) w = di * v * dj;
+                else w = scaled_f32(v, di, dj);
+            }
+            tile[32 * h + tx][ty + 8 * k] = w;
+        }
+    }
+    if (bad) dev_raise(st, SPD_DEV_NONFINITE);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + ty + 8 * k, j = j0 + 32 * h + tx;
+            if (i < n && j < n && j <= i) W[(long)i * ldw + j] = tile[ty + 8 * k][32 * h + tx];
+        }
 }

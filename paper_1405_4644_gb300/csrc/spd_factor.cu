@@ -315,7 +315,10 @@ static void tridiag_extremes(const double* a, const double* b, int k, double* lo
 // eighth; stops as soon as the bound exceeds `stop_above` (or the Krylov
 // space becomes invariant).  *bound = theta_max / theta_min of the last
 // check (+inf when theta_min <= 0: the float32 products do not resolve
-// lambda_min), 0 when the scratch could not be had (no bound).
+// lambda_min), 0 when the scratch could not be had (no bound).  From the
+// twelfth step on it also stops when the bound is below half the threshold
+// and grew by less than 10 % since the previous check: the decision then
+// falls to the test after the FP16 factor, as it would without a bound.
 spd_status lanczos_lower(spd_handle* h, const float* W, long ldw, int n, double stop_above, double* bound,
                          int* steps) {
     *bound = 0.0;
@@ -346,6 +349,7 @@ spd_status lanczos_lower(spd_handle* h, const float* W, long ldw, int n, double 
     ++h->launches, k_lz_normalize<<<LZ_CHUNKS, 256, 0, s>>>(y, Q, n, -1, npart, beta);
     spd_status st = SPD_OK;
     double ha[LZ_MAXK], hb[LZ_MAXK];
+    double prev = 0.0;
     int j = 0;
     for (; j < LZ_MAXK; ++j) {
         ++h->launches, k_lz_symv_tiles<<<(unsigned)tiles, 256, 0, s>>>(W, ldw, n, nb, Q + (size_t)j * ldq, P);
@@ -379,6 +383,8 @@ spd_status lanczos_lower(spd_handle* h, const float* W, long ldw, int n, double 
         *bound = lo > 0.0 ? hi / lo : INFINITY;
         *steps = kk;
         if (!(*bound <= stop_above) || kk < k || !(hb[k - 1] > 1e-7 * fabs(ha[k - 1]))) break;
+        if (k >= 12 && *bound <= 0.5 * stop_above && *bound <= 1.1 * prev) break;  // settled well below
+        prev = *bound;
     }
     // work of the symmetric products that ran: 2 n^2 flops, the lower
     // triangle read once (4 n^2 / 2 bytes) and the tile partials written and read
@@ -457,11 +463,13 @@ spd_status factor_once(spd_handle* h, int n, const double* A, int lda, int prec,
         ProfScope* pconv = new ProfScope(h, SPD_PHASE_CONVERT, 3.0 * n * (double)n / 2.0,
                                          8.0 * n * (double)n / 2.0 + (prec == SPD_PREC_FP64 ? 8.0 : 4.0) * n * (double)n / 2.0);
                                          ++(h)->launches, k_diag_scale<<<ceil_div(n, 256), 256, 0, s>>>(A, lda, n, (flags & SPD_SCALE_DIAG) ? 1 : 0, F->d, h->dst);
-        dim3 cg(ceil_div(n, 32), ceil_div(n, 32)), cb(32, 8);
+        const long nt = ceil_div(n, 64), ntiles = nt * (nt + 1) / 2;  // lower-triangle 64 x 64 tiles
         if (prec == SPD_PREC_FP64)
-            ++(h)->launches, k_scale_convert<double><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W64, F->ldw, h->dst);
+            ++(h)->launches, k_scale_convert<double><<<(unsigned)ntiles, 256, 0, s>>>(A, lda, n, F->d, F->W64,
+                                                                                          F->ldw, h->dst);
         else
-            ++(h)->launches, k_scale_convert<float><<<cg, cb, 0, s>>>(A, lda, n, F->d, F->W, F->ldw, h->dst);
+            ++(h)->launches, k_scale_convert<float><<<(unsigned)ntiles, 256, 0, s>>>(A, lda, n, F->d, F->W,
+                                                                                         F->ldw, h->dst);
         if (shift > 0.0) {  // SPD_FACTOR_SHIFT: factor the scaled matrix plus shift I
             if (prec == SPD_PREC_FP64)
                 ++(h)->launches, k_add_diag<double><<<ceil_div(n, 256), 256, 0, s>>>(F->W64, F->ldw, n, shift);
