@@ -11,10 +11,11 @@
 // the inverse.  One persistent cooperative kernel per sweep runs three
 // grid-wide phases per super-block, separated by bounded grid barriers:
 //   F   the SBB (SBB + 1) / 2 tile products X_I[b][c] r_I[c] (c <= b; for the
-//       backward sweep X_I[c][b]^T r_I[c], c >= b) into partial tiles, and
+//       backward sweep X_I[c][b]^T r_I[c], c >= b) into partial tiles; the
+//       last tile of block row b to arrive (an atomic count) adds the row's
+//       partials in a fixed order into y_I[b], written to the output vector
+//       (never over r_I, which other tiles of the phase may still read); and
 //       the fix-up of the previous panel update's split rows (below);
-//   A2  y_I[b] = the sum of row block b's partial tiles in a fixed order,
-//       written over r_I;
 //   B   the panel update: units (J, c) = the tile L_{J, I c} (backward
 //       L_{I c, J}^T) times y_I[c], J-major over every remaining 128-row block
 //       J, in equal contiguous ranges over all CTAs ("stream-K"), so the
@@ -26,7 +27,9 @@
 //       subtracted from r_J for every other row.
 // Every result is formed in an order fixed by the launch's grid, not by
 // timing.  The chain of the 128-block sweeps (one cross-SM hand-over per 128
-// rows) becomes three barriers per S rows.  The product of a 128x128 tile
+// rows) becomes two barriers per S rows.  The right-hand sides Y are reduced
+// in place and the result goes to O (forward: Y = the caller's vectors, O =
+// scratch; backward: Y = that scratch, O = the caller's vectors).  The product of a 128x128 tile
 // with a 128 x MC block uses the register tiles of k_trsv32.cuh.
 #pragma once
 #include "k_trsv32.cuh"
@@ -37,11 +40,13 @@ struct SbArgs {
     int n, NB;            // order and number of 128-blocks
     const float* X;       // super-block inverses: NS blocks of S x S floats, row-major
     int S, SBB, NS;       // super-block order (= 128 SBB), 128-blocks per super-block, super-blocks
-    float* Y;             // n x m, column-major (ld n), in place
-    int c0, mc;           // columns [c0, c0 + mc) in this pass
+    float* Y;             // right-hand sides, n x m column-major (ld n), reduced in place
+    int c0, mc;           // columns [c0, c0 + mc) of Y in this pass
+    float* O;             // the sweep's result, column-major (ld n), columns [oc0, oc0 + mc)
+    int oc0;
     float* P;             // partial tiles of phase F: SBB (SBB + 1) / 2 x 128 x MC floats
     float* P2;            // partial slots of phase B: 2 gridDim.x x 128 x MC floats
-    int* bar;             // [0] barrier arrivals, [1] abort (both zero at launch)
+    int* bar;             // [0] barrier arrivals, [1] abort, then NS SBB block-row tile counts (zero at launch)
     unsigned long long wait_ns;
     DevStatus* st;
     const int* gate;      // (may be NULL) return at once when *gate == 0
@@ -143,8 +148,8 @@ __device__ __forceinline__ void sb_stage(float* Yk, const SbArgs& a, long r0, in
     }
 }
 
-// Blocks [cs0, cs1) of y_I into YI (block c at YI + c 128 tv_ys), loads
-// issued eight per thread at a time
+// Blocks [cs0, cs1) of y_I (from the output vector O) into YI (block c at
+// YI + c 128 tv_ys), loads issued eight per thread at a time
 template <int MC>
 __device__ __forceinline__ void sb_stage_range(float* YI, const SbArgs& a, int jb0, int cs0, int cs1) {
     constexpr int BATCH = 8;
@@ -159,7 +164,7 @@ __device__ __forceinline__ void sb_stage_range(float* YI, const SbArgs& a, int j
                 const int blk = cs0 + e / (128 * MC), rem = e - (blk - cs0) * 128 * MC;
                 const int l = rem & 127, c = rem >> 7;
                 const long row = (long)(jb0 + blk) * 128 + l;
-                if (c < a.mc && row < a.n) v[k] = __ldcg(a.Y + (long)(a.c0 + c) * a.n + row);
+                if (c < a.mc && row < a.n) v[k] = __ldcg(a.O + (long)(a.oc0 + c) * a.n + row);
             }
         }
 #pragma unroll
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* YI = reinterpret_cast<float*>(smem_raw);  // [SBB][128][tv_ys] staged blocks of y_I (F: one)
     constexpr int YB = 128 * tv_ys<MC>();           // floats per staged block
-    __shared__ int s_abort;
+    __shared__ int s_abort, s_last;
     if (a.gate && *a.gate == 0) return;  // refinement over (capturable solves)
     const int tid = threadIdx.x;
     const int tq = tid >> 3, ts = tid & 7;
@@ -274,26 +279,38 @@ __global__ void __launch_bounds__(256, 1) k_trsv_sb(SbArgs a) {
                     for (int cc = 0; cc < MC; ++cc) pt[(4 * tq + j) * MC + cc] = acc[j][cc];
             }
             __syncthreads();
-        }
-        if (!sb_barrier(a, ++nbar, &s_abort)) return;
-        // A2: y_I[b] = its partials in order (forward c = 0..b, backward c =
-        // b..nb-1), the elements spread over every CTA, each one's loads
-        // issued together
-        for (int e = g * 256 + tid; e < nb * 128 * MC; e += G * 256) {
-            const int b = e / (128 * MC), rem = e - b * 128 * MC, r = rem / MC, cc = rem - r * MC;
-            float t[SPD_SB_BLOCKS];
-#pragma unroll
-            for (int k = 0; k < SPD_SB_BLOCKS; ++k) {
-                const int c = FWD ? k : b + k;
-                const bool in = FWD ? k <= b : c < nb;
-                t[k] = in ? __ldcg(a.P + ((long)(FWD ? sb_tri(b, c) : sb_tri(c, b)) * 128 + r) * MC + cc) : 0.f;
+            // the last tile of block row b to arrive adds the row's partials
+            // in c order (forward c = 0..b, backward c = b..nb-1) into y_I[b]
+            // in O, all of a thread's loads in flight together
+            if (tid == 0) {
+                __threadfence();
+                const int cnt = FWD ? b + 1 : nb - b;
+                s_last = atomicAdd(a.bar + 2 + t * a.SBB + b, 1) == cnt - 1;
+                __threadfence();
             }
-            float s = 0.f;
+            __syncthreads();
+            if (s_last) {
+                constexpr int EPT = (128 * MC + 255) / 256;
+                float v[SPD_SB_BLOCKS][EPT];
 #pragma unroll
-            for (int k = 0; k < SPD_SB_BLOCKS; ++k)
-                if (FWD ? k <= b : b + k < nb) s += t[k];
-            const long row = (long)(jb0 + b) * 128 + r;
-            if (cc < a.mc && row < a.n) a.Y[(long)(a.c0 + cc) * a.n + row] = s;
+                for (int k = 0; k < SPD_SB_BLOCKS; ++k)
+#pragma unroll
+                    for (int i = 0; i < EPT; ++i) {
+                        const int e = tid + 256 * i, c2 = FWD ? k : b + k;
+                        const bool in = (FWD ? k <= b : c2 < nb) && e < 128 * MC;
+                        v[k][i] = in ? __ldcg(a.P + (long)(FWD ? sb_tri(b, c2) : sb_tri(c2, b)) * 128 * MC + e) : 0.f;
+                    }
+#pragma unroll
+                for (int i = 0; i < EPT; ++i) {
+                    const int e = tid + 256 * i, r = e / MC, cc = e - r * MC;
+                    float s = 0.f;
+#pragma unroll
+                    for (int k = 0; k < SPD_SB_BLOCKS; ++k)
+                        if (FWD ? k <= b : b + k < nb) s += v[k][i];
+                    const long row = (long)(jb0 + b) * 128 + r;
+                    if (e < 128 * MC && cc < a.mc && row < a.n) a.O[(long)(a.oc0 + cc) * a.n + row] = s;
+                }
+            }
         }
         if (t + 1 == a.NS) break;  // no rows left to update
         if (!sb_barrier(a, ++nbar, &s_abort)) return;

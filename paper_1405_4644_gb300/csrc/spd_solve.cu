@@ -488,24 +488,32 @@ spd_status trsv_sb_pass(spd_handle* h, const spd_factor_t* F, float* Y, int n, i
     const int G = std::min(per_sm * h->sms, TV_SLOTS);
     const size_t pbytes = (size_t)round_up((long)(sizeof(float) * ntile * 128 * 16), 256);
     const size_t p2bytes = (size_t)round_up((long)(sizeof(float) * 2 * (size_t)G * 128 * 16), 256);
-    if (h->sb_bytes < pbytes + p2bytes + 256) {
+    const size_t zbytes = (size_t)round_up((long)(sizeof(float) * (size_t)n * 16), 256);
+    const int nbar = 2 + F->nsb * F->sbb;  // barrier words, then the block-row tile counts
+    const size_t bbytes = (size_t)round_up((long)(sizeof(int) * nbar), 256);
+    const size_t need = pbytes + p2bytes + zbytes + bbytes;
+    if (h->sb_bytes < need) {
         if (h->sb_buf) {
             CUDA_TRY(h, cudaStreamSynchronize(h->stream));
             CUDA_TRY(h, cudaFree(h->sb_buf));
         }
         h->sb_buf = nullptr;
         h->sb_bytes = 0;
-        CUDA_TRY(h, cudaMalloc(&h->sb_buf, pbytes + p2bytes + 256));
-        h->sb_bytes = pbytes + p2bytes + 256;
+        CUDA_TRY(h, cudaMalloc(&h->sb_buf, need));
+        h->sb_bytes = need;
     }
-    float* P = static_cast<float*>(h->sb_buf);
-    float* P2 = reinterpret_cast<float*>(static_cast<char*>(h->sb_buf) + pbytes);
-    int* bar = reinterpret_cast<int*>(static_cast<char*>(h->sb_buf) + pbytes + p2bytes);
+    char* base = static_cast<char*>(h->sb_buf);
+    float* P = reinterpret_cast<float*>(base);
+    float* P2 = reinterpret_cast<float*>(base + pbytes);
+    float* Z = reinterpret_cast<float*>(base + pbytes + p2bytes);  // the forward sweep's result
+    int* bar = reinterpret_cast<int*>(base + pbytes + p2bytes + zbytes);
     for (int dir = 0; dir < 2; ++dir) {
-        SbArgs a{F->W, F->ldw, n, F->nblk128, F->Xsb, F->sbb * 128, F->sbb, F->nsb, Y, c0, mc, P, P2, bar,
+        // forward: Y (columns c0..) reduced, result to Z; backward: Z reduced, result to Y
+        SbArgs a{F->W, F->ldw, n, F->nblk128, F->Xsb, F->sbb * 128, F->sbb, F->nsb,
+                 dir == 0 ? Y : Z, dir == 0 ? c0 : 0, mc, dir == 0 ? Z : Y, dir == 0 ? 0 : c0, P, P2, bar,
                  h->wait_ns, h->dst, h->async_on ? h->async_gate : nullptr};
         void* args[] = {&a};
-        CUDA_TRY(h, cudaMemsetAsync(bar, 0, 2 * sizeof(int), h->stream));
+        CUDA_TRY(h, cudaMemsetAsync(bar, 0, sizeof(int) * nbar, h->stream));
         ++h->launches;
         CUDA_TRY(h, coop_launch(dir == 0 ? (const void*)fwd : (const void*)bwd, dim3(G), dim3(256), args, smem,
                                 h->stream));
