@@ -433,9 +433,9 @@ DF32_OPS_PER_MADD = 12
 # MEASURED_TRAFFIC_RATIO reports that ratio of DRAM bytes to algorithmic bytes
 # (over a capture of its kernels) times its algorithmic bytes per launch.
 MEASURED_TRAFFIC = {
-    "solve": ((655e9 * 215.17e-6 + 586e9 * 240.16e-6) / 8192 ** 2,
-              "ncu DRAM throughput x duration of one forward + backward super-block sweep pair at n = 8192, "
-              "m = 16, scaled by n^2"),
+    "solve": ((542379520 + 7653376 + 542446080 + 7765760) / 16384 ** 2,
+              "ncu dram__bytes_read.sum + dram__bytes_write.sum of one forward + backward super-block sweep "
+              "pair at n = 16384, m = 16 (two-phase kernel), per n^2"),
 }
 # FP32 rate of one SM: a one-CTA kernel's ceiling
 FP32_SM_PEAK_TFLOPS = 128 * 2 * 2.07e9 / 1e12
