@@ -35,11 +35,49 @@ __device__ __forceinline__ void lz_tile(long t, int& I, int& J) {
     J = (int)(t - (long)i * (i + 1) / 2);
 }
 
+// The sixteen row sums of a warp (v[k]: this lane's part of row k) with 16
+// shuffles instead of 5 per row: at each step a lane keeps half of its
+// values, sends the other half to the partner (lane ^ 16, 8, 4, 2) and adds
+// what it receives; lane L ends with the total of row (L >> 1) & 15 (the
+// same in both lanes of a pair: the last addition is commutative).
+__device__ __forceinline__ float lz_reduce16(const float (&v)[16], int lane) {
+    float a8[8], a4[4], a2[2];
+    {
+        const bool b = (lane >> 4) & 1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float s = b ? v[i] : v[i + 8], k = b ? v[i + 8] : v[i];
+            a8[i] = k + __shfl_xor_sync(0xffffffffu, s, 16);
+        }
+    }
+    {
+        const bool b = (lane >> 3) & 1;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float s = b ? a8[i] : a8[i + 4], k = b ? a8[i + 4] : a8[i];
+            a4[i] = k + __shfl_xor_sync(0xffffffffu, s, 8);
+        }
+    }
+    {
+        const bool b = (lane >> 2) & 1;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const float s = b ? a4[i] : a4[i + 2], k = b ? a4[i + 2] : a4[i];
+            a2[i] = k + __shfl_xor_sync(0xffffffffu, s, 4);
+        }
+    }
+    const bool b = (lane >> 1) & 1;
+    const float s = b ? a2[0] : a2[1], k = b ? a2[1] : a2[0];
+    const float a1 = k + __shfl_xor_sync(0xffffffffu, s, 2);
+    return a1 + __shfl_xor_sync(0xffffffffu, a1, 1);
+}
+
 // 256 threads: warp w takes rows w, w + 8, .. of the tile (16 rows), lane l
 // the four columns 4l .. 4l + 3.  Entries outside the matrix (c >= n, r >= n)
 // and above the diagonal are masked, never read as data: the factor's
-// padding columns hold no values.
-__global__ void __launch_bounds__(256) k_lz_symv_tiles(const float* __restrict__ W, long ldw, int n, int nb,
+// padding columns hold no values.  Interior tiles below the diagonal (every
+// row and column inside the matrix) take a path without masks.
+__global__ void __launch_bounds__(256, 3) k_lz_symv_tiles(const float* __restrict__ W, long ldw, int n, int nb,
                                                      const float* __restrict__ x, float* __restrict__ P) {
     __shared__ float xs_i[LZ_T];
     __shared__ float ps[LZ_T];
@@ -64,23 +102,39 @@ __global__ void __launch_bounds__(256) k_lz_symv_tiles(const float* __restrict__
                                  : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float qa[4] = {0.f, 0.f, 0.f, 0.f};
+    float pk[16];
+    if (!diag && r0 + LZ_T <= n && c0 + LZ_T <= n) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
-        const int rl = warp + 8 * k, r = r0 + rl;
-        float v[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
-        float p = 0.f;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int c = c4 + q;
-            const bool in = (c < n) && (!diag || c <= r);  // r >= n rows were loaded as zeros
-            const float a = in ? v[q] : 0.f;
-            p = fmaf(a, xj[q], p);
-            // the transposed part: strictly below the diagonal only
-            const float at = (diag && c == r) ? 0.f : a;
-            qa[q] = fmaf(at, xs_i[rl], qa[q]);
+        for (int k = 0; k < 16; ++k) {
+            const float xi = xs_i[warp + 8 * k];
+            pk[k] = fmaf(w[k].x, xj[0], fmaf(w[k].y, xj[1], fmaf(w[k].z, xj[2], w[k].w * xj[3])));
+            qa[0] = fmaf(w[k].x, xi, qa[0]);
+            qa[1] = fmaf(w[k].y, xi, qa[1]);
+            qa[2] = fmaf(w[k].z, xi, qa[2]);
+            qa[3] = fmaf(w[k].w, xi, qa[3]);
         }
-        p = warp_sum(p);
-        if (lane == 0) ps[rl] = p;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const int rl = warp + 8 * k, r = r0 + rl;
+            float v[4] = {w[k].x, w[k].y, w[k].z, w[k].w};
+            float p = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int c = c4 + q;
+                const bool in = (c < n) && (!diag || c <= r);  // r >= n rows were loaded as zeros
+                const float a = in ? v[q] : 0.f;
+                p = fmaf(a, xj[q], p);
+                // the transposed part: strictly below the diagonal only
+                const float at = (diag && c == r) ? 0.f : a;
+                qa[q] = fmaf(at, xs_i[rl], qa[q]);
+            }
+            pk[k] = p;
+        }
+    }
+    {
+        const float p = lz_reduce16(pk, lane);
+        if ((lane & 1) == 0) ps[warp + 8 * ((lane >> 1) & 15)] = p;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) qs[warp][4 * lane + q] = qa[q];
